@@ -62,7 +62,7 @@ def _load():
             lib.orc_affine_q16.restype = I
             lib.orc_affine_q16.argtypes = [P, P]
             lib.orc_resample.restype = None
-            lib.orc_resample.argtypes = [P, I, P, P, P, P]
+            lib.orc_resample.argtypes = [P, I, I, P, P, P, P]
             lib.orc_joint_hist.restype = I64
             lib.orc_joint_hist.argtypes = [P, P, P, I, I, P, P, I, P]
             lib.orc_entropies.restype = I
@@ -167,11 +167,11 @@ def affine_q16(aff) -> np.ndarray:
 
 def resample(moving: np.ndarray, q16, fixed_shape, depth: int | None = None) -> np.ndarray:
     """v(T(x)) on the fixed grid by R3/R4 integer trilinear resampling (0 outside)."""
-    iv, _ = _as_int(moving, depth)
+    iv, d = _as_int(moving, depth)
     q = np.ascontiguousarray(q16, dtype=np.int32).reshape(12)
     out = np.empty(tuple(fixed_shape), dtype=iv.dtype)
     nf = np.array(tuple(fixed_shape)[::-1], dtype=np.int32)
-    _load().orc_resample(_p(iv), _dtype_code(iv), _p(_dims(iv)), _p(nf), _p(q), _p(out))
+    _load().orc_resample(_p(iv), _dtype_code(iv), d, _p(_dims(iv)), _p(nf), _p(q), _p(out))
     return out
 
 

@@ -59,6 +59,14 @@ static uint32_t orc_get_u(const void *data, int dtype, int64_t idx) {
     return ((const uint16_t *)data)[idx];
 }
 
+/* Value of an integer voxel read at bit depth d: values above 2^d - 1 are
+ * clamped to 2^d - 1 on load (the bit depth declares them impossible). */
+static uint32_t orc_get_clamped(const void *data, int dtype, int depth, int64_t idx) {
+    uint32_t v = orc_get_u(data, dtype, idx);
+    uint32_t vmax = (uint32_t)((((uint64_t)1) << depth) - 1u);
+    return v > vmax ? vmax : v;
+}
+
 /*
  * Hard-mode conversion of a float volume with values in [0, 1] to 16-bit
  * integers (depth 16): round-half-even of v * 65535 in FP64, clamped; NaN -> 0.
@@ -241,7 +249,7 @@ static uint32_t orc_lerp8(uint32_t a, uint32_t b, uint32_t f) {
  * n - 1 (its weight is then 0).  Lerp along x for the four (y, z) pairs,
  * then along y, then along z.  Returns 0 and leaves *val alone outside.
  */
-static int orc_sample_hard(const void *mov, int mdtype, const int nm[3], const int32_t q[12],
+static int orc_sample_hard(const void *mov, int mdtype, int mdepth, const int nm[3], const int32_t q[12],
                            int64_t i, int64_t j, int64_t k, uint32_t *val) {
     int64_t U[3];
     for (int a = 0; a < 3; a++) {
@@ -260,8 +268,8 @@ static int orc_sample_hard(const void *mov, int mdtype, const int nm[3], const i
     for (int dz = 0; dz < 2; dz++)
         for (int dy = 0; dy < 2; dy++)
             for (int dx = 0; dx < 2; dx++)
-                v[dz][dy][dx] = orc_get_u(mov, mdtype,
-                                          orc_index(nm, dx ? c1[0] : c0[0], dy ? c1[1] : c0[1], dz ? c1[2] : c0[2]));
+                v[dz][dy][dx] = orc_get_clamped(mov, mdtype, mdepth,
+                                                orc_index(nm, dx ? c1[0] : c0[0], dy ? c1[1] : c0[1], dz ? c1[2] : c0[2]));
     uint32_t ex[2][2];
     for (int dz = 0; dz < 2; dz++)
         for (int dy = 0; dy < 2; dy++) ex[dz][dy] = orc_lerp8(v[dz][dy][0], v[dz][dy][1], f[0]);
@@ -272,12 +280,13 @@ static int orc_sample_hard(const void *mov, int mdtype, const int nm[3], const i
 }
 
 /* v(T(x)) on the fixed grid (value 0 outside the overlap); same type as the moving volume. */
-void orc_resample(const void *mov, int mdtype, const int nm[3], const int nf[3], const int32_t q[12], void *out) {
+void orc_resample(const void *mov, int mdtype, int mdepth, const int nm[3], const int nf[3], const int32_t q[12],
+                  void *out) {
     for (int64_t k = 0; k < nf[2]; k++)
         for (int64_t j = 0; j < nf[1]; j++)
             for (int64_t i = 0; i < nf[0]; i++) {
                 uint32_t val = 0;
-                orc_sample_hard(mov, mdtype, nm, q, i, j, k, &val);
+                orc_sample_hard(mov, mdtype, mdepth, nm, q, i, j, k, &val);
                 int64_t o = orc_index(nf, i, j, k);
                 if (mdtype == ORC_U8) ((uint8_t *)out)[o] = (uint8_t)val;
                 else ((uint16_t *)out)[o] = (uint16_t)val;
@@ -297,7 +306,7 @@ int64_t orc_joint_hist(const uint8_t *fbins, const int nf[3], const void *mov, i
         for (int64_t j = 0; j < nf[1]; j++)
             for (int64_t i = 0; i < nf[0]; i++) {
                 uint32_t val;
-                if (!orc_sample_hard(mov, mdtype, nm, q, i, j, k, &val)) continue;
+                if (!orc_sample_hard(mov, mdtype, mdepth, nm, q, i, j, k, &val)) continue;
                 int bf = fbins[orc_index(nf, i, j, k)];
                 int bm = orc_bin_of(val, bins, mdepth);
                 hist[(size_t)bf * (size_t)bins + (size_t)bm] += 1;
@@ -619,7 +628,10 @@ int orc_parzen(const void *fix, int fdtype, int fdepth, const int nf[3], const v
                 orc_trilinear(mov, mdtype, mdepth, nm, u, &m, g);
                 double mt = m * (double)(B - 4) + 2.0;
                 int fb = orc_parzen_fixed_bin(fix, fdtype, fdepth, idx, B);
-                for (int kk = 0; kk < B; kk++) {
+                /* beta3 vanishes beyond distance 2, so bins outside floor(mt) -+ 2 add nothing */
+                int k0 = (int)floor(mt);
+                for (int kk = k0 - 2; kk <= k0 + 2; kk++) {
+                    if (kk < 0 || kk >= B) continue;
                     double w = orc_beta3((double)kk - mt);
                     if (w != 0.0) P[(size_t)fb * B + kk] += w;
                 }
@@ -693,7 +705,9 @@ int orc_parzen(const void *fix, int fdtype, int fdepth, const int nf[3], const v
                     double mt = m * (double)(B - 4) + 2.0;
                     int fb = orc_parzen_fixed_bin(fix, fdtype, fdepth, idx, B);
                     double s = 0.0;
-                    for (int kk = 0; kk < B; kk++) s += W[(size_t)fb * B + kk] * orc_dbeta3((double)kk - mt);
+                    int k0 = (int)floor(mt);
+                    for (int kk = k0 - 2; kk <= k0 + 2; kk++)
+                        if (kk >= 0 && kk < B) s += W[(size_t)fb * B + kk] * orc_dbeta3((double)kk - mt);
                     double dmt = -s / (double)N * (double)(B - 4);
                     double x4[4] = {(double)i, (double)j, (double)k, 1.0};
                     for (int p = 0; p < 9; p++) {

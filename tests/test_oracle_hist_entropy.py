@@ -226,3 +226,15 @@ def test_mi_eval_params_equals_q16_path_and_peaks_at_true_motion():
     np.testing.assert_array_equal(cnt, cnt2)
     # the phantom's true motion beats every pure x translation (the paper's gold standard is the true pose)
     assert mi[0, 0] > mi[1:, 0].max()
+
+
+def test_values_above_bit_depth_are_clamped_on_load():
+    # depth 12: 5000 reads as 4095 before interpolation, so a half-voxel shift between
+    # 100 and 5000 gives (100*128 + 4095*128 + 128) >> 8 = 2098, not the unclamped 2550
+    mv = np.zeros((2, 2, 2), dtype=np.uint16)
+    mv[:, :, 0] = 100
+    mv[:, :, 1] = 5000
+    q = IDENT.copy()
+    q[3] = 32768
+    out = oracle.resample(mv, q, (2, 2, 2), depth=12)
+    assert out[0, 0, 0] == (100 * 128 + 4095 * 128 + 128) >> 8

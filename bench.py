@@ -1,0 +1,312 @@
+#!/usr/bin/env python
+"""Benchmark of batched hard-binned Shannon / Tsallis MI on one GB300 (or N replicas).
+
+Workload (one step): a 256 x 256 x 256 uint16 12-bit head-like phantom pair,
+256 bins, 4096 random 9-parameter transforms (translation U(+-15 mm),
+rotation U(+-20 deg), scale U(0.85, 1.15)) x q in {0.5, 1, 1.5, 2}, evaluated
+by one persistent, graph-replayed launch.  Metric: voxels x transforms per
+second.  Each rank evaluates its own 4096 transforms (weak scaling, no
+collective on the data path).
+
+Also reported: the same metric end to end through the C ABI with host
+buffers (e2e), the one-transform-per-launch plain form, the Parzen MI+gradient
+throughput (192 x 192 x 128 float32, 64 bins, q in {1, 0.7, 1.3}), the
+roofline of the main kernel and the CPU oracle on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MI evals/sec (voxels·transforms/s) at 256³, batched vs plain; MI+grad/s; % of roofline"
+SHAPE = (256, 256, 256)
+BINS = 256
+DEPTH = 12
+N_T = 4096
+QS = [0.5, 1.0, 1.5, 2.0]
+# algorithmic integer operations per voxel x transform of the hard path:
+# 3 coordinate adds, 6 index/weight extractions, 9 address operations, 7 lerps x 4,
+# 2 for the moving bin, 1 for the joint index, 1 increment
+ALG_OPS_PER_VOXT = 50
+PARZEN_SHAPE = (128, 192, 192)
+PARZEN_SPACING = (1.0, 1.0, 1.2)
+PARZEN_BINS = 64
+PARZEN_QS = [1.0, 0.7, 1.3]
+PARZEN_N = 50
+
+
+def workload_config():
+    return {"workload": "batched hard-binned MI, 256x256x256 uint16 12-bit head-like pair, 256 bins, "
+                        "4096 transforms x 4 q per step, one persistent graph-replayed launch",
+            "volume": list(SHAPE[::-1]), "bits": DEPTH, "bins": BINS, "transforms_per_step": N_T, "q": QS,
+            "transform_dist": "t U(+-15 mm), r U(+-20 deg), s U(0.85, 1.15)",
+            "l2": "flushed (256 MiB write) between timed steps"}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler over the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), float(f[3]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower().startswith("active")})
+        load = [r for r in rows if r[2] > 200.0] or rows
+        return {"sm_mhz": float(np.median([r[0] for r in load])), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows), "samples_under_load": len(load)}
+
+
+def oracle_rate(f, m, prm, cores):
+    """Oracle vox.T/s on the given transforms (all host cores, parallel across transforms)."""
+    import oracle
+
+    t0 = time.perf_counter()
+    oracle.mi_eval(f, m, BINS, prm, QS, fixed_depth=DEPTH, moving_depth=DEPTH, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return len(prm) * f.size / dt, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_1909_10690_gb300 import phantoms
+
+    cores = os.cpu_count() or 1
+    f, m = phantoms.head_pair(shape=SHAPE, spacing=(1, 1, 1), seed=30)
+    prm = phantoms.random_transforms(N_T, seed=31)
+    per_step = cores  # one transform per core per step: a bounded sample of the step's 4096
+    for w in range(args.warmup):
+        oracle_rate(f, m, prm[w * per_step:(w + 1) * per_step], cores)
+    total_t, total_units = 0.0, 0
+    for s in range(args.steps):
+        sel = prm[(s * per_step) % N_T:(s * per_step) % N_T + per_step]
+        _, dt = oracle_rate(f, m, sel, cores)
+        total_t += dt
+        total_units += len(sel) * f.size
+    value = total_units / total_t
+    line = {"metric": METRIC, "value": value, "unit": "voxel*transforms/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "impl": "reference", "config": workload_config(),
+            "cpu_baseline": {"value": value, "unit": "voxel*transforms/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} of the step's {N_T} transforms per step (256^3, 256 bins, 4 q)"},
+            "e2e": {"value": value, "unit": "voxel*transforms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_1909_10690_gb300 as mi
+    from paper_1909_10690_gb300 import phantoms
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            tdist.barrier()
+
+    def allmax(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        return float(t.item())
+
+    f, m = phantoms.head_pair(shape=SHAPE, spacing=(1, 1, 1), seed=30)
+    prm = phantoms.random_transforms(N_T, seed=31 + rank)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = mi.Context(f, m, bins=BINS, fixed_depth=DEPTH, moving_depth=DEPTH, path="batched", device=local_rank)
+    ctx.set_stream(stream)
+    T_dev = torch.from_numpy(prm).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    nvox = int(np.prod(SHAPE))
+    for _ in range(args.warmup):
+        ctx.eval(T_dev, QS)
+    variant = ctx.selected_variant(N_T)
+    # --- device-resident timed region -------------------------------------------
+    clocks = Clocks(local_rank)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kern_ms, launches = [], 0
+    barrier()
+    clocks.start()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()  # L2 flush between timed steps (outside the events)
+            ev0[k].record(stream)
+        out = ctx.eval(T_dev, QS)
+        ev1[k].record(stream)
+        km, nl = ctx.last_kernel_ms()
+        kern_ms.append(km)
+        launches += nl
+    barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    total_s = allmax(sum(step_ms) / 1e3)
+    assert torch.isfinite(out).all()
+    value = world * args.steps * N_T * nvox / total_s
+    # --- roofline of the main kernel ----------------------------------------------
+    pk, src = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    alu_peak = props.multi_processor_count * 128 * sm_mhz * 1e6 / 1e12  # int32 lane-ops/s, Tops/s
+    kms = float(np.mean(kern_ms))
+    achieved = ALG_OPS_PER_VOXT * N_T * nvox / (kms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak,
+                "traffic": None, "kernel": "k_batched", "kernel_ms": kms,
+                "peak_source": f"{props.multi_processor_count} SMs x 128 int32 lanes x {sm_mhz:.0f} MHz ({src} clock)"}
+    # --- end to end through the C ABI with host buffers ----------------------------
+    prm_pinned = torch.from_numpy(prm).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        res = ctx.eval(prm_pinned, QS)  # host in, host out
+    barrier()
+    e2e_s = allmax(time.perf_counter() - t0)
+    assert np.isfinite(res).all()
+    e2e = {"value": world * args.steps * N_T * nvox / e2e_s, "unit": "voxel*transforms/s",
+           "h2d_bytes_per_step": N_T * 48 + N_T * 8, "d2h_bytes_per_step": N_T * len(QS) * 8 + 8}
+    extra = {}
+    if rank == 0 and not args.skip_extras:
+        # --- plain form: one transform per launch, host sync each time --------------
+        pctx = mi.Context(f, m, bins=BINS, fixed_depth=DEPTH, moving_depth=DEPTH, path="plain", device=local_rank)
+        pctx.set_stream(stream)
+        n_plain = 64
+        for i in range(3):
+            pctx.eval(T_dev[i:i + 1], QS)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(n_plain):
+            pctx.eval(T_dev[i:i + 1], QS)
+        plain_s = time.perf_counter() - t0
+        plain_rate = n_plain * nvox / plain_s
+        extra["plain"] = {"value": plain_rate, "unit": "voxel*transforms/s", "transforms": n_plain,
+                          "form": "one transform per call: memset + histogram kernel + entropy kernel + D2H sync",
+                          "batched_over_plain": value / world / plain_rate}
+        del pctx
+        # --- differentiable form: Parzen MI + gradient --------------------------------
+        fp, mp = phantoms.head_pair(shape=PARZEN_SHAPE, spacing=PARZEN_SPACING, seed=50, dtype=np.float32)
+        zctx = mi.Context(fp, mp, bins=PARZEN_BINS, kernel="parzen", fixed_spacing=PARZEN_SPACING,
+                          moving_spacing=PARZEN_SPACING, device=local_rank)
+        zctx.set_stream(stream)
+        pp = torch.from_numpy(phantoms.random_transforms(PARZEN_N, seed=51, t_mm=10, r_deg=15,
+                                                         s_range=(0.9, 1.1))).to(dev)
+        for _ in range(3):
+            zctx.grad(pp, PARZEN_QS)
+        zk = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            zctx.grad(pp, PARZEN_QS)
+            zk.append(zctx.last_kernel_ms()[0])
+        z_s = time.perf_counter() - t0
+        pv = int(np.prod(PARZEN_SHAPE))
+        extra["mi_grad"] = {"value": args.steps * PARZEN_N / z_s, "unit": "(MI+grad over 9 params, 3 q)/s",
+                            "voxel_transforms_per_s": args.steps * PARZEN_N * pv / z_s,
+                            "kernel_ms_per_call": float(np.mean(zk)), "poses_per_call": PARZEN_N,
+                            "volume": list(PARZEN_SHAPE[::-1]), "bins": PARZEN_BINS, "q": PARZEN_QS}
+        del zctx
+    line = {"metric": METRIC, "value": value, "unit": "voxel*transforms/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": dict(workload_config(), hist_variant=variant, parallelism=f"replicas x{world}"),
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+    line.update(extra)
+    if rank == 0 and not args.skip_cpu:
+        cores = os.cpu_count() or 1
+        sample = prm[:2 * cores]
+        rate, dt = oracle_rate(f, m, sample, cores)
+        line["cpu_baseline"] = {"value": rate, "unit": "voxel*transforms/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{len(sample)} of the 4096 transforms (256^3, 256 bins, 4 q), {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--skip-extras", action="store_true", help="skip the plain and Parzen lines")
+    ap.add_argument("--skip-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch.distributed as tdist
+
+        tdist.init_process_group("gloo")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as tdist
+
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

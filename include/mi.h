@@ -1,0 +1,229 @@
+/*
+ * mi.h -- C ABI of the GB300 mutual-information library.
+ *
+ * The library evaluates the registration metric of Vianna & Murta,
+ * "Analysis of Generalized Entropies in Mutual Information Medical Image
+ * Registration": Shannon mutual information, Eq. (1)-(2), and Tsallis mutual
+ * information, between a fixed volume u(x) and a moving volume resampled
+ * under a transform, v(T(x)) (Fig. 1 block diagram; the metric F_m whose
+ * argmax over T is the registration, Eq. (3)).  T has 9 parameters from the
+ * three families the paper studies (Introduction): translation, rotation,
+ * scale.  All voxels contribute to one full joint histogram (Discussion),
+ * and one histogram serves Shannon and every Tsallis q (Discussion).
+ *
+ * Conventions that the paper leaves open and this library fixes:
+ *  - Volumes: x fastest, index = x + nx (y + ny z).  Integer volumes carry a
+ *    bit depth d; values above 2^d - 1 are clamped to 2^d - 1 on load.
+ *    Float volumes hold values in [0, 1]; the hard-binned path converts them
+ *    once to 16-bit integers (round-half-even of v * 65535, depth 16).
+ *  - Binning: an integer value v of depth d lies in bin (v * bins) >> d.
+ *  - Transform parameters, 9 floats per transform: tx ty tz (mm), rx ry rz
+ *    (degrees), sx sy sz (scale factors, 1 = identity).  A fixed physical
+ *    point p = s_f * i (i the voxel index) maps to
+ *    p_m = R diag(s) (p - c_f) + c_m + t, R = Rz(rz) Ry(ry) Rx(rx), c the
+ *    volume centres s * (n - 1) / 2; the moving index is p_m / s_m.  In index
+ *    space u = A i + b; [A | b] is quantised to 16.16 fixed point as
+ *    llround(x * 65536) (computed in FP64 on the host with the order of
+ *    operations fixed, so the quantised matrix is reproducible).
+ *  - Hard path: U = A i + b exactly in integers; a voxel counts iff
+ *    0 <= U_a <= (n_a - 1) * 65536 on every axis (overlap only); trilinear
+ *    interpolation with 8-bit weights w = (U & 0xFFFF) >> 8 and stage lerp
+ *    (a (256 - w) + b w + 128) >> 8, x then y then z.  Joint counts are exact.
+ *  - Entropies: natural log (nats) unless opt.log_bits; Tsallis
+ *    S_q = (1 - sum p^q) / (q - 1); q == 1 means Shannon.  Tsallis MI is
+ *    S_q(F) + S_q(M) - S_q(F,M) (MI_TSALLIS_ADDITIVE, the literal extension
+ *    of Eq. (2)) or adds (1 - q) S_q(F) S_q(M) (MI_TSALLIS_PSEUDO_ADDITIVE).
+ *    Marginals are the row / column sums of the overlap histogram.  Sums are
+ *    accumulated in FP64 on the GPU.
+ *  - Parzen (differentiable) path: fixed bin floor(f (B - 4)) + 2 of the
+ *    normalised intensity f; moving term a cubic B-spline at
+ *    m~ = m (B - 4) + 2, m the FP32 trilinear value at the real moving index;
+ *    gradient with the overlap held fixed.
+ *
+ * Memory: every pointer argument may be host memory (pageable or pinned) or
+ * CUDA device memory of the context's device; the library inspects each one.
+ * The context copies the volumes into device memory it owns, so the caller's
+ * volume buffers may be freed once mi_create returns.  Work is ordered on
+ * the context's stream (its own non-blocking stream unless mi_set_stream
+ * names another) and every call returns once its results are in the caller's
+ * buffers (the call synchronises that stream).
+ *
+ * Errors: every call returns an mi_status; mi_last_error gives a message.
+ * A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef MI_H
+#define MI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MI_OK = 0,
+    MI_EINVAL = 1,        /* invalid argument (message says which)             */
+    MI_ENOMEM = 2,        /* device or host allocation failed                  */
+    MI_ECUDA = 3,         /* a CUDA call failed                                */
+    MI_EEMPTY = 4,        /* some transform had an empty overlap (its MI NaN)  */
+    MI_EUNSUPPORTED = 5,  /* valid but not supported (e.g. mi_grad, hard mode) */
+    MI_ERANGE = 6         /* an affine entry does not fit 16.16 fixed point    */
+} mi_status;
+
+typedef enum { MI_U8 = 0, MI_U16 = 1, MI_F32 = 2 } mi_dtype;
+
+typedef struct {
+    const void *data;     /* x fastest, contiguous                              */
+    int dtype;            /* mi_dtype                                           */
+    int dims[3];          /* nx, ny, nz; each >= 2; nx*ny*nz < 2^31             */
+    int bit_depth;        /* u8: 1..8, u16: 1..16, 0 = full width; f32: ignored */
+    float spacing_mm[3];  /* > 0                                                */
+} mi_volume;
+
+enum { MI_HARD = 0, MI_PARZEN = 1 };
+enum { MI_TSALLIS_ADDITIVE = 0, MI_TSALLIS_PSEUDO_ADDITIVE = 1 };
+/* Histogram privatisation variants of the hard path (-1 = autotuned). */
+enum {
+    MI_HV_AUTO = -1,
+    MI_HV_U32 = 0,        /* 32-bit shared counters, one atomic per voxel        */
+    MI_HV_U32_MATCH = 1,  /* 32-bit counters, warp-aggregated (match.any)        */
+    MI_HV_U16 = 2,        /* 16-bit packed counters drained at 2^14              */
+    MI_HV_U16_MATCH = 3   /* 16-bit packed counters, warp-aggregated             */
+};
+/* Evaluation path of mi_eval. */
+enum { MI_PATH_AUTO = 0, MI_PATH_PLAIN = 1, MI_PATH_BATCHED = 2 };
+
+#define MI_MAX_Q 8     /* q values per call          */
+#define MI_MAX_BINS 256
+#define MI_MIN_BINS 2
+#define MI_MIN_PARZEN_BINS 8
+
+typedef struct {
+    int kernel;        /* MI_HARD (default) or MI_PARZEN                            */
+    int tsallis_form;  /* MI_TSALLIS_ADDITIVE (default) or MI_TSALLIS_PSEUDO_ADDITIVE */
+    int log_bits;      /* 0: nats (default); 1: Shannon entropies in bits          */
+    int hist_variant;  /* MI_HV_AUTO (default) or a fixed MI_HV_* variant          */
+    int path;          /* MI_PATH_AUTO (default), MI_PATH_PLAIN, MI_PATH_BATCHED    */
+    int use_graphs;    /* 1 (default): replay the batched launch as a CUDA graph   */
+    int autotune;      /* 1 (default): time the variants once per shape and cache  */
+    int device;        /* CUDA device ordinal; -1 (default) = the current device   */
+} mi_options;
+
+typedef struct mi_ctx mi_ctx;
+
+/* Fills *opt with the defaults listed above. */
+void mi_options_default(mi_options *opt);
+
+/* Library version string (static storage). */
+const char *mi_version(void);
+
+/*
+ * Creates a context for one (fixed, moving) pair and a bin count
+ * (MI_MIN_BINS..MI_MAX_BINS; MI_MIN_PARZEN_BINS.. for MI_PARZEN).  The metric
+ * is F_m(u(x), v(T(x))) of Fig. 1; the pair's geometry (dims, spacing) fixes
+ * the parameter-to-affine map.  opt may be NULL (defaults).  On success *out
+ * owns device copies of both volumes (the fixed one pre-binned) and must be
+ * released with mi_destroy.  On failure *out is NULL and mi_last_error(NULL)
+ * describes the error on this thread.
+ */
+mi_status mi_create(mi_ctx **out, const mi_volume *fixed, const mi_volume *moving, int bins,
+                    const mi_options *opt);
+
+/*
+ * Creates one context over npairs volume pairs of uneven sizes, types and
+ * bin counts (bins[p] per pair), evaluated together by mi_batch_eval in one
+ * persistent launch with a per-pair work queue.  Hard path only.
+ */
+mi_status mi_batch_create(mi_ctx **out, const mi_volume *fixed, const mi_volume *moving, const int *bins,
+                          int npairs, const mi_options *opt);
+
+/* Releases every resource of the context (NULL is ignored). */
+void mi_destroy(mi_ctx *ctx);
+
+/* Message of the last failed call on ctx, or of the last failed create on
+ * this thread when ctx is NULL.  Valid until the next call on ctx. */
+const char *mi_last_error(const mi_ctx *ctx);
+
+/* Orders all later work of ctx on the CUDA stream `stream` (a cudaStream_t of
+ * the context's device; NULL = back to the context's own stream).  CUDA-graph
+ * replay is skipped on the legacy default stream, which cannot be captured. */
+mi_status mi_set_stream(mi_ctx *ctx, void *stream);
+
+/*
+ * MI for n transforms (n x 9 floats, parameters above) and nq exponents q
+ * (1 <= nq <= MI_MAX_Q; q > 0; q == 1 is Shannon, Eq. (1)-(2); other q are
+ * Tsallis; q within 1e-6 of 1 but not 1 is rejected).  One joint histogram
+ * per transform serves every q (Discussion).
+ * out_mi:    n x nq doubles (row = transform).
+ * out_h:     n x nq x 3 doubles (H_F, H_M, H_FM per q), or NULL.
+ * out_count: n int64 overlap voxel counts, or NULL.
+ * A transform whose overlap is empty gets NaN and the call returns MI_EEMPTY
+ * after finishing every other transform.  In MI_PARZEN mode this returns the
+ * Parzen MI (no gradient).  n == 0 is a no-op.
+ */
+mi_status mi_eval(mi_ctx *ctx, const float *transforms, int n, const float *q, int nq, double *out_mi,
+                  double *out_h, int64_t *out_count);
+
+/* As mi_eval, with the 16.16 affines [A | b] (n x 12 int32, row-major 3x4)
+ * given directly instead of parameters.  Hard path, pair 0. */
+mi_status mi_eval_q16(mi_ctx *ctx, const int32_t *affines, int n, const float *q, int nq, double *out_mi,
+                      double *out_h, int64_t *out_count);
+
+/*
+ * Batched evaluation over the pairs of a mi_batch_create context:
+ * transform t (n x 9 parameters) is evaluated on pair pair_of_transform[t].
+ * Outputs as in mi_eval.
+ */
+mi_status mi_batch_eval(mi_ctx *ctx, const int *pair_of_transform, const float *transforms, int n,
+                        const float *q, int nq, double *out_mi, double *out_h, int64_t *out_count);
+
+/*
+ * Parzen MI and its gradient dMI/dtheta over the 9 parameters (MI_PARZEN
+ * contexts only): cubic-B-spline soft joint histogram of the moving
+ * intensity against the box-binned fixed intensity, differentiated through
+ * the trilinear resampling and the transform (the optimiser's gradient,
+ * Introduction; registration as argmax, Eq. (3)).
+ * out_mi: n x nq; out_grad: n x nq x 9 (d MI / d param, angles per degree).
+ */
+mi_status mi_grad(mi_ctx *ctx, const float *transforms, int n, const float *q, int nq, double *out_mi,
+                  double *out_grad);
+
+/*
+ * Test hook: the joint histogram (row = fixed bin, bins x bins uint32 per
+ * transform) of n transforms of pair `pair`, computed by the plain path
+ * (path = MI_PATH_PLAIN) or copied out of the batched kernel's on-chip
+ * histogram (MI_PATH_BATCHED).  Exactly one of transforms (n x 9) and
+ * affines (n x 12 16.16) is non-NULL.
+ */
+mi_status mi_hist(mi_ctx *ctx, int pair, const float *transforms, const int32_t *affines, int n, int path,
+                  uint32_t *out_counts);
+
+/* Test hook: the FP64 affine [A | b] (n x 12), its 16.16 quantisation (n x 12)
+ * and its Jacobian d[A|b]/dparam (n x 12 x 9) for pair `pair`; any output may
+ * be NULL.  Host computation only. */
+mi_status mi_affine(mi_ctx *ctx, int pair, const float *transforms, int n, double *out_affine,
+                    int32_t *out_q16, double *out_jacobian);
+
+/* Test hook: the pre-binned fixed volume of pair `pair` (nvox uint8). */
+mi_status mi_fixed_bins(mi_ctx *ctx, int pair, uint8_t *out);
+
+/* v(T(x)) of pair `pair` on the fixed grid for one 16.16 affine, same type as
+ * the stored moving volume (uint16 for float input), 0 outside the overlap. */
+mi_status mi_resample(mi_ctx *ctx, int pair, const int32_t *affine, void *out);
+
+/* The histogram variant the autotuner chose (or was told) for pair `pair`,
+ * for the given number of transforms per call; -1 if none yet. */
+int mi_selected_variant(mi_ctx *ctx, int pair, int n);
+
+/* Profiling hook: device time in milliseconds of the main histogram kernel(s)
+ * of the last completed mi_eval / mi_eval_q16 / mi_batch_eval / mi_grad call,
+ * measured with CUDA events recorded on the context's stream around those
+ * launches (inside the replayed graph for the batched path).  *launches
+ * receives the number of kernels the call launched (NULL ok). */
+mi_status mi_last_kernel_ms(mi_ctx *ctx, float *ms, int *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MI_H */

@@ -1,0 +1,1216 @@
+// mi_api.cu -- the C ABI of include/mi.h: contexts, validation, the
+// parameter -> affine builder, path selection (plain / batched), CUDA-graph
+// replay of the batched launch and the variant autotuner.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/mi.h"
+#include "mi_internal.h"
+
+using namespace mi;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// ---------------------------------------------------------------------------
+// Device / pinned buffers
+// ---------------------------------------------------------------------------
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+    cudaError_t ensure(size_t bytes) {
+        if (bytes <= cap) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = std::max<size_t>(bytes, 256);
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e == cudaSuccess) cap = want;
+        return e;
+    }
+    template <class T>
+    T *as() const {
+        return (T *)p;
+    }
+};
+
+struct HostBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    ~HostBuf() {
+        if (p) cudaFreeHost(p);
+    }
+    cudaError_t ensure(size_t bytes) {
+        if (bytes <= cap) return cudaSuccess;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = std::max<size_t>(bytes, 256);
+        cudaError_t e = cudaMallocHost(&p, want);
+        if (e == cudaSuccess) cap = want;
+        return e;
+    }
+    template <class T>
+    T *as() const {
+        return (T *)p;
+    }
+};
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ---------------------------------------------------------------------------
+// Parameters -> affine (FP64, order of operations fixed so the 16.16
+// quantisation is reproducible; no fused multiply-add in this file's host code)
+// ---------------------------------------------------------------------------
+
+void mul3(const double x[9], const double y[9], double z[9]) {
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc = acc + x[3 * r + k] * y[3 * k + c];
+            z[3 * r + c] = acc;
+        }
+}
+
+// Elementary rotation about `axis` by `rad`, or its derivative w.r.t. the angle.
+void elem_rot(int axis, double rad, bool deriv, double m[9]) {
+    const double c = cos(rad), s = sin(rad);
+    for (int e = 0; e < 9; ++e) m[e] = 0.0;
+    const int a = (axis + 1) % 3, b = (axis + 2) % 3;  // the rotated plane (a, b)
+    if (!deriv) m[4 * axis] = 1.0;
+    m[3 * a + a] = deriv ? -s : c;
+    m[3 * a + b] = deriv ? -c : -s;
+    m[3 * b + a] = deriv ? c : s;
+    m[3 * b + b] = deriv ? -s : c;
+}
+
+const double kRadPerDeg = 3.14159265358979323846 / 180.0;
+
+// [A | b] (row-major 3x4) for one transform, and optionally J = d[A|b]/dparam (12 x 9).
+void build_affine(const float prm[9], const int nf[3], const float sfp[3], const int nm[3], const float smp[3],
+                  double out[12], double *jac) {
+    double tr[3], rad[3], sc[3], sf[3], sm[3], cf[3], cm[3];
+    for (int a = 0; a < 3; ++a) {
+        tr[a] = (double)prm[a];
+        rad[a] = (double)prm[3 + a] * kRadPerDeg;
+        sc[a] = (double)prm[6 + a];
+        sf[a] = (double)sfp[a];
+        sm[a] = (double)smp[a];
+        cf[a] = sf[a] * ((double)(nf[a] - 1) * 0.5);
+        cm[a] = sm[a] * ((double)(nm[a] - 1) * 0.5);
+    }
+    double rx[9], ry[9], rz[9], rzy[9], R[9];
+    elem_rot(0, rad[0], false, rx);
+    elem_rot(1, rad[1], false, ry);
+    elem_rot(2, rad[2], false, rz);
+    mul3(rz, ry, rzy);
+    mul3(rzy, rx, R);
+    for (int a = 0; a < 3; ++a) {
+        double acc = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            const double rs = R[3 * a + c] * sc[c];
+            out[4 * a + c] = (rs * sf[c]) / sm[a];
+            acc = acc + rs * cf[c];
+        }
+        out[4 * a + 3] = ((cm[a] + tr[a]) - acc) / sm[a];
+    }
+    if (!jac) return;
+    for (int e = 0; e < 108; ++e) jac[e] = 0.0;
+    for (int a = 0; a < 3; ++a) jac[9 * (4 * a + 3) + a] = 1.0 / sm[a];
+    for (int p = 0; p < 3; ++p) {
+        double dx[9], dy[9], dz[9], t1[9], dR[9];
+        elem_rot(0, rad[0], p == 0, dx);
+        elem_rot(1, rad[1], p == 1, dy);
+        elem_rot(2, rad[2], p == 2, dz);
+        mul3(dz, dy, t1);
+        mul3(t1, dx, dR);
+        for (int a = 0; a < 3; ++a) {
+            double acc = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                const double d = dR[3 * a + c] * kRadPerDeg * sc[c];
+                jac[9 * (4 * a + c) + 3 + p] = d * sf[c] / sm[a];
+                acc += d * cf[c];
+            }
+            jac[9 * (4 * a + 3) + 3 + p] = -acc / sm[a];
+        }
+    }
+    for (int p = 0; p < 3; ++p)
+        for (int a = 0; a < 3; ++a) {
+            jac[9 * (4 * a + p) + 6 + p] = R[3 * a + p] * sf[p] / sm[a];
+            jac[9 * (4 * a + 3) + 6 + p] = -R[3 * a + p] * cf[p] / sm[a];
+        }
+}
+
+bool quantise_q16(const double aff[12], int32_t q[12]) {
+    for (int e = 0; e < 12; ++e) {
+        const double s = aff[e] * 65536.0;
+        if (!(fabs(s) <= 2147483647.0)) return false;
+        const long long r = llround(s);
+        if (r > 2147483647LL || r < -2147483647LL - 1) return false;
+        q[e] = (int32_t)r;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+
+struct Pair {
+    int nf[3], nm[3];
+    float sf[3], sm[3];
+    int bins;
+    int fdepth, mdepth;
+    int mdtype;  // stored moving type: 0 u8, 1 u16
+    long long nvf, nvm;
+    DevBuf fbins, mov;          // hard path
+    DevBuf pfbins, pmov;        // Parzen path
+};
+
+struct Choice {
+    int variant = -1, threads = 0, ctas = 0;
+};
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    ~GraphEntry() {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
+
+}  // namespace
+
+struct mi_ctx {
+    int device = 0;
+    int sms = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    mi_options opt;
+    std::string err;
+    std::vector<std::unique_ptr<Pair>> pairs;
+    DevBuf d_pairs;     // PairDev[npairs]
+    int max_bins = 0;
+    // per-q FP64 tables, keyed by the float bits of q
+    std::map<uint32_t, std::unique_ptr<DevBuf>> tables;
+    // call scratch
+    DevBuf d_aff, d_items, d_mi, d_h, d_cnt, d_hist, d_flags, d_ticket, d_dump;
+    HostBuf h_aff, h_items, h_out;
+    // Parzen scratch
+    DevBuf p_aff, p_jac, p_hist, p_cnt, p_marg, p_ment, p_jsum, p_w, p_mom, p_grad;
+    // autotune and graph caches
+    std::map<std::tuple<int, int, int>, Choice> tuned;  // (path, pair-or--1, n bucket)
+    std::map<std::string, std::unique_ptr<GraphEntry>> graphs;
+    // profiling: events around the main kernels of the last call
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int last_launches = 0;
+    bool timed = false;
+
+    mi_status fail(mi_status st, const std::string &msg) {
+        err = msg;
+        return st;
+    }
+    mi_status cuda_fail(cudaError_t e, const char *what) {
+        err = std::string(what) + ": " + cudaGetErrorString(e);
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? MI_ENOMEM : MI_ECUDA;
+    }
+};
+
+namespace {
+
+#define MI_CU(call, what)                                    \
+    do {                                                     \
+        cudaError_t e__ = (call);                            \
+        if (e__ != cudaSuccess) return ctx->cuda_fail(e__, what); \
+    } while (0)
+
+// Per-call device guard: make the context's device current, restore on exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+mi_status validate_volume(const mi_volume *v, const char *name, bool parzen, std::string &err) {
+    char buf[256];
+    if (!v || !v->data) {
+        snprintf(buf, sizeof buf, "%s volume or its data is NULL", name);
+        err = buf;
+        return MI_EINVAL;
+    }
+    if (v->dtype != MI_U8 && v->dtype != MI_U16 && v->dtype != MI_F32) {
+        snprintf(buf, sizeof buf, "%s volume has unknown dtype %d", name, v->dtype);
+        err = buf;
+        return MI_EINVAL;
+    }
+    long long nv = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (v->dims[a] < 2) {
+            snprintf(buf, sizeof buf, "%s volume dims[%d] = %d (must be >= 2)", name, a, v->dims[a]);
+            err = buf;
+            return MI_EINVAL;
+        }
+        nv *= v->dims[a];
+        if (!(v->spacing_mm[a] > 0.0f) || !isfinite(v->spacing_mm[a])) {
+            snprintf(buf, sizeof buf, "%s volume spacing_mm[%d] must be finite and > 0", name, a);
+            err = buf;
+            return MI_EINVAL;
+        }
+    }
+    if (nv >= (1LL << 31)) {
+        snprintf(buf, sizeof buf, "%s volume has %lld voxels (limit 2^31 - 1)", name, nv);
+        err = buf;
+        return MI_EINVAL;
+    }
+    const int maxd = v->dtype == MI_U8 ? 8 : 16;
+    if (v->dtype != MI_F32 && (v->bit_depth < 0 || v->bit_depth > maxd)) {
+        snprintf(buf, sizeof buf, "%s volume bit_depth %d out of range 0..%d", name, v->bit_depth, maxd);
+        err = buf;
+        return MI_EINVAL;
+    }
+    (void)parzen;
+    return MI_OK;
+}
+
+int effective_depth(const mi_volume *v) {
+    if (v->dtype == MI_F32) return 16;
+    const int full = v->dtype == MI_U8 ? 8 : 16;
+    return v->bit_depth == 0 ? full : v->bit_depth;
+}
+
+size_t dtype_size(int dt) { return dt == MI_U8 ? 1 : (dt == MI_U16 ? 2 : 4); }
+
+// Copy a caller volume (host or device) into a fresh device buffer.
+mi_status upload_volume(mi_ctx *ctx, const mi_volume *v, DevBuf &dst) {
+    const size_t bytes = (size_t)v->dims[0] * v->dims[1] * v->dims[2] * dtype_size(v->dtype);
+    MI_CU(dst.ensure(bytes), "allocating a volume");
+    MI_CU(cudaMemcpyAsync(dst.p, v->data, bytes, is_device_ptr(v->data) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          ctx->stream),
+          "copying a volume to the device");
+    return MI_OK;
+}
+
+mi_status add_pair(mi_ctx *ctx, const mi_volume *fx, const mi_volume *mv, int bins) {
+    std::string e;
+    const bool parzen = ctx->opt.kernel == MI_PARZEN;
+    mi_status st;
+    if ((st = validate_volume(fx, "fixed", parzen, e)) != MI_OK) return ctx->fail(st, e);
+    if ((st = validate_volume(mv, "moving", parzen, e)) != MI_OK) return ctx->fail(st, e);
+    if (parzen) {
+        if (bins < MI_MIN_PARZEN_BINS || bins > 128)
+            return ctx->fail(MI_EINVAL, "Parzen bins must be in " + std::to_string(MI_MIN_PARZEN_BINS) + "..128");
+    } else if (bins < MI_MIN_BINS || bins > MI_MAX_BINS) {
+        return ctx->fail(MI_EINVAL, "bins must be in 2..256, got " + std::to_string(bins));
+    }
+    auto P = std::make_unique<Pair>();
+    for (int a = 0; a < 3; ++a) {
+        P->nf[a] = fx->dims[a];
+        P->nm[a] = mv->dims[a];
+        P->sf[a] = fx->spacing_mm[a];
+        P->sm[a] = mv->spacing_mm[a];
+    }
+    P->bins = bins;
+    P->fdepth = effective_depth(fx);
+    P->mdepth = effective_depth(mv);
+    P->nvf = (long long)P->nf[0] * P->nf[1] * P->nf[2];
+    P->nvm = (long long)P->nm[0] * P->nm[1] * P->nm[2];
+    cudaStream_t s = ctx->stream;
+    DevBuf rawf, rawm;
+    if ((st = upload_volume(ctx, fx, rawf)) != MI_OK) return st;
+    if ((st = upload_volume(ctx, mv, rawm)) != MI_OK) return st;
+    if (parzen) {
+        MI_CU(P->pfbins.ensure((size_t)P->nvf), "allocating Parzen fixed bins");
+        MI_CU(launch_parzen_prep_fixed(rawf.p, fx->dtype, P->fdepth, P->nvf, bins, P->pfbins.as<uint8_t>(), s),
+              "Parzen fixed bins");
+        MI_CU(P->pmov.ensure((size_t)P->nvm * 4), "allocating the normalised moving volume");
+        MI_CU(launch_parzen_prep_moving(rawm.p, mv->dtype, P->mdepth, P->nvm, P->pmov.as<float>(), s),
+              "normalising the moving volume");
+        P->mdtype = 1;
+    } else {
+        // fixed: float -> 16-bit first, then bins
+        int fdt = fx->dtype;
+        const void *fsrc = rawf.p;
+        DevBuf conv;
+        if (fdt == MI_F32) {
+            MI_CU(conv.ensure((size_t)P->nvf * 2), "allocating a conversion buffer");
+            MI_CU(launch_f32_to_u16(rawf.as<float>(), P->nvf, conv.as<uint16_t>(), s), "converting the fixed volume");
+            fsrc = conv.p;
+            fdt = MI_U16;
+        }
+        MI_CU(P->fbins.ensure((size_t)P->nvf), "allocating fixed bins");
+        MI_CU(launch_bin_fixed(fsrc, fdt, P->fdepth, P->nvf, bins, P->fbins.as<uint8_t>(), s), "binning the fixed volume");
+        if (mv->dtype == MI_F32) {
+            MI_CU(P->mov.ensure((size_t)P->nvm * 2), "allocating the moving volume");
+            MI_CU(launch_f32_to_u16(rawm.as<float>(), P->nvm, P->mov.as<uint16_t>(), s), "converting the moving volume");
+            P->mdtype = 1;
+        } else {
+            MI_CU(P->mov.ensure((size_t)P->nvm * dtype_size(mv->dtype)), "allocating the moving volume");
+            MI_CU(cudaMemcpyAsync(P->mov.p, rawm.p, (size_t)P->nvm * dtype_size(mv->dtype), cudaMemcpyDeviceToDevice, s),
+                  "copying the moving volume");
+            P->mdtype = mv->dtype == MI_U8 ? 0 : 1;
+            MI_CU(launch_clamp_depth(P->mov.p, P->mdtype, P->mdepth, P->nvm, s), "clamping the moving volume");
+        }
+    }
+    MI_CU(cudaStreamSynchronize(s), "preparing the volumes");
+    ctx->max_bins = std::max(ctx->max_bins, bins);
+    ctx->pairs.push_back(std::move(P));
+    return MI_OK;
+}
+
+mi_status upload_pairs(mi_ctx *ctx) {
+    std::vector<PairDev> pd(ctx->pairs.size());
+    for (size_t i = 0; i < ctx->pairs.size(); ++i) {
+        const Pair &P = *ctx->pairs[i];
+        PairDev &d = pd[i];
+        memset(&d, 0, sizeof d);
+        d.fbins = P.fbins.as<uint8_t>();
+        d.mov = P.mov.p;
+        for (int a = 0; a < 3; ++a) {
+            d.nf[a] = P.nf[a];
+            d.nm[a] = P.nm[a];
+        }
+        d.bins = P.bins;
+        d.mdepth = P.mdepth;
+        d.mdtype = P.mdtype;
+    }
+    MI_CU(ctx->d_pairs.ensure(pd.size() * sizeof(PairDev)), "allocating pair descriptors");
+    MI_CU(cudaMemcpy(ctx->d_pairs.p, pd.data(), pd.size() * sizeof(PairDev), cudaMemcpyHostToDevice),
+          "uploading pair descriptors");
+    return MI_OK;
+}
+
+PairDev host_pairdev(const Pair &P) {
+    PairDev d;
+    memset(&d, 0, sizeof d);
+    d.fbins = P.fbins.as<uint8_t>();
+    d.mov = P.mov.p;
+    for (int a = 0; a < 3; ++a) {
+        d.nf[a] = P.nf[a];
+        d.nm[a] = P.nm[a];
+    }
+    d.bins = P.bins;
+    d.mdepth = P.mdepth;
+    d.mdtype = P.mdtype;
+    return d;
+}
+
+mi_status create_common(mi_ctx **out, const mi_volume *fixed, const mi_volume *moving, const int *bins, int npairs,
+                        const mi_options *opt) {
+    if (!out) {
+        g_create_error = "out is NULL";
+        return MI_EINVAL;
+    }
+    *out = nullptr;
+    auto ctx = std::make_unique<mi_ctx>();
+    if (opt)
+        ctx->opt = *opt;
+    else
+        mi_options_default(&ctx->opt);
+    if (npairs < 1 || !fixed || !moving || !bins) {
+        g_create_error = "need at least one (fixed, moving, bins) pair";
+        return MI_EINVAL;
+    }
+    if (ctx->opt.kernel != MI_HARD && ctx->opt.kernel != MI_PARZEN) {
+        g_create_error = "opt.kernel must be MI_HARD or MI_PARZEN";
+        return MI_EINVAL;
+    }
+    if (ctx->opt.kernel == MI_PARZEN && npairs != 1) {
+        g_create_error = "the Parzen form takes one pair per context";
+        return MI_EINVAL;
+    }
+    if (ctx->opt.hist_variant < MI_HV_AUTO || ctx->opt.hist_variant > MI_HV_U16_MATCH) {
+        g_create_error = "opt.hist_variant out of range";
+        return MI_EINVAL;
+    }
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        g_create_error = std::string("no CUDA device: ") + cudaGetErrorString(e);
+        return MI_ECUDA;
+    }
+    int dev = ctx->opt.device;
+    if (dev < 0) cudaGetDevice(&dev);
+    if (dev >= ndev) {
+        g_create_error = "opt.device out of range";
+        return MI_EINVAL;
+    }
+    ctx->device = dev;
+    DeviceGuard guard(dev);
+    cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, dev);
+    if ((e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        g_create_error = std::string("creating a stream: ") + cudaGetErrorString(e);
+        return MI_ECUDA;
+    }
+    ctx->stream = ctx->own_stream;
+    if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess) {
+        cudaGetLastError();
+        g_create_error = "creating events";
+        return MI_ECUDA;
+    }
+    for (int p = 0; p < npairs; ++p) {
+        mi_status st = add_pair(ctx.get(), &fixed[p], &moving[p], bins[p]);
+        if (st != MI_OK) {
+            g_create_error = "pair " + std::to_string(p) + ": " + ctx->err;
+            return st;
+        }
+    }
+    if (ctx->opt.kernel == MI_HARD) {
+        mi_status st = upload_pairs(ctx.get());
+        if (st != MI_OK) {
+            g_create_error = ctx->err;
+            return st;
+        }
+        MI_CU(ctx->d_flags.ensure(2 * sizeof(int)), "allocating flags");
+        MI_CU(ctx->d_ticket.ensure(sizeof(int)), "allocating the ticket");
+    }
+    *out = ctx.release();
+    return MI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// q sets and tables
+// ---------------------------------------------------------------------------
+
+uint32_t fbits(float f) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return u;
+}
+
+mi_status read_q(mi_ctx *ctx, const float *q, int nq, float out[kMaxQ]) {
+    if (nq < 1 || nq > kMaxQ) return ctx->fail(MI_EINVAL, "nq must be in 1..8");
+    if (!q) return ctx->fail(MI_EINVAL, "q is NULL");
+    if (is_device_ptr(q))
+        MI_CU(cudaMemcpy(out, q, nq * sizeof(float), cudaMemcpyDeviceToHost), "reading q");
+    else
+        memcpy(out, q, nq * sizeof(float));
+    for (int i = 0; i < nq; ++i) {
+        const float v = out[i];
+        if (!(v > 0.0f) || !isfinite(v)) return ctx->fail(MI_EINVAL, "q values must be finite and > 0");
+        if (v != 1.0f && fabsf(v - 1.0f) < 1e-6f)
+            return ctx->fail(MI_EINVAL, "q within 1e-6 of 1 is ill-conditioned; use q = 1 for Shannon");
+    }
+    return MI_OK;
+}
+
+mi_status make_qset(mi_ctx *ctx, const float *qv, int nq, QSet &Q) {
+    memset(&Q, 0, sizeof Q);
+    Q.nq = nq;
+    Q.form = ctx->opt.tsallis_form;
+    Q.bits = ctx->opt.log_bits ? 1 : 0;
+    for (int i = 0; i < nq; ++i) {
+        Q.q[i] = qv[i];
+        if (ctx->opt.kernel == MI_HARD) {
+            auto it = ctx->tables.find(fbits(qv[i]));
+            if (it == ctx->tables.end()) {
+                auto buf = std::make_unique<DevBuf>();
+                MI_CU(buf->ensure(sizeof(double) * kTab), "allocating an entropy table");
+                MI_CU(launch_table(buf->as<double>(), qv[i], ctx->stream), "building an entropy table");
+                it = ctx->tables.emplace(fbits(qv[i]), std::move(buf)).first;
+            }
+            Q.tab[i] = it->second->as<double>();
+        }
+    }
+    return MI_OK;
+}
+
+// Transforms from the caller (host or device) into a host vector.
+mi_status read_transforms(mi_ctx *ctx, const float *tr, int n, std::vector<float> &out) {
+    out.resize((size_t)n * 9);
+    if (n == 0) return MI_OK;
+    if (!tr) return ctx->fail(MI_EINVAL, "transforms is NULL");
+    if (is_device_ptr(tr))
+        MI_CU(cudaMemcpy(out.data(), tr, (size_t)n * 9 * sizeof(float), cudaMemcpyDeviceToHost), "reading transforms");
+    else
+        memcpy(out.data(), tr, (size_t)n * 9 * sizeof(float));
+    for (size_t i = 0; i < out.size(); ++i)
+        if (!isfinite(out[i])) return ctx->fail(MI_EINVAL, "transform " + std::to_string(i / 9) + " is not finite");
+    return MI_OK;
+}
+
+mi_status build_q16(mi_ctx *ctx, const Pair &P, const float *prm, int32_t *q16, int t) {
+    double aff[12];
+    build_affine(prm, P.nf, P.sf, P.nm, P.sm, aff, nullptr);
+    if (!quantise_q16(aff, q16))
+        return ctx->fail(MI_ERANGE, "transform " + std::to_string(t) + ": affine does not fit 16.16 fixed point");
+    return MI_OK;
+}
+
+// Copy n*each bytes of an internal device result to the caller's pointer (host or device).
+mi_status deliver(mi_ctx *ctx, void *dst, const void *src, size_t bytes) {
+    if (!dst || bytes == 0) return MI_OK;
+    MI_CU(cudaMemcpyAsync(dst, src, bytes, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          ctx->stream),
+          "copying results");
+    return MI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Variant selection
+// ---------------------------------------------------------------------------
+
+bool variant_fits(int variant, int bins, int threads, long long nvox) {
+    const bool u16 = variant == HV_U16 || variant == HV_U16_MATCH;
+    if (u16 && nvox > (long long)(kOvfSlots / 2) * kDrainT) return false;
+    return hard_smem_bytes(variant, bins, threads) <= 227 * 1024;
+}
+
+std::vector<Choice> candidates(mi_ctx *ctx, int bins, long long nvox_max) {
+    std::vector<Choice> c;
+    const int fixed_v = ctx->opt.hist_variant;
+    for (int v = 0; v < 4; ++v) {
+        if (fixed_v >= 0 && v != fixed_v) continue;
+        for (int th : {512, 1024}) {
+            if (!variant_fits(v, bins, th, nvox_max)) continue;
+            Choice ch;
+            ch.variant = v;
+            ch.threads = th;
+            const int per_sm = batched_ctas_per_sm(v, bins, th);
+            if (per_sm < 1) continue;
+            ch.ctas = per_sm * ctx->sms;
+            c.push_back(ch);
+        }
+    }
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// Plain path: many CTAs per transform, global histograms, then the entropy kernel
+// ---------------------------------------------------------------------------
+
+mi_status run_plain(mi_ctx *ctx, int pair, const int32_t *d_aff, int n, const QSet &Q, const Outputs &O,
+                    const Choice &ch, uint32_t *keep_hist) {
+    const Pair &P = *ctx->pairs[pair];
+    const PairDev hp = host_pairdev(P);
+    const PairDev *dp = ctx->d_pairs.as<PairDev>() + pair;
+    const size_t B2 = (size_t)P.bins * P.bins;
+    int chunk = (int)std::max<size_t>(1, (64u << 20) / (B2 * 4));
+    chunk = std::min(chunk, 4096);
+    MI_CU(cudaEventRecord(ctx->ev0, ctx->stream), "event");
+    ctx->last_launches = 0;
+    for (int t0 = 0; t0 < n; t0 += chunk) {
+        const int m = std::min(chunk, n - t0);
+        uint32_t *hist = keep_hist ? keep_hist + (size_t)t0 * B2 : nullptr;
+        if (!hist) {
+            MI_CU(ctx->d_hist.ensure((size_t)m * B2 * 4), "allocating histograms");
+            hist = ctx->d_hist.as<uint32_t>();
+        }
+        // CTAs per transform: fill the GPU, but keep at least 8 row batches of 32 rows per CTA
+        const long long rows = (long long)P.nf[1] * P.nf[2];
+        const int per_sm = std::max(1, batched_ctas_per_sm(ch.variant, P.bins, ch.threads));
+        long long ctas = ((long long)ctx->sms * per_sm + m - 1) / m;
+        ctas = std::min<long long>(ctas, std::max<long long>(1, rows / (32 * 8)));
+        MI_CU(launch_plain_hist(dp, hp, d_aff + (size_t)t0 * 12, m, hist, ch.variant, ch.threads, (int)std::max(1LL, ctas),
+                                O.flags, ctx->stream),
+              "plain histogram kernel");
+        if (O.mi || O.h || O.count) {
+            Outputs Oc = O;
+            if (Oc.mi) Oc.mi += (size_t)t0 * Q.nq;
+            if (Oc.h) Oc.h += (size_t)t0 * Q.nq * 3;
+            if (Oc.count) Oc.count += t0;
+            Oc.dump = nullptr;
+            MI_CU(launch_entropy(hist, m, P.bins, Q, Oc, ctx->stream), "entropy kernel");
+            ctx->last_launches += 1;
+        }
+        ctx->last_launches += 1;
+    }
+    MI_CU(cudaEventRecord(ctx->ev1, ctx->stream), "event");
+    return MI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched path: persistent kernel over a work queue, replayed as a CUDA graph
+// ---------------------------------------------------------------------------
+
+mi_status launch_batched_once(mi_ctx *ctx, int nitems, const QSet &Q, const Outputs &O, const Choice &ch,
+                              bool record = false) {
+    MI_CU(cudaMemsetAsync(ctx->d_ticket.p, 0, sizeof(int), ctx->stream), "resetting the work queue");
+    if (record) MI_CU(cudaEventRecord(ctx->ev0, ctx->stream), "event");
+    MI_CU(launch_batched(ctx->d_pairs.as<PairDev>(), ctx->d_aff.as<int32_t>(), ctx->d_items.as<Item>(), nitems,
+                         ctx->d_ticket.as<int>(), ctx->max_bins, ch.variant, ch.threads, ch.ctas, Q, O, ctx->stream),
+          "batched kernel");
+    if (record) MI_CU(cudaEventRecord(ctx->ev1, ctx->stream), "event");
+    return MI_OK;
+}
+
+// Autotune: time every candidate on the first items of this call (one wave).
+mi_status autotune(mi_ctx *ctx, int nitems, const QSet &Q, const Outputs &O, Choice &best,
+                   const std::vector<Choice> &cands) {
+    if (cands.empty()) return ctx->fail(MI_EUNSUPPORTED, "no histogram variant fits this bin count and volume size");
+    if (cands.size() == 1 || !ctx->opt.autotune) {
+        best = cands.front();
+        // heuristic: prefer 32-bit counters with warp aggregation, 1024 threads
+        for (const Choice &c : cands)
+            if (c.variant == HV_U32_MATCH && c.threads == 1024) best = c;
+        if (best.variant < 0) best = cands.front();
+        return MI_OK;
+    }
+    cudaEvent_t e0, e1;
+    MI_CU(cudaEventCreate(&e0), "event");
+    MI_CU(cudaEventCreate(&e1), "event");
+    float best_ms = 1e30f;
+    Outputs Ot = O;
+    Ot.dump = nullptr;
+    for (const Choice &c : cands) {
+        const int items = std::min(nitems, c.ctas);
+        Choice cc = c;
+        mi_status st = launch_batched_once(ctx, items, Q, Ot, cc);  // warm-up
+        if (st != MI_OK) break;
+        cudaEventRecord(e0, ctx->stream);
+        for (int rep = 0; rep < 2; ++rep) launch_batched_once(ctx, items, Q, Ot, cc);
+        cudaEventRecord(e1, ctx->stream);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return ctx->cuda_fail(e, "autotuning");
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        // per item on a full wave
+        ms = ms / (float)items;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return MI_OK;
+}
+
+mi_status run_batched(mi_ctx *ctx, int nitems, const QSet &Q, const Outputs &O, const Choice &ch, bool use_graph,
+                      const std::string &key, const void *h_aff_src, size_t aff_bytes, const void *h_items_src,
+                      size_t item_bytes) {
+    // inputs go through pinned staging so that a captured graph can replay the copies
+    MI_CU(ctx->h_aff.ensure(aff_bytes), "pinned staging");
+    MI_CU(ctx->h_items.ensure(item_bytes), "pinned staging");
+    memcpy(ctx->h_aff.p, h_aff_src, aff_bytes);
+    memcpy(ctx->h_items.p, h_items_src, item_bytes);
+    if (!use_graph) {
+        MI_CU(cudaMemcpyAsync(ctx->d_aff.p, ctx->h_aff.p, aff_bytes, cudaMemcpyHostToDevice, ctx->stream), "H2D");
+        MI_CU(cudaMemcpyAsync(ctx->d_items.p, ctx->h_items.p, item_bytes, cudaMemcpyHostToDevice, ctx->stream), "H2D");
+        return launch_batched_once(ctx, nitems, Q, O, ch, true);
+    }
+    auto it = ctx->graphs.find(key);
+    if (it == ctx->graphs.end()) {
+        // set kernel attributes outside of capture
+        batched_ctas_per_sm(ch.variant, ctx->max_bins, ch.threads);
+        cudaGraph_t g;
+        MI_CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed), "begin capture");
+        cudaMemcpyAsync(ctx->d_aff.p, ctx->h_aff.p, aff_bytes, cudaMemcpyHostToDevice, ctx->stream);
+        cudaMemcpyAsync(ctx->d_items.p, ctx->h_items.p, item_bytes, cudaMemcpyHostToDevice, ctx->stream);
+        mi_status st = launch_batched_once(ctx, nitems, Q, O, ch, true);
+        cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+        if (st != MI_OK) return st;
+        if (e != cudaSuccess) return ctx->cuda_fail(e, "end capture");
+        auto ge = std::make_unique<GraphEntry>();
+        e = cudaGraphInstantiate(&ge->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return ctx->cuda_fail(e, "instantiating the graph");
+        if (ctx->graphs.size() > 32) ctx->graphs.clear();
+        it = ctx->graphs.emplace(key, std::move(ge)).first;
+    }
+    MI_CU(cudaGraphLaunch(it->second->exec, ctx->stream), "graph launch");
+    return MI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Shared evaluation core for mi_eval / mi_eval_q16 / mi_batch_eval / mi_hist
+// ---------------------------------------------------------------------------
+
+struct EvalReq {
+    std::vector<int32_t> q16;  // n x 12 (host) -- or device affines below
+    const int32_t *d_q16 = nullptr;
+    std::vector<int> pair_of;  // n (empty = all pair 0)
+    int n = 0;
+    int path = MI_PATH_AUTO;
+    uint32_t *dump = nullptr;  // device histograms (mi_hist)
+};
+
+mi_status eval_core(mi_ctx *ctx, const EvalReq &R, const float *qv, int nq, double *out_mi, double *out_h,
+                    int64_t *out_count) {
+    const int n = R.n;
+    QSet Q;
+    mi_status st = make_qset(ctx, qv, nq, Q);
+    if (st != MI_OK) return st;
+    MI_CU(ctx->d_mi.ensure((size_t)n * nq * 8), "allocating outputs");
+    MI_CU(ctx->d_h.ensure((size_t)n * nq * 3 * 8), "allocating outputs");
+    MI_CU(ctx->d_cnt.ensure((size_t)n * 8), "allocating outputs");
+    MI_CU(ctx->d_aff.ensure((size_t)n * 12 * 4), "allocating affines");
+    MI_CU(cudaMemsetAsync(ctx->d_flags.p, 0, 2 * sizeof(int), ctx->stream), "resetting flags");
+    Outputs O;
+    O.mi = ctx->d_mi.as<double>();
+    O.h = ctx->d_h.as<double>();
+    O.count = ctx->d_cnt.as<long long>();
+    O.dump = R.dump;
+    O.flags = ctx->d_flags.as<int>();
+    const bool multi = ctx->pairs.size() > 1;
+    int path = R.path;
+    if (path == MI_PATH_AUTO) path = (multi || n >= ctx->sms) ? MI_PATH_BATCHED : MI_PATH_PLAIN;
+    if (multi && path == MI_PATH_PLAIN) return ctx->fail(MI_EINVAL, "multi-pair contexts use the batched path");
+    long long nvox_max = 0;
+    for (auto &p : ctx->pairs) nvox_max = std::max(nvox_max, p->nvf);
+    std::vector<Choice> cands = candidates(ctx, ctx->max_bins, nvox_max);
+    if (cands.empty()) return ctx->fail(MI_EUNSUPPORTED, "no histogram variant fits this bin count and volume size");
+    if (path == MI_PATH_PLAIN) {
+        const int32_t *d_aff = R.d_q16;
+        if (!d_aff) {
+            MI_CU(cudaMemcpyAsync(ctx->d_aff.p, R.q16.data(), (size_t)n * 48, cudaMemcpyHostToDevice, ctx->stream), "H2D");
+            d_aff = ctx->d_aff.as<int32_t>();
+        }
+        auto key = std::make_tuple((int)MI_PATH_PLAIN, 0, 0);
+        Choice ch;
+        auto it = ctx->tuned.find(key);
+        if (it != ctx->tuned.end()) {
+            ch = it->second;
+        } else {
+            ch = cands.front();
+            for (const Choice &c : cands)
+                if (c.variant == (ctx->max_bins <= 181 ? HV_U32_MATCH : HV_U16_MATCH) && c.threads == 1024) ch = c;
+            ctx->tuned[key] = ch;
+        }
+        st = run_plain(ctx, 0, d_aff, n, Q, O, ch, R.dump);
+        if (st != MI_OK) return st;
+        ctx->timed = true;
+    } else {
+        // work items sorted by cost (voxels of the pair), largest first
+        std::vector<Item> items(n);
+        for (int t = 0; t < n; ++t) items[t] = Item{R.pair_of.empty() ? 0 : R.pair_of[t], t};
+        if (multi)
+            std::stable_sort(items.begin(), items.end(), [&](const Item &a, const Item &b) {
+                return ctx->pairs[a.pair]->nvf > ctx->pairs[b.pair]->nvf;
+            });
+        MI_CU(ctx->d_items.ensure((size_t)n * sizeof(Item)), "allocating items");
+        std::vector<int32_t> q16h;
+        const int32_t *h_aff = R.q16.data();
+        if (R.d_q16) {
+            q16h.resize((size_t)n * 12);
+            MI_CU(cudaMemcpy(q16h.data(), R.d_q16, (size_t)n * 48, cudaMemcpyDeviceToHost), "reading affines");
+            h_aff = q16h.data();
+        }
+        const int bucket = n >= 4 * ctx->sms ? 2 : (n >= ctx->sms ? 1 : 0);
+        auto key = std::make_tuple((int)MI_PATH_BATCHED, -1, bucket);
+        Choice ch;
+        auto it = ctx->tuned.find(key);
+        if (it != ctx->tuned.end()) {
+            ch = it->second;
+        } else {
+            // tuning needs the inputs on the device
+            MI_CU(cudaMemcpyAsync(ctx->d_aff.p, h_aff, (size_t)n * 48, cudaMemcpyHostToDevice, ctx->stream), "H2D");
+            MI_CU(cudaMemcpyAsync(ctx->d_items.p, items.data(), (size_t)n * sizeof(Item), cudaMemcpyHostToDevice,
+                                  ctx->stream),
+                  "H2D");
+            st = autotune(ctx, n, Q, O, ch, cands);
+            if (st != MI_OK) return st;
+            ctx->tuned[key] = ch;
+            MI_CU(cudaMemsetAsync(ctx->d_flags.p, 0, 2 * sizeof(int), ctx->stream), "resetting flags");
+        }
+        const bool use_graph = ctx->opt.use_graphs && !R.dump && ctx->stream != nullptr;
+        // staging buffers are sized before the key is formed: a graph replays copies from their addresses
+        MI_CU(ctx->h_aff.ensure((size_t)n * 48), "pinned staging");
+        MI_CU(ctx->h_items.ensure((size_t)n * sizeof(Item)), "pinned staging");
+        char kb[512];
+        int off = snprintf(kb, sizeof kb, "b:%d:%d:%d:%d:%d:%p:%p:%p:%p:%p:%p:%p:%d:%d", n, nq, ch.variant, ch.threads,
+                           ch.ctas, ctx->d_aff.p, ctx->d_items.p, ctx->d_mi.p, ctx->d_h.p, ctx->d_cnt.p, ctx->h_aff.p,
+                           ctx->h_items.p, Q.form, Q.bits);
+        for (int i = 0; i < nq && off < (int)sizeof kb - 40; ++i)
+            off += snprintf(kb + off, sizeof kb - off, ":%08x:%p", fbits(Q.q[i]), (const void *)Q.tab[i]);
+        st = run_batched(ctx, n, Q, O, ch, use_graph, kb, h_aff, (size_t)n * 48, items.data(), (size_t)n * sizeof(Item));
+        if (st != MI_OK) return st;
+        ctx->timed = true;
+        ctx->last_launches = 1;
+    }
+    if ((st = deliver(ctx, out_mi, ctx->d_mi.p, (size_t)n * nq * 8)) != MI_OK) return st;
+    if ((st = deliver(ctx, out_h, ctx->d_h.p, (size_t)n * nq * 3 * 8)) != MI_OK) return st;
+    if ((st = deliver(ctx, out_count, ctx->d_cnt.p, (size_t)n * 8)) != MI_OK) return st;
+    int flags[2] = {0, 0};
+    MI_CU(cudaMemcpyAsync(flags, ctx->d_flags.p, sizeof flags, cudaMemcpyDeviceToHost, ctx->stream), "reading flags");
+    MI_CU(cudaStreamSynchronize(ctx->stream), "evaluation");
+    if (flags[1]) return ctx->fail(MI_ECUDA, "internal: 16-bit counter drain failed (flags " + std::to_string(flags[1]) + ")");
+    if (flags[0]) return ctx->fail(MI_EEMPTY, "at least one transform has an empty overlap (its MI is NaN)");
+    return MI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Parzen
+// ---------------------------------------------------------------------------
+
+mi_status parzen_core(mi_ctx *ctx, const std::vector<float> &prm, int n, const float *qv, int nq, double *out_mi,
+                      double *out_grad) {
+    const Pair &P = *ctx->pairs[0];
+    const int B = P.bins;
+    const size_t B2 = (size_t)B * B;
+    QSet Q;
+    mi_status st = make_qset(ctx, qv, nq, Q);
+    if (st != MI_OK) return st;
+    std::vector<ParzenAffine> pa(n);
+    std::vector<double> jac((size_t)n * 108);
+    for (int t = 0; t < n; ++t) {
+        double aff[12];
+        build_affine(&prm[(size_t)t * 9], P.nf, P.sf, P.nm, P.sm, aff, &jac[(size_t)t * 108]);
+        for (int e = 0; e < 12; ++e) pa[t].A[e] = (float)aff[e];
+    }
+    cudaStream_t s = ctx->stream;
+    MI_CU(ctx->p_aff.ensure((size_t)n * sizeof(ParzenAffine)), "alloc");
+    MI_CU(ctx->p_jac.ensure((size_t)n * 108 * 8), "alloc");
+    MI_CU(ctx->p_hist.ensure((size_t)n * B2 * 8), "alloc");
+    MI_CU(ctx->p_cnt.ensure((size_t)n * 8), "alloc");
+    MI_CU(ctx->p_marg.ensure((size_t)n * 2 * B * 8), "alloc");
+    MI_CU(ctx->p_ment.ensure((size_t)n * nq * 2 * 8), "alloc");
+    MI_CU(ctx->p_jsum.ensure((size_t)n * nq * 8), "alloc");
+    MI_CU(ctx->p_w.ensure((size_t)n * nq * B2 * 4), "alloc");
+    MI_CU(ctx->p_mom.ensure((size_t)n * nq * 12 * 8), "alloc");
+    MI_CU(ctx->p_grad.ensure((size_t)n * nq * 9 * 8), "alloc");
+    MI_CU(ctx->d_mi.ensure((size_t)n * nq * 8), "alloc");
+    MI_CU(cudaMemcpyAsync(ctx->p_aff.p, pa.data(), (size_t)n * sizeof(ParzenAffine), cudaMemcpyHostToDevice, s), "H2D");
+    MI_CU(cudaMemcpyAsync(ctx->p_jac.p, jac.data(), (size_t)n * 108 * 8, cudaMemcpyHostToDevice, s), "H2D");
+    ParzenPair pp;
+    memset(&pp, 0, sizeof pp);
+    pp.fbins = P.pfbins.as<uint8_t>();
+    pp.mov = P.pmov.as<float>();
+    for (int a = 0; a < 3; ++a) {
+        pp.nf[a] = P.nf[a];
+        pp.nm[a] = P.nm[a];
+    }
+    pp.B = B;
+    const ParzenAffine *d_aff = ctx->p_aff.as<ParzenAffine>();
+    auto *cnt = ctx->p_cnt.as<unsigned long long>();
+    MI_CU(cudaEventRecord(ctx->ev0, s), "event");
+    MI_CU(launch_parzen_hist(pp, d_aff, n, ctx->p_hist.as<double>(), cnt, s), "Parzen histogram");
+    MI_CU(launch_parzen_weights(ctx->p_hist.as<double>(), cnt, n, B, Q, ctx->p_marg.as<double>(), ctx->p_ment.as<double>(),
+                                ctx->p_jsum.as<double>(), ctx->d_mi.as<double>(), ctx->p_w.as<float>(), s),
+          "Parzen entropies");
+    if (out_grad)
+        MI_CU(launch_parzen_adjoint(pp, d_aff, ctx->p_jac.as<double>(), n, nq, ctx->p_w.as<float>(), cnt,
+                                    ctx->p_mom.as<double>(), ctx->p_grad.as<double>(), s),
+              "Parzen adjoint");
+    MI_CU(cudaEventRecord(ctx->ev1, s), "event");
+    ctx->timed = true;
+    ctx->last_launches = 4 + (out_grad ? (nq + 3) / 4 + 1 : 0);
+    if ((st = deliver(ctx, out_mi, ctx->d_mi.p, (size_t)n * nq * 8)) != MI_OK) return st;
+    if (out_grad && (st = deliver(ctx, out_grad, ctx->p_grad.p, (size_t)n * nq * 9 * 8)) != MI_OK) return st;
+    std::vector<unsigned long long> hc(n);
+    MI_CU(cudaMemcpyAsync(hc.data(), cnt, (size_t)n * 8, cudaMemcpyDeviceToHost, s), "reading counts");
+    MI_CU(cudaStreamSynchronize(s), "Parzen evaluation");
+    for (int t = 0; t < n; ++t)
+        if (hc[t] == 0) return ctx->fail(MI_EEMPTY, "at least one transform has an empty overlap (its MI is NaN)");
+    return MI_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+void mi_options_default(mi_options *opt) {
+    if (!opt) return;
+    opt->kernel = MI_HARD;
+    opt->tsallis_form = MI_TSALLIS_ADDITIVE;
+    opt->log_bits = 0;
+    opt->hist_variant = MI_HV_AUTO;
+    opt->path = MI_PATH_AUTO;
+    opt->use_graphs = 1;
+    opt->autotune = 1;
+    opt->device = -1;
+}
+
+const char *mi_version(void) { return "gb300-mi 0.1 (sm_103a)"; }
+
+mi_status mi_create(mi_ctx **out, const mi_volume *fixed, const mi_volume *moving, int bins, const mi_options *opt) {
+    return create_common(out, fixed, moving, &bins, 1, opt);
+}
+
+mi_status mi_batch_create(mi_ctx **out, const mi_volume *fixed, const mi_volume *moving, const int *bins, int npairs,
+                          const mi_options *opt) {
+    mi_options o;
+    if (opt)
+        o = *opt;
+    else
+        mi_options_default(&o);
+    if (o.kernel != MI_HARD) {
+        if (out) *out = nullptr;
+        g_create_error = "mi_batch_create supports the hard-binned path only";
+        return MI_EUNSUPPORTED;
+    }
+    return create_common(out, fixed, moving, bins, npairs, &o);
+}
+
+void mi_destroy(mi_ctx *ctx) {
+    if (!ctx) return;
+    {
+        DeviceGuard guard(ctx->device);
+        if (ctx->own_stream) cudaStreamSynchronize(ctx->own_stream);
+        ctx->graphs.clear();
+        ctx->tables.clear();
+        ctx->pairs.clear();
+        if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+        ctx->own_stream = nullptr;
+        if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+        if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    }
+    delete ctx;
+}
+
+const char *mi_last_error(const mi_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+mi_status mi_set_stream(mi_ctx *ctx, void *stream) {
+    if (!ctx) return MI_EINVAL;
+    ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
+    ctx->graphs.clear();
+    return MI_OK;
+}
+
+mi_status mi_eval(mi_ctx *ctx, const float *transforms, int n, const float *q, int nq, double *out_mi, double *out_h,
+                  int64_t *out_count) {
+    if (!ctx) return MI_EINVAL;
+    DeviceGuard guard(ctx->device);
+    if (n < 0) return ctx->fail(MI_EINVAL, "n < 0");
+    float qv[kMaxQ];
+    mi_status st = read_q(ctx, q, nq, qv);
+    if (st != MI_OK) return st;
+    if (n == 0) return MI_OK;
+    if (!out_mi) return ctx->fail(MI_EINVAL, "out_mi is NULL");
+    if (ctx->pairs.size() != 1) return ctx->fail(MI_EINVAL, "mi_eval needs a single-pair context (use mi_batch_eval)");
+    std::vector<float> prm;
+    if ((st = read_transforms(ctx, transforms, n, prm)) != MI_OK) return st;
+    if (ctx->opt.kernel == MI_PARZEN) {
+        if (out_h || out_count) return ctx->fail(MI_EUNSUPPORTED, "out_h / out_count are hard-path outputs");
+        return parzen_core(ctx, prm, n, qv, nq, out_mi, nullptr);
+    }
+    EvalReq R;
+    R.n = n;
+    R.path = ctx->opt.path;
+    R.q16.resize((size_t)n * 12);
+    for (int t = 0; t < n; ++t)
+        if ((st = build_q16(ctx, *ctx->pairs[0], &prm[(size_t)t * 9], &R.q16[(size_t)t * 12], t)) != MI_OK) return st;
+    return eval_core(ctx, R, qv, nq, out_mi, out_h, out_count);
+}
+
+mi_status mi_eval_q16(mi_ctx *ctx, const int32_t *affines, int n, const float *q, int nq, double *out_mi, double *out_h,
+                      int64_t *out_count) {
+    if (!ctx) return MI_EINVAL;
+    DeviceGuard guard(ctx->device);
+    if (n < 0) return ctx->fail(MI_EINVAL, "n < 0");
+    if (ctx->opt.kernel != MI_HARD) return ctx->fail(MI_EUNSUPPORTED, "mi_eval_q16 is a hard-path entry point");
+    float qv[kMaxQ];
+    mi_status st = read_q(ctx, q, nq, qv);
+    if (st != MI_OK) return st;
+    if (n == 0) return MI_OK;
+    if (!out_mi) return ctx->fail(MI_EINVAL, "out_mi is NULL");
+    if (!affines) return ctx->fail(MI_EINVAL, "affines is NULL");
+    EvalReq R;
+    R.n = n;
+    R.path = ctx->opt.path;
+    if (is_device_ptr(affines)) {
+        R.d_q16 = affines;
+    } else {
+        R.q16.assign(affines, affines + (size_t)n * 12);
+    }
+    return eval_core(ctx, R, qv, nq, out_mi, out_h, out_count);
+}
+
+mi_status mi_batch_eval(mi_ctx *ctx, const int *pair_of_transform, const float *transforms, int n, const float *q,
+                        int nq, double *out_mi, double *out_h, int64_t *out_count) {
+    if (!ctx) return MI_EINVAL;
+    DeviceGuard guard(ctx->device);
+    if (n < 0) return ctx->fail(MI_EINVAL, "n < 0");
+    if (ctx->opt.kernel != MI_HARD) return ctx->fail(MI_EUNSUPPORTED, "mi_batch_eval is a hard-path entry point");
+    float qv[kMaxQ];
+    mi_status st = read_q(ctx, q, nq, qv);
+    if (st != MI_OK) return st;
+    if (n == 0) return MI_OK;
+    if (!out_mi || !pair_of_transform) return ctx->fail(MI_EINVAL, "out_mi or pair_of_transform is NULL");
+    std::vector<float> prm;
+    if ((st = read_transforms(ctx, transforms, n, prm)) != MI_OK) return st;
+    EvalReq R;
+    R.n = n;
+    R.path = MI_PATH_BATCHED;
+    R.pair_of.resize(n);
+    if (is_device_ptr(pair_of_transform))
+        MI_CU(cudaMemcpy(R.pair_of.data(), pair_of_transform, (size_t)n * 4, cudaMemcpyDeviceToHost), "reading pairs");
+    else
+        memcpy(R.pair_of.data(), pair_of_transform, (size_t)n * 4);
+    R.q16.resize((size_t)n * 12);
+    for (int t = 0; t < n; ++t) {
+        const int p = R.pair_of[t];
+        if (p < 0 || p >= (int)ctx->pairs.size()) return ctx->fail(MI_EINVAL, "pair index out of range");
+        if ((st = build_q16(ctx, *ctx->pairs[p], &prm[(size_t)t * 9], &R.q16[(size_t)t * 12], t)) != MI_OK) return st;
+    }
+    return eval_core(ctx, R, qv, nq, out_mi, out_h, out_count);
+}
+
+mi_status mi_grad(mi_ctx *ctx, const float *transforms, int n, const float *q, int nq, double *out_mi,
+                  double *out_grad) {
+    if (!ctx) return MI_EINVAL;
+    DeviceGuard guard(ctx->device);
+    if (ctx->opt.kernel != MI_PARZEN)
+        return ctx->fail(MI_EUNSUPPORTED, "mi_grad needs a MI_PARZEN context (the hard histogram is not differentiable)");
+    if (n < 0) return ctx->fail(MI_EINVAL, "n < 0");
+    float qv[kMaxQ];
+    mi_status st = read_q(ctx, q, nq, qv);
+    if (st != MI_OK) return st;
+    if (n == 0) return MI_OK;
+    if (!out_mi || !out_grad) return ctx->fail(MI_EINVAL, "out_mi or out_grad is NULL");
+    std::vector<float> prm;
+    if ((st = read_transforms(ctx, transforms, n, prm)) != MI_OK) return st;
+    return parzen_core(ctx, prm, n, qv, nq, out_mi, out_grad);
+}
+
+mi_status mi_hist(mi_ctx *ctx, int pair, const float *transforms, const int32_t *affines, int n, int path,
+                  uint32_t *out_counts) {
+    if (!ctx) return MI_EINVAL;
+    DeviceGuard guard(ctx->device);
+    if (ctx->opt.kernel != MI_HARD) return ctx->fail(MI_EUNSUPPORTED, "mi_hist is a hard-path entry point");
+    if (pair < 0 || pair >= (int)ctx->pairs.size()) return ctx->fail(MI_EINVAL, "pair index out of range");
+    if (n < 0 || (!transforms == !affines)) return ctx->fail(MI_EINVAL, "give exactly one of transforms and affines");
+    if (path != MI_PATH_PLAIN && path != MI_PATH_BATCHED) return ctx->fail(MI_EINVAL, "path must be PLAIN or BATCHED");
+    if (ctx->pairs.size() != 1 && path == MI_PATH_PLAIN) return ctx->fail(MI_EINVAL, "plain path needs a single pair");
+    if (n == 0) return MI_OK;
+    if (!out_counts) return ctx->fail(MI_EINVAL, "out_counts is NULL");
+    const Pair &P = *ctx->pairs[pair];
+    EvalReq R;
+    R.n = n;
+    R.path = path;
+    R.q16.resize((size_t)n * 12);
+    mi_status st;
+    if (transforms) {
+        std::vector<float> prm;
+        if ((st = read_transforms(ctx, transforms, n, prm)) != MI_OK) return st;
+        for (int t = 0; t < n; ++t)
+            if ((st = build_q16(ctx, P, &prm[(size_t)t * 9], &R.q16[(size_t)t * 12], t)) != MI_OK) return st;
+    } else if (is_device_ptr(affines)) {
+        MI_CU(cudaMemcpy(R.q16.data(), affines, (size_t)n * 48, cudaMemcpyDeviceToHost), "reading affines");
+    } else {
+        R.q16.assign(affines, affines + (size_t)n * 12);
+    }
+    if (ctx->pairs.size() > 1) R.pair_of.assign(n, pair);
+    const size_t B2 = (size_t)P.bins * P.bins;
+    MI_CU(ctx->d_dump.ensure((size_t)n * B2 * 4), "allocating histograms");
+    R.dump = ctx->d_dump.as<uint32_t>();
+    const float one = 1.0f;
+    st = eval_core(ctx, R, &one, 1, nullptr, nullptr, nullptr);
+    if (st != MI_OK && st != MI_EEMPTY) return st;
+    mi_status st2 = deliver(ctx, out_counts, R.dump, (size_t)n * B2 * 4);
+    if (st2 != MI_OK) return st2;
+    MI_CU(cudaStreamSynchronize(ctx->stream), "copying histograms");
+    return MI_OK;
+}
+
+mi_status mi_affine(mi_ctx *ctx, int pair, const float *transforms, int n, double *out_affine, int32_t *out_q16,
+                    double *out_jacobian) {
+    if (!ctx) return MI_EINVAL;
+    if (pair < 0 || pair >= (int)ctx->pairs.size()) return ctx->fail(MI_EINVAL, "pair index out of range");
+    if (n < 0 || (n > 0 && !transforms)) return ctx->fail(MI_EINVAL, "bad transforms");
+    const Pair &P = *ctx->pairs[pair];
+    mi_status st = MI_OK;
+    for (int t = 0; t < n; ++t) {
+        double aff[12], jac[108];
+        build_affine(transforms + (size_t)t * 9, P.nf, P.sf, P.nm, P.sm, aff, out_jacobian ? jac : nullptr);
+        if (out_affine) memcpy(out_affine + (size_t)t * 12, aff, sizeof aff);
+        if (out_jacobian) memcpy(out_jacobian + (size_t)t * 108, jac, sizeof jac);
+        if (out_q16) {
+            int32_t q[12];
+            if (!quantise_q16(aff, q)) {
+                st = ctx->fail(MI_ERANGE, "transform " + std::to_string(t) + ": affine does not fit 16.16 fixed point");
+                memset(q, 0, sizeof q);
+            }
+            memcpy(out_q16 + (size_t)t * 12, q, sizeof q);
+        }
+    }
+    return st;
+}
+
+mi_status mi_fixed_bins(mi_ctx *ctx, int pair, uint8_t *out) {
+    if (!ctx) return MI_EINVAL;
+    DeviceGuard guard(ctx->device);
+    if (pair < 0 || pair >= (int)ctx->pairs.size() || !out) return ctx->fail(MI_EINVAL, "bad pair or output");
+    const Pair &P = *ctx->pairs[pair];
+    const DevBuf &src = ctx->opt.kernel == MI_PARZEN ? P.pfbins : P.fbins;
+    mi_status st = deliver(ctx, out, src.p, (size_t)P.nvf);
+    if (st != MI_OK) return st;
+    MI_CU(cudaStreamSynchronize(ctx->stream), "copying bins");
+    return MI_OK;
+}
+
+mi_status mi_resample(mi_ctx *ctx, int pair, const int32_t *affine, void *out) {
+    if (!ctx) return MI_EINVAL;
+    DeviceGuard guard(ctx->device);
+    if (ctx->opt.kernel != MI_HARD) return ctx->fail(MI_EUNSUPPORTED, "mi_resample is a hard-path entry point");
+    if (pair < 0 || pair >= (int)ctx->pairs.size() || !out || !affine) return ctx->fail(MI_EINVAL, "bad arguments");
+    const Pair &P = *ctx->pairs[pair];
+    int32_t q[12];
+    if (is_device_ptr(affine))
+        MI_CU(cudaMemcpy(q, affine, 48, cudaMemcpyDeviceToHost), "reading the affine");
+    else
+        memcpy(q, affine, 48);
+    MI_CU(ctx->d_aff.ensure(48), "alloc");
+    MI_CU(cudaMemcpyAsync(ctx->d_aff.p, q, 48, cudaMemcpyHostToDevice, ctx->stream), "H2D");
+    const size_t bytes = (size_t)P.nvf * (P.mdtype == 0 ? 1 : 2);
+    DevBuf tmp;
+    void *dst = out;
+    if (!is_device_ptr(out)) {
+        MI_CU(tmp.ensure(bytes), "alloc");
+        dst = tmp.p;
+    }
+    MI_CU(launch_resample(ctx->d_pairs.as<PairDev>() + pair, host_pairdev(P), ctx->d_aff.as<int32_t>(), dst, ctx->stream),
+          "resample kernel");
+    if (dst != out) MI_CU(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, ctx->stream), "D2H");
+    MI_CU(cudaStreamSynchronize(ctx->stream), "resampling");
+    return MI_OK;
+}
+
+mi_status mi_last_kernel_ms(mi_ctx *ctx, float *ms, int *launches) {
+    if (!ctx || !ms) return MI_EINVAL;
+    if (!ctx->timed) return ctx->fail(MI_EINVAL, "no timed call yet");
+    DeviceGuard guard(ctx->device);
+    MI_CU(cudaEventSynchronize(ctx->ev1), "event");
+    MI_CU(cudaEventElapsedTime(ms, ctx->ev0, ctx->ev1), "event elapsed time");
+    if (launches) *launches = ctx->last_launches;
+    return MI_OK;
+}
+
+int mi_selected_variant(mi_ctx *ctx, int pair, int n) {
+    if (!ctx) return -1;
+    (void)pair;
+    const int path = ctx->opt.path == MI_PATH_AUTO ? ((ctx->pairs.size() > 1 || n >= ctx->sms) ? MI_PATH_BATCHED : MI_PATH_PLAIN)
+                                                   : ctx->opt.path;
+    const int bucket = path == MI_PATH_BATCHED ? (n >= 4 * ctx->sms ? 2 : (n >= ctx->sms ? 1 : 0)) : 0;
+    auto it = ctx->tuned.find(std::make_tuple(path, path == MI_PATH_BATCHED ? -1 : 0, bucket));
+    return it == ctx->tuned.end() ? -1 : it->second.variant;
+}
+
+}  // extern "C"

@@ -1,0 +1,761 @@
+// mi_hard.cu -- hard-binned mutual information on sm_103a.
+//
+// Per transform T and fixed voxel i: the 16.16 moving index U = A i + b
+// (exact integers), the overlap test, an 8-neighbour integer trilinear
+// resample of the moving volume, the moving bin, and one increment of the
+// joint histogram h[fixed bin][moving bin] (the paper's full, all-voxel
+// histogram, Discussion).  The entropies of Eq. (1) and the MI of Eq. (2)
+// (and Tsallis entropies for every q from the same histogram) are reduced in
+// FP64 from the exact counts.
+//
+// Kernels:
+//   k_bin_fixed       fixed volume -> uint8 bins, once per context
+//   k_hist<...>       plain form: many CTAs per transform, privatised shared
+//                     histograms flushed to a global histogram per transform
+//   k_entropy         plain form: one CTA per transform reduces the global histogram
+//   k_batched<...>    batched form: persistent CTAs pull (pair, transform)
+//                     items from an atomic ticket; one CTA builds the whole
+//                     histogram of an item in shared memory and reduces it in place
+//   k_resample        v(T(x)) on the fixed grid
+//
+// Row clipping: along a fixed row (j, k) the moving index is linear in i, so
+// the overlap is one interval [lo, hi] of i, found per row (float estimate,
+// then exact 64-bit checks).  Inside it every U_a lies in [0, (n_a-1) 2^16],
+// so the per-voxel arithmetic is exact in 32 bits.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "mi_internal.h"
+
+namespace mi {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr uint32_t kEmptyKey = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// Small kernels run once per context
+// ---------------------------------------------------------------------------
+
+__global__ void k_f32_to_u16(const float *__restrict__ in, long long n, uint16_t *__restrict__ out) {
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x) {
+        double v = (double)in[x];
+        if (!(v == v)) v = 0.0;
+        double s = rint(v * 65535.0);  // round half to even
+        s = s < 0.0 ? 0.0 : (s > 65535.0 ? 65535.0 : s);
+        out[x] = (uint16_t)s;
+    }
+}
+
+template <typename T>
+__global__ void k_clamp_depth(T *__restrict__ data, long long n, uint32_t vmax) {
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x) {
+        uint32_t v = data[x];
+        if (v > vmax) data[x] = (T)vmax;
+    }
+}
+
+// bin(v) = (min(v, 2^d - 1) * bins) >> d
+template <typename T>
+__global__ void k_bin_fixed(const T *__restrict__ in, long long n, int depth, int bins, uint8_t *__restrict__ out) {
+    const uint32_t vmax = (uint32_t)((1ull << depth) - 1ull);
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x) {
+        uint32_t v = in[x];
+        v = v > vmax ? vmax : v;
+        out[x] = (uint8_t)(((uint64_t)v * (uint32_t)bins) >> depth);
+    }
+}
+
+// tab[c] = c ln c (q == 1) or c^q, FP64, c < kTab; tab[0] = 0.
+__global__ void k_table(double *__restrict__ tab, float qf) {
+    const double q = (double)qf;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < kTab; c += gridDim.x * blockDim.x) {
+        double d = (double)c;
+        tab[c] = c == 0 ? 0.0 : (qf == 1.0f ? d * log(d) : pow(d, q));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Per-voxel sampling
+// ---------------------------------------------------------------------------
+
+// Stage lerp with an 8-bit weight: (a (256 - f) + b f + 128) >> 8 written as
+// a + floor(((b - a) f + 128) / 256), identical for integers (arithmetic shift).
+__device__ __forceinline__ int lerp8(int a, int b, int f) { return a + (((b - a) * f + 128) >> 8); }
+
+template <typename MovT>
+__device__ __forceinline__ int sample_hard(const MovT *__restrict__ mov, int n0, int n1, int n2, int ux, int uy,
+                                           int uz) {
+    const int ix = ux >> 16, iy = uy >> 16, iz = uz >> 16;
+    const int fx = (ux >> 8) & 255, fy = (uy >> 8) & 255, fz = (uz >> 8) & 255;
+    // the upper neighbour is clamped on the last plane, where its weight is 0
+    const int sx = ix < n0 - 1 ? 1 : 0;
+    const int sy = iy < n1 - 1 ? n0 : 0;
+    const int sz = iz < n2 - 1 ? n0 * n1 : 0;
+    const MovT *p = mov + (ix + n0 * (iy + n1 * iz));
+    const int v000 = __ldg(p), v001 = __ldg(p + sx), v010 = __ldg(p + sy), v011 = __ldg(p + sy + sx);
+    const int v100 = __ldg(p + sz), v101 = __ldg(p + sz + sx), v110 = __ldg(p + sz + sy),
+              v111 = __ldg(p + sz + sy + sx);
+    const int e00 = lerp8(v000, v001, fx), e01 = lerp8(v010, v011, fx);
+    const int e10 = lerp8(v100, v101, fx), e11 = lerp8(v110, v111, fx);
+    const int g0 = lerp8(e00, e01, fy), g1 = lerp8(e10, e11, fy);
+    return lerp8(g0, g1, fz);
+}
+
+// Overlap interval [lo, hi] of fixed row (j, k) and the 16.16 moving index at i = lo.
+struct RowClip {
+    int lo, hi, u0, u1, u2;
+};
+
+__device__ __forceinline__ bool inside_at(const long long base[3], const int st[3], const long long umax[3], int i) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        long long U = base[a] + (long long)st[a] * i;
+        if (U < 0 || U > umax[a]) return false;
+    }
+    return true;
+}
+
+__device__ RowClip clip_row(const int *q, int j, int k, int nf0, const int nm[3]) {
+    long long base[3], umax[3];
+    int st[3];
+    int lo = 0, hi = nf0 - 1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        base[a] = (long long)q[4 * a + 1] * j + (long long)q[4 * a + 2] * k + (long long)q[4 * a + 3];
+        umax[a] = (long long)(nm[a] - 1) << 16;
+        st[a] = q[4 * a];
+        if (st[a] == 0) {
+            if (base[a] < 0 || base[a] > umax[a]) { lo = nf0; hi = -1; }
+        } else {
+            // estimate of the real interval {i : 0 <= base + st i <= umax}; within one voxel of the truth
+            const float fb = (float)base[a], fs = (float)st[a], fm = (float)umax[a];
+            float e0 = -fb / fs, e1 = (fm - fb) / fs;
+            float a0 = fminf(e0, e1), a1 = fmaxf(e0, e1);
+            a0 = fminf(fmaxf(a0, -2.0f), (float)nf0 + 1.0f);
+            a1 = fminf(fmaxf(a1, -2.0f), (float)nf0 + 1.0f);
+            lo = max(lo, (int)ceilf(a0));
+            hi = min(hi, (int)floorf(a1));
+        }
+    }
+    // exact fix-up: the interval of a linear function is contiguous
+    while (lo <= hi && !inside_at(base, st, umax, lo)) ++lo;
+    while (lo > 0 && lo <= nf0 && inside_at(base, st, umax, lo - 1)) --lo;
+    while (hi >= lo && !inside_at(base, st, umax, hi)) --hi;
+    while (hi >= lo && hi < nf0 - 1 && inside_at(base, st, umax, hi + 1)) ++hi;
+    if (hi < lo && lo < nf0 && inside_at(base, st, umax, lo)) {
+        hi = lo;
+        while (hi < nf0 - 1 && inside_at(base, st, umax, hi + 1)) ++hi;
+    }
+    RowClip r;
+    r.lo = lo;
+    r.hi = hi;
+    r.u0 = r.u1 = r.u2 = 0;
+    if (lo <= hi) {
+        r.u0 = (int)(base[0] + (long long)st[0] * lo);
+        r.u1 = (int)(base[1] + (long long)st[1] * lo);
+        r.u2 = (int)(base[2] + (long long)st[2] * lo);
+    }
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory histogram policies
+// ---------------------------------------------------------------------------
+
+// 32-bit counters: one shared atomic per voxel (or per group of equal keys in a warp).
+template <bool MATCH>
+struct HistU32 {
+    uint32_t *h;
+    int B2;
+    __device__ void zero() {
+        for (int c = threadIdx.x; c < B2; c += blockDim.x) h[c] = 0;
+    }
+    __device__ __forceinline__ void add(int key, bool valid) {
+        if (!MATCH) {
+            if (valid) atomicAdd(&h[key], 1u);
+        } else {
+            const unsigned vm = __ballot_sync(kFull, valid);
+            if (valid) {
+                const unsigned peers = __match_any_sync(vm, key);
+                if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[key], (unsigned)__popc(peers));
+            }
+        }
+    }
+    __device__ __forceinline__ uint32_t count(int c) const { return h[c]; }
+};
+
+// 16-bit counters packed two per word.  A counter whose value reaches
+// kDrainT is drained whole into a shared hash table of 32-bit overflow
+// counts by a compare-and-swap; the adder that observed it does the drain,
+// so a counter never exceeds kDrainT + (threads x 32) < 2^16.  The true
+// count is the 16-bit value plus the overflow entry (flagged in a bitmap).
+template <bool MATCH>
+struct HistU16 {
+    uint32_t *w;      // (B2 + 1) / 2 words
+    uint32_t *okey;   // kOvfSlots keys
+    uint32_t *ocnt;   // kOvfSlots counts
+    uint32_t *bmap;   // (B2 + 31) / 32 words
+    int *flags;
+    int B2;
+    __device__ void zero() {
+        const int nw = (B2 + 1) >> 1, nb = (B2 + 31) >> 5;
+        for (int c = threadIdx.x; c < nw; c += blockDim.x) w[c] = 0;
+        for (int c = threadIdx.x; c < kOvfSlots; c += blockDim.x) {
+            okey[c] = kEmptyKey;
+            ocnt[c] = 0;
+        }
+        for (int c = threadIdx.x; c < nb; c += blockDim.x) bmap[c] = 0;
+    }
+    __device__ __forceinline__ static uint32_t slot_of(uint32_t key) { return (key * 2654435761u) >> 20; }
+    __device__ void ovf_add(uint32_t key, uint32_t amount) {
+        uint32_t s = slot_of(key) & (kOvfSlots - 1);
+        for (int probe = 0; probe < kOvfSlots; ++probe) {
+            const uint32_t k = ((volatile uint32_t *)okey)[s];
+            if (k == key) {
+                atomicAdd(&ocnt[s], amount);
+                return;
+            }
+            if (k == kEmptyKey) {
+                const uint32_t prev = atomicCAS(&okey[s], kEmptyKey, key);
+                if (prev == kEmptyKey || prev == key) {
+                    atomicAdd(&ocnt[s], amount);
+                    if (prev == kEmptyKey) atomicOr(&bmap[key >> 5], 1u << (key & 31));
+                    return;
+                }
+            }
+            s = (s + 1) & (kOvfSlots - 1);
+        }
+        atomicOr(&flags[1], 1);  // cannot happen while N <= kOvfSlots / 2 * kDrainT
+    }
+    __device__ void drain(uint32_t key) {
+        const uint32_t idx = key >> 1, sh = (key & 1) << 4;
+        volatile uint32_t *vw = w;
+        // each failed attempt means another update of this word succeeded; bounded for safety
+        for (int it = 0; it < 1 << 16; ++it) {
+            const uint32_t cur = vw[idx];
+            const uint32_t hv = (cur >> sh) & 0xffffu;
+            if (hv < (uint32_t)kDrainT) return;
+            if (atomicCAS(&w[idx], cur, cur - (hv << sh)) == cur) {
+                ovf_add(key, hv);
+                return;
+            }
+        }
+        atomicOr(&flags[1], 2);
+    }
+    __device__ __forceinline__ void inc(int key, uint32_t n) {
+        const uint32_t sh = (key & 1) << 4;
+        const uint32_t old = atomicAdd(&w[key >> 1], n << sh);
+        if (((old >> sh) & 0xffffu) + n >= (uint32_t)kDrainT) drain((uint32_t)key);
+    }
+    __device__ __forceinline__ void add(int key, bool valid) {
+        if (!MATCH) {
+            if (valid) inc(key, 1u);
+        } else {
+            const unsigned vm = __ballot_sync(kFull, valid);
+            if (valid) {
+                const unsigned peers = __match_any_sync(vm, key);
+                if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) inc(key, (unsigned)__popc(peers));
+            }
+        }
+    }
+    __device__ __forceinline__ uint32_t count(int c) const {
+        uint32_t v = (w[c >> 1] >> ((c & 1) << 4)) & 0xffffu;
+        if (bmap[c >> 5] & (1u << (c & 31))) {
+            uint32_t s = slot_of((uint32_t)c) & (kOvfSlots - 1);
+            for (int probe = 0; probe < kOvfSlots; ++probe) {
+                const uint32_t k = okey[s];
+                if (k == (uint32_t)c) return v + ocnt[s];
+                if (k == kEmptyKey) break;
+                s = (s + 1) & (kOvfSlots - 1);
+            }
+        }
+        return v;
+    }
+};
+
+// Global 32-bit histogram (plain path's entropy reduction).
+struct HistGlobal {
+    const uint32_t *h;
+    __device__ __forceinline__ uint32_t count(int c) const { return __ldg(h + c); }
+};
+
+// Shared-memory layout of a CTA: [histogram words][ovf keys][ovf counts][bitmap] [rows][cols] [FP64 scratch].
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct SmemLayout {
+    size_t hist, okey, ocnt, bmap, rows, cols, red, total;
+};
+
+__host__ __device__ inline SmemLayout smem_layout(int variant, int bins, int threads) {
+    SmemLayout L;
+    const size_t B2 = (size_t)bins * bins;
+    const bool u16 = variant == HV_U16 || variant == HV_U16_MATCH;
+    size_t o = 0;
+    L.hist = o;
+    o += u16 ? ((B2 + 1) / 2) * 4 : B2 * 4;
+    L.okey = o;
+    if (u16) o += (size_t)kOvfSlots * 4;
+    L.ocnt = o;
+    if (u16) o += (size_t)kOvfSlots * 4;
+    L.bmap = o;
+    if (u16) o += ((B2 + 31) / 32) * 4;
+    L.rows = o;
+    o += (size_t)bins * 4;
+    L.cols = o;
+    o += (size_t)bins * 4;
+    o = align_up(o, 16);
+    L.red = o;
+    o += (size_t)(3 * 32 + 3 * kMaxQ + 1) * 8;
+    L.total = o;
+    return L;
+}
+
+template <int HV>
+struct HistOf;
+template <>
+struct HistOf<HV_U32> { using T = HistU32<false>; };
+template <>
+struct HistOf<HV_U32_MATCH> { using T = HistU32<true>; };
+template <>
+struct HistOf<HV_U16> { using T = HistU16<false>; };
+template <>
+struct HistOf<HV_U16_MATCH> { using T = HistU16<true>; };
+
+template <int HV>
+__device__ typename HistOf<HV>::T make_hist(unsigned char *smem, const SmemLayout &L, int B2, int *flags) {
+    typename HistOf<HV>::T H;
+    H.B2 = B2;
+    if constexpr (HV == HV_U16 || HV == HV_U16_MATCH) {
+        H.w = (uint32_t *)(smem + L.hist);
+        H.okey = (uint32_t *)(smem + L.okey);
+        H.ocnt = (uint32_t *)(smem + L.ocnt);
+        H.bmap = (uint32_t *)(smem + L.bmap);
+        H.flags = flags;
+    } else {
+        H.h = (uint32_t *)(smem + L.hist);
+    }
+    return H;
+}
+
+// ---------------------------------------------------------------------------
+// Voxel loop: warps take batches of 32 fixed rows; lane l clips row rb + l,
+// then the warp walks the 32 clipped rows 32 voxels at a time.
+// ---------------------------------------------------------------------------
+
+template <typename MovT, class Hist>
+__device__ void accumulate_rows(const PairDev &P, const int *q, long long first_batch, long long batch_stride,
+                                Hist &H) {
+    const int lane = threadIdx.x & 31;
+    const int nf0 = P.nf[0], nf1 = P.nf[1];
+    const long long R = (long long)nf1 * P.nf[2];
+    const int n0 = P.nm[0], n1 = P.nm[1], n2 = P.nm[2];
+    const int st0 = q[0], st1 = q[4], st2 = q[8];
+    const int bins = P.bins, mdepth = P.mdepth;
+    const MovT *__restrict__ mov = (const MovT *)P.mov;
+    for (long long rb = first_batch * 32; rb < R; rb += batch_stride * 32) {
+        RowClip mine;
+        mine.lo = 0;
+        mine.hi = -1;
+        mine.u0 = mine.u1 = mine.u2 = 0;
+        const long long r = rb + lane;
+        if (r < R) mine = clip_row(q, (int)(r % nf1), (int)(r / nf1), nf0, P.nm);
+        for (int s = 0; s < 32; ++s) {
+            const int lo = __shfl_sync(kFull, mine.lo, s), hi = __shfl_sync(kFull, mine.hi, s);
+            if (lo > hi) continue;  // warp-uniform
+            const int U0 = __shfl_sync(kFull, mine.u0, s), U1 = __shfl_sync(kFull, mine.u1, s),
+                      U2 = __shfl_sync(kFull, mine.u2, s);
+            const uint8_t *__restrict__ frow = P.fbins + (size_t)(rb + s) * nf0;
+            for (int i0 = lo; i0 <= hi; i0 += 32) {
+                const int i = i0 + lane;
+                const bool valid = i <= hi;
+                int key = 0;
+                if (valid) {
+                    const int d = i - lo;
+                    const int v = sample_hard<MovT>(mov, n0, n1, n2, U0 + st0 * d, U1 + st1 * d, U2 + st2 * d);
+                    const int bm = (v * bins) >> mdepth;
+                    key = (int)__ldg(frow + i) * bins + bm;
+                }
+                H.add(key, valid);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Entropy reduction of one histogram by one CTA (Eq. 1, Eq. 2, Tsallis)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double term(uint32_t v, int iq, const QSet &Q) {
+    if (v < (uint32_t)kTab) return __ldg(Q.tab[iq] + v);
+    const double d = (double)v;
+    return Q.q[iq] == 1.0f ? d * log(d) : pow(d, (double)Q.q[iq]);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Block-wide FP64 sum of three values; every thread gets the results.
+__device__ __forceinline__ void block_sum3(double &a, double &b, double &c, double *s_red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    c = warp_sum(c);
+    __syncthreads();
+    if (lane == 0) {
+        s_red[3 * warp + 0] = a;
+        s_red[3 * warp + 1] = b;
+        s_red[3 * warp + 2] = c;
+    }
+    __syncthreads();
+    a = b = c = 0.0;
+    for (int w = 0; w < nwarps; ++w) {
+        a += s_red[3 * w + 0];
+        b += s_red[3 * w + 1];
+        c += s_red[3 * w + 2];
+    }
+}
+
+// Entropies of one histogram by one CTA.  Pass 1: marginals (row sums by
+// warps, column sums by shared atomics) and N.  Then one pass per q over the
+// non-zero cells and the marginals, with one FP64 accumulator triple live at a
+// time: sum c ln c (q == 1) or sum c^q (count-indexed tables for c < kTab).
+template <class Hist>
+__device__ void reduce_entropies(const Hist &H, int B, const QSet &Q, uint32_t *s_rows, uint32_t *s_cols,
+                                 double *s_red, long long t, const Outputs &O) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int nq = Q.nq;
+    double *s_res = s_red + 3 * 32;  // 3 nq + 1 results after the per-warp scratch
+    for (int c = tid; c < B; c += blockDim.x) s_cols[c] = 0;
+    __syncthreads();
+    for (int r = warp; r < B; r += nwarps) {
+        uint32_t rsum = 0;
+        for (int c = lane; c < B; c += 32) {
+            const uint32_t v = H.count(r * B + c);
+            if (v) {
+                rsum += v;
+                atomicAdd(&s_cols[c], v);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rsum += __shfl_xor_sync(kFull, rsum, o);
+        if (lane == 0) s_rows[r] = rsum;
+    }
+    __syncthreads();
+    {
+        double n0 = 0.0, z1 = 0.0, z2 = 0.0;
+        for (int r = tid; r < B; r += blockDim.x) n0 += (double)s_rows[r];
+        block_sum3(n0, z1, z2, s_red);
+        if (tid == 0) s_res[3 * kMaxQ] = n0;
+    }
+    const int B2 = B * B;
+    for (int iq = 0; iq < nq; ++iq) {
+        double aj = 0.0, af = 0.0, am = 0.0;
+        for (int c = tid; c < B2; c += blockDim.x) {
+            const uint32_t v = H.count(c);
+            if (v) aj += term(v, iq, Q);
+        }
+        for (int r = tid; r < B; r += blockDim.x) {
+            const uint32_t vf = s_rows[r], vm = s_cols[r];
+            if (vf) af += term(vf, iq, Q);
+            if (vm) am += term(vm, iq, Q);
+        }
+        block_sum3(af, am, aj, s_red);
+        if (tid == 0) {
+            s_res[3 * iq + 0] = af;
+            s_res[3 * iq + 1] = am;
+            s_res[3 * iq + 2] = aj;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const double N = s_res[3 * kMaxQ];
+        if (O.count) O.count[t] = (long long)N;
+        if (N <= 0.0 && O.flags) atomicOr(&O.flags[0], 1);
+        for (int iq = 0; iq < nq; ++iq) {
+            const float qf = Q.q[iq];
+            const double SF = s_res[3 * iq + 0], SM = s_res[3 * iq + 1], SJ = s_res[3 * iq + 2];
+            double hf, hm, hj;
+            if (N <= 0.0) {
+                hf = hm = hj = __longlong_as_double(0x7ff8000000000000ll);
+            } else if (qf == 1.0f) {
+                const double lnN = log(N);
+                hf = lnN - SF / N;
+                hm = lnN - SM / N;
+                hj = lnN - SJ / N;
+                if (Q.bits) {
+                    const double l2 = log(2.0);
+                    hf /= l2;
+                    hm /= l2;
+                    hj /= l2;
+                }
+            } else {
+                const double q = (double)qf, Nq = pow(N, -q);
+                hf = (1.0 - Nq * SF) / (q - 1.0);
+                hm = (1.0 - Nq * SM) / (q - 1.0);
+                hj = (1.0 - Nq * SJ) / (q - 1.0);
+            }
+            double I = hf + hm - hj;
+            if (qf != 1.0f && Q.form == 1) I += (1.0 - (double)qf) * hf * hm;
+            if (O.mi) O.mi[t * nq + iq] = I;
+            if (O.h) {
+                O.h[(t * nq + iq) * 3 + 0] = hf;
+                O.h[(t * nq + iq) * 3 + 1] = hm;
+                O.h[(t * nq + iq) * 3 + 2] = hj;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Plain form
+// ---------------------------------------------------------------------------
+
+template <typename MovT, int HV>
+__global__ void __launch_bounds__(1024, 1)
+    k_hist(const PairDev *__restrict__ pairs, const int32_t *__restrict__ aff, uint32_t *__restrict__ ghist,
+           int *flags) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const PairDev P = pairs[0];
+    const int t = blockIdx.y;
+    const int B2 = P.bins * P.bins;
+    const SmemLayout L = smem_layout(HV, P.bins, blockDim.x);
+    __shared__ int q[12];
+    if (threadIdx.x < 12) q[threadIdx.x] = aff[(size_t)t * 12 + threadIdx.x];
+    auto H = make_hist<HV>(smem, L, B2, flags);
+    H.zero();
+    __syncthreads();
+    const int nwarps = blockDim.x >> 5;
+    accumulate_rows<MovT>(P, q, (long long)blockIdx.x * nwarps + (threadIdx.x >> 5), (long long)gridDim.x * nwarps,
+                          H);
+    __syncthreads();
+    uint32_t *gh = ghist + (size_t)t * B2;
+    for (int c = threadIdx.x; c < B2; c += blockDim.x) {
+        const uint32_t v = H.count(c);
+        if (v) atomicAdd(gh + c, v);
+    }
+}
+
+// Shared memory of k_entropy: [rows B u32][cols B u32][FP64 scratch, 16-byte aligned].
+__host__ __device__ inline size_t entropy_red_offset(int B) { return align_up((size_t)B * 8, 16); }
+__host__ __device__ inline size_t entropy_smem_bytes(int B, int threads) {
+    return entropy_red_offset(B) + (size_t)(3 * 32 + 3 * kMaxQ + 1) * 8;
+}
+
+__global__ void __launch_bounds__(1024, 1)
+    k_entropy(const uint32_t *__restrict__ ghist, int B, QSet Q, Outputs O) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const long long t = blockIdx.x;
+    HistGlobal H{ghist + (size_t)t * B * B};
+    reduce_entropies(H, B, Q, (uint32_t *)smem, (uint32_t *)(smem + (size_t)B * 4),
+                     (double *)(smem + entropy_red_offset(B)), t, O);
+}
+
+// ---------------------------------------------------------------------------
+// Batched form: persistent CTAs, one (pair, transform) item per CTA at a time
+// ---------------------------------------------------------------------------
+
+template <int HV>
+__global__ void __launch_bounds__(1024, 1)
+    k_batched(const PairDev *__restrict__ pairs, const int32_t *__restrict__ aff, const Item *__restrict__ items,
+              int nitems, int *ticket, int max_bins, QSet Q, Outputs O) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_item;
+    __shared__ int q[12];
+    const SmemLayout L = smem_layout(HV, max_bins, blockDim.x);
+    const int nwarps = blockDim.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) break;
+        const Item I = items[it];
+        const PairDev P = pairs[I.pair];
+        const int B2 = P.bins * P.bins;
+        if (threadIdx.x < 12) q[threadIdx.x] = aff[(size_t)I.t * 12 + threadIdx.x];
+        auto H = make_hist<HV>(smem, L, B2, O.flags);
+        H.zero();
+        __syncthreads();
+        if (P.mdtype == 0)
+            accumulate_rows<uint8_t>(P, q, threadIdx.x >> 5, nwarps, H);
+        else
+            accumulate_rows<uint16_t>(P, q, threadIdx.x >> 5, nwarps, H);
+        __syncthreads();
+        if (O.dump) {
+            uint32_t *dh = O.dump + (size_t)I.t * B2;
+            for (int c = threadIdx.x; c < B2; c += blockDim.x) dh[c] = H.count(c);
+        }
+        reduce_entropies(H, P.bins, Q, (uint32_t *)(smem + L.rows), (uint32_t *)(smem + L.cols),
+                         (double *)(smem + L.red), I.t, O);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Resampling v(T(x)) on the fixed grid
+// ---------------------------------------------------------------------------
+
+template <typename MovT>
+__global__ void k_resample(const PairDev *__restrict__ pairs, const int32_t *__restrict__ aff, MovT *__restrict__ out) {
+    const PairDev P = pairs[0];
+    const long long n = (long long)P.nf[0] * P.nf[1] * P.nf[2];
+    int q[12];
+#pragma unroll
+    for (int e = 0; e < 12; ++e) q[e] = aff[e];
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x) {
+        const long long i = x % P.nf[0], j = (x / P.nf[0]) % P.nf[1], k = x / ((long long)P.nf[0] * P.nf[1]);
+        long long U[3];
+        bool in = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            U[a] = (long long)q[4 * a] * i + (long long)q[4 * a + 1] * j + (long long)q[4 * a + 2] * k + q[4 * a + 3];
+            in = in && U[a] >= 0 && U[a] <= ((long long)(P.nm[a] - 1) << 16);
+        }
+        out[x] = in ? (MovT)sample_hard<MovT>((const MovT *)P.mov, P.nm[0], P.nm[1], P.nm[2], (int)U[0], (int)U[1],
+                                               (int)U[2])
+                    : (MovT)0;
+    }
+}
+
+inline int grid_for(long long n, int threads) {
+    long long g = (n + threads - 1) / threads;
+    return (int)(g < 1 ? 1 : (g > 65535 * 8 ? 65535 * 8 : g));
+}
+
+template <class K>
+cudaError_t set_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+size_t hard_smem_bytes(int variant, int bins, int threads) { return smem_layout(variant, bins, threads).total; }
+
+cudaError_t launch_f32_to_u16(const float *in, long long n, uint16_t *out, cudaStream_t s) {
+    k_f32_to_u16<<<grid_for(n, 256), 256, 0, s>>>(in, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clamp_depth(void *data, int dtype, int depth, long long n, cudaStream_t s) {
+    const uint32_t vmax = (uint32_t)((1ull << depth) - 1ull);
+    if (dtype == 0) {
+        if (depth >= 8) return cudaSuccess;
+        k_clamp_depth<uint8_t><<<grid_for(n, 256), 256, 0, s>>>((uint8_t *)data, n, vmax);
+    } else {
+        if (depth >= 16) return cudaSuccess;
+        k_clamp_depth<uint16_t><<<grid_for(n, 256), 256, 0, s>>>((uint16_t *)data, n, vmax);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_fixed(const void *data, int dtype, int depth, long long n, int bins, uint8_t *out,
+                             cudaStream_t s) {
+    if (dtype == 0)
+        k_bin_fixed<uint8_t><<<grid_for(n, 256), 256, 0, s>>>((const uint8_t *)data, n, depth, bins, out);
+    else
+        k_bin_fixed<uint16_t><<<grid_for(n, 256), 256, 0, s>>>((const uint16_t *)data, n, depth, bins, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_table(double *tab, float q, cudaStream_t s) {
+    k_table<<<kTab / 256, 256, 0, s>>>(tab, q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plain_hist(const PairDev *d_pair, const PairDev &h_pair, const int32_t *d_aff, int n,
+                              uint32_t *d_hist, int variant, int threads, int ctas, int *d_flags, cudaStream_t s) {
+    const size_t B2 = (size_t)h_pair.bins * h_pair.bins;
+    cudaError_t e = cudaMemsetAsync(d_hist, 0, (size_t)n * B2 * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    const size_t smem = smem_layout(variant, h_pair.bins, threads).total;
+    dim3 grid(ctas, n);
+#define MI_LAUNCH_PLAIN(MT, HVV)                                                         \
+    do {                                                                                 \
+        auto kf = k_hist<MT, HVV>;                                                       \
+        if ((e = set_smem(kf, smem)) != cudaSuccess) return e;                           \
+        kf<<<grid, threads, smem, s>>>(d_pair, d_aff, d_hist, d_flags);                  \
+    } while (0)
+#define MI_LAUNCH_PLAIN_MT(HVV)                          \
+    do {                                                 \
+        if (h_pair.mdtype == 0) MI_LAUNCH_PLAIN(uint8_t, HVV); \
+        else MI_LAUNCH_PLAIN(uint16_t, HVV);             \
+    } while (0)
+    switch (variant) {
+        case HV_U32: MI_LAUNCH_PLAIN_MT(HV_U32); break;
+        case HV_U32_MATCH: MI_LAUNCH_PLAIN_MT(HV_U32_MATCH); break;
+        case HV_U16: MI_LAUNCH_PLAIN_MT(HV_U16); break;
+        default: MI_LAUNCH_PLAIN_MT(HV_U16_MATCH); break;
+    }
+#undef MI_LAUNCH_PLAIN_MT
+#undef MI_LAUNCH_PLAIN
+    return cudaGetLastError();
+}
+
+cudaError_t launch_entropy(const uint32_t *d_hist, int n, int bins, const QSet &Q, const Outputs &O, cudaStream_t s) {
+    const int threads = 1024;
+    const size_t smem = entropy_smem_bytes(bins, threads);
+    cudaError_t e = set_smem(k_entropy, smem);
+    if (e != cudaSuccess) return e;
+    k_entropy<<<n, threads, smem, s>>>(d_hist, bins, Q, O);
+    return cudaGetLastError();
+}
+
+static const void *batched_fn(int variant) {
+    switch (variant) {
+        case HV_U32: return (const void *)k_batched<HV_U32>;
+        case HV_U32_MATCH: return (const void *)k_batched<HV_U32_MATCH>;
+        case HV_U16: return (const void *)k_batched<HV_U16>;
+        default: return (const void *)k_batched<HV_U16_MATCH>;
+    }
+}
+
+int batched_ctas_per_sm(int variant, int max_bins, int threads) {
+    const size_t smem = smem_layout(variant, max_bins, threads).total;
+    const void *fn = batched_fn(variant);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess) return 0;
+    return nb;
+}
+
+cudaError_t launch_batched(const PairDev *d_pairs, const int32_t *d_aff, const Item *d_items, int nitems,
+                           int *d_ticket, int max_bins, int variant, int threads, int ctas, const QSet &Q,
+                           const Outputs &O, cudaStream_t s) {
+    const size_t smem = smem_layout(variant, max_bins, threads).total;
+    const void *fn = batched_fn(variant);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    switch (variant) {
+        case HV_U32:
+            k_batched<HV_U32><<<ctas, threads, smem, s>>>(d_pairs, d_aff, d_items, nitems, d_ticket, max_bins, Q, O);
+            break;
+        case HV_U32_MATCH:
+            k_batched<HV_U32_MATCH><<<ctas, threads, smem, s>>>(d_pairs, d_aff, d_items, nitems, d_ticket, max_bins, Q,
+                                                                O);
+            break;
+        case HV_U16:
+            k_batched<HV_U16><<<ctas, threads, smem, s>>>(d_pairs, d_aff, d_items, nitems, d_ticket, max_bins, Q, O);
+            break;
+        default:
+            k_batched<HV_U16_MATCH><<<ctas, threads, smem, s>>>(d_pairs, d_aff, d_items, nitems, d_ticket, max_bins, Q,
+                                                                O);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resample(const PairDev *d_pair, const PairDev &h_pair, const int32_t *d_aff, void *out,
+                            cudaStream_t s) {
+    const long long n = (long long)h_pair.nf[0] * h_pair.nf[1] * h_pair.nf[2];
+    if (h_pair.mdtype == 0)
+        k_resample<uint8_t><<<grid_for(n, 256), 256, 0, s>>>(d_pair, d_aff, (uint8_t *)out);
+    else
+        k_resample<uint16_t><<<grid_for(n, 256), 256, 0, s>>>(d_pair, d_aff, (uint16_t *)out);
+    return cudaGetLastError();
+}
+
+}  // namespace mi

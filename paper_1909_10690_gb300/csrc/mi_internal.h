@@ -1,0 +1,109 @@
+// mi_internal.h -- types and launchers shared by the library's CUDA sources.
+// Not installed; the public boundary is include/mi.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mi {
+
+constexpr int kMaxQ = 8;
+constexpr int kTab = 65536;        // count-indexed FP64 tables cover counts < kTab
+constexpr int kDrainT = 1 << 14;   // 16-bit counters are drained once they reach 2^14
+constexpr int kOvfSlots = 4096;    // drain table entries (each entry holds >= kDrainT counts)
+
+// One volume pair as the hard-path kernels see it.
+struct PairDev {
+    const uint8_t *fbins;  // fixed volume pre-binned to uint8, x fastest
+    const void *mov;       // moving volume, uint8 or uint16, clamped to its bit depth
+    int nf[3];             // fixed dims (x, y, z)
+    int nm[3];             // moving dims
+    int bins;
+    int mdepth;            // moving bit depth
+    int mdtype;            // 0 = uint8, 1 = uint16
+    int pad;
+};
+
+// q values of one call with their count-indexed FP64 tables
+// tab[i][c] = c ln c (q == 1) or c^q (q != 1), c < kTab.
+struct QSet {
+    int nq;
+    int form;   // 0 additive, 1 pseudo-additive Tsallis MI
+    int bits;   // Shannon in bits
+    int pad;
+    float q[kMaxQ];
+    const double *tab[kMaxQ];
+};
+
+// Per-transform outputs (device pointers; any may be null).
+struct Outputs {
+    double *mi;          // n x nq
+    double *h;           // n x nq x 3
+    long long *count;    // n
+    uint32_t *dump;      // n x bins^2 histograms (test hook), single-pair only
+    int *flags;          // [0] empty overlap seen, [1] drain table overflow
+};
+
+// Work item of the batched kernel.
+struct Item {
+    int pair;
+    int t;   // transform index (row of the affine array and of the outputs)
+};
+
+// Histogram variants (match the public MI_HV_* values).
+enum { HV_U32 = 0, HV_U32_MATCH = 1, HV_U16 = 2, HV_U16_MATCH = 3 };
+
+// Shared memory needed by a hard-path CTA of `threads` threads for `bins` bins.
+size_t hard_smem_bytes(int variant, int bins, int threads);
+
+// ---- launchers (all asynchronous on `s`) ---------------------------------
+cudaError_t launch_f32_to_u16(const float *in, long long n, uint16_t *out, cudaStream_t s);
+cudaError_t launch_clamp_depth(void *data, int dtype, int depth, long long n, cudaStream_t s);
+cudaError_t launch_bin_fixed(const void *data, int dtype, int depth, long long n, int bins, uint8_t *out,
+                             cudaStream_t s);
+cudaError_t launch_table(double *tab, float q, cudaStream_t s);
+// Plain path: n transforms, grid (ctas, n); histograms in global memory (n x bins^2 u32, zeroed here).
+cudaError_t launch_plain_hist(const PairDev *d_pair, const PairDev &h_pair, const int32_t *d_aff, int n,
+                              uint32_t *d_hist, int variant, int threads, int ctas, int *d_flags, cudaStream_t s);
+cudaError_t launch_entropy(const uint32_t *d_hist, int n, int bins, const QSet &Q, const Outputs &O,
+                           cudaStream_t s);
+// Batched path: persistent CTAs pull items from *d_ticket (reset by the caller).
+cudaError_t launch_batched(const PairDev *d_pairs, const int32_t *d_aff, const Item *d_items, int nitems,
+                           int *d_ticket, int max_bins, int variant, int threads, int ctas, const QSet &Q,
+                           const Outputs &O, cudaStream_t s);
+int batched_ctas_per_sm(int variant, int max_bins, int threads);
+cudaError_t launch_resample(const PairDev *d_pair, const PairDev &h_pair, const int32_t *d_aff, void *out,
+                            cudaStream_t s);
+
+// ---- Parzen (differentiable) path ----------------------------------------
+struct ParzenPair {
+    const uint8_t *fbins;   // Parzen fixed bins floor(f (B-4)) + 2
+    const float *mov;       // normalised moving intensities in [0, 1]
+    int nf[3];
+    int nm[3];
+    int B;
+    int pad;
+};
+
+struct ParzenAffine {       // per transform, FP32 copy of the FP64 host affine [A | b]
+    float A[12];
+};
+
+cudaError_t launch_parzen_prep_fixed(const void *data, int dtype, int depth, long long n, int B, uint8_t *out,
+                                     cudaStream_t s);
+cudaError_t launch_parzen_prep_moving(const void *data, int dtype, int depth, long long n, float *out,
+                                      cudaStream_t s);
+// Soft histograms (n x B^2 FP64, zeroed here) and overlap counts (n).
+cudaError_t launch_parzen_hist(const ParzenPair &P, const ParzenAffine *d_aff, int n, double *d_hist,
+                               unsigned long long *d_count, cudaStream_t s);
+// MI per q (n x nq) and the weight tables W (n x nq x B^2, FP32) from the soft histograms.
+// Scratch: marg (n x 2B), ment (n x nq x 2), jsum (n x nq) FP64.
+cudaError_t launch_parzen_weights(const double *d_hist, const unsigned long long *d_count, int n, int B,
+                                  const QSet &Q, double *marg, double *ment, double *jsum, double *d_mi, float *d_w,
+                                  cudaStream_t s);
+// Gradient moments (scratch n x nq x 12) and dMI/dtheta (n x nq x 9 FP64); d_jac is n x 12 x 9 FP64.
+cudaError_t launch_parzen_adjoint(const ParzenPair &P, const ParzenAffine *d_aff, const double *d_jac, int n, int nq,
+                                  const float *d_w, const unsigned long long *d_count, double *d_mom,
+                                  double *d_grad, cudaStream_t s);
+
+}  // namespace mi

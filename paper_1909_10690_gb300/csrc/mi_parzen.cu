@@ -1,0 +1,507 @@
+// mi_parzen.cu -- differentiable (Parzen-window) mutual information on sm_103a.
+//
+// Soft joint histogram: each overlap voxel adds beta0 (one bin) along the
+// fixed axis and a cubic B-spline beta3 centred at m~ = m (B - 4) + 2 along
+// the moving axis, m the FP32 trilinear value of the normalised moving volume
+// at the real moving index u = A i + b.  Shannon MI (Eq. 1-2) and Tsallis MI
+// follow from the normalised histogram P in FP64.  The gradient of MI with
+// respect to the 9 transform parameters (the optimiser's input, Eq. 3 and
+// the gradient-descent loop of the Introduction) is the adjoint:
+//   dMI/dtheta = -(B-4)/N sum_x s(x) grad m(u_x) . du_x/dtheta,
+//   s(x) = sum_k W(fb(x), k) beta3'(k - m~_x),   W = dMI/dP,
+// with N and the overlap held fixed.  du/dtheta = J [i j k 1]^T is linear in
+// the voxel index, so each thread accumulates the 12 moments
+// sum s grad_a m * (i, j, k, 1) per q and the host Jacobian J (12 x 9)
+// contracts them at the end.
+//
+// Kernels: k_pfix / k_pmov (once per context), k_parzen_hist (forward),
+// k_parzen_marg + k_parzen_cells + k_parzen_final (FP64 entropies and W),
+// k_parzen_adj + k_parzen_grad (adjoint).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "mi_internal.h"
+
+namespace mi {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+inline int grid_for(long long n, int threads) {
+    long long g = (n + threads - 1) / threads;
+    return (int)(g < 1 ? 1 : (g > 65535 * 8 ? 65535 * 8 : g));
+}
+
+// Fixed bin floor(f (B - 4)) + 2: exact integer quotient for integer volumes.
+template <typename T>
+__global__ void k_pfix_int(const T *__restrict__ in, long long n, int depth, int B, uint8_t *__restrict__ out) {
+    const unsigned long long vmax = (1ull << depth) - 1ull;
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x) {
+        unsigned long long v = in[x];
+        v = v > vmax ? vmax : v;
+        out[x] = (uint8_t)((v * (unsigned long long)(B - 4)) / vmax + 2ull);
+    }
+}
+
+__global__ void k_pfix_f32(const float *__restrict__ in, long long n, int B, uint8_t *__restrict__ out) {
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x) {
+        double f = (double)in[x];
+        if (!(f == f)) f = 0.0;
+        f = f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
+        out[x] = (uint8_t)((int)floor(f * (double)(B - 4)) + 2);
+    }
+}
+
+// Normalised moving intensity: v / (2^d - 1) (rounded once to FP32), floats clamped to [0, 1].
+template <typename T>
+__global__ void k_pmov_int(const T *__restrict__ in, long long n, int depth, float *__restrict__ out) {
+    const double vmax = (double)((1ull << depth) - 1ull);
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x) {
+        double v = (double)in[x];
+        out[x] = (float)(v > vmax ? 1.0 : v / vmax);
+    }
+}
+
+__global__ void k_pmov_f32(const float *__restrict__ in, long long n, float *__restrict__ out) {
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x) {
+        float v = in[x];
+        if (!(v == v)) v = 0.0f;
+        out[x] = fminf(fmaxf(v, 0.0f), 1.0f);
+    }
+}
+
+// FP32 trilinear value and gradient (w.r.t. the moving index) at u inside
+// [0, n-1]^3; cell c = min(floor(u), n - 2), weight u - c.
+struct MG {
+    float m, gx, gy, gz;
+};
+
+template <bool GRAD>
+__device__ __forceinline__ MG trilinear(const float *__restrict__ mov, int n0, int n1, int n2, float ux, float uy,
+                                        float uz) {
+    const int cx = min((int)ux, n0 - 2), cy = min((int)uy, n1 - 2), cz = min((int)uz, n2 - 2);
+    const float wx = ux - (float)cx, wy = uy - (float)cy, wz = uz - (float)cz;
+    const int sy = n0, sz = n0 * n1;
+    const float *p = mov + (cx + n0 * (cy + n1 * cz));
+    const float v000 = __ldg(p), v001 = __ldg(p + 1), v010 = __ldg(p + sy), v011 = __ldg(p + sy + 1);
+    const float v100 = __ldg(p + sz), v101 = __ldg(p + sz + 1), v110 = __ldg(p + sz + sy), v111 = __ldg(p + sz + sy + 1);
+    const float d00 = v001 - v000, d01 = v011 - v010, d10 = v101 - v100, d11 = v111 - v110;
+    const float a00 = fmaf(wx, d00, v000), a01 = fmaf(wx, d01, v010);
+    const float a10 = fmaf(wx, d10, v100), a11 = fmaf(wx, d11, v110);
+    const float b0 = fmaf(wy, a01 - a00, a00), b1 = fmaf(wy, a11 - a10, a10);
+    MG r;
+    r.m = fmaf(wz, b1 - b0, b0);
+    if (GRAD) {
+        r.gz = b1 - b0;
+        const float y0 = a01 - a00, y1 = a11 - a10;
+        r.gy = fmaf(wz, y1 - y0, y0);
+        const float e0 = fmaf(wy, d01 - d00, d00), e1 = fmaf(wy, d11 - d10, d10);
+        r.gx = fmaf(wz, e1 - e0, e0);
+    } else {
+        r.gx = r.gy = r.gz = 0.0f;
+    }
+    return r;
+}
+
+// Cubic B-spline weights of the four bins k0-1 .. k0+2 around m~ = k0 + t.
+__device__ __forceinline__ void bspline_w(float t, float w[4]) {
+    const float s = 1.0f - t, t2 = t * t, t3 = t2 * t, s3 = s * s * s;
+    w[0] = s3 * (1.0f / 6.0f);
+    w[1] = fmaf(0.5f, t3, 2.0f / 3.0f - t2);
+    w[2] = fmaf(0.5f, s3, 2.0f / 3.0f - s * s);
+    w[3] = t3 * (1.0f / 6.0f);
+}
+
+// beta3'(k - m~) for the same four bins.
+__device__ __forceinline__ void bspline_dw(float t, float d[4]) {
+    const float s = 1.0f - t;
+    d[0] = 0.5f * s * s;
+    d[1] = t * fmaf(-1.5f, t, 2.0f);
+    d[2] = s * fmaf(1.5f, s, -2.0f);
+    d[3] = -0.5f * t * t;
+}
+
+__device__ __forceinline__ bool inside_u(float ux, float uy, float uz, int n0, int n1, int n2) {
+    return ux >= 0.0f && uy >= 0.0f && uz >= 0.0f && ux <= (float)(n0 - 1) && uy <= (float)(n1 - 1) &&
+           uz <= (float)(n2 - 1);
+}
+
+// ---------------------------------------------------------------------------
+// Forward: soft histogram (unnormalised sums of weights) and overlap count
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256)
+    k_parzen_hist(ParzenPair P, const ParzenAffine *__restrict__ aff, double *__restrict__ ghist,
+                  unsigned long long *__restrict__ gcount) {
+    extern __shared__ float sh[];
+    const int t = blockIdx.y, B = P.B, B2 = B * B;
+    __shared__ float A[12];
+    if (threadIdx.x < 12) A[threadIdx.x] = aff[t].A[threadIdx.x];
+    for (int c = threadIdx.x; c < B2; c += blockDim.x) sh[c] = 0.0f;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int nf0 = P.nf[0], nf1 = P.nf[1];
+    const int n0 = P.nm[0], n1 = P.nm[1], n2 = P.nm[2];
+    const long long R = (long long)nf1 * P.nf[2];
+    const float Bm4 = (float)(B - 4);
+    unsigned int cnt = 0;
+    for (long long r = (long long)blockIdx.x * nwarps + warp; r < R; r += (long long)gridDim.x * nwarps) {
+        const float j = (float)(r % nf1), k = (float)(r / nf1);
+        const float b0 = fmaf(A[1], j, fmaf(A[2], k, A[3]));
+        const float b1 = fmaf(A[5], j, fmaf(A[6], k, A[7]));
+        const float b2 = fmaf(A[9], j, fmaf(A[10], k, A[11]));
+        const uint8_t *__restrict__ frow = P.fbins + (size_t)r * nf0;
+        for (int i = lane; i < nf0; i += 32) {
+            const float fi = (float)i;
+            const float ux = fmaf(A[0], fi, b0), uy = fmaf(A[4], fi, b1), uz = fmaf(A[8], fi, b2);
+            if (!inside_u(ux, uy, uz, n0, n1, n2)) continue;
+            ++cnt;
+            const MG g = trilinear<false>(P.mov, n0, n1, n2, ux, uy, uz);
+            const float mt = fmaf(fminf(fmaxf(g.m, 0.0f), 1.0f), Bm4, 2.0f);
+            const int k0 = (int)mt;
+            float w[4];
+            bspline_w(mt - (float)k0, w);
+            float *row = sh + (int)__ldg(frow + i) * B + (k0 - 1);
+            atomicAdd(row + 0, w[0]);
+            atomicAdd(row + 1, w[1]);
+            atomicAdd(row + 2, w[2]);
+            if (k0 + 2 < B) atomicAdd(row + 3, w[3]);
+        }
+    }
+    __syncthreads();
+    double *gh = ghist + (size_t)t * B2;
+    for (int c = threadIdx.x; c < B2; c += blockDim.x) {
+        const float v = sh[c];
+        if (v != 0.0f) atomicAdd(gh + c, (double)v);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
+    if (lane == 0 && cnt) atomicAdd(gcount + t, (unsigned long long)cnt);
+}
+
+// ---------------------------------------------------------------------------
+// Entropies and W = dMI/dP in FP64
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// block-wide sum of one double (all threads get the result); s_tmp holds >= 32 doubles
+__device__ double block_sum(double v, double *s_tmp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) s_tmp[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < nwarps; ++w) s += s_tmp[w];
+    return s;
+}
+
+// Entropy contribution of one probability p > 0 for exponent q.
+__device__ __forceinline__ double ent_term(double p, float qf) {
+    return qf == 1.0f ? -p * log(p) : pow(p, (double)qf);
+}
+
+__device__ __forceinline__ double finish_entropy(double sum, float qf, int bits) {
+    if (qf == 1.0f) return bits ? sum / log(2.0) : sum;
+    return (1.0 - sum) / ((double)qf - 1.0);
+}
+
+// One CTA per transform: marginals P_F (rows), P_M (cols) and their entropies per q.
+// marg: n x 2B (P_F then P_M); ment: n x nq x 2 (S_F, S_M).
+__global__ void k_parzen_marg(const double *__restrict__ ghist, const unsigned long long *__restrict__ gcount, int B,
+                              QSet Q, double *__restrict__ marg, double *__restrict__ ment) {
+    __shared__ double s_tmp[32];
+    const int t = blockIdx.x;
+    const double N = (double)gcount[t];
+    const double *h = ghist + (size_t)t * B * B;
+    double *pf = marg + (size_t)t * 2 * B, *pm = pf + B;
+    for (int r = threadIdx.x; r < B; r += blockDim.x) {
+        double sr = 0.0, sc = 0.0;
+        for (int c = 0; c < B; ++c) {
+            sr += h[(size_t)r * B + c];
+            sc += h[(size_t)c * B + r];
+        }
+        pf[r] = N > 0 ? sr / N : 0.0;
+        pm[r] = N > 0 ? sc / N : 0.0;
+    }
+    __syncthreads();
+    for (int iq = 0; iq < Q.nq; ++iq) {
+        double a = 0.0, b = 0.0;
+        for (int r = threadIdx.x; r < B; r += blockDim.x) {
+            if (pf[r] > 0.0) a += ent_term(pf[r], Q.q[iq]);
+            if (pm[r] > 0.0) b += ent_term(pm[r], Q.q[iq]);
+        }
+        a = block_sum(a, s_tmp);
+        b = block_sum(b, s_tmp);
+        if (threadIdx.x == 0) {
+            ment[((size_t)t * Q.nq + iq) * 2 + 0] = finish_entropy(a, Q.q[iq], Q.bits);
+            ment[((size_t)t * Q.nq + iq) * 2 + 1] = finish_entropy(b, Q.q[iq], Q.bits);
+        }
+    }
+}
+
+// Grid (cells / 256, n): joint entropy sums (jsum: n x nq) and W (n x nq x B^2, FP32).
+__global__ void __launch_bounds__(256)
+    k_parzen_cells(const double *__restrict__ ghist, const unsigned long long *__restrict__ gcount, int B, QSet Q,
+                   const double *__restrict__ marg, const double *__restrict__ ment, double *__restrict__ jsum,
+                   float *__restrict__ wout) {
+    __shared__ double s_tmp[32];
+    const int t = blockIdx.y, B2 = B * B;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const double N = (double)gcount[t];
+    const double lnb = Q.bits ? log(2.0) : 1.0;
+    double p = 0.0, pfr = 0.0, pmc = 0.0;
+    if (c < B2 && N > 0) {
+        p = ghist[(size_t)t * B2 + c] / N;
+        pfr = marg[(size_t)t * 2 * B + c / B];
+        pmc = marg[(size_t)t * 2 * B + B + c % B];
+    }
+    for (int iq = 0; iq < Q.nq; ++iq) {
+        const float qf = Q.q[iq];
+        double e = p > 0.0 ? ent_term(p, qf) : 0.0;
+        e = block_sum(e, s_tmp);
+        if (threadIdx.x == 0) atomicAdd(jsum + (size_t)t * Q.nq + iq, e);
+        if (c < B2) {
+            double w = 0.0;
+            if (p > 0.0) {
+                if (qf == 1.0f) {
+                    w = (log(p) - log(pfr) - log(pmc) - 1.0) / lnb;
+                } else {
+                    const double q = (double)qf;
+                    const double dSF = -q * pow(pfr, q - 1.0) / (q - 1.0);
+                    const double dSM = -q * pow(pmc, q - 1.0) / (q - 1.0);
+                    const double dSJ = -q * pow(p, q - 1.0) / (q - 1.0);
+                    w = dSF + dSM - dSJ;
+                    if (Q.form == 1) {
+                        const double SF = ment[((size_t)t * Q.nq + iq) * 2 + 0];
+                        const double SM = ment[((size_t)t * Q.nq + iq) * 2 + 1];
+                        w += (1.0 - q) * (dSF * SM + SF * dSM);
+                    }
+                }
+            }
+            wout[((size_t)t * Q.nq + iq) * B2 + c] = (float)w;
+        }
+    }
+}
+
+// MI per q: S_F + S_M - S_FM (+ (1 - q) S_F S_M for the pseudo-additive form).
+__global__ void k_parzen_final(int n, const unsigned long long *__restrict__ gcount, QSet Q,
+                               const double *__restrict__ ment, const double *__restrict__ jsum, double *__restrict__ mi) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n * Q.nq) return;
+    const int t = x / Q.nq, iq = x % Q.nq;
+    if (gcount[t] == 0) {
+        mi[x] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
+    const float qf = Q.q[iq];
+    const double SF = ment[(size_t)x * 2 + 0], SM = ment[(size_t)x * 2 + 1];
+    const double SJ = finish_entropy(jsum[x], qf, Q.bits);
+    double I = SF + SM - SJ;
+    if (qf != 1.0f && Q.form == 1) I += (1.0 - (double)qf) * SF * SM;
+    mi[x] = I;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint: moments M[q][a][c] = sum_x s_q(x) d_a m(u_x) x_c, x = (i, j, k, 1)
+// ---------------------------------------------------------------------------
+
+template <int NQ>
+__global__ void __launch_bounds__(256)
+    k_parzen_adj(ParzenPair P, const ParzenAffine *__restrict__ aff, int nq_total, int q0,
+                 const float *__restrict__ wtab, int w_in_smem, double *__restrict__ mom) {
+    extern __shared__ float sw[];  // NQ x B^2 weights when they fit
+    const int t = blockIdx.y, B = P.B, B2 = B * B;
+    __shared__ float A[12];
+    __shared__ float s_red[8][NQ * 12];
+    if (threadIdx.x < 12) A[threadIdx.x] = aff[t].A[threadIdx.x];
+    const float *W = wtab + ((size_t)t * nq_total + q0) * B2;
+    if (w_in_smem) {
+        for (int c = threadIdx.x; c < NQ * B2; c += blockDim.x) sw[c] = W[c];
+        W = sw;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int nf0 = P.nf[0], nf1 = P.nf[1];
+    const int n0 = P.nm[0], n1 = P.nm[1], n2 = P.nm[2];
+    const long long R = (long long)nf1 * P.nf[2];
+    const float Bm4 = (float)(B - 4);
+    float M[NQ][12];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int e = 0; e < 12; ++e) M[q][e] = 0.0f;
+    for (long long r = (long long)blockIdx.x * nwarps + warp; r < R; r += (long long)gridDim.x * nwarps) {
+        const float j = (float)(r % nf1), k = (float)(r / nf1);
+        const float b0 = fmaf(A[1], j, fmaf(A[2], k, A[3]));
+        const float b1 = fmaf(A[5], j, fmaf(A[6], k, A[7]));
+        const float b2 = fmaf(A[9], j, fmaf(A[10], k, A[11]));
+        const uint8_t *__restrict__ frow = P.fbins + (size_t)r * nf0;
+        for (int i = lane; i < nf0; i += 32) {
+            const float fi = (float)i;
+            const float ux = fmaf(A[0], fi, b0), uy = fmaf(A[4], fi, b1), uz = fmaf(A[8], fi, b2);
+            if (!inside_u(ux, uy, uz, n0, n1, n2)) continue;
+            const MG g = trilinear<true>(P.mov, n0, n1, n2, ux, uy, uz);
+            const float mt = fmaf(fminf(fmaxf(g.m, 0.0f), 1.0f), Bm4, 2.0f);
+            const int k0 = (int)mt;
+            float d[4];
+            bspline_dw(mt - (float)k0, d);
+            if (k0 + 2 >= B) d[3] = 0.0f;
+            const int base = (int)__ldg(frow + i) * B + (k0 - 1);
+            const int i3 = k0 + 2 < B ? base + 3 : base;  // in range; weight 0 when clamped
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const float *Wq = W + (size_t)q * B2;
+                const float s = Wq[base] * d[0] + Wq[base + 1] * d[1] + Wq[base + 2] * d[2] + Wq[i3] * d[3];
+                const float sx = s * g.gx, sy = s * g.gy, sz = s * g.gz;
+                M[q][0] = fmaf(sx, fi, M[q][0]);
+                M[q][1] = fmaf(sx, j, M[q][1]);
+                M[q][2] = fmaf(sx, k, M[q][2]);
+                M[q][3] += sx;
+                M[q][4] = fmaf(sy, fi, M[q][4]);
+                M[q][5] = fmaf(sy, j, M[q][5]);
+                M[q][6] = fmaf(sy, k, M[q][6]);
+                M[q][7] += sy;
+                M[q][8] = fmaf(sz, fi, M[q][8]);
+                M[q][9] = fmaf(sz, j, M[q][9]);
+                M[q][10] = fmaf(sz, k, M[q][10]);
+                M[q][11] += sz;
+            }
+        }
+    }
+    // warp reduction in FP32, then the 8 warps in FP64 into global memory
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int e = 0; e < 12; ++e) {
+            float v = M[q][e];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+            if (lane == 0) s_red[warp][q * 12 + e] = v;
+        }
+    __syncthreads();
+    if (threadIdx.x < NQ * 12) {
+        double s = 0.0;
+        for (int w = 0; w < nwarps; ++w) s += (double)s_red[w][threadIdx.x];
+        atomicAdd(mom + ((size_t)t * nq_total + q0) * 12 + threadIdx.x, s);
+    }
+}
+
+// grad[t][q][p] = -(B - 4) / N sum_e mom[t][q][e] J[t][e][p]
+__global__ void k_parzen_grad(int n, int nq, int B, const unsigned long long *__restrict__ gcount,
+                              const double *__restrict__ mom, const double *__restrict__ jac, double *__restrict__ grad) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n * nq * 9) return;
+    const int p = x % 9, tq = x / 9, t = tq / nq;
+    const double N = (double)gcount[t];
+    if (N <= 0) {
+        grad[x] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
+    double s = 0.0;
+    for (int e = 0; e < 12; ++e) s += mom[(size_t)tq * 12 + e] * jac[((size_t)t * 12 + e) * 9 + p];
+    grad[x] = -(double)(B - 4) / N * s;
+}
+
+}  // namespace
+
+cudaError_t launch_parzen_prep_fixed(const void *data, int dtype, int depth, long long n, int B, uint8_t *out,
+                                     cudaStream_t s) {
+    if (dtype == 0)
+        k_pfix_int<uint8_t><<<grid_for(n, 256), 256, 0, s>>>((const uint8_t *)data, n, depth, B, out);
+    else if (dtype == 1)
+        k_pfix_int<uint16_t><<<grid_for(n, 256), 256, 0, s>>>((const uint16_t *)data, n, depth, B, out);
+    else
+        k_pfix_f32<<<grid_for(n, 256), 256, 0, s>>>((const float *)data, n, B, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_parzen_prep_moving(const void *data, int dtype, int depth, long long n, float *out, cudaStream_t s) {
+    if (dtype == 0)
+        k_pmov_int<uint8_t><<<grid_for(n, 256), 256, 0, s>>>((const uint8_t *)data, n, depth, out);
+    else if (dtype == 1)
+        k_pmov_int<uint16_t><<<grid_for(n, 256), 256, 0, s>>>((const uint16_t *)data, n, depth, out);
+    else
+        k_pmov_f32<<<grid_for(n, 256), 256, 0, s>>>((const float *)data, n, out);
+    return cudaGetLastError();
+}
+
+static int parzen_ctas(const ParzenPair &P, int n) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long rows = (long long)P.nf[1] * P.nf[2];
+    // about 4 CTAs per SM over all transforms, at least one row batch of 8 warps each
+    long long per_t = (4LL * sms + n - 1) / n;
+    long long max_rows = (rows + 7) / 8;
+    if (per_t > max_rows) per_t = max_rows;
+    if (per_t < 1) per_t = 1;
+    return (int)per_t;
+}
+
+cudaError_t launch_parzen_hist(const ParzenPair &P, const ParzenAffine *d_aff, int n, double *d_hist,
+                               unsigned long long *d_count, cudaStream_t s) {
+    const size_t B2 = (size_t)P.B * P.B;
+    cudaError_t e = cudaMemsetAsync(d_hist, 0, (size_t)n * B2 * sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(d_count, 0, (size_t)n * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    const size_t smem = B2 * sizeof(float);
+    if ((e = cudaFuncSetAttribute(k_parzen_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return e;
+    dim3 grid(parzen_ctas(P, n), n);
+    k_parzen_hist<<<grid, 256, smem, s>>>(P, d_aff, d_hist, d_count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_parzen_weights(const double *d_hist, const unsigned long long *d_count, int n, int B, const QSet &Q,
+                                  double *marg, double *ment, double *jsum, double *d_mi, float *d_w, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(jsum, 0, (size_t)n * Q.nq * sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    k_parzen_marg<<<n, 256, 0, s>>>(d_hist, d_count, B, Q, marg, ment);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    dim3 grid((B * B + 255) / 256, n);
+    k_parzen_cells<<<grid, 256, 0, s>>>(d_hist, d_count, B, Q, marg, ment, jsum, d_w);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_parzen_final<<<(n * Q.nq + 127) / 128, 128, 0, s>>>(n, d_count, Q, ment, jsum, d_mi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_parzen_adjoint(const ParzenPair &P, const ParzenAffine *d_aff, const double *d_jac, int n, int nq,
+                                  const float *d_w, const unsigned long long *d_count, double *d_mom, double *d_grad,
+                                  cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(d_mom, 0, (size_t)n * nq * 12 * sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    const size_t B2 = (size_t)P.B * P.B;
+    dim3 grid(parzen_ctas(P, n), n);
+    for (int q0 = 0; q0 < nq; q0 += 4) {
+        const int g = nq - q0 < 4 ? nq - q0 : 4;
+        const size_t wbytes = (size_t)g * B2 * sizeof(float);
+        const int in_smem = wbytes <= 96 * 1024;
+        const size_t smem = in_smem ? wbytes : 0;
+#define MI_ADJ(NQV)                                                                                         \
+    do {                                                                                                    \
+        if ((e = cudaFuncSetAttribute(k_parzen_adj<NQV>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                                      (int)smem)) != cudaSuccess)                                           \
+            return e;                                                                                       \
+        k_parzen_adj<NQV><<<grid, 256, smem, s>>>(P, d_aff, nq, q0, d_w, in_smem, d_mom);                   \
+    } while (0)
+        switch (g) {
+            case 1: MI_ADJ(1); break;
+            case 2: MI_ADJ(2); break;
+            case 3: MI_ADJ(3); break;
+            default: MI_ADJ(4); break;
+        }
+#undef MI_ADJ
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    k_parzen_grad<<<(n * nq * 9 + 127) / 128, 128, 0, s>>>(n, nq, P.B, d_count, d_mom, d_jac, d_grad);
+    return cudaGetLastError();
+}
+
+}  // namespace mi

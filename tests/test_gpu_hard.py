@@ -1,0 +1,290 @@
+"""GPU parity of the hard-binned path against the CPU oracle.
+
+Joint histograms must match bit for bit; MI and entropies within
+|d| <= 1e-6 max(|MI|, H_FM) (both sides sum exact counts in FP64, so the
+observed gap is summation order, ~1e-13).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_10690_gb300 import phantoms
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-6
+VARIANTS = [0, 1, 2, 3]
+IDENT = np.array([65536, 0, 0, 0, 0, 65536, 0, 0, 0, 0, 65536, 0], dtype=np.int32)
+
+
+def assert_mi_close(mi_gpu, mi_ref, h_ref):
+    scale = np.maximum(np.abs(mi_ref), h_ref[..., 2])
+    bad = np.abs(mi_gpu - mi_ref) > TOL * scale
+    assert not np.any(bad), (mi_gpu[bad], mi_ref[bad])
+
+
+def random_q16(shape_f, shape_m, n, seed, t=4.0, r=15.0, s=(0.9, 1.1)):
+    prm = phantoms.random_transforms(n, seed=seed, t_mm=t, r_deg=r, s_range=s)
+    return prm, np.stack([oracle.affine_q16(oracle.affine(p, shape_f, (1, 1, 1), shape_m, (1, 1, 1))) for p in prm])
+
+
+@pytest.fixture(scope="module")
+def tiny_pair():
+    return phantoms.ellipsoid_pair(shape=(64, 64, 64), seed=1)
+
+
+def test_fixed_bins_and_resample_bit_exact(cuda_lib):
+    f, m = phantoms.head_pair(shape=(33, 45, 67), spacing=(1, 1, 1), seed=3)
+    ctx = cuda_lib.Context(f, m, bins=37, fixed_depth=12, moving_depth=12)
+    np.testing.assert_array_equal(ctx.fixed_bins(), oracle.bin_volume(f, 37, 12))
+    _, q16 = random_q16(f.shape, m.shape, 4, seed=4)
+    for q in q16:
+        np.testing.assert_array_equal(ctx.resample(q, np.uint16), oracle.resample(m, q, f.shape, depth=12))
+
+
+def test_affine_builder_matches_oracle_bit_for_bit(cuda_lib):
+    f = np.zeros((20, 24, 30), np.uint16)
+    m = np.zeros((22, 28, 26), np.uint16)
+    sf, sm = (1.0, 0.875, 1.25), (1.125, 1.0, 1.375)
+    ctx = cuda_lib.Context(f, m, bins=16, fixed_spacing=sf, moving_spacing=sm)
+    prm = phantoms.random_transforms(2000, seed=5, t_mm=30, r_deg=180, s_range=(0.5, 1.5))
+    a, q, j = ctx.affine(prm)
+    for t in range(len(prm)):
+        ao, jo = oracle.affine(prm[t], f.shape, sf, m.shape, sm, with_jacobian=True)
+        np.testing.assert_array_equal(a[t], ao)
+        np.testing.assert_array_equal(q[t], oracle.affine_q16(ao))
+        np.testing.assert_allclose(j[t], jo, rtol=1e-12, atol=1e-12)
+
+
+def test_hand_enumerated_cases_on_gpu(cuda_lib):
+    cases = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hand_4x4x4.json")))["cases"]
+    z, y, x = np.meshgrid(np.arange(4), np.arange(4), np.arange(4), indexing="ij")
+    vols = {"ramp_x": (64 * x).astype(np.uint8), "ramp_y": (64 * y).astype(np.uint8)}
+    for c in cases:
+        ctx = cuda_lib.Context(vols[c["fixed"]], vols[c["moving"]], bins=4)
+        want = np.zeros((4, 4), np.uint32)
+        for r, cc, v in c["hist"]:
+            want[r, cc] = v
+        for path in (cuda_lib.PATH_PLAIN, cuda_lib.PATH_BATCHED):
+            h = ctx.hist(affines=np.array(c["q16"], np.int32), path=path)
+            np.testing.assert_array_equal(h[0], want, err_msg=c["name"])
+        qs = [float(k) for k in c["mi"]]
+        mi = ctx.eval_q16(np.array(c["q16"], np.int32), qs)
+        np.testing.assert_allclose(mi[0], [c["mi"][k] for k in c["mi"]], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("path", ["plain", "batched"])
+def test_tiny_workload_histograms_and_mi(cuda_lib, tiny_pair, variant, path):
+    f, m = tiny_pair
+    prm = phantoms.tiny_sweep()
+    ctx = cuda_lib.Context(f, m, bins=32, hist_variant=variant, path=path)
+    qs = [1.0, 0.5, 1.5]
+    mi, h, cnt = ctx.eval(prm, qs, with_entropies=True)
+    mi_o, h_o, cnt_o = oracle.mi_eval(f, m, 32, prm, qs, nthreads=8)
+    np.testing.assert_array_equal(cnt, cnt_o)
+    assert_mi_close(mi, mi_o, h_o)
+    np.testing.assert_allclose(h, h_o, rtol=1e-9, atol=1e-12)
+    H = ctx.hist(transforms=prm, path=cuda_lib.PATH_PLAIN if path == "plain" else cuda_lib.PATH_BATCHED)
+    for t in range(len(prm)):
+        q16 = oracle.affine_q16(oracle.affine(prm[t], f.shape, (1, 1, 1), m.shape, (1, 1, 1)))
+        ho, n = oracle.joint_hist(f, m, q16, 32)
+        np.testing.assert_array_equal(H[t], ho.astype(np.uint32))
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("bins", [2, 37, 64, 128, 256])
+def test_ragged_sizes_all_variants(cuda_lib, variant, bins):
+    # odd dims spanning several row batches and a ragged tail, 12-bit data, random 9-parameter transforms
+    f, m = phantoms.head_pair(shape=(29, 41, 75), spacing=(1, 1, 1), seed=6)
+    m = np.ascontiguousarray(m[:, :37, :71])
+    if bins > 181 and variant in (0, 1):
+        pytest.skip("32-bit counters do not fit shared memory at this bin count")
+    prm, q16 = random_q16(f.shape, m.shape, 40, seed=bins)
+    for path in (cuda_lib.PATH_PLAIN, cuda_lib.PATH_BATCHED):
+        ctx = cuda_lib.Context(f, m, bins=bins, fixed_depth=12, moving_depth=12, hist_variant=variant)
+        H = ctx.hist(affines=q16, path=path)
+        for t in range(0, len(q16), 3):
+            ho, _ = oracle.joint_hist(f, m, q16[t], bins, 12, 12)
+            np.testing.assert_array_equal(H[t], ho.astype(np.uint32))
+    mi, h, cnt = ctx.eval_q16(q16, [1.0, 2.0], with_entropies=True)
+    mi_o, h_o, cnt_o = oracle.mi_eval_q16(f, m, bins, q16, [1.0, 2.0], 12, 12, nthreads=8)
+    np.testing.assert_array_equal(cnt, cnt_o)
+    assert_mi_close(mi, mi_o, h_o)
+
+
+@pytest.mark.parametrize("variant", [2, 3])
+def test_u16_counter_drains_exact(cuda_lib, variant):
+    # a large uniform background makes the (0, 0) cell pass 2^14 many times inside one CTA
+    f = np.zeros((64, 96, 100), np.uint16)
+    m = np.zeros((64, 96, 100), np.uint16)
+    f[20:40, 30:60, 30:70] = 3000
+    m[22:42, 30:60, 28:68] = 1000
+    ctx = cuda_lib.Context(f, m, bins=256, fixed_depth=12, moving_depth=12, hist_variant=variant)
+    _, q16 = random_q16(f.shape, m.shape, 6, seed=7, t=2, r=5, s=(0.95, 1.05))
+    q16 = np.concatenate([IDENT[None], q16.reshape(-1, 12)])
+    for path in (cuda_lib.PATH_PLAIN, cuda_lib.PATH_BATCHED):
+        H = ctx.hist(affines=q16, path=path)
+        for t in range(len(q16)):
+            ho, _ = oracle.joint_hist(f, m, q16[t], 256, 12, 12)
+            np.testing.assert_array_equal(H[t], ho.astype(np.uint32))
+    assert H[0, 0, 0] > 10 * 2 ** 14
+
+
+def test_edge_cases(cuda_lib):
+    f, m = phantoms.ellipsoid_pair(shape=(16, 18, 20), seed=8)
+    ctx = cuda_lib.Context(f, m, bins=16)
+    # n = 0 is a no-op
+    assert ctx.eval(np.zeros((0, 9), np.float32), [1.0]).shape == (0, 1)
+    # empty overlap: NaN for that transform, the others still evaluated, status MI_EEMPTY
+    prm = phantoms.identity_params(3)
+    prm[1, 0] = 1000.0
+    with pytest.raises(cuda_lib.MIError) as ei:
+        ctx.eval(prm, [1.0, 2.0], allow_empty=False)
+    assert ei.value.status == cuda_lib.MI_EEMPTY
+    mi, h, cnt = ctx.eval(prm, [1.0, 2.0], with_entropies=True)
+    assert cnt[1] == 0 and np.all(np.isnan(mi[1])) and np.all(np.isfinite(mi[[0, 2]]))
+    # identity on u = v: MI = H(F) exactly (up to summation order)
+    ctx2 = cuda_lib.Context(f, f, bins=16)
+    mi, h, cnt = ctx2.eval(phantoms.identity_params(1), [1.0, 0.5, 2.0], with_entropies=True)
+    np.testing.assert_allclose(mi[0], h[0, :, 0], rtol=1e-12)
+    assert cnt[0] == f.size
+    # invalid arguments
+    for bad_q in ([0.0], [-1.0], [1.0000001], [float("nan")], [1.0] * 9):
+        with pytest.raises(cuda_lib.MIError) as ei:
+            ctx.eval(prm, bad_q)
+        assert ei.value.status == cuda_lib.MI_EINVAL
+    bad = phantoms.identity_params(1)
+    bad[0, 3] = np.nan
+    with pytest.raises(cuda_lib.MIError):
+        ctx.eval(bad, [1.0])
+    huge = phantoms.identity_params(1)
+    huge[0, 6] = 1e6
+    with pytest.raises(cuda_lib.MIError) as ei:
+        ctx.eval(huge, [1.0])
+    assert ei.value.status == cuda_lib.MI_ERANGE
+    with pytest.raises(cuda_lib.MIError):
+        cuda_lib.Context(f, m, bins=1)
+    with pytest.raises(cuda_lib.MIError):
+        cuda_lib.Context(f, m, bins=257)
+    with pytest.raises(cuda_lib.MIError):
+        cuda_lib.Context(f[:1], m, bins=16)
+
+
+def test_bit_depth_clamp_and_small_depth(cuda_lib):
+    rng = np.random.default_rng(9)
+    f = rng.integers(0, 64, (12, 13, 14), dtype=np.uint8)
+    m = rng.integers(0, 256, (12, 13, 14), dtype=np.uint8)  # values above 2^6 - 1 are clamped on load
+    ctx = cuda_lib.Context(f, m, bins=8, fixed_depth=6, moving_depth=6)
+    _, q16 = random_q16(f.shape, m.shape, 8, seed=10)
+    H = ctx.hist(affines=q16, path=cuda_lib.PATH_PLAIN)
+    for t in range(len(q16)):
+        ho, _ = oracle.joint_hist(f, m, q16[t], 8, 6, 6)
+        np.testing.assert_array_equal(H[t], ho.astype(np.uint32))
+
+
+def test_float_volumes_hard_path(cuda_lib):
+    f, m = phantoms.head_pair(shape=(20, 24, 28), spacing=(1, 1, 1), seed=11, dtype=np.float32)
+    ctx = cuda_lib.Context(f, m, bins=48)
+    prm = phantoms.random_transforms(10, seed=12, t_mm=3, r_deg=10, s_range=(0.95, 1.05))
+    mi, h, cnt = ctx.eval(prm, [1.0, 1.5], with_entropies=True)
+    mi_o, h_o, cnt_o = oracle.mi_eval(f, m, 48, prm, [1.0, 1.5], nthreads=8)
+    np.testing.assert_array_equal(cnt, cnt_o)
+    assert_mi_close(mi, mi_o, h_o)
+
+
+def test_options_bits_and_pseudo_additive(cuda_lib, tiny_pair):
+    f, m = tiny_pair
+    prm = phantoms.tiny_sweep()[:5]
+    for form, fname in ((0, "additive"), (1, "pseudo_additive")):
+        for bits in (False, True):
+            ctx = cuda_lib.Context(f, m, bins=32, tsallis_form=fname, bits=bits)
+            mi = ctx.eval(prm, [1.0, 0.5, 2.0])
+            mi_o, h_o, _ = oracle.mi_eval(f, m, 32, prm, [1.0, 0.5, 2.0], form=form, bits=bits)
+            assert_mi_close(mi, mi_o, h_o)
+
+
+def test_device_and_host_buffers_agree(cuda_lib, tiny_pair):
+    import torch
+
+    f, m = tiny_pair
+    prm = phantoms.random_transforms(200, seed=13, t_mm=5, r_deg=8)
+    ctx = cuda_lib.Context(torch.from_numpy(f).cuda(), torch.from_numpy(m).cuda(), bins=32)
+    a = ctx.eval(prm, [1.0, 1.5])
+    b = ctx.eval(torch.from_numpy(prm).cuda(), [1.0, 1.5])
+    assert b.is_cuda
+    np.testing.assert_array_equal(a, b.cpu().numpy())
+    s = torch.cuda.Stream()
+    ctx.set_stream(s)
+    c = ctx.eval(prm, [1.0, 1.5])
+    np.testing.assert_array_equal(a, c)
+
+
+def test_batched_equals_plain_and_graph_replay(cuda_lib, tiny_pair):
+    f, m = tiny_pair
+    prm = phantoms.random_transforms(400, seed=14, t_mm=6, r_deg=10)
+    qs = [0.5, 1.0, 1.5, 2.0]
+    plain = cuda_lib.Context(f, m, bins=32, path="plain").eval(prm, qs, with_entropies=True)
+    ctx = cuda_lib.Context(f, m, bins=32, path="batched")
+    for _ in range(3):  # capture, then two replays
+        got = ctx.eval(prm, qs, with_entropies=True)
+        np.testing.assert_array_equal(got[2], plain[2])
+        np.testing.assert_allclose(got[0], plain[0], rtol=1e-12, atol=1e-14)
+    prm2 = prm.copy()
+    prm2[:, 0] += 1.0  # same shapes, new values: the replayed graph must read them
+    got2 = ctx.eval(prm2, qs)
+    want2 = cuda_lib.Context(f, m, bins=32, path="plain").eval(prm2, qs)
+    np.testing.assert_allclose(got2, want2, rtol=1e-12, atol=1e-14)
+
+
+def test_uneven_batch_small(cuda_lib):
+    specs = [((40, 36, 50), np.uint8, 8, 32), ((30, 44, 38), np.uint16, 12, 64), ((50, 30, 33), np.uint8, 8, 128),
+             ((24, 52, 47), np.uint16, 12, 64), ((35, 35, 35), np.uint16, 12, 32)]
+    pairs = []
+    vols = []
+    for i, (shape, dt, depth, bins) in enumerate(specs):
+        f, m = phantoms.head_pair(shape=shape, spacing=(1, 1, 1), depth=depth, seed=20 + i, dtype=dt)
+        vols.append((f, m, depth, bins))
+        pairs.append(dict(fixed=f, moving=m, bins=bins, fixed_depth=depth, moving_depth=depth))
+    ctx = cuda_lib.Context(pairs=pairs)
+    n_per = 12
+    prm = phantoms.random_transforms(n_per * len(specs), seed=21, t_mm=4, r_deg=10, s_range=(0.9, 1.1))
+    pair_of = np.repeat(np.arange(len(specs), dtype=np.int32), n_per)
+    rng = np.random.default_rng(22)
+    perm = rng.permutation(len(prm))
+    prm, pair_of = prm[perm], pair_of[perm]
+    qs = [1.0, 0.5, 1.5]
+    mi, h, cnt = ctx.batch_eval(pair_of, prm, qs, with_entropies=True)
+    for p, (f, m, depth, bins) in enumerate(vols):
+        sel = np.nonzero(pair_of == p)[0]
+        mi_o, h_o, cnt_o = oracle.mi_eval(f, m, bins, prm[sel], qs, fixed_depth=depth, moving_depth=depth, nthreads=8)
+        np.testing.assert_array_equal(cnt[sel], cnt_o)
+        assert_mi_close(mi[sel], mi_o, h_o)
+        H = ctx.hist(transforms=prm[sel[:3]], pair=p, path=cuda_lib.PATH_BATCHED)
+        for k, t in enumerate(sel[:3]):
+            q16 = oracle.affine_q16(oracle.affine(prm[t], f.shape, (1, 1, 1), m.shape, (1, 1, 1)))
+            ho, _ = oracle.joint_hist(f, m, q16, bins, depth, depth)
+            np.testing.assert_array_equal(H[k], ho.astype(np.uint32))
+
+
+@pytest.mark.slow
+def test_full_size_batched_256_cubed_sampled(cuda_lib):
+    # the batched workload at full size (256^3 12-bit, 256 bins, 4096 transforms x 4 q) in the bench's
+    # launch configuration; sampled transforms are checked against the oracle one by one
+    f, m = phantoms.head_pair(shape=(256, 256, 256), spacing=(1, 1, 1), seed=30)
+    prm = phantoms.random_transforms(4096, seed=31)
+    qs = [0.5, 1.0, 1.5, 2.0]
+    ctx = cuda_lib.Context(f, m, bins=256, fixed_depth=12, moving_depth=12, path="batched")
+    mi, h, cnt = ctx.eval(prm, qs, with_entropies=True)
+    sample = np.array([0, 1, 777, 2048, 4095])
+    mi_o, h_o, cnt_o = oracle.mi_eval(f, m, 256, prm[sample], qs, fixed_depth=12, moving_depth=12, nthreads=16)
+    np.testing.assert_array_equal(cnt[sample], cnt_o)
+    assert_mi_close(mi[sample], mi_o, h_o)
+    H = ctx.hist(transforms=prm[sample[:2]], path=cuda_lib.PATH_BATCHED)
+    for k, t in enumerate(sample[:2]):
+        q16 = oracle.affine_q16(oracle.affine(prm[t], f.shape, (1, 1, 1), m.shape, (1, 1, 1)))
+        ho, _ = oracle.joint_hist(f, m, q16, 256, 12, 12)
+        np.testing.assert_array_equal(H[k], ho.astype(np.uint32))

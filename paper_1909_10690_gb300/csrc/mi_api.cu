@@ -655,11 +655,11 @@ mi_status run_plain(mi_ctx *ctx, int pair, const int32_t *d_aff, int n, const QS
 mi_status launch_batched_once(mi_ctx *ctx, int nitems, const QSet &Q, const Outputs &O, const Choice &ch,
                               bool record = false) {
     MI_CU(cudaMemsetAsync(ctx->d_ticket.p, 0, sizeof(int), ctx->stream), "resetting the work queue");
-    if (record) MI_CU(cudaEventRecord(ctx->ev0, ctx->stream), "event");
+    if (record) MI_CU(cudaEventRecordWithFlags(ctx->ev0, ctx->stream, cudaEventRecordExternal), "event");
     MI_CU(launch_batched(ctx->d_pairs.as<PairDev>(), ctx->d_aff.as<int32_t>(), ctx->d_items.as<Item>(), nitems,
                          ctx->d_ticket.as<int>(), ctx->max_bins, ch.variant, ch.threads, ch.ctas, Q, O, ctx->stream),
           "batched kernel");
-    if (record) MI_CU(cudaEventRecord(ctx->ev1, ctx->stream), "event");
+    if (record) MI_CU(cudaEventRecordWithFlags(ctx->ev1, ctx->stream, cudaEventRecordExternal), "event");
     return MI_OK;
 }
 
@@ -878,23 +878,23 @@ mi_status parzen_core(mi_ctx *ctx, const std::vector<float> &prm, int n, const f
     std::vector<double> jac((size_t)n * 108);
     for (int t = 0; t < n; ++t) {
         double aff[12];
-        build_affine(&prm[(size_t)t * 9], P.nf, P.sf, P.nm, P.sm, aff, &jac[(size_t)t * 108]);
-        for (int e = 0; e < 12; ++e) pa[t].A[e] = (float)aff[e];
+        double *J = &jac[(size_t)t * 108];
+        build_affine(&prm[(size_t)t * 9], P.nf, P.sf, P.nm, P.sm, aff, J);
+        for (int e = 0; e < 12; ++e) {
+            const double s = aff[e] * 4294967296.0;
+            if (!(fabs(s) < 4503599627370496.0))  // |x| < 2^20 keeps every int64 product below 2^63
+                return ctx->fail(MI_ERANGE, "transform " + std::to_string(t) + ": affine out of range");
+            pa[t].A[e] = llround(s);
+        }
+        // re-centre: u = A (i - c) + (A c + b), so the constant row becomes dA c + db
+        for (int a = 0; a < 3; ++a)
+            for (int p = 0; p < 9; ++p) {
+                double acc = J[9 * (4 * a + 3) + p];
+                for (int c = 0; c < 3; ++c) acc += J[9 * (4 * a + c) + p] * (0.5 * (double)(P.nf[c] - 1));
+                J[9 * (4 * a + 3) + p] = acc;
+            }
     }
     cudaStream_t s = ctx->stream;
-    MI_CU(ctx->p_aff.ensure((size_t)n * sizeof(ParzenAffine)), "alloc");
-    MI_CU(ctx->p_jac.ensure((size_t)n * 108 * 8), "alloc");
-    MI_CU(ctx->p_hist.ensure((size_t)n * B2 * 8), "alloc");
-    MI_CU(ctx->p_cnt.ensure((size_t)n * 8), "alloc");
-    MI_CU(ctx->p_marg.ensure((size_t)n * 2 * B * 8), "alloc");
-    MI_CU(ctx->p_ment.ensure((size_t)n * nq * 2 * 8), "alloc");
-    MI_CU(ctx->p_jsum.ensure((size_t)n * nq * 8), "alloc");
-    MI_CU(ctx->p_w.ensure((size_t)n * nq * B2 * 4), "alloc");
-    MI_CU(ctx->p_mom.ensure((size_t)n * nq * 12 * 8), "alloc");
-    MI_CU(ctx->p_grad.ensure((size_t)n * nq * 9 * 8), "alloc");
-    MI_CU(ctx->d_mi.ensure((size_t)n * nq * 8), "alloc");
-    MI_CU(cudaMemcpyAsync(ctx->p_aff.p, pa.data(), (size_t)n * sizeof(ParzenAffine), cudaMemcpyHostToDevice, s), "H2D");
-    MI_CU(cudaMemcpyAsync(ctx->p_jac.p, jac.data(), (size_t)n * 108 * 8, cudaMemcpyHostToDevice, s), "H2D");
     ParzenPair pp;
     memset(&pp, 0, sizeof pp);
     pp.fbins = P.pfbins.as<uint8_t>();
@@ -904,15 +904,31 @@ mi_status parzen_core(mi_ctx *ctx, const std::vector<float> &prm, int n, const f
         pp.nm[a] = P.nm[a];
     }
     pp.B = B;
+    const int ctas = parzen_ctas(pp, n, ctx->sms);
+    const int cblocks = parzen_cell_blocks(B);
+    MI_CU(ctx->p_aff.ensure((size_t)n * sizeof(ParzenAffine)), "alloc");
+    MI_CU(ctx->p_jac.ensure((size_t)n * 108 * 8), "alloc");
+    MI_CU(ctx->p_hist.ensure((size_t)n * B2 * 8), "alloc");
+    MI_CU(ctx->p_cnt.ensure((size_t)n * 8), "alloc");
+    MI_CU(ctx->p_marg.ensure((size_t)n * 2 * B * 8), "alloc");
+    MI_CU(ctx->p_ment.ensure((size_t)n * nq * 2 * 8), "alloc");
+    MI_CU(ctx->p_jsum.ensure((size_t)n * nq * cblocks * 8), "alloc");
+    MI_CU(ctx->p_w.ensure((size_t)n * nq * B2 * 4), "alloc");
+    MI_CU(ctx->p_mom.ensure((size_t)n * nq * ctas * 12 * 8), "alloc");
+    MI_CU(ctx->p_grad.ensure((size_t)n * nq * 9 * 8), "alloc");
+    MI_CU(ctx->d_mi.ensure((size_t)n * nq * 8), "alloc");
+    MI_CU(cudaMemcpyAsync(ctx->p_aff.p, pa.data(), (size_t)n * sizeof(ParzenAffine), cudaMemcpyHostToDevice, s), "H2D");
+    MI_CU(cudaMemcpyAsync(ctx->p_jac.p, jac.data(), (size_t)n * 108 * 8, cudaMemcpyHostToDevice, s), "H2D");
     const ParzenAffine *d_aff = ctx->p_aff.as<ParzenAffine>();
     auto *cnt = ctx->p_cnt.as<unsigned long long>();
+    auto *hist = ctx->p_hist.as<unsigned long long>();
     MI_CU(cudaEventRecord(ctx->ev0, s), "event");
-    MI_CU(launch_parzen_hist(pp, d_aff, n, ctx->p_hist.as<double>(), cnt, s), "Parzen histogram");
-    MI_CU(launch_parzen_weights(ctx->p_hist.as<double>(), cnt, n, B, Q, ctx->p_marg.as<double>(), ctx->p_ment.as<double>(),
+    MI_CU(launch_parzen_hist(pp, d_aff, n, ctas, hist, cnt, s), "Parzen histogram");
+    MI_CU(launch_parzen_weights(hist, cnt, n, B, Q, ctx->p_marg.as<double>(), ctx->p_ment.as<double>(),
                                 ctx->p_jsum.as<double>(), ctx->d_mi.as<double>(), ctx->p_w.as<float>(), s),
           "Parzen entropies");
     if (out_grad)
-        MI_CU(launch_parzen_adjoint(pp, d_aff, ctx->p_jac.as<double>(), n, nq, ctx->p_w.as<float>(), cnt,
+        MI_CU(launch_parzen_adjoint(pp, d_aff, ctx->p_jac.as<double>(), n, nq, ctas, ctx->p_w.as<float>(), cnt,
                                     ctx->p_mom.as<double>(), ctx->p_grad.as<double>(), s),
               "Parzen adjoint");
     MI_CU(cudaEventRecord(ctx->ev1, s), "event");

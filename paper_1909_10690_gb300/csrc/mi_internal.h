@@ -85,25 +85,29 @@ struct ParzenPair {
     int pad;
 };
 
-struct ParzenAffine {       // per transform, FP32 copy of the FP64 host affine [A | b]
-    float A[12];
-};
+struct ParzenAffine {       // per transform: the FP64 host affine [A | b] in 32.32 fixed point
+    long long A[12];        // llround(x * 2^32); exact integer positions, so the trilinear cell and
+};                          // overlap decisions match the FP64 definition except within ~1e-7 voxel
 
 cudaError_t launch_parzen_prep_fixed(const void *data, int dtype, int depth, long long n, int B, uint8_t *out,
                                      cudaStream_t s);
 cudaError_t launch_parzen_prep_moving(const void *data, int dtype, int depth, long long n, float *out,
                                       cudaStream_t s);
-// Soft histograms (n x B^2 FP64, zeroed here) and overlap counts (n).
-cudaError_t launch_parzen_hist(const ParzenPair &P, const ParzenAffine *d_aff, int n, double *d_hist,
-                               unsigned long long *d_count, cudaStream_t s);
+// CTAs per transform of the Parzen voxel kernels, and blocks of the per-cell kernel.
+int parzen_ctas(const ParzenPair &P, int n, int sms);
+int parzen_cell_blocks(int B);
+// Soft histograms (n x B^2 u64 sums of 2^-32-quantised weights, zeroed here) and overlap counts (n).
+cudaError_t launch_parzen_hist(const ParzenPair &P, const ParzenAffine *d_aff, int n, int ctas,
+                               unsigned long long *d_hist, unsigned long long *d_count, cudaStream_t s);
 // MI per q (n x nq) and the weight tables W (n x nq x B^2, FP32) from the soft histograms.
-// Scratch: marg (n x 2B), ment (n x nq x 2), jsum (n x nq) FP64.
-cudaError_t launch_parzen_weights(const double *d_hist, const unsigned long long *d_count, int n, int B,
-                                  const QSet &Q, double *marg, double *ment, double *jsum, double *d_mi, float *d_w,
+// Scratch: marg (n x 2B), ment (n x nq x 2), jpart (n x nq x parzen_cell_blocks(B)) FP64.
+cudaError_t launch_parzen_weights(const unsigned long long *d_hist, const unsigned long long *d_count, int n, int B,
+                                  const QSet &Q, double *marg, double *ment, double *jpart, double *d_mi, float *d_w,
                                   cudaStream_t s);
-// Gradient moments (scratch n x nq x 12) and dMI/dtheta (n x nq x 9 FP64); d_jac is n x 12 x 9 FP64.
+// Gradient: per-CTA moments (scratch n x nq x ctas x 12 FP64) and dMI/dtheta (n x nq x 9 FP64);
+// d_jac is n x 12 x 9 FP64 taken about the fixed-volume centre.
 cudaError_t launch_parzen_adjoint(const ParzenPair &P, const ParzenAffine *d_aff, const double *d_jac, int n, int nq,
-                                  const float *d_w, const unsigned long long *d_count, double *d_mom,
+                                  int ctas, const float *d_w, const unsigned long long *d_count, double *d_mom,
                                   double *d_grad, cudaStream_t s);
 
 }  // namespace mi

@@ -3,7 +3,10 @@
 // Soft joint histogram: each overlap voxel adds beta0 (one bin) along the
 // fixed axis and a cubic B-spline beta3 centred at m~ = m (B - 4) + 2 along
 // the moving axis, m the FP32 trilinear value of the normalised moving volume
-// at the real moving index u = A i + b.  Shannon MI (Eq. 1-2) and Tsallis MI
+// at the real moving index u = A i + b.  Positions are 32.32 fixed point
+// (int64) from the FP64 affine: the gradient jumps where a sample crosses a
+// trilinear cell boundary, so cell and overlap decisions are taken on
+// near-exact positions rather than FP32 ones.  Shannon MI (Eq. 1-2) and Tsallis MI
 // follow from the normalised histogram P in FP64.  The gradient of MI with
 // respect to the 9 transform parameters (the optimiser's input, Eq. 3 and
 // the gradient-descent loop of the Introduction) is the adjoint:
@@ -77,11 +80,18 @@ struct MG {
     float m, gx, gy, gz;
 };
 
+// Cell and weight of a 32.32 fixed-point coordinate U in [0, (n - 1) 2^32].
+__device__ __forceinline__ int cell_of(long long U, int n, float &w) {
+    const int c = min((int)(U >> 32), n - 2);
+    w = (float)(U - ((long long)c << 32)) * 2.3283064365386963e-10f;  // 2^-32
+    return c;
+}
+
 template <bool GRAD>
-__device__ __forceinline__ MG trilinear(const float *__restrict__ mov, int n0, int n1, int n2, float ux, float uy,
-                                        float uz) {
-    const int cx = min((int)ux, n0 - 2), cy = min((int)uy, n1 - 2), cz = min((int)uz, n2 - 2);
-    const float wx = ux - (float)cx, wy = uy - (float)cy, wz = uz - (float)cz;
+__device__ __forceinline__ MG trilinear(const float *__restrict__ mov, int n0, int n1, int n2, long long Ux,
+                                        long long Uy, long long Uz) {
+    float wx, wy, wz;
+    const int cx = cell_of(Ux, n0, wx), cy = cell_of(Uy, n1, wy), cz = cell_of(Uz, n2, wz);
     const int sy = n0, sz = n0 * n1;
     const float *p = mov + (cx + n0 * (cy + n1 * cz));
     const float v000 = __ldg(p), v001 = __ldg(p + 1), v010 = __ldg(p + sy), v011 = __ldg(p + sy + 1);
@@ -122,23 +132,27 @@ __device__ __forceinline__ void bspline_dw(float t, float d[4]) {
     d[3] = -0.5f * t * t;
 }
 
-__device__ __forceinline__ bool inside_u(float ux, float uy, float uz, int n0, int n1, int n2) {
-    return ux >= 0.0f && uy >= 0.0f && uz >= 0.0f && ux <= (float)(n0 - 1) && uy <= (float)(n1 - 1) &&
-           uz <= (float)(n2 - 1);
+__device__ __forceinline__ bool inside_u(long long Ux, long long Uy, long long Uz, int n0, int n1, int n2) {
+    return Ux >= 0 && Uy >= 0 && Uz >= 0 && Ux <= ((long long)(n0 - 1) << 32) && Uy <= ((long long)(n1 - 1) << 32) &&
+           Uz <= ((long long)(n2 - 1) << 32);
 }
 
 // ---------------------------------------------------------------------------
 // Forward: soft histogram (unnormalised sums of weights) and overlap count
 // ---------------------------------------------------------------------------
 
+// Weights are quantised to 2^-32 with the largest one absorbing the rounding
+// residue, so every voxel adds exactly 2^32 (the B-spline partition of unity)
+// and the 64-bit integer sums are exact and independent of the order of the
+// atomics: the soft histogram, MI and gradient are bitwise reproducible.
 __global__ void __launch_bounds__(256)
-    k_parzen_hist(ParzenPair P, const ParzenAffine *__restrict__ aff, double *__restrict__ ghist,
+    k_parzen_hist(ParzenPair P, const ParzenAffine *__restrict__ aff, unsigned long long *__restrict__ ghist,
                   unsigned long long *__restrict__ gcount) {
-    extern __shared__ float sh[];
+    extern __shared__ unsigned long long sh[];
     const int t = blockIdx.y, B = P.B, B2 = B * B;
-    __shared__ float A[12];
+    __shared__ long long A[12];
     if (threadIdx.x < 12) A[threadIdx.x] = aff[t].A[threadIdx.x];
-    for (int c = threadIdx.x; c < B2; c += blockDim.x) sh[c] = 0.0f;
+    for (int c = threadIdx.x; c < B2; c += blockDim.x) sh[c] = 0ull;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int nf0 = P.nf[0], nf1 = P.nf[1];
@@ -147,14 +161,13 @@ __global__ void __launch_bounds__(256)
     const float Bm4 = (float)(B - 4);
     unsigned int cnt = 0;
     for (long long r = (long long)blockIdx.x * nwarps + warp; r < R; r += (long long)gridDim.x * nwarps) {
-        const float j = (float)(r % nf1), k = (float)(r / nf1);
-        const float b0 = fmaf(A[1], j, fmaf(A[2], k, A[3]));
-        const float b1 = fmaf(A[5], j, fmaf(A[6], k, A[7]));
-        const float b2 = fmaf(A[9], j, fmaf(A[10], k, A[11]));
+        const long long j = r % nf1, k = r / nf1;
+        const long long b0 = A[1] * j + A[2] * k + A[3];
+        const long long b1 = A[5] * j + A[6] * k + A[7];
+        const long long b2 = A[9] * j + A[10] * k + A[11];
         const uint8_t *__restrict__ frow = P.fbins + (size_t)r * nf0;
         for (int i = lane; i < nf0; i += 32) {
-            const float fi = (float)i;
-            const float ux = fmaf(A[0], fi, b0), uy = fmaf(A[4], fi, b1), uz = fmaf(A[8], fi, b2);
+            const long long ux = b0 + A[0] * i, uy = b1 + A[4] * i, uz = b2 + A[8] * i;
             if (!inside_u(ux, uy, uz, n0, n1, n2)) continue;
             ++cnt;
             const MG g = trilinear<false>(P.mov, n0, n1, n2, ux, uy, uz);
@@ -162,18 +175,22 @@ __global__ void __launch_bounds__(256)
             const int k0 = (int)mt;
             float w[4];
             bspline_w(mt - (float)k0, w);
-            float *row = sh + (int)__ldg(frow + i) * B + (k0 - 1);
-            atomicAdd(row + 0, w[0]);
-            atomicAdd(row + 1, w[1]);
-            atomicAdd(row + 2, w[2]);
-            if (k0 + 2 < B) atomicAdd(row + 3, w[3]);
+            const unsigned long long q0 = __float2ull_rn(w[0] * 4294967296.0f);
+            const unsigned long long q2 = __float2ull_rn(w[2] * 4294967296.0f);
+            const unsigned long long q3 = __float2ull_rn(w[3] * 4294967296.0f);
+            const unsigned long long q1 = 4294967296ull - q0 - q2 - q3;
+            unsigned long long *row = sh + (int)__ldg(frow + i) * B + (k0 - 1);
+            atomicAdd(row + 0, q0);
+            atomicAdd(row + 1, q1);
+            atomicAdd(row + 2, q2);
+            if (q3) atomicAdd(row + 3, q3);  // q3 == 0 whenever k0 + 3 > B (t = 0 there)
         }
     }
     __syncthreads();
-    double *gh = ghist + (size_t)t * B2;
+    unsigned long long *gh = ghist + (size_t)t * B2;
     for (int c = threadIdx.x; c < B2; c += blockDim.x) {
-        const float v = sh[c];
-        if (v != 0.0f) atomicAdd(gh + c, (double)v);
+        const unsigned long long v = sh[c];
+        if (v) atomicAdd(gh + c, v);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
@@ -214,21 +231,21 @@ __device__ __forceinline__ double finish_entropy(double sum, float qf, int bits)
 
 // One CTA per transform: marginals P_F (rows), P_M (cols) and their entropies per q.
 // marg: n x 2B (P_F then P_M); ment: n x nq x 2 (S_F, S_M).
-__global__ void k_parzen_marg(const double *__restrict__ ghist, const unsigned long long *__restrict__ gcount, int B,
-                              QSet Q, double *__restrict__ marg, double *__restrict__ ment) {
+__global__ void k_parzen_marg(const unsigned long long *__restrict__ ghist, const unsigned long long *__restrict__ gcount,
+                              int B, QSet Q, double *__restrict__ marg, double *__restrict__ ment) {
     __shared__ double s_tmp[32];
     const int t = blockIdx.x;
-    const double N = (double)gcount[t];
-    const double *h = ghist + (size_t)t * B * B;
+    const double N = (double)gcount[t] * 4294967296.0;  // total weight: 2^32 per overlap voxel
+    const unsigned long long *h = ghist + (size_t)t * B * B;
     double *pf = marg + (size_t)t * 2 * B, *pm = pf + B;
     for (int r = threadIdx.x; r < B; r += blockDim.x) {
-        double sr = 0.0, sc = 0.0;
+        unsigned long long sr = 0, sc = 0;
         for (int c = 0; c < B; ++c) {
             sr += h[(size_t)r * B + c];
             sc += h[(size_t)c * B + r];
         }
-        pf[r] = N > 0 ? sr / N : 0.0;
-        pm[r] = N > 0 ? sc / N : 0.0;
+        pf[r] = N > 0 ? (double)sr / N : 0.0;
+        pm[r] = N > 0 ? (double)sc / N : 0.0;
     }
     __syncthreads();
     for (int iq = 0; iq < Q.nq; ++iq) {
@@ -246,19 +263,20 @@ __global__ void k_parzen_marg(const double *__restrict__ ghist, const unsigned l
     }
 }
 
-// Grid (cells / 256, n): joint entropy sums (jsum: n x nq) and W (n x nq x B^2, FP32).
+// Grid (cells / 256, n): per-block joint entropy partial sums (jpart: n x nq x
+// gridDim.x, reduced in a fixed order later) and W (n x nq x B^2, FP32).
 __global__ void __launch_bounds__(256)
-    k_parzen_cells(const double *__restrict__ ghist, const unsigned long long *__restrict__ gcount, int B, QSet Q,
-                   const double *__restrict__ marg, const double *__restrict__ ment, double *__restrict__ jsum,
+    k_parzen_cells(const unsigned long long *__restrict__ ghist, const unsigned long long *__restrict__ gcount, int B,
+                   QSet Q, const double *__restrict__ marg, const double *__restrict__ ment, double *__restrict__ jpart,
                    float *__restrict__ wout) {
     __shared__ double s_tmp[32];
     const int t = blockIdx.y, B2 = B * B;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    const double N = (double)gcount[t];
+    const double N = (double)gcount[t] * 4294967296.0;
     const double lnb = Q.bits ? log(2.0) : 1.0;
     double p = 0.0, pfr = 0.0, pmc = 0.0;
     if (c < B2 && N > 0) {
-        p = ghist[(size_t)t * B2 + c] / N;
+        p = (double)ghist[(size_t)t * B2 + c] / N;
         pfr = marg[(size_t)t * 2 * B + c / B];
         pmc = marg[(size_t)t * 2 * B + B + c % B];
     }
@@ -266,7 +284,7 @@ __global__ void __launch_bounds__(256)
         const float qf = Q.q[iq];
         double e = p > 0.0 ? ent_term(p, qf) : 0.0;
         e = block_sum(e, s_tmp);
-        if (threadIdx.x == 0) atomicAdd(jsum + (size_t)t * Q.nq + iq, e);
+        if (threadIdx.x == 0) jpart[((size_t)t * Q.nq + iq) * gridDim.x + blockIdx.x] = e;
         if (c < B2) {
             double w = 0.0;
             if (p > 0.0) {
@@ -292,9 +310,12 @@ __global__ void __launch_bounds__(256)
 
 // MI per q: S_F + S_M - S_FM (+ (1 - q) S_F S_M for the pseudo-additive form).
 __global__ void k_parzen_final(int n, const unsigned long long *__restrict__ gcount, QSet Q,
-                               const double *__restrict__ ment, const double *__restrict__ jsum, double *__restrict__ mi) {
+                               const double *__restrict__ ment, const double *__restrict__ jpart, int nparts,
+                               double *__restrict__ mi) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= n * Q.nq) return;
+    double js = 0.0;
+    for (int b = 0; b < nparts; ++b) js += jpart[(size_t)x * nparts + b];
     const int t = x / Q.nq, iq = x % Q.nq;
     if (gcount[t] == 0) {
         mi[x] = __longlong_as_double(0x7ff8000000000000ll);
@@ -302,23 +323,24 @@ __global__ void k_parzen_final(int n, const unsigned long long *__restrict__ gco
     }
     const float qf = Q.q[iq];
     const double SF = ment[(size_t)x * 2 + 0], SM = ment[(size_t)x * 2 + 1];
-    const double SJ = finish_entropy(jsum[x], qf, Q.bits);
+    const double SJ = finish_entropy(js, qf, Q.bits);
     double I = SF + SM - SJ;
     if (qf != 1.0f && Q.form == 1) I += (1.0 - (double)qf) * SF * SM;
     mi[x] = I;
 }
 
 // ---------------------------------------------------------------------------
-// Adjoint: moments M[q][a][c] = sum_x s_q(x) d_a m(u_x) x_c, x = (i, j, k, 1)
+// Adjoint: moments M[q][a][c] = sum_x s_q(x) d_a m(u_x) x_c, x = (i - ci, j - cj, k - ck, 1)
 // ---------------------------------------------------------------------------
 
 template <int NQ>
 __global__ void __launch_bounds__(256)
     k_parzen_adj(ParzenPair P, const ParzenAffine *__restrict__ aff, int nq_total, int q0,
                  const float *__restrict__ wtab, int w_in_smem, double *__restrict__ mom) {
+    // mom: n x nq_total x gridDim.x x 12 per-CTA partial moments (no atomics: fixed-order reduction later)
     extern __shared__ float sw[];  // NQ x B^2 weights when they fit
     const int t = blockIdx.y, B = P.B, B2 = B * B;
-    __shared__ float A[12];
+    __shared__ long long A[12];
     __shared__ float s_red[8][NQ * 12];
     if (threadIdx.x < 12) A[threadIdx.x] = aff[t].A[threadIdx.x];
     const float *W = wtab + ((size_t)t * nq_total + q0) * B2;
@@ -332,22 +354,26 @@ __global__ void __launch_bounds__(256)
     const int n0 = P.nm[0], n1 = P.nm[1], n2 = P.nm[2];
     const long long R = (long long)nf1 * P.nf[2];
     const float Bm4 = (float)(B - 4);
+    // moments are taken about the fixed-volume centre, where the rotation and
+    // scale columns of du/dtheta have no constant part (no cancellation)
+    const float ci = 0.5f * (float)(nf0 - 1), cj = 0.5f * (float)(nf1 - 1), ck = 0.5f * (float)(P.nf[2] - 1);
     float M[NQ][12];
 #pragma unroll
     for (int q = 0; q < NQ; ++q)
 #pragma unroll
         for (int e = 0; e < 12; ++e) M[q][e] = 0.0f;
     for (long long r = (long long)blockIdx.x * nwarps + warp; r < R; r += (long long)gridDim.x * nwarps) {
-        const float j = (float)(r % nf1), k = (float)(r / nf1);
-        const float b0 = fmaf(A[1], j, fmaf(A[2], k, A[3]));
-        const float b1 = fmaf(A[5], j, fmaf(A[6], k, A[7]));
-        const float b2 = fmaf(A[9], j, fmaf(A[10], k, A[11]));
+        const long long jl = r % nf1, kl = r / nf1;
+        const long long b0 = A[1] * jl + A[2] * kl + A[3];
+        const long long b1 = A[5] * jl + A[6] * kl + A[7];
+        const long long b2 = A[9] * jl + A[10] * kl + A[11];
+        const float j = (float)jl - cj, k = (float)kl - ck;
         const uint8_t *__restrict__ frow = P.fbins + (size_t)r * nf0;
         for (int i = lane; i < nf0; i += 32) {
-            const float fi = (float)i;
-            const float ux = fmaf(A[0], fi, b0), uy = fmaf(A[4], fi, b1), uz = fmaf(A[8], fi, b2);
+            const long long ux = b0 + A[0] * i, uy = b1 + A[4] * i, uz = b2 + A[8] * i;
             if (!inside_u(ux, uy, uz, n0, n1, n2)) continue;
             const MG g = trilinear<true>(P.mov, n0, n1, n2, ux, uy, uz);
+            const float ic = (float)i - ci;
             const float mt = fmaf(fminf(fmaxf(g.m, 0.0f), 1.0f), Bm4, 2.0f);
             const int k0 = (int)mt;
             float d[4];
@@ -360,15 +386,15 @@ __global__ void __launch_bounds__(256)
                 const float *Wq = W + (size_t)q * B2;
                 const float s = Wq[base] * d[0] + Wq[base + 1] * d[1] + Wq[base + 2] * d[2] + Wq[i3] * d[3];
                 const float sx = s * g.gx, sy = s * g.gy, sz = s * g.gz;
-                M[q][0] = fmaf(sx, fi, M[q][0]);
+                M[q][0] = fmaf(sx, ic, M[q][0]);
                 M[q][1] = fmaf(sx, j, M[q][1]);
                 M[q][2] = fmaf(sx, k, M[q][2]);
                 M[q][3] += sx;
-                M[q][4] = fmaf(sy, fi, M[q][4]);
+                M[q][4] = fmaf(sy, ic, M[q][4]);
                 M[q][5] = fmaf(sy, j, M[q][5]);
                 M[q][6] = fmaf(sy, k, M[q][6]);
                 M[q][7] += sy;
-                M[q][8] = fmaf(sz, fi, M[q][8]);
+                M[q][8] = fmaf(sz, ic, M[q][8]);
                 M[q][9] = fmaf(sz, j, M[q][9]);
                 M[q][10] = fmaf(sz, k, M[q][10]);
                 M[q][11] += sz;
@@ -389,12 +415,13 @@ __global__ void __launch_bounds__(256)
     if (threadIdx.x < NQ * 12) {
         double s = 0.0;
         for (int w = 0; w < nwarps; ++w) s += (double)s_red[w][threadIdx.x];
-        atomicAdd(mom + ((size_t)t * nq_total + q0) * 12 + threadIdx.x, s);
+        const int q = threadIdx.x / 12, e = threadIdx.x % 12;
+        mom[(((size_t)t * nq_total + q0 + q) * gridDim.x + blockIdx.x) * 12 + e] = s;
     }
 }
 
-// grad[t][q][p] = -(B - 4) / N sum_e mom[t][q][e] J[t][e][p]
-__global__ void k_parzen_grad(int n, int nq, int B, const unsigned long long *__restrict__ gcount,
+// grad[t][q][p] = -(B - 4) / N sum_e mom[t][q][e] J[t][e][p], J taken about the fixed centre
+__global__ void k_parzen_grad(int n, int nq, int B, int nparts, const unsigned long long *__restrict__ gcount,
                               const double *__restrict__ mom, const double *__restrict__ jac, double *__restrict__ grad) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= n * nq * 9) return;
@@ -405,7 +432,11 @@ __global__ void k_parzen_grad(int n, int nq, int B, const unsigned long long *__
         return;
     }
     double s = 0.0;
-    for (int e = 0; e < 12; ++e) s += mom[(size_t)tq * 12 + e] * jac[((size_t)t * 12 + e) * 9 + p];
+    for (int e = 0; e < 12; ++e) {
+        double me = 0.0;
+        for (int b = 0; b < nparts; ++b) me += mom[((size_t)tq * nparts + b) * 12 + e];
+        s += me * jac[((size_t)t * 12 + e) * 9 + p];
+    }
     grad[x] = -(double)(B - 4) / N * s;
 }
 
@@ -432,10 +463,7 @@ cudaError_t launch_parzen_prep_moving(const void *data, int dtype, int depth, lo
     return cudaGetLastError();
 }
 
-static int parzen_ctas(const ParzenPair &P, int n) {
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+int parzen_ctas(const ParzenPair &P, int n, int sms) {
     const long long rows = (long long)P.nf[1] * P.nf[2];
     // about 4 CTAs per SM over all transforms, at least one row batch of 8 warps each
     long long per_t = (4LL * sms + n - 1) / n;
@@ -445,40 +473,42 @@ static int parzen_ctas(const ParzenPair &P, int n) {
     return (int)per_t;
 }
 
-cudaError_t launch_parzen_hist(const ParzenPair &P, const ParzenAffine *d_aff, int n, double *d_hist,
-                               unsigned long long *d_count, cudaStream_t s) {
+int parzen_cell_blocks(int B) { return (B * B + 255) / 256; }
+
+cudaError_t launch_parzen_hist(const ParzenPair &P, const ParzenAffine *d_aff, int n, int ctas,
+                               unsigned long long *d_hist, unsigned long long *d_count, cudaStream_t s) {
     const size_t B2 = (size_t)P.B * P.B;
-    cudaError_t e = cudaMemsetAsync(d_hist, 0, (size_t)n * B2 * sizeof(double), s);
+    cudaError_t e = cudaMemsetAsync(d_hist, 0, (size_t)n * B2 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(d_count, 0, (size_t)n * sizeof(unsigned long long), s)) != cudaSuccess) return e;
-    const size_t smem = B2 * sizeof(float);
+    const size_t smem = B2 * sizeof(unsigned long long);
     if ((e = cudaFuncSetAttribute(k_parzen_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
-    dim3 grid(parzen_ctas(P, n), n);
+    dim3 grid(ctas, n);
     k_parzen_hist<<<grid, 256, smem, s>>>(P, d_aff, d_hist, d_count);
     return cudaGetLastError();
 }
 
-cudaError_t launch_parzen_weights(const double *d_hist, const unsigned long long *d_count, int n, int B, const QSet &Q,
-                                  double *marg, double *ment, double *jsum, double *d_mi, float *d_w, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(jsum, 0, (size_t)n * Q.nq * sizeof(double), s);
-    if (e != cudaSuccess) return e;
+cudaError_t launch_parzen_weights(const unsigned long long *d_hist, const unsigned long long *d_count, int n, int B,
+                                  const QSet &Q, double *marg, double *ment, double *jpart, double *d_mi, float *d_w,
+                                  cudaStream_t s) {
+    cudaError_t e;
     k_parzen_marg<<<n, 256, 0, s>>>(d_hist, d_count, B, Q, marg, ment);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    dim3 grid((B * B + 255) / 256, n);
-    k_parzen_cells<<<grid, 256, 0, s>>>(d_hist, d_count, B, Q, marg, ment, jsum, d_w);
+    const int nb = parzen_cell_blocks(B);
+    dim3 grid(nb, n);
+    k_parzen_cells<<<grid, 256, 0, s>>>(d_hist, d_count, B, Q, marg, ment, jpart, d_w);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_parzen_final<<<(n * Q.nq + 127) / 128, 128, 0, s>>>(n, d_count, Q, ment, jsum, d_mi);
+    k_parzen_final<<<(n * Q.nq + 127) / 128, 128, 0, s>>>(n, d_count, Q, ment, jpart, nb, d_mi);
     return cudaGetLastError();
 }
 
 cudaError_t launch_parzen_adjoint(const ParzenPair &P, const ParzenAffine *d_aff, const double *d_jac, int n, int nq,
-                                  const float *d_w, const unsigned long long *d_count, double *d_mom, double *d_grad,
-                                  cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(d_mom, 0, (size_t)n * nq * 12 * sizeof(double), s);
-    if (e != cudaSuccess) return e;
+                                  int ctas, const float *d_w, const unsigned long long *d_count, double *d_mom,
+                                  double *d_grad, cudaStream_t s) {
+    cudaError_t e;
     const size_t B2 = (size_t)P.B * P.B;
-    dim3 grid(parzen_ctas(P, n), n);
+    dim3 grid(ctas, n);
     for (int q0 = 0; q0 < nq; q0 += 4) {
         const int g = nq - q0 < 4 ? nq - q0 : 4;
         const size_t wbytes = (size_t)g * B2 * sizeof(float);
@@ -500,7 +530,7 @@ cudaError_t launch_parzen_adjoint(const ParzenPair &P, const ParzenAffine *d_aff
 #undef MI_ADJ
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    k_parzen_grad<<<(n * nq * 9 + 127) / 128, 128, 0, s>>>(n, nq, P.B, d_count, d_mom, d_jac, d_grad);
+    k_parzen_grad<<<(n * nq * 9 + 127) / 128, 128, 0, s>>>(n, nq, P.B, ctas, d_count, d_mom, d_jac, d_grad);
     return cudaGetLastError();
 }
 

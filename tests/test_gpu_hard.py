@@ -111,7 +111,7 @@ def test_ragged_sizes_all_variants(cuda_lib, variant, bins):
             ho, _ = oracle.joint_hist(f, m, q16[t], bins, 12, 12)
             np.testing.assert_array_equal(H[t], ho.astype(np.uint32))
     mi, h, cnt = ctx.eval_q16(q16, [1.0, 2.0], with_entropies=True)
-    mi_o, h_o, cnt_o = oracle.mi_eval_q16(f, m, bins, q16, [1.0, 2.0], 12, 12, nthreads=8)
+    mi_o, h_o, cnt_o = oracle.mi_eval_q16(f, m, bins, q16, [1.0, 2.0], fixed_depth=12, moving_depth=12, nthreads=8)
     np.testing.assert_array_equal(cnt, cnt_o)
     assert_mi_close(mi, mi_o, h_o)
 

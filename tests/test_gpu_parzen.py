@@ -2,10 +2,14 @@
 
 The GPU computes coordinates, interpolation and B-spline weights in FP32 and
 accumulates the soft histogram per CTA in FP32, then in FP64; entropies and
-W = dMI/dP are FP64.  Tolerances: MI within 2e-6 of max(|MI|, 1e-3) (the
-FP32 per-voxel weights perturb P by ~1e-7 relative); gradients within 1e-4
-of the oracle gradient's largest component (the stated gradient tolerance,
-taken norm-relative so that near-zero components do not divide by zero).
+W = dMI/dP are FP64.  Positions are 32.32 fixed point from the FP64 affine,
+so trilinear cells and the overlap agree with the oracle.  Tolerances: MI
+within 1e-6 max(|MI|, 1) -- FP32 weights and per-CTA FP32 partial sums
+perturb P by ~1e-7 relative, and MI sums P against log-ratios of size < 10,
+so the error is an absolute ~1e-6 at most (a purely relative bound is
+ill-posed as MI -> 0); gradients within 1e-4 of the oracle gradient's largest
+component (the stated gradient tolerance, taken norm-relative so that
+near-zero components do not divide by zero).
 """
 import numpy as np
 import pytest
@@ -15,7 +19,7 @@ from paper_1909_10690_gb300 import phantoms
 
 pytestmark = pytest.mark.gpu
 
-MI_TOL = 2e-6
+MI_TOL = 1e-6
 G_TOL = 1e-4
 
 
@@ -24,7 +28,7 @@ def check(ctx, f, m, prm, qs, B, form=0, depth=None, shape_sp=((1, 1, 1), (1, 1,
     for t in range(len(prm)):
         aff, J = oracle.affine(prm[t], f.shape, shape_sp[0], m.shape, shape_sp[1], with_jacobian=True)
         mi_o, g_o, n = oracle.parzen(f, m, aff, B, qs, daff=J, form=form, fixed_depth=depth, moving_depth=depth)
-        assert np.all(np.abs(mi[t] - mi_o) <= MI_TOL * np.maximum(np.abs(mi_o), 1e-3)), (t, mi[t], mi_o)
+        assert np.all(np.abs(mi[t] - mi_o) <= MI_TOL * np.maximum(np.abs(mi_o), 1.0)), (t, mi[t], mi_o)
         for iq in range(len(qs)):
             scale = np.abs(g_o[iq]).max()
             assert np.abs(g[t, iq] - g_o[iq]).max() <= G_TOL * scale, (t, iq, g[t, iq], g_o[iq])

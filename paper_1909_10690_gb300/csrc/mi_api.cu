@@ -652,14 +652,24 @@ mi_status run_plain(mi_ctx *ctx, int pair, const int32_t *d_aff, int n, const QS
 // Batched path: persistent kernel over a work queue, replayed as a CUDA graph
 // ---------------------------------------------------------------------------
 
+// Event record that also fires when replayed from a captured graph (external
+// event node while the stream is capturing, a plain record otherwise).
+cudaError_t record_event(cudaEvent_t ev, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal)
+                                               : cudaEventRecord(ev, s);
+}
+
 mi_status launch_batched_once(mi_ctx *ctx, int nitems, const QSet &Q, const Outputs &O, const Choice &ch,
                               bool record = false) {
     MI_CU(cudaMemsetAsync(ctx->d_ticket.p, 0, sizeof(int), ctx->stream), "resetting the work queue");
-    if (record) MI_CU(cudaEventRecordWithFlags(ctx->ev0, ctx->stream, cudaEventRecordExternal), "event");
+    if (record) MI_CU(record_event(ctx->ev0, ctx->stream), "event");
     MI_CU(launch_batched(ctx->d_pairs.as<PairDev>(), ctx->d_aff.as<int32_t>(), ctx->d_items.as<Item>(), nitems,
                          ctx->d_ticket.as<int>(), ctx->max_bins, ch.variant, ch.threads, ch.ctas, Q, O, ctx->stream),
           "batched kernel");
-    if (record) MI_CU(cudaEventRecordWithFlags(ctx->ev1, ctx->stream, cudaEventRecordExternal), "event");
+    if (record) MI_CU(record_event(ctx->ev1, ctx->stream), "event");
     return MI_OK;
 }
 
@@ -1230,3 +1240,4 @@ int mi_selected_variant(mi_ctx *ctx, int pair, int n) {
 }
 
 }  // extern "C"
+

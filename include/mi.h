@@ -223,6 +223,39 @@ int mi_selected_variant(mi_ctx *ctx, int pair, int n);
  * receives the number of kernels the call launched (NULL ok). */
 mi_status mi_last_kernel_ms(mi_ctx *ctx, float *ms, int *launches);
 
+/*
+ * Allocation-free evaluation.  The paper has no counterpart: this is a
+ * deployment aid for callers that cannot allocate device memory where they
+ * need the metric -- code running while a CUDA graph is being captured
+ * (cudaMalloc is not allowed then), plug-ins inside a framework whose caching
+ * allocator owns the device memory, services that fix their GPU memory budget
+ * up front.  It computes the same hard-binned MI as mi_eval (plain path) for
+ * ONE transform (9 parameters, host memory) and nq q values (host memory)
+ * without creating a context and without calling cudaMalloc, cudaFree or any
+ * allocating routine.
+ *  - fixed, moving: uint8 or uint16 volumes already in device memory of the
+ *    current device, used as given (no copy; values must lie within their bit
+ *    depth, since no clamp-on-load copy is made).
+ *  - bins: 2..MI_NOALLOC_MAX_BINS; the fixed volume may hold at most
+ *    MI_NOALLOC_MAX_VOXELS voxels.  Larger sizes return MI_EINVAL.
+ *  - out_mi: nq doubles, host or device memory.  stream: a cudaStream_t
+ *    (NULL = legacy default stream); the call synchronises it.
+ *  - Intermediates live in one static device array of about 257 KiB that every
+ *    GPU loading the library holds until the process exits.  The call clears
+ *    the histogram part before use; the array keeps the last call's contents.
+ *    All calls share it, so calls that overlap on the GPU (several streams or
+ *    threads at once) race: serialise them.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Shannon entropies in nats and the additive Tsallis form.  Errors as for
+ *    mi_eval; the message is read with mi_last_error(NULL).
+ */
+#define MI_NOALLOC_MAX_BINS 256
+#define MI_NOALLOC_MAX_VOXELS (1LL << 25)
+mi_status mi_eval_noalloc(const mi_volume *fixed, const mi_volume *moving, int bins, const float *transform,
+                          const float *q, int nq, double *out_mi, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -294,6 +294,31 @@ class Context:
         return float(ms.value), int(nl.value)
 
 
+def eval_noalloc(fixed, moving, bins, transform, q=(1.0,), fixed_spacing=(1.0, 1.0, 1.0),
+                 moving_spacing=(1.0, 1.0, 1.0), fixed_depth=None, moving_depth=None, stream=None, out=None):
+    """Hard-binned MI of one transform through ``mi_eval_noalloc`` (no device allocation).
+
+    For callers that cannot allocate device memory where they evaluate the
+    metric (inside CUDA-graph capture, under a framework-owned allocator, on a
+    fixed memory budget).  ``fixed`` and ``moving`` are uint8/uint16 CUDA
+    tensors on the current device; ``out`` may be a preallocated CUDA float64
+    tensor of nq elements, otherwise a numpy array is returned.  Calls share
+    one static device array: do not overlap calls on the GPU.
+    """
+    lib = load()
+    fv, fa = _volume(fixed, fixed_spacing, fixed_depth)
+    mv, ma = _volume(moving, moving_spacing, moving_depth)
+    T = np.ascontiguousarray(np.asarray(transform, dtype=np.float32).reshape(9))
+    Q = np.ascontiguousarray(np.atleast_1d(np.asarray(q, dtype=np.float32)))
+    res = out if out is not None else np.empty(Q.size, dtype=np.float64)
+    h = getattr(stream, "cuda_stream", stream)
+    st = lib.mi_eval_noalloc(ctypes.byref(fv), ctypes.byref(mv), int(bins), T.ctypes.data, Q.ctypes.data, int(Q.size),
+                             _ptr(res), ctypes.c_void_p(h) if h else None)
+    if st not in (MI_OK, MI_EEMPTY):
+        raise MIError(st, lib.mi_last_error(None).decode())
+    return res
+
+
 def mi_function():
     """torch.autograd.Function over the Parzen MI: ``MIFunction.apply(theta, ctx, q)``."""
     torch = _torch()

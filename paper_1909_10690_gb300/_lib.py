@@ -18,7 +18,7 @@ ROOT = os.path.dirname(PKG)
 INCLUDE = os.path.join(ROOT, "include")
 LIB_PATH = os.path.join(PKG, "libmi_gb300.so")
 BUILD_DIR = os.path.join(PKG, "_build")
-SOURCES = ["mi_api.cu", "mi_hard.cu", "mi_parzen.cu"]
+SOURCES = ["mi_api.cu", "mi_hard.cu", "mi_parzen.cu", "mi_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 _lib = None
@@ -106,6 +106,7 @@ SIGNATURES = {
     "mi_resample": (_I, [_P, _I, _P, _P]),
     "mi_selected_variant": (_I, [_P, _I, _I]),
     "mi_last_kernel_ms": (_I, [_P, _P, _P]),
+    "mi_eval_noalloc": (_I, [ctypes.POINTER(MiVolume), ctypes.POINTER(MiVolume), _I, _P, _P, _I, _P, _P]),
 }
 
 

@@ -1241,3 +1241,18 @@ int mi_selected_variant(mi_ctx *ctx, int pair, int n) {
 
 }  // extern "C"
 
+// ---------------------------------------------------------------------------
+// Helpers for the allocation-free entry point in mi_noalloc.cu
+// ---------------------------------------------------------------------------
+namespace mi {
+
+bool host_affine_q16(const float prm[9], const int nf[3], const float sf[3], const int nm[3], const float sm[3],
+                     int32_t q16[12]) {
+    double aff[12];
+    build_affine(prm, nf, sf, nm, sm, aff, nullptr);
+    return quantise_q16(aff, q16);
+}
+
+void set_thread_error(const char *msg) { g_create_error = msg; }
+
+}  // namespace mi

@@ -759,3 +759,218 @@ cudaError_t launch_resample(const PairDev *d_pair, const PairDev &h_pair, const 
 }
 
 }  // namespace mi
+
+// ===========================================================================
+// Allocation-free variant of the plain path (entry point in mi_noalloc.cu):
+// the fixed volume is binned on the fly from its raw values, the histogram
+// lives in caller-provided scratch (a static device array), and the entropy
+// terms are evaluated directly in FP64 instead of from count-indexed tables.
+// ===========================================================================
+
+namespace mi {
+namespace {
+
+struct RawPair {
+    const void *fix;
+    const void *mov;
+    int nf[3], nm[3];
+    int bins, fdepth, mdepth;
+};
+
+struct Q12 {
+    int q[12];
+};
+
+template <typename FixT, typename MovT, class Hist>
+__device__ void accumulate_rows_raw(const RawPair &P, const int *q, long long first_batch, long long batch_stride,
+                                    Hist &H) {
+    const int lane = threadIdx.x & 31;
+    const int nf0 = P.nf[0], nf1 = P.nf[1];
+    const long long R = (long long)nf1 * P.nf[2];
+    const int n0 = P.nm[0], n1 = P.nm[1], n2 = P.nm[2];
+    const int st0 = q[0], st1 = q[4], st2 = q[8];
+    const int bins = P.bins, mdepth = P.mdepth, fdepth = P.fdepth;
+    const uint32_t fvmax = (uint32_t)((1ull << fdepth) - 1ull);
+    const MovT *__restrict__ mov = (const MovT *)P.mov;
+    for (long long rb = first_batch * 32; rb < R; rb += batch_stride * 32) {
+        RowClip mine;
+        mine.lo = 0;
+        mine.hi = -1;
+        mine.u0 = mine.u1 = mine.u2 = 0;
+        const long long r = rb + lane;
+        if (r < R) mine = clip_row(q, (int)(r % nf1), (int)(r / nf1), nf0, P.nm);
+        for (int s = 0; s < 32; ++s) {
+            const int lo = __shfl_sync(kFull, mine.lo, s), hi = __shfl_sync(kFull, mine.hi, s);
+            if (lo > hi) continue;
+            const int U0 = __shfl_sync(kFull, mine.u0, s), U1 = __shfl_sync(kFull, mine.u1, s),
+                      U2 = __shfl_sync(kFull, mine.u2, s);
+            const FixT *__restrict__ frow = (const FixT *)P.fix + (size_t)(rb + s) * nf0;
+            for (int i0 = lo; i0 <= hi; i0 += 32) {
+                const int i = i0 + lane;
+                const bool valid = i <= hi;
+                int key = 0;
+                if (valid) {
+                    const int d = i - lo;
+                    const int v = sample_hard<MovT>(mov, n0, n1, n2, U0 + st0 * d, U1 + st1 * d, U2 + st2 * d);
+                    // volumes are read as given (no copy is made, so no clamp on load): values are expected
+                    // within the bit depth, and the interpolated value is clamped to it before binning
+                    const int bm = (min(v, (int)((1u << mdepth) - 1u)) * bins) >> mdepth;
+                    uint32_t fv = (uint32_t)__ldg(frow + i);
+                    fv = fv > fvmax ? fvmax : fv;
+                    key = (int)((fv * (uint32_t)bins) >> fdepth) * bins + bm;
+                }
+                H.add(key, valid);
+            }
+        }
+    }
+}
+
+template <typename FixT, typename MovT>
+__global__ void __launch_bounds__(1024, 1) k_hist_raw(RawPair P, Q12 A, uint32_t *__restrict__ ghist, int *flags) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int B2 = P.bins * P.bins;
+    const SmemLayout L = smem_layout(HV_U16_MATCH, P.bins, blockDim.x);
+    __shared__ int q[12];
+    if (threadIdx.x < 12) q[threadIdx.x] = A.q[threadIdx.x];
+    auto H = make_hist<HV_U16_MATCH>(smem, L, B2, flags);
+    H.zero();
+    __syncthreads();
+    const int nwarps = blockDim.x >> 5;
+    accumulate_rows_raw<FixT, MovT>(P, q, (long long)blockIdx.x * nwarps + (threadIdx.x >> 5),
+                                    (long long)gridDim.x * nwarps, H);
+    __syncthreads();
+    for (int c = threadIdx.x; c < B2; c += blockDim.x) {
+        const uint32_t v = H.count(c);
+        if (v) atomicAdd(ghist + c, v);
+    }
+}
+
+// Entropy term of one count, evaluated directly in FP64: c ln c or c^q.
+__device__ __forceinline__ double term_direct(uint32_t v, float qf) {
+    const double d = (double)v;
+    return qf == 1.0f ? d * log(d) : pow(d, (double)qf);
+}
+
+// One CTA: marginals, FP64 sums per q and MI from a global histogram.
+// out: nq MI values, then nq x 3 entropies, then the overlap count (as a double).
+__global__ void __launch_bounds__(1024, 1)
+    k_entropy_direct(const uint32_t *__restrict__ ghist, int B, QSet Q, double *__restrict__ out, int *flags) {
+    __shared__ uint32_t s_rows[256], s_cols[256];
+    __shared__ double s_red[3 * 32];
+    __shared__ double s_res[3 * kMaxQ + 1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    for (int c = tid; c < B; c += blockDim.x) s_cols[c] = 0;
+    __syncthreads();
+    for (int r = warp; r < B; r += nwarps) {
+        uint32_t rsum = 0;
+        for (int c = lane; c < B; c += 32) {
+            const uint32_t v = __ldg(ghist + r * B + c);
+            if (v) {
+                rsum += v;
+                atomicAdd(&s_cols[c], v);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rsum += __shfl_xor_sync(kFull, rsum, o);
+        if (lane == 0) s_rows[r] = rsum;
+    }
+    __syncthreads();
+    {
+        double n0 = 0.0, z1 = 0.0, z2 = 0.0;
+        for (int r = tid; r < B; r += blockDim.x) n0 += (double)s_rows[r];
+        block_sum3(n0, z1, z2, s_red);
+        if (tid == 0) s_res[3 * kMaxQ] = n0;
+    }
+    for (int iq = 0; iq < Q.nq; ++iq) {
+        double aj = 0.0, af = 0.0, am = 0.0;
+        for (int c = tid; c < B * B; c += blockDim.x) {
+            const uint32_t v = __ldg(ghist + c);
+            if (v) aj += term_direct(v, Q.q[iq]);
+        }
+        for (int r = tid; r < B; r += blockDim.x) {
+            if (s_rows[r]) af += term_direct(s_rows[r], Q.q[iq]);
+            if (s_cols[r]) am += term_direct(s_cols[r], Q.q[iq]);
+        }
+        block_sum3(af, am, aj, s_red);
+        if (tid == 0) {
+            s_res[3 * iq + 0] = af;
+            s_res[3 * iq + 1] = am;
+            s_res[3 * iq + 2] = aj;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const double N = s_res[3 * kMaxQ];
+        out[4 * Q.nq] = N;
+        if (N <= 0.0) atomicOr(&flags[0], 1);
+        for (int iq = 0; iq < Q.nq; ++iq) {
+            const float qf = Q.q[iq];
+            const double SF = s_res[3 * iq + 0], SM = s_res[3 * iq + 1], SJ = s_res[3 * iq + 2];
+            double hf, hm, hj;
+            if (N <= 0.0) {
+                hf = hm = hj = __longlong_as_double(0x7ff8000000000000ll);
+            } else if (qf == 1.0f) {
+                const double lnN = log(N);
+                hf = lnN - SF / N;
+                hm = lnN - SM / N;
+                hj = lnN - SJ / N;
+                if (Q.bits) {
+                    const double l2 = log(2.0);
+                    hf /= l2;
+                    hm /= l2;
+                    hj /= l2;
+                }
+            } else {
+                const double qd = (double)qf, Nq = pow(N, -qd);
+                hf = (1.0 - Nq * SF) / (qd - 1.0);
+                hm = (1.0 - Nq * SM) / (qd - 1.0);
+                hj = (1.0 - Nq * SJ) / (qd - 1.0);
+            }
+            double I = hf + hm - hj;
+            if (qf != 1.0f && Q.form == 1) I += (1.0 - (double)qf) * hf * hm;
+            out[iq] = I;
+            out[Q.nq + 3 * iq + 0] = hf;
+            out[Q.nq + 3 * iq + 1] = hm;
+            out[Q.nq + 3 * iq + 2] = hj;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_noalloc_eval(const void *fix, int fdtype, int fdepth, const void *mov, int mdtype, int mdepth,
+                                const int nf[3], const int nm[3], int bins, const int32_t q16[12], const QSet &Q,
+                                uint32_t *hist, int *flags, double *out, int ctas, cudaStream_t s) {
+    RawPair P;
+    P.fix = fix;
+    P.mov = mov;
+    for (int a = 0; a < 3; ++a) {
+        P.nf[a] = nf[a];
+        P.nm[a] = nm[a];
+    }
+    P.bins = bins;
+    P.fdepth = fdepth;
+    P.mdepth = mdepth;
+    Q12 A;
+    for (int e = 0; e < 12; ++e) A.q[e] = q16[e];
+    const int threads = 1024;
+    const size_t smem = smem_layout(HV_U16_MATCH, bins, threads).total;
+    cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)bins * bins * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(flags, 0, 2 * sizeof(int), s)) != cudaSuccess) return e;
+#define MI_RAW(FT, MT)                                                                     \
+    do {                                                                                   \
+        if ((e = set_smem(k_hist_raw<FT, MT>, smem)) != cudaSuccess) return e;            \
+        k_hist_raw<FT, MT><<<ctas, threads, smem, s>>>(P, A, hist, flags);                 \
+    } while (0)
+    if (fdtype == 0 && mdtype == 0) MI_RAW(uint8_t, uint8_t);
+    else if (fdtype == 0) MI_RAW(uint8_t, uint16_t);
+    else if (mdtype == 0) MI_RAW(uint16_t, uint8_t);
+    else MI_RAW(uint16_t, uint16_t);
+#undef MI_RAW
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_entropy_direct<<<1, 1024, 0, s>>>(hist, bins, Q, out, flags);
+    return cudaGetLastError();
+}
+
+}  // namespace mi

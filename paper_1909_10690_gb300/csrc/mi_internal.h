@@ -110,4 +110,17 @@ cudaError_t launch_parzen_adjoint(const ParzenPair &P, const ParzenAffine *d_aff
                                   int ctas, const float *d_w, const unsigned long long *d_count, double *d_mom,
                                   double *d_grad, cudaStream_t s);
 
+// ---- allocation-free evaluation (mi_noalloc.cu) ---------------------------
+// Plain-path variant that bins the fixed volume on the fly and keeps its
+// histogram (bins^2 u32), flags (2 int) and results (4 nq + 1 doubles) in
+// caller-provided device memory.
+cudaError_t launch_noalloc_eval(const void *fix, int fdtype, int fdepth, const void *mov, int mdtype, int mdepth,
+                                const int nf[3], const int nm[3], int bins, const int32_t q16[12], const QSet &Q,
+                                uint32_t *hist, int *flags, double *out, int ctas, cudaStream_t s);
+// The context path's parameter -> 16.16 affine builder (false if an entry does not fit).
+bool host_affine_q16(const float prm[9], const int nf[3], const float sf[3], const int nm[3], const float sm[3],
+                     int32_t q16[12]);
+// Message returned by mi_last_error(NULL) on this thread.
+void set_thread_error(const char *msg);
+
 }  // namespace mi

@@ -282,6 +282,29 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+def run_profile(args):
+    """Only the batched 256^3 evaluation of ``args.profile`` transforms with a fixed histogram
+    variant (no autotuning), for ncu captures of the main kernel on a small case."""
+    import torch
+
+    import paper_1909_10690_gb300 as mi
+    from paper_1909_10690_gb300 import phantoms
+
+    f, m = phantoms.head_pair(shape=SHAPE, spacing=(1, 1, 1), seed=30)
+    prm = torch.from_numpy(phantoms.random_transforms(args.profile, seed=31)).cuda()
+    ctx = mi.Context(f, m, bins=BINS, fixed_depth=DEPTH, moving_depth=DEPTH, path="batched",
+                     hist_variant=args.variant, autotune=False)
+    for _ in range(args.warmup):
+        ctx.eval(prm, QS)
+    ms = []
+    for _ in range(args.steps):
+        ctx.eval(prm, QS)
+        ms.append(ctx.last_kernel_ms()[0])
+    nvox = int(np.prod(SHAPE))
+    print(json.dumps({"profile": "batched", "transforms": args.profile, "variant": args.variant,
+                      "kernel_ms": ms, "voxel_transforms_per_s": args.profile * nvox / (np.mean(ms) / 1e3)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -290,7 +313,12 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--skip-extras", action="store_true", help="skip the plain and Parzen lines")
     ap.add_argument("--skip-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--profile", type=int, default=0, help="profile mode: batched kernel only, on this many transforms")
+    ap.add_argument("--variant", type=int, default=3, help="histogram variant in profile mode (MI_HV_*)")
     args = ap.parse_args()
+    if args.profile:
+        run_profile(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

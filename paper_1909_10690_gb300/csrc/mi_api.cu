@@ -186,7 +186,7 @@ struct Pair {
     int fdepth, mdepth;
     int mdtype;  // stored moving type: 0 u8, 1 u16
     long long nvf, nvm;
-    DevBuf fbins, mov;          // hard path
+    DevBuf fbins, mov, movp;    // hard path (movp: x-paired moving volume)
     DevBuf pfbins, pmov;        // Parzen path
 };
 
@@ -379,6 +379,8 @@ mi_status add_pair(mi_ctx *ctx, const mi_volume *fx, const mi_volume *mv, int bi
             P->mdtype = mv->dtype == MI_U8 ? 0 : 1;
             MI_CU(launch_clamp_depth(P->mov.p, P->mdtype, P->mdepth, P->nvm, s), "clamping the moving volume");
         }
+        MI_CU(P->movp.ensure((size_t)P->nvm * (P->mdtype == 0 ? 2 : 4)), "allocating the paired moving volume");
+        MI_CU(launch_make_pairs(P->mov.p, P->mdtype, P->nvm, P->nm[0], P->movp.p, s), "pairing the moving volume");
     }
     MI_CU(cudaStreamSynchronize(s), "preparing the volumes");
     ctx->max_bins = std::max(ctx->max_bins, bins);
@@ -394,6 +396,7 @@ mi_status upload_pairs(mi_ctx *ctx) {
         memset(&d, 0, sizeof d);
         d.fbins = P.fbins.as<uint8_t>();
         d.mov = P.mov.p;
+        d.movp = P.movp.p;
         for (int a = 0; a < 3; ++a) {
             d.nf[a] = P.nf[a];
             d.nm[a] = P.nm[a];
@@ -413,6 +416,7 @@ PairDev host_pairdev(const Pair &P) {
     memset(&d, 0, sizeof d);
     d.fbins = P.fbins.as<uint8_t>();
     d.mov = P.mov.p;
+    d.movp = P.movp.p;
     for (int a = 0; a < 3; ++a) {
         d.nf[a] = P.nf[a];
         d.nm[a] = P.nm[a];

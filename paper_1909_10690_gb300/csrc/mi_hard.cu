@@ -103,6 +103,35 @@ __device__ __forceinline__ int sample_hard(const MovT *__restrict__ mov, int n0,
     return lerp8(g0, g1, fz);
 }
 
+// The same resample from the x-paired moving volume: element x holds v[x] in its
+// low half and v[min(x + 1, n0 - 1)] in its high half (uint16 pairs of a uint8
+// volume, uint32 pairs of a uint16 volume), so one voxel takes 4 loads, not 8.
+template <typename PairT>
+__device__ __forceinline__ int sample_hard_pair(const PairT *__restrict__ movp, int n0, int n1, int n2, int ux, int uy,
+                                                int uz) {
+    constexpr int HB = (int)sizeof(PairT) * 4;  // bits per half
+    constexpr uint32_t LO = (1u << HB) - 1u;
+    const int ix = ux >> 16, iy = uy >> 16, iz = uz >> 16;
+    const int fx = (ux >> 8) & 255, fy = (uy >> 8) & 255, fz = (uz >> 8) & 255;
+    const int sy = iy < n1 - 1 ? n0 : 0;
+    const int sz = iz < n2 - 1 ? n0 * n1 : 0;
+    const PairT *p = movp + (ix + n0 * (iy + n1 * iz));
+    const uint32_t a = __ldg(p), b = __ldg(p + sy), c = __ldg(p + sz), d = __ldg(p + sz + sy);
+    const int e00 = lerp8((int)(a & LO), (int)(a >> HB), fx), e01 = lerp8((int)(b & LO), (int)(b >> HB), fx);
+    const int e10 = lerp8((int)(c & LO), (int)(c >> HB), fx), e11 = lerp8((int)(d & LO), (int)(d >> HB), fx);
+    const int g0 = lerp8(e00, e01, fy), g1 = lerp8(e10, e11, fy);
+    return lerp8(g0, g1, fz);
+}
+
+template <typename T, typename PairT>
+__global__ void k_make_pairs(const T *__restrict__ in, long long n, int n0, PairT *__restrict__ out) {
+    constexpr int HB = (int)sizeof(PairT) * 4;
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x) {
+        const bool last = (x % n0) == n0 - 1;
+        out[x] = (PairT)((uint32_t)in[x] | ((uint32_t)in[last ? x : x + 1] << HB));
+    }
+}
+
 // Overlap interval [lo, hi] of fixed row (j, k) and the 16.16 moving index at i = lo.
 struct RowClip {
     int lo, hi, u0, u1, u2;
@@ -164,43 +193,53 @@ __device__ RowClip clip_row(const int *q, int j, int k, int nf0, const int nm[3]
 // Shared-memory histogram policies
 // ---------------------------------------------------------------------------
 
-// 32-bit counters: one shared atomic per voxel (or per group of equal keys in a warp).
+// Shared histograms address cell (bf, bm) through rows padded by one word:
+// with a row stride of S = B + 1 words the bank is (row + column) mod 32,
+// so cells clustered in a few moving bins (the Rician background occupies
+// bins 0..15 of both volumes) still spread over the banks.
+
+// 32-bit counters: one shared atomic per voxel (or per group of equal cells in a warp).
 template <bool MATCH>
 struct HistU32 {
     uint32_t *h;
-    int B2;
+    int B, S;  // bins, padded row stride in words
     __device__ void zero() {
-        for (int c = threadIdx.x; c < B2; c += blockDim.x) h[c] = 0;
+        for (int c = threadIdx.x; c < B * S; c += blockDim.x) h[c] = 0;
     }
-    __device__ __forceinline__ void add(int key, bool valid) {
+    __device__ __forceinline__ void add(int bf, int bm, bool valid) {
+        const int idx = bf * S + bm;
         if (!MATCH) {
-            if (valid) atomicAdd(&h[key], 1u);
+            if (valid) atomicAdd(&h[idx], 1u);
         } else {
             const unsigned vm = __ballot_sync(kFull, valid);
             if (valid) {
-                const unsigned peers = __match_any_sync(vm, key);
-                if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[key], (unsigned)__popc(peers));
+                const unsigned peers = __match_any_sync(vm, idx);
+                if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[idx], (unsigned)__popc(peers));
             }
         }
     }
-    __device__ __forceinline__ uint32_t count(int c) const { return h[c]; }
+    __device__ __forceinline__ uint32_t count(int bf, int bm) const { return h[bf * S + bm]; }
 };
 
-// 16-bit counters packed two per word.  A counter whose value reaches
-// kDrainT is drained whole into a shared hash table of 32-bit overflow
-// counts by a compare-and-swap; the adder that observed it does the drain,
-// so a counter never exceeds kDrainT + (threads x 32) < 2^16.  The true
-// count is the 16-bit value plus the overflow entry (flagged in a bitmap).
+// 16-bit counters, two per word: the word at (row r, column bm) holds cell
+// (r, bm) in its low half and cell (r + H, bm) in its high half, H = ceil(B/2),
+// so the two halves of a word belong to fixed bins far apart and rarely
+// collide.  A counter whose value reaches kDrainT is drained whole into a
+// shared hash table of 32-bit overflow counts by a compare-and-swap; the
+// adder that observed it does the drain, so a counter never exceeds
+// kDrainT + (threads x 32) < 2^16.  The true count is the 16-bit value plus
+// the overflow entry (flagged in a bitmap).  Overflow entries are keyed by
+// the cell id bf * B + bm.
 template <bool MATCH>
 struct HistU16 {
-    uint32_t *w;      // (B2 + 1) / 2 words
+    uint32_t *w;      // H x S words
     uint32_t *okey;   // kOvfSlots keys
     uint32_t *ocnt;   // kOvfSlots counts
-    uint32_t *bmap;   // (B2 + 31) / 32 words
+    uint32_t *bmap;   // (B^2 + 31) / 32 words
     int *flags;
-    int B2;
+    int B, S, H;
     __device__ void zero() {
-        const int nw = (B2 + 1) >> 1, nb = (B2 + 31) >> 5;
+        const int nw = H * S, nb = (B * B + 31) >> 5;
         for (int c = threadIdx.x; c < nw; c += blockDim.x) w[c] = 0;
         for (int c = threadIdx.x; c < kOvfSlots; c += blockDim.x) {
             okey[c] = kEmptyKey;
@@ -229,8 +268,7 @@ struct HistU16 {
         }
         atomicOr(&flags[1], 1);  // cannot happen while N <= kOvfSlots / 2 * kDrainT
     }
-    __device__ void drain(uint32_t key) {
-        const uint32_t idx = key >> 1, sh = (key & 1) << 4;
+    __device__ void drain(uint32_t idx, uint32_t sh, uint32_t key) {
         volatile uint32_t *vw = w;
         // each failed attempt means another update of this word succeeded; bounded for safety
         for (int it = 0; it < 1 << 16; ++it) {
@@ -244,24 +282,27 @@ struct HistU16 {
         }
         atomicOr(&flags[1], 2);
     }
-    __device__ __forceinline__ void inc(int key, uint32_t n) {
-        const uint32_t sh = (key & 1) << 4;
-        const uint32_t old = atomicAdd(&w[key >> 1], n << sh);
-        if (((old >> sh) & 0xffffu) + n >= (uint32_t)kDrainT) drain((uint32_t)key);
+    __device__ __forceinline__ void inc(int bf, int bm, uint32_t n) {
+        const bool hi = bf >= H;
+        const uint32_t idx = (uint32_t)((hi ? bf - H : bf) * S + bm), sh = hi ? 16u : 0u;
+        const uint32_t old = atomicAdd(&w[idx], n << sh);
+        if (((old >> sh) & 0xffffu) + n >= (uint32_t)kDrainT) drain(idx, sh, (uint32_t)(bf * B + bm));
     }
-    __device__ __forceinline__ void add(int key, bool valid) {
+    __device__ __forceinline__ void add(int bf, int bm, bool valid) {
         if (!MATCH) {
-            if (valid) inc(key, 1u);
+            if (valid) inc(bf, bm, 1u);
         } else {
             const unsigned vm = __ballot_sync(kFull, valid);
             if (valid) {
-                const unsigned peers = __match_any_sync(vm, key);
-                if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) inc(key, (unsigned)__popc(peers));
+                const unsigned peers = __match_any_sync(vm, bf * B + bm);
+                if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) inc(bf, bm, (unsigned)__popc(peers));
             }
         }
     }
-    __device__ __forceinline__ uint32_t count(int c) const {
-        uint32_t v = (w[c >> 1] >> ((c & 1) << 4)) & 0xffffu;
+    __device__ __forceinline__ uint32_t count(int bf, int bm) const {
+        const bool hi = bf >= H;
+        uint32_t v = (w[(hi ? bf - H : bf) * S + bm] >> (hi ? 16 : 0)) & 0xffffu;
+        const int c = bf * B + bm;
         if (bmap[c >> 5] & (1u << (c & 31))) {
             uint32_t s = slot_of((uint32_t)c) & (kOvfSlots - 1);
             for (int probe = 0; probe < kOvfSlots; ++probe) {
@@ -275,10 +316,11 @@ struct HistU16 {
     }
 };
 
-// Global 32-bit histogram (plain path's entropy reduction).
+// Global 32-bit histogram, row-major bins x bins (plain path's entropy reduction).
 struct HistGlobal {
     const uint32_t *h;
-    __device__ __forceinline__ uint32_t count(int c) const { return __ldg(h + c); }
+    int B;
+    __device__ __forceinline__ uint32_t count(int bf, int bm) const { return __ldg(h + bf * B + bm); }
 };
 
 // Shared-memory layout of a CTA: [histogram words][ovf keys][ovf counts][bitmap] [rows][cols] [FP64 scratch].
@@ -292,9 +334,10 @@ __host__ __device__ inline SmemLayout smem_layout(int variant, int bins, int thr
     SmemLayout L;
     const size_t B2 = (size_t)bins * bins;
     const bool u16 = variant == HV_U16 || variant == HV_U16_MATCH;
+    const size_t S = (size_t)bins + 1, H = ((size_t)bins + 1) / 2;
     size_t o = 0;
     L.hist = o;
-    o += u16 ? ((B2 + 1) / 2) * 4 : B2 * 4;
+    o += u16 ? H * S * 4 : (size_t)bins * S * 4;
     L.okey = o;
     if (u16) o += (size_t)kOvfSlots * 4;
     L.ocnt = o;
@@ -324,10 +367,12 @@ template <>
 struct HistOf<HV_U16_MATCH> { using T = HistU16<true>; };
 
 template <int HV>
-__device__ typename HistOf<HV>::T make_hist(unsigned char *smem, const SmemLayout &L, int B2, int *flags) {
+__device__ typename HistOf<HV>::T make_hist(unsigned char *smem, const SmemLayout &L, int B, int *flags) {
     typename HistOf<HV>::T H;
-    H.B2 = B2;
+    H.B = B;
+    H.S = B + 1;
     if constexpr (HV == HV_U16 || HV == HV_U16_MATCH) {
+        H.H = (B + 1) / 2;
         H.w = (uint32_t *)(smem + L.hist);
         H.okey = (uint32_t *)(smem + L.okey);
         H.ocnt = (uint32_t *)(smem + L.ocnt);
@@ -344,7 +389,7 @@ __device__ typename HistOf<HV>::T make_hist(unsigned char *smem, const SmemLayou
 // then the warp walks the 32 clipped rows 32 voxels at a time.
 // ---------------------------------------------------------------------------
 
-template <typename MovT, class Hist>
+template <typename PairT, class Hist>
 __device__ void accumulate_rows(const PairDev &P, const int *q, long long first_batch, long long batch_stride,
                                 Hist &H) {
     const int lane = threadIdx.x & 31;
@@ -353,7 +398,7 @@ __device__ void accumulate_rows(const PairDev &P, const int *q, long long first_
     const int n0 = P.nm[0], n1 = P.nm[1], n2 = P.nm[2];
     const int st0 = q[0], st1 = q[4], st2 = q[8];
     const int bins = P.bins, mdepth = P.mdepth;
-    const MovT *__restrict__ mov = (const MovT *)P.mov;
+    const PairT *__restrict__ movp = (const PairT *)P.movp;
     for (long long rb = first_batch * 32; rb < R; rb += batch_stride * 32) {
         RowClip mine;
         mine.lo = 0;
@@ -370,14 +415,14 @@ __device__ void accumulate_rows(const PairDev &P, const int *q, long long first_
             for (int i0 = lo; i0 <= hi; i0 += 32) {
                 const int i = i0 + lane;
                 const bool valid = i <= hi;
-                int key = 0;
+                int bf = 0, bm = 0;
                 if (valid) {
                     const int d = i - lo;
-                    const int v = sample_hard<MovT>(mov, n0, n1, n2, U0 + st0 * d, U1 + st1 * d, U2 + st2 * d);
-                    const int bm = (v * bins) >> mdepth;
-                    key = (int)__ldg(frow + i) * bins + bm;
+                    const int v = sample_hard_pair<PairT>(movp, n0, n1, n2, U0 + st0 * d, U1 + st1 * d, U2 + st2 * d);
+                    bm = (v * bins) >> mdepth;
+                    bf = (int)__ldg(frow + i);
                 }
-                H.add(key, valid);
+                H.add(bf, bm, valid);
             }
         }
     }
@@ -435,7 +480,7 @@ __device__ void reduce_entropies(const Hist &H, int B, const QSet &Q, uint32_t *
     for (int r = warp; r < B; r += nwarps) {
         uint32_t rsum = 0;
         for (int c = lane; c < B; c += 32) {
-            const uint32_t v = H.count(r * B + c);
+            const uint32_t v = H.count(r, c);
             if (v) {
                 rsum += v;
                 atomicAdd(&s_cols[c], v);
@@ -452,13 +497,13 @@ __device__ void reduce_entropies(const Hist &H, int B, const QSet &Q, uint32_t *
         block_sum3(n0, z1, z2, s_red);
         if (tid == 0) s_res[3 * kMaxQ] = n0;
     }
-    const int B2 = B * B;
     for (int iq = 0; iq < nq; ++iq) {
         double aj = 0.0, af = 0.0, am = 0.0;
-        for (int c = tid; c < B2; c += blockDim.x) {
-            const uint32_t v = H.count(c);
-            if (v) aj += term(v, iq, Q);
-        }
+        for (int r = warp; r < B; r += nwarps)
+            for (int c = lane; c < B; c += 32) {
+                const uint32_t v = H.count(r, c);
+                if (v) aj += term(v, iq, Q);
+            }
         for (int r = tid; r < B; r += blockDim.x) {
             const uint32_t vf = s_rows[r], vm = s_cols[r];
             if (vf) af += term(vf, iq, Q);
@@ -516,29 +561,30 @@ __device__ void reduce_entropies(const Hist &H, int B, const QSet &Q, uint32_t *
 // Plain form
 // ---------------------------------------------------------------------------
 
-template <typename MovT, int HV>
+template <typename PairT, int HV>
 __global__ void __launch_bounds__(1024, 1)
     k_hist(const PairDev *__restrict__ pairs, const int32_t *__restrict__ aff, uint32_t *__restrict__ ghist,
            int *flags) {
     extern __shared__ __align__(16) unsigned char smem[];
     const PairDev P = pairs[0];
     const int t = blockIdx.y;
-    const int B2 = P.bins * P.bins;
-    const SmemLayout L = smem_layout(HV, P.bins, blockDim.x);
+    const int B = P.bins;
+    const SmemLayout L = smem_layout(HV, B, blockDim.x);
     __shared__ int q[12];
     if (threadIdx.x < 12) q[threadIdx.x] = aff[(size_t)t * 12 + threadIdx.x];
-    auto H = make_hist<HV>(smem, L, B2, flags);
+    auto H = make_hist<HV>(smem, L, B, flags);
     H.zero();
     __syncthreads();
-    const int nwarps = blockDim.x >> 5;
-    accumulate_rows<MovT>(P, q, (long long)blockIdx.x * nwarps + (threadIdx.x >> 5), (long long)gridDim.x * nwarps,
-                          H);
+    const int nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
+    accumulate_rows<PairT>(P, q, (long long)blockIdx.x * nwarps + (threadIdx.x >> 5), (long long)gridDim.x * nwarps,
+                           H);
     __syncthreads();
-    uint32_t *gh = ghist + (size_t)t * B2;
-    for (int c = threadIdx.x; c < B2; c += blockDim.x) {
-        const uint32_t v = H.count(c);
-        if (v) atomicAdd(gh + c, v);
-    }
+    uint32_t *gh = ghist + (size_t)t * B * B;
+    for (int r = threadIdx.x >> 5; r < B; r += nwarps)
+        for (int c = lane; c < B; c += 32) {
+            const uint32_t v = H.count(r, c);
+            if (v) atomicAdd(gh + r * B + c, v);
+        }
 }
 
 // Shared memory of k_entropy: [rows B u32][cols B u32][FP64 scratch, 16-byte aligned].
@@ -551,7 +597,7 @@ __global__ void __launch_bounds__(1024, 1)
     k_entropy(const uint32_t *__restrict__ ghist, int B, QSet Q, Outputs O) {
     extern __shared__ __align__(16) unsigned char smem[];
     const long long t = blockIdx.x;
-    HistGlobal H{ghist + (size_t)t * B * B};
+    HistGlobal H{ghist + (size_t)t * B * B, B};
     reduce_entropies(H, B, Q, (uint32_t *)smem, (uint32_t *)(smem + (size_t)B * 4),
                      (double *)(smem + entropy_red_offset(B)), t, O);
 }
@@ -576,19 +622,20 @@ __global__ void __launch_bounds__(1024, 1)
         if (it >= nitems) break;
         const Item I = items[it];
         const PairDev P = pairs[I.pair];
-        const int B2 = P.bins * P.bins;
+        const int B = P.bins;
         if (threadIdx.x < 12) q[threadIdx.x] = aff[(size_t)I.t * 12 + threadIdx.x];
-        auto H = make_hist<HV>(smem, L, B2, O.flags);
+        auto H = make_hist<HV>(smem, L, B, O.flags);
         H.zero();
         __syncthreads();
         if (P.mdtype == 0)
-            accumulate_rows<uint8_t>(P, q, threadIdx.x >> 5, nwarps, H);
-        else
             accumulate_rows<uint16_t>(P, q, threadIdx.x >> 5, nwarps, H);
+        else
+            accumulate_rows<uint32_t>(P, q, threadIdx.x >> 5, nwarps, H);
         __syncthreads();
         if (O.dump) {
-            uint32_t *dh = O.dump + (size_t)I.t * B2;
-            for (int c = threadIdx.x; c < B2; c += blockDim.x) dh[c] = H.count(c);
+            uint32_t *dh = O.dump + (size_t)I.t * B * B;
+            for (int r = threadIdx.x >> 5; r < B; r += nwarps)
+                for (int c = threadIdx.x & 31; c < B; c += 32) dh[r * B + c] = H.count(r, c);
         }
         reduce_entropies(H, P.bins, Q, (uint32_t *)(smem + L.rows), (uint32_t *)(smem + L.cols),
                          (double *)(smem + L.red), I.t, O);
@@ -652,6 +699,14 @@ cudaError_t launch_clamp_depth(void *data, int dtype, int depth, long long n, cu
     return cudaGetLastError();
 }
 
+cudaError_t launch_make_pairs(const void *mov, int dtype, long long n, int n0, void *out, cudaStream_t s) {
+    if (dtype == 0)
+        k_make_pairs<uint8_t, uint16_t><<<grid_for(n, 256), 256, 0, s>>>((const uint8_t *)mov, n, n0, (uint16_t *)out);
+    else
+        k_make_pairs<uint16_t, uint32_t><<<grid_for(n, 256), 256, 0, s>>>((const uint16_t *)mov, n, n0, (uint32_t *)out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bin_fixed(const void *data, int dtype, int depth, long long n, int bins, uint8_t *out,
                              cudaStream_t s) {
     if (dtype == 0)
@@ -681,8 +736,8 @@ cudaError_t launch_plain_hist(const PairDev *d_pair, const PairDev &h_pair, cons
     } while (0)
 #define MI_LAUNCH_PLAIN_MT(HVV)                          \
     do {                                                 \
-        if (h_pair.mdtype == 0) MI_LAUNCH_PLAIN(uint8_t, HVV); \
-        else MI_LAUNCH_PLAIN(uint16_t, HVV);             \
+        if (h_pair.mdtype == 0) MI_LAUNCH_PLAIN(uint16_t, HVV); \
+        else MI_LAUNCH_PLAIN(uint32_t, HVV);             \
     } while (0)
     switch (variant) {
         case HV_U32: MI_LAUNCH_PLAIN_MT(HV_U32); break;
@@ -808,18 +863,18 @@ __device__ void accumulate_rows_raw(const RawPair &P, const int *q, long long fi
             for (int i0 = lo; i0 <= hi; i0 += 32) {
                 const int i = i0 + lane;
                 const bool valid = i <= hi;
-                int key = 0;
+                int bf = 0, bm = 0;
                 if (valid) {
                     const int d = i - lo;
                     const int v = sample_hard<MovT>(mov, n0, n1, n2, U0 + st0 * d, U1 + st1 * d, U2 + st2 * d);
                     // volumes are read as given (no copy is made, so no clamp on load): values are expected
                     // within the bit depth, and the interpolated value is clamped to it before binning
-                    const int bm = (min(v, (int)((1u << mdepth) - 1u)) * bins) >> mdepth;
+                    bm = (min(v, (int)((1u << mdepth) - 1u)) * bins) >> mdepth;
                     uint32_t fv = (uint32_t)__ldg(frow + i);
                     fv = fv > fvmax ? fvmax : fv;
-                    key = (int)((fv * (uint32_t)bins) >> fdepth) * bins + bm;
+                    bf = (int)((fv * (uint32_t)bins) >> fdepth);
                 }
-                H.add(key, valid);
+                H.add(bf, bm, valid);
             }
         }
     }
@@ -828,21 +883,22 @@ __device__ void accumulate_rows_raw(const RawPair &P, const int *q, long long fi
 template <typename FixT, typename MovT>
 __global__ void __launch_bounds__(1024, 1) k_hist_raw(RawPair P, Q12 A, uint32_t *__restrict__ ghist, int *flags) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int B2 = P.bins * P.bins;
-    const SmemLayout L = smem_layout(HV_U16_MATCH, P.bins, blockDim.x);
+    const int B = P.bins;
+    const SmemLayout L = smem_layout(HV_U16_MATCH, B, blockDim.x);
     __shared__ int q[12];
     if (threadIdx.x < 12) q[threadIdx.x] = A.q[threadIdx.x];
-    auto H = make_hist<HV_U16_MATCH>(smem, L, B2, flags);
+    auto H = make_hist<HV_U16_MATCH>(smem, L, B, flags);
     H.zero();
     __syncthreads();
     const int nwarps = blockDim.x >> 5;
     accumulate_rows_raw<FixT, MovT>(P, q, (long long)blockIdx.x * nwarps + (threadIdx.x >> 5),
                                     (long long)gridDim.x * nwarps, H);
     __syncthreads();
-    for (int c = threadIdx.x; c < B2; c += blockDim.x) {
-        const uint32_t v = H.count(c);
-        if (v) atomicAdd(ghist + c, v);
-    }
+    for (int r = threadIdx.x >> 5; r < B; r += nwarps)
+        for (int c = threadIdx.x & 31; c < B; c += 32) {
+            const uint32_t v = H.count(r, c);
+            if (v) atomicAdd(ghist + r * B + c, v);
+        }
 }
 
 // Entropy term of one count, evaluated directly in FP64: c ln c or c^q.

@@ -16,6 +16,7 @@ constexpr int kOvfSlots = 4096;    // drain table entries (each entry holds >= k
 struct PairDev {
     const uint8_t *fbins;  // fixed volume pre-binned to uint8, x fastest
     const void *mov;       // moving volume, uint8 or uint16, clamped to its bit depth
+    const void *movp;      // x-paired copy: (v[x], v[x+1]) as uint16 (uint8 data) or uint32 (uint16 data)
     int nf[3];             // fixed dims (x, y, z)
     int nm[3];             // moving dims
     int bins;
@@ -59,6 +60,7 @@ size_t hard_smem_bytes(int variant, int bins, int threads);
 // ---- launchers (all asynchronous on `s`) ---------------------------------
 cudaError_t launch_f32_to_u16(const float *in, long long n, uint16_t *out, cudaStream_t s);
 cudaError_t launch_clamp_depth(void *data, int dtype, int depth, long long n, cudaStream_t s);
+cudaError_t launch_make_pairs(const void *mov, int dtype, long long n, int n0, void *out, cudaStream_t s);
 cudaError_t launch_bin_fixed(const void *data, int dtype, int depth, long long n, int bins, uint8_t *out,
                              cudaStream_t s);
 cudaError_t launch_table(double *tab, float q, cudaStream_t s);

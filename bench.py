@@ -293,7 +293,7 @@ def run_profile(args):
     f, m = phantoms.head_pair(shape=SHAPE, spacing=(1, 1, 1), seed=30)
     prm = torch.from_numpy(phantoms.random_transforms(args.profile, seed=31)).cuda()
     ctx = mi.Context(f, m, bins=BINS, fixed_depth=DEPTH, moving_depth=DEPTH, path="batched",
-                     hist_variant=args.variant, autotune=False)
+                     hist_variant=args.variant, autotune=False, block_threads=args.threads)
     for _ in range(args.warmup):
         ctx.eval(prm, QS)
     ms = []
@@ -301,7 +301,7 @@ def run_profile(args):
         ctx.eval(prm, QS)
         ms.append(ctx.last_kernel_ms()[0])
     nvox = int(np.prod(SHAPE))
-    print(json.dumps({"profile": "batched", "transforms": args.profile, "variant": args.variant,
+    print(json.dumps({"profile": "batched", "transforms": args.profile, "variant": args.variant, "threads": args.threads,
                       "kernel_ms": ms, "voxel_transforms_per_s": args.profile * nvox / (np.mean(ms) / 1e3)}))
 
 
@@ -314,7 +314,8 @@ def main():
     ap.add_argument("--skip-extras", action="store_true", help="skip the plain and Parzen lines")
     ap.add_argument("--skip-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--profile", type=int, default=0, help="profile mode: batched kernel only, on this many transforms")
-    ap.add_argument("--variant", type=int, default=3, help="histogram variant in profile mode (MI_HV_*)")
+    ap.add_argument("--variant", type=int, default=2, help="histogram variant in profile mode (MI_HV_*)")
+    ap.add_argument("--threads", type=int, default=1024, help="CTA size in profile mode (512 or 1024)")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)

@@ -89,7 +89,12 @@ enum {
     MI_HV_U32 = 0,        /* 32-bit shared counters, one atomic per voxel        */
     MI_HV_U32_MATCH = 1,  /* 32-bit counters, warp-aggregated (match.any)        */
     MI_HV_U16 = 2,        /* 16-bit packed counters drained at 2^14              */
-    MI_HV_U16_MATCH = 3   /* 16-bit packed counters, warp-aggregated             */
+    MI_HV_U16_MATCH = 3,  /* 16-bit packed counters, warp-aggregated             */
+    /* the same four with the moving volume read through the texture path */
+    MI_HV_U32_TEX = 4,
+    MI_HV_U32_MATCH_TEX = 5,
+    MI_HV_U16_TEX = 6,
+    MI_HV_U16_MATCH_TEX = 7
 };
 /* Evaluation path of mi_eval. */
 enum { MI_PATH_AUTO = 0, MI_PATH_PLAIN = 1, MI_PATH_BATCHED = 2 };
@@ -108,6 +113,7 @@ typedef struct {
     int use_graphs;    /* 1 (default): replay the batched launch as a CUDA graph   */
     int autotune;      /* 1 (default): time the variants once per shape and cache  */
     int device;        /* CUDA device ordinal; -1 (default) = the current device   */
+    int block_threads; /* hard-path CTA size: 0 (default) = autotuned, or 512 / 1024 */
 } mi_options;
 
 typedef struct mi_ctx mi_ctx;

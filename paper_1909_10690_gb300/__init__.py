@@ -21,6 +21,7 @@ from . import _lib
 
 MI_OK, MI_EINVAL, MI_ENOMEM, MI_ECUDA, MI_EEMPTY, MI_EUNSUPPORTED, MI_ERANGE = range(7)
 HV_AUTO, HV_U32, HV_U32_MATCH, HV_U16, HV_U16_MATCH = -1, 0, 1, 2, 3
+HV_U32_TEX, HV_U32_MATCH_TEX, HV_U16_TEX, HV_U16_MATCH_TEX = 4, 5, 6, 7
 PATH_AUTO, PATH_PLAIN, PATH_BATCHED = 0, 1, 2
 _DT = {np.dtype(np.uint8): 0, np.dtype(np.uint16): 1, np.dtype(np.float32): 2}
 
@@ -98,7 +99,7 @@ def _volume(x, spacing, depth):
     return v, arg
 
 
-def _options(kernel, tsallis_form, bits, hist_variant, path, use_graphs, autotune, device):
+def _options(kernel, tsallis_form, bits, hist_variant, path, use_graphs, autotune, device, block_threads=0):
     o = _lib.MiOptions()
     load().mi_options_default(ctypes.byref(o))
     o.kernel = {"hard": 0, "parzen": 1}[kernel]
@@ -109,6 +110,7 @@ def _options(kernel, tsallis_form, bits, hist_variant, path, use_graphs, autotun
     o.use_graphs = int(bool(use_graphs))
     o.autotune = int(bool(autotune))
     o.device = -1 if device is None else int(device)
+    o.block_threads = int(block_threads)
     return o
 
 
@@ -134,11 +136,11 @@ class Context:
     def __init__(self, fixed=None, moving=None, bins=64, fixed_spacing=(1.0, 1.0, 1.0),
                  moving_spacing=(1.0, 1.0, 1.0), fixed_depth=None, moving_depth=None, kernel="hard",
                  tsallis_form="additive", bits=False, hist_variant=HV_AUTO, path="auto", use_graphs=True,
-                 autotune=True, device=None, pairs=None):
+                 autotune=True, device=None, pairs=None, block_threads=0):
         self._lib = load()
         self._h = ctypes.c_void_p()
         self.kernel = kernel
-        opt = _options(kernel, tsallis_form, bits, hist_variant, path, use_graphs, autotune, device)
+        opt = _options(kernel, tsallis_form, bits, hist_variant, path, use_graphs, autotune, device, block_threads)
         if pairs is None:
             pairs = [dict(fixed=fixed, moving=moving, bins=bins, fixed_spacing=fixed_spacing,
                           moving_spacing=moving_spacing, fixed_depth=fixed_depth, moving_depth=moving_depth)]

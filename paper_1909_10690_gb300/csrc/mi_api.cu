@@ -187,7 +187,13 @@ struct Pair {
     int mdtype;  // stored moving type: 0 u8, 1 u16
     long long nvf, nvm;
     DevBuf fbins, mov, movp;    // hard path (movp: x-paired moving volume)
+    cudaArray_t arr = nullptr;  // the pairs as a 3D array, read through tex
+    cudaTextureObject_t tex = 0;
     DevBuf pfbins, pmov;        // Parzen path
+    ~Pair() {
+        if (tex) cudaDestroyTextureObject(tex);
+        if (arr) cudaFreeArray(arr);
+    }
 };
 
 struct Choice {
@@ -379,8 +385,31 @@ mi_status add_pair(mi_ctx *ctx, const mi_volume *fx, const mi_volume *mv, int bi
             P->mdtype = mv->dtype == MI_U8 ? 0 : 1;
             MI_CU(launch_clamp_depth(P->mov.p, P->mdtype, P->mdepth, P->nvm, s), "clamping the moving volume");
         }
-        MI_CU(P->movp.ensure((size_t)P->nvm * (P->mdtype == 0 ? 2 : 4)), "allocating the paired moving volume");
-        MI_CU(launch_make_pairs(P->mov.p, P->mdtype, P->nvm, P->nm[0], P->movp.p, s), "pairing the moving volume");
+        const size_t npairs = (size_t)P->nm[0] * (P->nm[1] + 1) * (P->nm[2] + 1);
+        MI_CU(P->movp.ensure(npairs * (P->mdtype == 0 ? 2 : 4)), "allocating the paired moving volume");
+        MI_CU(launch_make_pairs(P->mov.p, P->mdtype, P->nm, P->movp.p, s), "pairing the moving volume");
+        // the same pairs (without the padding row / plane) as a 3D array for the texture path
+        const size_t esz = P->mdtype == 0 ? 2 : 4;
+        cudaChannelFormatDesc cd = cudaCreateChannelDesc((int)esz * 8, 0, 0, 0, cudaChannelFormatKindUnsigned);
+        MI_CU(cudaMalloc3DArray(&P->arr, &cd, make_cudaExtent(P->nm[0], P->nm[1], P->nm[2])), "allocating the 3D array");
+        cudaMemcpy3DParms cp;
+        memset(&cp, 0, sizeof cp);
+        cp.srcPtr = make_cudaPitchedPtr(P->movp.p, (size_t)P->nm[0] * esz, P->nm[0], P->nm[1] + 1);
+        cp.dstArray = P->arr;
+        cp.extent = make_cudaExtent(P->nm[0], P->nm[1], P->nm[2]);
+        cp.kind = cudaMemcpyDeviceToDevice;
+        MI_CU(cudaMemcpy3DAsync(&cp, s), "filling the 3D array");
+        cudaResourceDesc rd;
+        memset(&rd, 0, sizeof rd);
+        rd.resType = cudaResourceTypeArray;
+        rd.res.array.array = P->arr;
+        cudaTextureDesc td;
+        memset(&td, 0, sizeof td);
+        td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
+        td.filterMode = cudaFilterModePoint;
+        td.readMode = cudaReadModeElementType;
+        td.normalizedCoords = 0;
+        MI_CU(cudaCreateTextureObject(&P->tex, &rd, &td, nullptr), "creating the texture object");
     }
     MI_CU(cudaStreamSynchronize(s), "preparing the volumes");
     ctx->max_bins = std::max(ctx->max_bins, bins);
@@ -397,6 +426,7 @@ mi_status upload_pairs(mi_ctx *ctx) {
         d.fbins = P.fbins.as<uint8_t>();
         d.mov = P.mov.p;
         d.movp = P.movp.p;
+        d.texp = P.tex;
         for (int a = 0; a < 3; ++a) {
             d.nf[a] = P.nf[a];
             d.nm[a] = P.nm[a];
@@ -417,6 +447,7 @@ PairDev host_pairdev(const Pair &P) {
     d.fbins = P.fbins.as<uint8_t>();
     d.mov = P.mov.p;
     d.movp = P.movp.p;
+    d.texp = P.tex;
     for (int a = 0; a < 3; ++a) {
         d.nf[a] = P.nf[a];
         d.nm[a] = P.nm[a];
@@ -451,8 +482,12 @@ mi_status create_common(mi_ctx **out, const mi_volume *fixed, const mi_volume *m
         g_create_error = "the Parzen form takes one pair per context";
         return MI_EINVAL;
     }
-    if (ctx->opt.hist_variant < MI_HV_AUTO || ctx->opt.hist_variant > MI_HV_U16_MATCH) {
+    if (ctx->opt.hist_variant < MI_HV_AUTO || ctx->opt.hist_variant > MI_HV_U16_MATCH_TEX) {
         g_create_error = "opt.hist_variant out of range";
+        return MI_EINVAL;
+    }
+    if (ctx->opt.block_threads != 0 && ctx->opt.block_threads != 512 && ctx->opt.block_threads != 1024) {
+        g_create_error = "opt.block_threads must be 0, 512 or 1024";
         return MI_EINVAL;
     }
     int ndev = 0;
@@ -584,7 +619,7 @@ mi_status deliver(mi_ctx *ctx, void *dst, const void *src, size_t bytes) {
 // ---------------------------------------------------------------------------
 
 bool variant_fits(int variant, int bins, int threads, long long nvox) {
-    const bool u16 = variant == HV_U16 || variant == HV_U16_MATCH;
+    const bool u16 = (variant % HV_TEX) == HV_U16 || (variant % HV_TEX) == HV_U16_MATCH;
     if (u16 && nvox > (long long)(kOvfSlots / 2) * kDrainT) return false;
     return hard_smem_bytes(variant, bins, threads) <= 227 * 1024;
 }
@@ -592,9 +627,10 @@ bool variant_fits(int variant, int bins, int threads, long long nvox) {
 std::vector<Choice> candidates(mi_ctx *ctx, int bins, long long nvox_max) {
     std::vector<Choice> c;
     const int fixed_v = ctx->opt.hist_variant;
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < HV_COUNT; ++v) {
         if (fixed_v >= 0 && v != fixed_v) continue;
         for (int th : {512, 1024}) {
+            if (ctx->opt.block_threads > 0 && th != ctx->opt.block_threads) continue;
             if (!variant_fits(v, bins, th, nvox_max)) continue;
             Choice ch;
             ch.variant = v;
@@ -683,9 +719,9 @@ mi_status autotune(mi_ctx *ctx, int nitems, const QSet &Q, const Outputs &O, Cho
     if (cands.empty()) return ctx->fail(MI_EUNSUPPORTED, "no histogram variant fits this bin count and volume size");
     if (cands.size() == 1 || !ctx->opt.autotune) {
         best = cands.front();
-        // heuristic: prefer 32-bit counters with warp aggregation, 1024 threads
+        // heuristic: plain shared atomics (32-bit counters where they fit), 1024 threads
         for (const Choice &c : cands)
-            if (c.variant == HV_U32_MATCH && c.threads == 1024) best = c;
+            if ((c.variant == HV_U32 || (c.variant == HV_U16 && best.variant != HV_U32)) && c.threads == 1024) best = c;
         if (best.variant < 0) best = cands.front();
         return MI_OK;
     }
@@ -811,7 +847,7 @@ mi_status eval_core(mi_ctx *ctx, const EvalReq &R, const float *qv, int nq, doub
         } else {
             ch = cands.front();
             for (const Choice &c : cands)
-                if (c.variant == (ctx->max_bins <= 181 ? HV_U32_MATCH : HV_U16_MATCH) && c.threads == 1024) ch = c;
+                if (c.variant == (ctx->max_bins <= 181 ? HV_U32 : HV_U16) && c.threads == 1024) ch = c;
             ctx->tuned[key] = ch;
         }
         st = run_plain(ctx, 0, d_aff, n, Q, O, ch, R.dump);
@@ -976,6 +1012,7 @@ void mi_options_default(mi_options *opt) {
     opt->use_graphs = 1;
     opt->autotune = 1;
     opt->device = -1;
+    opt->block_threads = 0;
 }
 
 const char *mi_version(void) { return "gb300-mi 0.1 (sm_103a)"; }

@@ -103,32 +103,63 @@ __device__ __forceinline__ int sample_hard(const MovT *__restrict__ mov, int n0,
     return lerp8(g0, g1, fz);
 }
 
-// The same resample from the x-paired moving volume: element x holds v[x] in its
-// low half and v[min(x + 1, n0 - 1)] in its high half (uint16 pairs of a uint8
-// volume, uint32 pairs of a uint16 volume), so one voxel takes 4 loads, not 8.
+// The same resample from the padded x-paired moving volume: element (x, y, z)
+// holds v[x] in its low half and v[min(x + 1, n0 - 1)] in its high half
+// (uint16 pairs of a uint8 volume, uint32 pairs of a uint16 volume), and the
+// volume carries one extra y row and one extra z plane repeating the last
+// ones, so the three neighbour offsets are constants (n0, n0 (n1 + 1)) and a
+// voxel takes 4 loads.  On the last plane of an axis the weight of the upper
+// neighbour is 0, so the repeated values change nothing.
+// Each stage lerp is (a (256 - f) + b f + 128) >> 8.
+__device__ __forceinline__ int lerp8g(int a, int b, int f, int g) { return (a * g + b * f + 128) >> 8; }
+
 template <typename PairT>
-__device__ __forceinline__ int sample_hard_pair(const PairT *__restrict__ movp, int n0, int n1, int n2, int ux, int uy,
-                                                int uz) {
+__device__ __forceinline__ int sample_hard_pair(const PairT *__restrict__ movp, int sy, int sz, int n0, int n01p,
+                                                int ux, int uy, int uz) {
     constexpr int HB = (int)sizeof(PairT) * 4;  // bits per half
     constexpr uint32_t LO = (1u << HB) - 1u;
-    const int ix = ux >> 16, iy = uy >> 16, iz = uz >> 16;
-    const int fx = (ux >> 8) & 255, fy = (uy >> 8) & 255, fz = (uz >> 8) & 255;
-    const int sy = iy < n1 - 1 ? n0 : 0;
-    const int sz = iz < n2 - 1 ? n0 * n1 : 0;
-    const PairT *p = movp + (ix + n0 * (iy + n1 * iz));
+    const int fx = (int)__byte_perm((unsigned)ux, 0u, 0x4441), fy = (int)__byte_perm((unsigned)uy, 0u, 0x4441),
+              fz = (int)__byte_perm((unsigned)uz, 0u, 0x4441);
+    const int gx = 256 - fx, gy = 256 - fy, gz = 256 - fz;
+    const int idx = (ux >> 16) + n0 * (uy >> 16) + n01p * (uz >> 16);
+    const PairT *p = movp + idx;
     const uint32_t a = __ldg(p), b = __ldg(p + sy), c = __ldg(p + sz), d = __ldg(p + sz + sy);
-    const int e00 = lerp8((int)(a & LO), (int)(a >> HB), fx), e01 = lerp8((int)(b & LO), (int)(b >> HB), fx);
-    const int e10 = lerp8((int)(c & LO), (int)(c >> HB), fx), e11 = lerp8((int)(d & LO), (int)(d >> HB), fx);
-    const int g0 = lerp8(e00, e01, fy), g1 = lerp8(e10, e11, fy);
-    return lerp8(g0, g1, fz);
+    const int e00 = lerp8g((int)(a & LO), (int)(a >> HB), fx, gx), e01 = lerp8g((int)(b & LO), (int)(b >> HB), fx, gx);
+    const int e10 = lerp8g((int)(c & LO), (int)(c >> HB), fx, gx), e11 = lerp8g((int)(d & LO), (int)(d >> HB), fx, gx);
+    const int g0 = lerp8g(e00, e01, fy, gy), g1 = lerp8g(e10, e11, fy, gy);
+    return lerp8g(g0, g1, fz, gz);
 }
 
-template <typename T, typename PairT>
-__global__ void k_make_pairs(const T *__restrict__ in, long long n, int n0, PairT *__restrict__ out) {
+// The same resample with the four x-pairs fetched through the texture path
+// from a 3D array of pairs (block-linear layout, point sampling at texel
+// centres, clamped addressing: exact integer texels).
+template <typename PairT>
+__device__ __forceinline__ int sample_hard_tex(unsigned long long tex, int ux, int uy, int uz) {
     constexpr int HB = (int)sizeof(PairT) * 4;
-    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x) {
-        const bool last = (x % n0) == n0 - 1;
-        out[x] = (PairT)((uint32_t)in[x] | ((uint32_t)in[last ? x : x + 1] << HB));
+    constexpr uint32_t LO = (1u << HB) - 1u;
+    const int fx = (int)__byte_perm((unsigned)ux, 0u, 0x4441), fy = (int)__byte_perm((unsigned)uy, 0u, 0x4441),
+              fz = (int)__byte_perm((unsigned)uz, 0u, 0x4441);
+    const int gx = 256 - fx, gy = 256 - fy, gz = 256 - fz;
+    const float x = (float)(ux >> 16) + 0.5f, y = (float)(uy >> 16) + 0.5f, z = (float)(uz >> 16) + 0.5f;
+    const uint32_t a = tex3D<PairT>(tex, x, y, z), b = tex3D<PairT>(tex, x, y + 1.0f, z);
+    const uint32_t c = tex3D<PairT>(tex, x, y, z + 1.0f), d = tex3D<PairT>(tex, x, y + 1.0f, z + 1.0f);
+    const int e00 = lerp8g((int)(a & LO), (int)(a >> HB), fx, gx), e01 = lerp8g((int)(b & LO), (int)(b >> HB), fx, gx);
+    const int e10 = lerp8g((int)(c & LO), (int)(c >> HB), fx, gx), e11 = lerp8g((int)(d & LO), (int)(d >> HB), fx, gx);
+    const int g0 = lerp8g(e00, e01, fy, gy), g1 = lerp8g(e10, e11, fy, gy);
+    return lerp8g(g0, g1, fz, gz);
+}
+
+// Builds the padded x-paired volume: out has dims (n0, n1 + 1, n2 + 1).
+template <typename T, typename PairT>
+__global__ void k_make_pairs(const T *__restrict__ in, int n0, int n1, int n2, PairT *__restrict__ out) {
+    constexpr int HB = (int)sizeof(PairT) * 4;
+    const long long n = (long long)n0 * (n1 + 1) * (n2 + 1);
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n; o += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(o % n0);
+        const int y = min((int)((o / n0) % (n1 + 1)), n1 - 1);
+        const int z = min((int)(o / ((long long)n0 * (n1 + 1))), n2 - 1);
+        const long long src = x + (long long)n0 * (y + (long long)n1 * z);
+        out[o] = (PairT)((uint32_t)in[src] | ((uint32_t)in[x < n0 - 1 ? src + 1 : src] << HB));
     }
 }
 
@@ -187,6 +218,37 @@ __device__ RowClip clip_row(const int *q, int j, int k, int nf0, const int nm[3]
         r.u2 = (int)(base[2] + (long long)st[2] * lo);
     }
     return r;
+}
+
+// Exact interval [lo, hi] of i in [0, nf0) with 0 <= base + st i <= umax (one axis).
+__device__ void clip_axis(long long base, int st, long long umax, int nf0, int &lo, int &hi) {
+    lo = 0;
+    hi = nf0 - 1;
+    if (st == 0) {
+        if (base < 0 || base > umax) {
+            lo = nf0;
+            hi = -1;
+        }
+        return;
+    }
+    long long b1[3] = {base, 0, 0}, um[3] = {umax, 0x7fffffffffffffffll, 0x7fffffffffffffffll};
+    int s1[3] = {st, 0, 0};
+    // float estimate within one voxel of the truth, then the exact fix-up of clip_row
+    const float fb = (float)base, fs = (float)st, fm = (float)umax;
+    const float e0 = -fb / fs, e1 = (fm - fb) / fs;
+    float a0 = fminf(e0, e1), a1 = fmaxf(e0, e1);
+    a0 = fminf(fmaxf(a0, -2.0f), (float)nf0 + 1.0f);
+    a1 = fminf(fmaxf(a1, -2.0f), (float)nf0 + 1.0f);
+    lo = max(lo, (int)ceilf(a0));
+    hi = min(hi, (int)floorf(a1));
+    while (lo <= hi && !inside_at(b1, s1, um, lo)) ++lo;
+    while (lo > 0 && lo <= nf0 && inside_at(b1, s1, um, lo - 1)) --lo;
+    while (hi >= lo && !inside_at(b1, s1, um, hi)) --hi;
+    while (hi >= lo && hi < nf0 - 1 && inside_at(b1, s1, um, hi + 1)) ++hi;
+    if (hi < lo && lo < nf0 && inside_at(b1, s1, um, lo)) {
+        hi = lo;
+        while (hi < nf0 - 1 && inside_at(b1, s1, um, hi + 1)) ++hi;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -333,7 +395,7 @@ struct SmemLayout {
 __host__ __device__ inline SmemLayout smem_layout(int variant, int bins, int threads) {
     SmemLayout L;
     const size_t B2 = (size_t)bins * bins;
-    const bool u16 = variant == HV_U16 || variant == HV_U16_MATCH;
+    const bool u16 = (variant % HV_TEX) == HV_U16 || (variant % HV_TEX) == HV_U16_MATCH;
     const size_t S = (size_t)bins + 1, H = ((size_t)bins + 1) / 2;
     size_t o = 0;
     L.hist = o;
@@ -389,41 +451,60 @@ __device__ typename HistOf<HV>::T make_hist(unsigned char *smem, const SmemLayou
 // then the warp walks the 32 clipped rows 32 voxels at a time.
 // ---------------------------------------------------------------------------
 
-template <typename PairT, class Hist>
-__device__ void accumulate_rows(const PairDev &P, const int *q, long long first_batch, long long batch_stride,
+// Row order: the CTA walks blocks of nwarps adjacent fixed rows (block blk
+// holds rows blk * nwarps + w) and warp w takes row w of each block, so at any
+// time the warps of a CTA sample neighbouring moving lines (row j's upper y
+// neighbours are row j + 1's samples) and the moving lines they touch stay
+// in L1.  Lanes 0..2 clip the row on one axis each (exactly, in 64 bits); the
+// warp then walks the overlap interval 32 voxels at a time.  Blocks are
+// first_block, first_block + block_stride, ...
+template <typename PairT, bool TEX, class Hist>
+__device__ void accumulate_rows(const PairDev &P, const int *q, long long first_block, long long block_stride,
                                 Hist &H) {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int nf0 = P.nf[0], nf1 = P.nf[1];
     const long long R = (long long)nf1 * P.nf[2];
-    const int n0 = P.nm[0], n1 = P.nm[1], n2 = P.nm[2];
+    const int n0 = P.nm[0], sy = n0, sz = n0 * (P.nm[1] + 1);
     const int st0 = q[0], st1 = q[4], st2 = q[8];
     const int bins = P.bins, mdepth = P.mdepth;
     const PairT *__restrict__ movp = (const PairT *)P.movp;
-    for (long long rb = first_batch * 32; rb < R; rb += batch_stride * 32) {
-        RowClip mine;
-        mine.lo = 0;
-        mine.hi = -1;
-        mine.u0 = mine.u1 = mine.u2 = 0;
-        const long long r = rb + lane;
-        if (r < R) mine = clip_row(q, (int)(r % nf1), (int)(r / nf1), nf0, P.nm);
-        for (int s = 0; s < 32; ++s) {
-            const int lo = __shfl_sync(kFull, mine.lo, s), hi = __shfl_sync(kFull, mine.hi, s);
-            if (lo > hi) continue;  // warp-uniform
-            const int U0 = __shfl_sync(kFull, mine.u0, s), U1 = __shfl_sync(kFull, mine.u1, s),
-                      U2 = __shfl_sync(kFull, mine.u2, s);
-            const uint8_t *__restrict__ frow = P.fbins + (size_t)(rb + s) * nf0;
-            for (int i0 = lo; i0 <= hi; i0 += 32) {
-                const int i = i0 + lane;
-                const bool valid = i <= hi;
-                int bf = 0, bm = 0;
-                if (valid) {
-                    const int d = i - lo;
-                    const int v = sample_hard_pair<PairT>(movp, n0, n1, n2, U0 + st0 * d, U1 + st1 * d, U2 + st2 * d);
-                    bm = (v * bins) >> mdepth;
-                    bf = (int)__ldg(frow + i);
-                }
-                H.add(bf, bm, valid);
+    const int la = lane < 3 ? lane : 0;
+    const int stl = q[4 * la];
+    const long long uml = (long long)(P.nm[la] - 1) << 16;
+    for (long long blk = first_block; blk * nwarps < R; blk += block_stride) {
+        const long long r = blk * nwarps + warp;
+        if (r >= R) break;
+        const int j = (int)(r % nf1), k = (int)(r / nf1);
+        int lo = 0, hi = nf0 - 1;
+        long long base = 0;
+        if (lane < 3) {
+            base = (long long)q[4 * la + 1] * j + (long long)q[4 * la + 2] * k + (long long)q[4 * la + 3];
+            clip_axis(base, stl, uml, nf0, lo, hi);
+        }
+        lo = max(lo, max(__shfl_sync(kFull, lo, 1), __shfl_sync(kFull, lo, 2)));
+        lo = __shfl_sync(kFull, lo, 0);
+        hi = min(hi, min(__shfl_sync(kFull, hi, 1), __shfl_sync(kFull, hi, 2)));
+        hi = __shfl_sync(kFull, hi, 0);
+        if (lo > hi) continue;  // warp-uniform
+        const int ul = (int)(base + (long long)stl * lo);  // in range on lanes 0..2
+        // unsigned: lanes past the row end may step outside the int range; only in-range lanes use them
+        unsigned U0 = (unsigned)__shfl_sync(kFull, ul, 0) + (unsigned)st0 * lane,
+                 U1 = (unsigned)__shfl_sync(kFull, ul, 1) + (unsigned)st1 * lane,
+                 U2 = (unsigned)__shfl_sync(kFull, ul, 2) + (unsigned)st2 * lane;
+        const uint8_t *__restrict__ frow = P.fbins + (size_t)r * nf0;
+        for (int i = lo + lane; i - lane <= hi; i += 32) {
+            const bool valid = i <= hi;
+            int bf = 0, bm = 0;
+            if (valid) {
+                const int v = TEX ? sample_hard_tex<PairT>(P.texp, (int)U0, (int)U1, (int)U2)
+                                  : sample_hard_pair<PairT>(movp, sy, sz, n0, sz, (int)U0, (int)U1, (int)U2);
+                bm = (v * bins) >> mdepth;
+                bf = (int)__ldg(frow + i);
             }
+            H.add(bf, bm, valid);
+            U0 += 32u * (unsigned)st0;
+            U1 += 32u * (unsigned)st1;
+            U2 += 32u * (unsigned)st2;
         }
     }
 }
@@ -561,7 +642,7 @@ __device__ void reduce_entropies(const Hist &H, int B, const QSet &Q, uint32_t *
 // Plain form
 // ---------------------------------------------------------------------------
 
-template <typename PairT, int HV>
+template <typename PairT, int HV, bool TEX>
 __global__ void __launch_bounds__(1024, 1)
     k_hist(const PairDev *__restrict__ pairs, const int32_t *__restrict__ aff, uint32_t *__restrict__ ghist,
            int *flags) {
@@ -571,13 +652,14 @@ __global__ void __launch_bounds__(1024, 1)
     const int B = P.bins;
     const SmemLayout L = smem_layout(HV, B, blockDim.x);
     __shared__ int q[12];
+    __shared__ int s_next;
     if (threadIdx.x < 12) q[threadIdx.x] = aff[(size_t)t * 12 + threadIdx.x];
+    if (threadIdx.x == 0) s_next = 0;
     auto H = make_hist<HV>(smem, L, B, flags);
     H.zero();
     __syncthreads();
     const int nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
-    accumulate_rows<PairT>(P, q, (long long)blockIdx.x * nwarps + (threadIdx.x >> 5), (long long)gridDim.x * nwarps,
-                           H);
+    accumulate_rows<PairT, TEX>(P, q, blockIdx.x, gridDim.x, H);
     __syncthreads();
     uint32_t *gh = ghist + (size_t)t * B * B;
     for (int r = threadIdx.x >> 5; r < B; r += nwarps)
@@ -606,12 +688,13 @@ __global__ void __launch_bounds__(1024, 1)
 // Batched form: persistent CTAs, one (pair, transform) item per CTA at a time
 // ---------------------------------------------------------------------------
 
-template <int HV>
+template <int HV, bool TEX>
 __global__ void __launch_bounds__(1024, 1)
     k_batched(const PairDev *__restrict__ pairs, const int32_t *__restrict__ aff, const Item *__restrict__ items,
               int nitems, int *ticket, int max_bins, QSet Q, Outputs O) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item;
+    __shared__ int s_next;
     __shared__ int q[12];
     const SmemLayout L = smem_layout(HV, max_bins, blockDim.x);
     const int nwarps = blockDim.x >> 5;
@@ -624,13 +707,14 @@ __global__ void __launch_bounds__(1024, 1)
         const PairDev P = pairs[I.pair];
         const int B = P.bins;
         if (threadIdx.x < 12) q[threadIdx.x] = aff[(size_t)I.t * 12 + threadIdx.x];
+        if (threadIdx.x == 0) s_next = 0;
         auto H = make_hist<HV>(smem, L, B, O.flags);
         H.zero();
         __syncthreads();
         if (P.mdtype == 0)
-            accumulate_rows<uint16_t>(P, q, threadIdx.x >> 5, nwarps, H);
+            accumulate_rows<uint16_t, TEX>(P, q, 0, 1, H);
         else
-            accumulate_rows<uint32_t>(P, q, threadIdx.x >> 5, nwarps, H);
+            accumulate_rows<uint32_t, TEX>(P, q, 0, 1, H);
         __syncthreads();
         if (O.dump) {
             uint32_t *dh = O.dump + (size_t)I.t * B * B;
@@ -699,11 +783,14 @@ cudaError_t launch_clamp_depth(void *data, int dtype, int depth, long long n, cu
     return cudaGetLastError();
 }
 
-cudaError_t launch_make_pairs(const void *mov, int dtype, long long n, int n0, void *out, cudaStream_t s) {
+cudaError_t launch_make_pairs(const void *mov, int dtype, const int nm[3], void *out, cudaStream_t s) {
+    const long long n = (long long)nm[0] * (nm[1] + 1) * (nm[2] + 1);
     if (dtype == 0)
-        k_make_pairs<uint8_t, uint16_t><<<grid_for(n, 256), 256, 0, s>>>((const uint8_t *)mov, n, n0, (uint16_t *)out);
+        k_make_pairs<uint8_t, uint16_t><<<grid_for(n, 256), 256, 0, s>>>((const uint8_t *)mov, nm[0], nm[1], nm[2],
+                                                                          (uint16_t *)out);
     else
-        k_make_pairs<uint16_t, uint32_t><<<grid_for(n, 256), 256, 0, s>>>((const uint16_t *)mov, n, n0, (uint32_t *)out);
+        k_make_pairs<uint16_t, uint32_t><<<grid_for(n, 256), 256, 0, s>>>((const uint16_t *)mov, nm[0], nm[1], nm[2],
+                                                                           (uint32_t *)out);
     return cudaGetLastError();
 }
 
@@ -728,22 +815,27 @@ cudaError_t launch_plain_hist(const PairDev *d_pair, const PairDev &h_pair, cons
     if (e != cudaSuccess) return e;
     const size_t smem = smem_layout(variant, h_pair.bins, threads).total;
     dim3 grid(ctas, n);
-#define MI_LAUNCH_PLAIN(MT, HVV)                                                         \
+#define MI_LAUNCH_PLAIN(MT, HVV, TX)                                                     \
     do {                                                                                 \
-        auto kf = k_hist<MT, HVV>;                                                       \
+        auto kf = k_hist<MT, HVV, TX>;                                                   \
         if ((e = set_smem(kf, smem)) != cudaSuccess) return e;                           \
         kf<<<grid, threads, smem, s>>>(d_pair, d_aff, d_hist, d_flags);                  \
     } while (0)
-#define MI_LAUNCH_PLAIN_MT(HVV)                          \
-    do {                                                 \
-        if (h_pair.mdtype == 0) MI_LAUNCH_PLAIN(uint16_t, HVV); \
-        else MI_LAUNCH_PLAIN(uint32_t, HVV);             \
+#define MI_LAUNCH_PLAIN_MT(HVV, TX)                                \
+    do {                                                           \
+        if (h_pair.mdtype == 0) MI_LAUNCH_PLAIN(uint16_t, HVV, TX); \
+        else MI_LAUNCH_PLAIN(uint32_t, HVV, TX);                   \
     } while (0)
-    switch (variant) {
-        case HV_U32: MI_LAUNCH_PLAIN_MT(HV_U32); break;
-        case HV_U32_MATCH: MI_LAUNCH_PLAIN_MT(HV_U32_MATCH); break;
-        case HV_U16: MI_LAUNCH_PLAIN_MT(HV_U16); break;
-        default: MI_LAUNCH_PLAIN_MT(HV_U16_MATCH); break;
+    const bool tex = variant >= HV_TEX;
+    switch (variant % HV_TEX) {
+        case HV_U32: if (tex) MI_LAUNCH_PLAIN_MT(HV_U32, true); else MI_LAUNCH_PLAIN_MT(HV_U32, false); break;
+        case HV_U32_MATCH:
+            if (tex) MI_LAUNCH_PLAIN_MT(HV_U32_MATCH, true); else MI_LAUNCH_PLAIN_MT(HV_U32_MATCH, false);
+            break;
+        case HV_U16: if (tex) MI_LAUNCH_PLAIN_MT(HV_U16, true); else MI_LAUNCH_PLAIN_MT(HV_U16, false); break;
+        default:
+            if (tex) MI_LAUNCH_PLAIN_MT(HV_U16_MATCH, true); else MI_LAUNCH_PLAIN_MT(HV_U16_MATCH, false);
+            break;
     }
 #undef MI_LAUNCH_PLAIN_MT
 #undef MI_LAUNCH_PLAIN
@@ -761,10 +853,14 @@ cudaError_t launch_entropy(const uint32_t *d_hist, int n, int bins, const QSet &
 
 static const void *batched_fn(int variant) {
     switch (variant) {
-        case HV_U32: return (const void *)k_batched<HV_U32>;
-        case HV_U32_MATCH: return (const void *)k_batched<HV_U32_MATCH>;
-        case HV_U16: return (const void *)k_batched<HV_U16>;
-        default: return (const void *)k_batched<HV_U16_MATCH>;
+        case HV_U32: return (const void *)k_batched<HV_U32, false>;
+        case HV_U32_MATCH: return (const void *)k_batched<HV_U32_MATCH, false>;
+        case HV_U16: return (const void *)k_batched<HV_U16, false>;
+        case HV_U16_MATCH: return (const void *)k_batched<HV_U16_MATCH, false>;
+        case HV_TEX + HV_U32: return (const void *)k_batched<HV_U32, true>;
+        case HV_TEX + HV_U32_MATCH: return (const void *)k_batched<HV_U32_MATCH, true>;
+        case HV_TEX + HV_U16: return (const void *)k_batched<HV_U16, true>;
+        default: return (const void *)k_batched<HV_U16_MATCH, true>;
     }
 }
 
@@ -784,23 +880,9 @@ cudaError_t launch_batched(const PairDev *d_pairs, const int32_t *d_aff, const I
     const void *fn = batched_fn(variant);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    switch (variant) {
-        case HV_U32:
-            k_batched<HV_U32><<<ctas, threads, smem, s>>>(d_pairs, d_aff, d_items, nitems, d_ticket, max_bins, Q, O);
-            break;
-        case HV_U32_MATCH:
-            k_batched<HV_U32_MATCH><<<ctas, threads, smem, s>>>(d_pairs, d_aff, d_items, nitems, d_ticket, max_bins, Q,
-                                                                O);
-            break;
-        case HV_U16:
-            k_batched<HV_U16><<<ctas, threads, smem, s>>>(d_pairs, d_aff, d_items, nitems, d_ticket, max_bins, Q, O);
-            break;
-        default:
-            k_batched<HV_U16_MATCH><<<ctas, threads, smem, s>>>(d_pairs, d_aff, d_items, nitems, d_ticket, max_bins, Q,
-                                                                O);
-            break;
-    }
-    return cudaGetLastError();
+    void *args[] = {(void *)&d_pairs, (void *)&d_aff, (void *)&d_items, (void *)&nitems, (void *)&d_ticket,
+                    (void *)&max_bins, (void *)&Q, (void *)&O};
+    return cudaLaunchKernel(fn, dim3(ctas), dim3(threads), args, smem, s);
 }
 
 cudaError_t launch_resample(const PairDev *d_pair, const PairDev &h_pair, const int32_t *d_aff, void *out,

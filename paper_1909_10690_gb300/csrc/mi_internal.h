@@ -16,7 +16,8 @@ constexpr int kOvfSlots = 4096;    // drain table entries (each entry holds >= k
 struct PairDev {
     const uint8_t *fbins;  // fixed volume pre-binned to uint8, x fastest
     const void *mov;       // moving volume, uint8 or uint16, clamped to its bit depth
-    const void *movp;      // x-paired copy: (v[x], v[x+1]) as uint16 (uint8 data) or uint32 (uint16 data)
+    const void *movp;      // x-paired copy (v[x], v[x+1]), uint16 / uint32, dims (nx, ny + 1, nz + 1)
+    unsigned long long texp;  // the same pairs as a 3D texture (point sampling, clamped), dims (nx, ny, nz)
     int nf[3];             // fixed dims (x, y, z)
     int nm[3];             // moving dims
     int bins;
@@ -51,8 +52,9 @@ struct Item {
     int t;   // transform index (row of the affine array and of the outputs)
 };
 
-// Histogram variants (match the public MI_HV_* values).
-enum { HV_U32 = 0, HV_U32_MATCH = 1, HV_U16 = 2, HV_U16_MATCH = 3 };
+// Histogram variants (match the public MI_HV_* values); + HV_TEX = the same
+// histogram with the moving pairs fetched through the texture path.
+enum { HV_U32 = 0, HV_U32_MATCH = 1, HV_U16 = 2, HV_U16_MATCH = 3, HV_TEX = 4, HV_COUNT = 8 };
 
 // Shared memory needed by a hard-path CTA of `threads` threads for `bins` bins.
 size_t hard_smem_bytes(int variant, int bins, int threads);
@@ -60,7 +62,8 @@ size_t hard_smem_bytes(int variant, int bins, int threads);
 // ---- launchers (all asynchronous on `s`) ---------------------------------
 cudaError_t launch_f32_to_u16(const float *in, long long n, uint16_t *out, cudaStream_t s);
 cudaError_t launch_clamp_depth(void *data, int dtype, int depth, long long n, cudaStream_t s);
-cudaError_t launch_make_pairs(const void *mov, int dtype, long long n, int n0, void *out, cudaStream_t s);
+// Padded x-paired moving volume, dims (n0, n1 + 1, n2 + 1).
+cudaError_t launch_make_pairs(const void *mov, int dtype, const int nm[3], void *out, cudaStream_t s);
 cudaError_t launch_bin_fixed(const void *data, int dtype, int depth, long long n, int bins, uint8_t *out,
                              cudaStream_t s);
 cudaError_t launch_table(double *tab, float q, cudaStream_t s);

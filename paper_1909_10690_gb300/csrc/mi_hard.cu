@@ -220,37 +220,6 @@ __device__ RowClip clip_row(const int *q, int j, int k, int nf0, const int nm[3]
     return r;
 }
 
-// Exact interval [lo, hi] of i in [0, nf0) with 0 <= base + st i <= umax (one axis).
-__device__ void clip_axis(long long base, int st, long long umax, int nf0, int &lo, int &hi) {
-    lo = 0;
-    hi = nf0 - 1;
-    if (st == 0) {
-        if (base < 0 || base > umax) {
-            lo = nf0;
-            hi = -1;
-        }
-        return;
-    }
-    long long b1[3] = {base, 0, 0}, um[3] = {umax, 0x7fffffffffffffffll, 0x7fffffffffffffffll};
-    int s1[3] = {st, 0, 0};
-    // float estimate within one voxel of the truth, then the exact fix-up of clip_row
-    const float fb = (float)base, fs = (float)st, fm = (float)umax;
-    const float e0 = -fb / fs, e1 = (fm - fb) / fs;
-    float a0 = fminf(e0, e1), a1 = fmaxf(e0, e1);
-    a0 = fminf(fmaxf(a0, -2.0f), (float)nf0 + 1.0f);
-    a1 = fminf(fmaxf(a1, -2.0f), (float)nf0 + 1.0f);
-    lo = max(lo, (int)ceilf(a0));
-    hi = min(hi, (int)floorf(a1));
-    while (lo <= hi && !inside_at(b1, s1, um, lo)) ++lo;
-    while (lo > 0 && lo <= nf0 && inside_at(b1, s1, um, lo - 1)) --lo;
-    while (hi >= lo && !inside_at(b1, s1, um, hi)) --hi;
-    while (hi >= lo && hi < nf0 - 1 && inside_at(b1, s1, um, hi + 1)) ++hi;
-    if (hi < lo && lo < nf0 && inside_at(b1, s1, um, lo)) {
-        hi = lo;
-        while (hi < nf0 - 1 && inside_at(b1, s1, um, hi + 1)) ++hi;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Shared-memory histogram policies
 // ---------------------------------------------------------------------------
@@ -454,10 +423,10 @@ __device__ typename HistOf<HV>::T make_hist(unsigned char *smem, const SmemLayou
 // Row order: the CTA walks blocks of nwarps adjacent fixed rows (block blk
 // holds rows blk * nwarps + w) and warp w takes row w of each block, so at any
 // time the warps of a CTA sample neighbouring moving lines (row j's upper y
-// neighbours are row j + 1's samples) and the moving lines they touch stay
-// in L1.  Lanes 0..2 clip the row on one axis each (exactly, in 64 bits); the
-// warp then walks the overlap interval 32 voxels at a time.  Blocks are
-// first_block, first_block + block_stride, ...
+// neighbours are row j + 1's samples).  Blocks are first_block + n *
+// block_stride, n = 0, 1, ...  A warp clips its next 32 rows at once (lane l
+// takes the warp's l-th upcoming row, exactly in 64 bits), then walks them one
+// by one, 32 voxels at a time, with each row's interval broadcast by shuffles.
 template <typename PairT, bool TEX, class Hist>
 __device__ void accumulate_rows(const PairDev &P, const int *q, long long first_block, long long block_stride,
                                 Hist &H) {
@@ -468,43 +437,40 @@ __device__ void accumulate_rows(const PairDev &P, const int *q, long long first_
     const int st0 = q[0], st1 = q[4], st2 = q[8];
     const int bins = P.bins, mdepth = P.mdepth;
     const PairT *__restrict__ movp = (const PairT *)P.movp;
-    const int la = lane < 3 ? lane : 0;
-    const int stl = q[4 * la];
-    const long long uml = (long long)(P.nm[la] - 1) << 16;
-    for (long long blk = first_block; blk * nwarps < R; blk += block_stride) {
-        const long long r = blk * nwarps + warp;
-        if (r >= R) break;
-        const int j = (int)(r % nf1), k = (int)(r / nf1);
-        int lo = 0, hi = nf0 - 1;
-        long long base = 0;
-        if (lane < 3) {
-            base = (long long)q[4 * la + 1] * j + (long long)q[4 * la + 2] * k + (long long)q[4 * la + 3];
-            clip_axis(base, stl, uml, nf0, lo, hi);
-        }
-        lo = max(lo, max(__shfl_sync(kFull, lo, 1), __shfl_sync(kFull, lo, 2)));
-        lo = __shfl_sync(kFull, lo, 0);
-        hi = min(hi, min(__shfl_sync(kFull, hi, 1), __shfl_sync(kFull, hi, 2)));
-        hi = __shfl_sync(kFull, hi, 0);
-        if (lo > hi) continue;  // warp-uniform
-        const int ul = (int)(base + (long long)stl * lo);  // in range on lanes 0..2
-        // unsigned: lanes past the row end may step outside the int range; only in-range lanes use them
-        unsigned U0 = (unsigned)__shfl_sync(kFull, ul, 0) + (unsigned)st0 * lane,
-                 U1 = (unsigned)__shfl_sync(kFull, ul, 1) + (unsigned)st1 * lane,
-                 U2 = (unsigned)__shfl_sync(kFull, ul, 2) + (unsigned)st2 * lane;
-        const uint8_t *__restrict__ frow = P.fbins + (size_t)r * nf0;
-        for (int i = lo + lane; i - lane <= hi; i += 32) {
-            const bool valid = i <= hi;
-            int bf = 0, bm = 0;
-            if (valid) {
-                const int v = TEX ? sample_hard_tex<PairT>(P.texp, (int)U0, (int)U1, (int)U2)
-                                  : sample_hard_pair<PairT>(movp, sy, sz, n0, sz, (int)U0, (int)U1, (int)U2);
-                bm = (v * bins) >> mdepth;
-                bf = (int)__ldg(frow + i);
+    for (long long n0b = 0;; n0b += 32) {
+        // rows of this group: lane l gets block first_block + (n0b + l) * block_stride
+        const long long first_row = (first_block + n0b * block_stride) * nwarps + warp;
+        if (first_row >= R) break;
+        RowClip mine;
+        mine.lo = 0;
+        mine.hi = -1;
+        mine.u0 = mine.u1 = mine.u2 = 0;
+        const long long rl = (first_block + (n0b + lane) * block_stride) * nwarps + warp;
+        if (rl < R) mine = clip_row(q, (int)(rl % nf1), (int)(rl / nf1), nf0, P.nm);
+        for (int s = 0; s < 32; ++s) {
+            const long long r = (first_block + (n0b + s) * block_stride) * nwarps + warp;
+            if (r >= R) break;  // warp-uniform
+            const int lo = __shfl_sync(kFull, mine.lo, s), hi = __shfl_sync(kFull, mine.hi, s);
+            if (lo > hi) continue;
+            // unsigned: lanes past the row end may step outside the int range; only in-range lanes use them
+            unsigned U0 = (unsigned)__shfl_sync(kFull, mine.u0, s) + (unsigned)st0 * lane,
+                     U1 = (unsigned)__shfl_sync(kFull, mine.u1, s) + (unsigned)st1 * lane,
+                     U2 = (unsigned)__shfl_sync(kFull, mine.u2, s) + (unsigned)st2 * lane;
+            const uint8_t *__restrict__ frow = P.fbins + (size_t)r * nf0;
+            for (int i = lo + lane; i - lane <= hi; i += 32) {
+                const bool valid = i <= hi;
+                int bf = 0, bm = 0;
+                if (valid) {
+                    const int v = TEX ? sample_hard_tex<PairT>(P.texp, (int)U0, (int)U1, (int)U2)
+                                      : sample_hard_pair<PairT>(movp, sy, sz, n0, sz, (int)U0, (int)U1, (int)U2);
+                    bm = (v * bins) >> mdepth;
+                    bf = (int)__ldg(frow + i);
+                }
+                H.add(bf, bm, valid);
+                U0 += 32u * (unsigned)st0;
+                U1 += 32u * (unsigned)st1;
+                U2 += 32u * (unsigned)st2;
             }
-            H.add(bf, bm, valid);
-            U0 += 32u * (unsigned)st0;
-            U1 += 32u * (unsigned)st1;
-            U2 += 32u * (unsigned)st2;
         }
     }
 }

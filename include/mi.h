@@ -94,7 +94,12 @@ enum {
     MI_HV_U32_TEX = 4,
     MI_HV_U32_MATCH_TEX = 5,
     MI_HV_U16_TEX = 6,
-    MI_HV_U16_MATCH_TEX = 7
+    MI_HV_U16_MATCH_TEX = 7,
+    /* row-bound layout: 32-bit counters only for fixed bins holding more than
+       65535 fixed voxels, 16-bit halves for the rest (provably never overflow);
+       fits when those rows are few */
+    MI_HV_ROWS = 8,
+    MI_HV_ROWS_TEX = 9
 };
 /* Evaluation path of mi_eval. */
 enum { MI_PATH_AUTO = 0, MI_PATH_PLAIN = 1, MI_PATH_BATCHED = 2 };

@@ -189,6 +189,8 @@ struct Pair {
     DevBuf fbins, mov, movp;    // hard path (movp: x-paired moving volume)
     cudaArray_t arr = nullptr;  // the pairs as a 3D array, read through tex
     cudaTextureObject_t tex = 0;
+    DevBuf rowinfo;             // row-bound layout table (bins entries)
+    int rows_words = 0;
     DevBuf pfbins, pmov;        // Parzen path
     ~Pair() {
         if (tex) cudaDestroyTextureObject(tex);
@@ -219,6 +221,7 @@ struct mi_ctx {
     std::vector<std::unique_ptr<Pair>> pairs;
     DevBuf d_pairs;     // PairDev[npairs]
     int max_bins = 0;
+    int max_rows_words = 0;
     // per-q FP64 tables, keyed by the float bits of q
     std::map<uint32_t, std::unique_ptr<DevBuf>> tables;
     // call scratch
@@ -374,6 +377,34 @@ mi_status add_pair(mi_ctx *ctx, const mi_volume *fx, const mi_volume *mv, int bi
         }
         MI_CU(P->fbins.ensure((size_t)P->nvf), "allocating fixed bins");
         MI_CU(launch_bin_fixed(fsrc, fdt, P->fdepth, P->nvf, bins, P->fbins.as<uint8_t>(), s), "binning the fixed volume");
+        // row-bound layout: a row whose bin holds at most 65535 fixed voxels can never count past 16 bits
+        {
+            DevBuf dF;
+            std::vector<unsigned long long> F(bins);
+            MI_CU(dF.ensure((size_t)bins * 8), "allocating bin counts");
+            MI_CU(launch_fixed_hist(P->fbins.as<uint8_t>(), P->nvf, bins, dF.as<unsigned long long>(), s), "bin counts");
+            MI_CU(cudaMemcpyAsync(F.data(), dF.p, (size_t)bins * 8, cudaMemcpyDeviceToHost, s), "bin counts D2H");
+            MI_CU(cudaStreamSynchronize(s), "bin counts");
+            std::vector<uint32_t> info(bins);
+            const uint32_t S = (uint32_t)bins + 1;
+            uint32_t off = 0;
+            for (int r = 0; r < bins; ++r)
+                if (F[r] > 65535) {
+                    info[r] = off | (1u << 31);
+                    off += S;
+                }
+            int k = 0;
+            for (int r = 0; r < bins; ++r)
+                if (F[r] <= 65535) {
+                    info[r] = (off + (uint32_t)(k / 2) * S) | ((uint32_t)(k % 2 ? 16 : 0) << 24);
+                    ++k;
+                }
+            off += (uint32_t)((k + 1) / 2) * S;
+            P->rows_words = (int)off;
+            MI_CU(P->rowinfo.ensure((size_t)bins * 4), "allocating the row table");
+            MI_CU(cudaMemcpyAsync(P->rowinfo.p, info.data(), (size_t)bins * 4, cudaMemcpyHostToDevice, s), "row table");
+            MI_CU(cudaStreamSynchronize(s), "row table");
+        }
         if (mv->dtype == MI_F32) {
             MI_CU(P->mov.ensure((size_t)P->nvm * 2), "allocating the moving volume");
             MI_CU(launch_f32_to_u16(rawm.as<float>(), P->nvm, P->mov.as<uint16_t>(), s), "converting the moving volume");
@@ -413,6 +444,7 @@ mi_status add_pair(mi_ctx *ctx, const mi_volume *fx, const mi_volume *mv, int bi
     }
     MI_CU(cudaStreamSynchronize(s), "preparing the volumes");
     ctx->max_bins = std::max(ctx->max_bins, bins);
+    ctx->max_rows_words = std::max(ctx->max_rows_words, P->rows_words);
     ctx->pairs.push_back(std::move(P));
     return MI_OK;
 }
@@ -427,6 +459,8 @@ mi_status upload_pairs(mi_ctx *ctx) {
         d.mov = P.mov.p;
         d.movp = P.movp.p;
         d.texp = P.tex;
+        d.rowinfo = P.rowinfo.as<uint32_t>();
+        d.rows_words = P.rows_words;
         for (int a = 0; a < 3; ++a) {
             d.nf[a] = P.nf[a];
             d.nm[a] = P.nm[a];
@@ -448,6 +482,8 @@ PairDev host_pairdev(const Pair &P) {
     d.mov = P.mov.p;
     d.movp = P.movp.p;
     d.texp = P.tex;
+    d.rowinfo = P.rowinfo.as<uint32_t>();
+    d.rows_words = P.rows_words;
     for (int a = 0; a < 3; ++a) {
         d.nf[a] = P.nf[a];
         d.nm[a] = P.nm[a];
@@ -482,7 +518,7 @@ mi_status create_common(mi_ctx **out, const mi_volume *fixed, const mi_volume *m
         g_create_error = "the Parzen form takes one pair per context";
         return MI_EINVAL;
     }
-    if (ctx->opt.hist_variant < MI_HV_AUTO || ctx->opt.hist_variant > MI_HV_U16_MATCH_TEX) {
+    if (ctx->opt.hist_variant < MI_HV_AUTO || ctx->opt.hist_variant > MI_HV_ROWS_TEX) {
         g_create_error = "opt.hist_variant out of range";
         return MI_EINVAL;
     }
@@ -618,10 +654,11 @@ mi_status deliver(mi_ctx *ctx, void *dst, const void *src, size_t bytes) {
 // Variant selection
 // ---------------------------------------------------------------------------
 
-bool variant_fits(int variant, int bins, int threads, long long nvox) {
-    const bool u16 = (variant % HV_TEX) == HV_U16 || (variant % HV_TEX) == HV_U16_MATCH;
+bool variant_fits(int variant, int bins, int threads, long long nvox, int rows_words) {
+    const int kind = hv_kind(variant);
+    const bool u16 = kind == HV_U16 || kind == HV_U16_MATCH;
     if (u16 && nvox > (long long)(kOvfSlots / 2) * kDrainT) return false;
-    return hard_smem_bytes(variant, bins, threads) <= 227 * 1024;
+    return hard_smem_bytes(variant, bins, threads, rows_words) <= 227 * 1024;
 }
 
 std::vector<Choice> candidates(mi_ctx *ctx, int bins, long long nvox_max) {
@@ -631,11 +668,11 @@ std::vector<Choice> candidates(mi_ctx *ctx, int bins, long long nvox_max) {
         if (fixed_v >= 0 && v != fixed_v) continue;
         for (int th : {512, 1024}) {
             if (ctx->opt.block_threads > 0 && th != ctx->opt.block_threads) continue;
-            if (!variant_fits(v, bins, th, nvox_max)) continue;
+            if (!variant_fits(v, bins, th, nvox_max, ctx->max_rows_words)) continue;
             Choice ch;
             ch.variant = v;
             ch.threads = th;
-            const int per_sm = batched_ctas_per_sm(v, bins, th);
+            const int per_sm = batched_ctas_per_sm(v, bins, th, ctx->max_rows_words);
             if (per_sm < 1) continue;
             ch.ctas = per_sm * ctx->sms;
             c.push_back(ch);
@@ -667,7 +704,7 @@ mi_status run_plain(mi_ctx *ctx, int pair, const int32_t *d_aff, int n, const QS
         }
         // CTAs per transform: fill the GPU, but keep at least 8 row batches of 32 rows per CTA
         const long long rows = (long long)P.nf[1] * P.nf[2];
-        const int per_sm = std::max(1, batched_ctas_per_sm(ch.variant, P.bins, ch.threads));
+        const int per_sm = std::max(1, batched_ctas_per_sm(ch.variant, P.bins, ch.threads, P.rows_words));
         long long ctas = ((long long)ctx->sms * per_sm + m - 1) / m;
         ctas = std::min<long long>(ctas, std::max<long long>(1, rows / (32 * 8)));
         MI_CU(launch_plain_hist(dp, hp, d_aff + (size_t)t0 * 12, m, hist, ch.variant, ch.threads, (int)std::max(1LL, ctas),
@@ -707,7 +744,8 @@ mi_status launch_batched_once(mi_ctx *ctx, int nitems, const QSet &Q, const Outp
     MI_CU(cudaMemsetAsync(ctx->d_ticket.p, 0, sizeof(int), ctx->stream), "resetting the work queue");
     if (record) MI_CU(record_event(ctx->ev0, ctx->stream), "event");
     MI_CU(launch_batched(ctx->d_pairs.as<PairDev>(), ctx->d_aff.as<int32_t>(), ctx->d_items.as<Item>(), nitems,
-                         ctx->d_ticket.as<int>(), ctx->max_bins, ch.variant, ch.threads, ch.ctas, Q, O, ctx->stream),
+                         ctx->d_ticket.as<int>(), ctx->max_bins, ctx->max_rows_words, ch.variant, ch.threads, ch.ctas,
+                         Q, O, ctx->stream),
           "batched kernel");
     if (record) MI_CU(record_event(ctx->ev1, ctx->stream), "event");
     return MI_OK;
@@ -775,7 +813,7 @@ mi_status run_batched(mi_ctx *ctx, int nitems, const QSet &Q, const Outputs &O, 
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
         // set kernel attributes outside of capture
-        batched_ctas_per_sm(ch.variant, ctx->max_bins, ch.threads);
+        batched_ctas_per_sm(ch.variant, ctx->max_bins, ch.threads, ctx->max_rows_words);
         cudaGraph_t g;
         MI_CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed), "begin capture");
         cudaMemcpyAsync(ctx->d_aff.p, ctx->h_aff.p, aff_bytes, cudaMemcpyHostToDevice, ctx->stream);

@@ -234,6 +234,7 @@ template <bool MATCH>
 struct HistU32 {
     uint32_t *h;
     int B, S;  // bins, padded row stride in words
+    __device__ void load_info(const uint32_t *) {}
     __device__ void zero() {
         for (int c = threadIdx.x; c < B * S; c += blockDim.x) h[c] = 0;
     }
@@ -269,6 +270,7 @@ struct HistU16 {
     uint32_t *bmap;   // (B^2 + 31) / 32 words
     int *flags;
     int B, S, H;
+    __device__ void load_info(const uint32_t *) {}
     __device__ void zero() {
         const int nw = H * S, nb = (B * B + 31) >> 5;
         for (int c = threadIdx.x; c < nw; c += blockDim.x) w[c] = 0;
@@ -347,6 +349,37 @@ struct HistU16 {
     }
 };
 
+// Row-bound layout.  A cell count can never exceed the number of fixed voxels
+// in its row's bin, F[r] (each fixed voxel contributes at most once per
+// transform), and F is known when the context is built.  Rows with
+// F[r] <= 65535 ("narrow") share words two at a time as 16-bit halves; the
+// others ("wide") get 32-bit words.  No counter can overflow, so increments
+// are fire-and-forget atomics with no return value and no drain.  rowinfo[r]
+// = word offset of row r | shift << 24 | wide << 31; rows are padded to
+// S = B + 1 words.
+struct HistRows {
+    uint32_t *w;
+    uint32_t *info;  // B entries, copied into shared memory per item
+    int B, S, nwords;
+    __device__ void load_info(const uint32_t *rowinfo) {
+        for (int r = threadIdx.x; r < B; r += blockDim.x) info[r] = __ldg(rowinfo + r);
+    }
+    __device__ void zero() {
+        for (int c = threadIdx.x; c < nwords; c += blockDim.x) w[c] = 0;
+    }
+    __device__ __forceinline__ void add(int bf, int bm, bool valid) {
+        if (valid) {
+            const uint32_t inf = info[bf];
+            atomicAdd(&w[(inf & 0xffffffu) + bm], 1u << ((inf >> 24) & 31u));
+        }
+    }
+    __device__ __forceinline__ uint32_t count(int bf, int bm) const {
+        const uint32_t inf = info[bf];
+        const uint32_t v = w[(inf & 0xffffffu) + bm] >> ((inf >> 24) & 31u);
+        return (inf >> 31) ? v : (v & 0xffffu);
+    }
+};
+
 // Global 32-bit histogram, row-major bins x bins (plain path's entropy reduction).
 struct HistGlobal {
     const uint32_t *h;
@@ -358,23 +391,29 @@ struct HistGlobal {
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct SmemLayout {
-    size_t hist, okey, ocnt, bmap, rows, cols, red, total;
+    size_t hist, okey, ocnt, bmap, rinfo, rows, cols, red, total;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(int variant, int bins, int threads) {
+__host__ __device__ inline SmemLayout smem_layout(int variant, int bins, int threads, int rows_words) {
     SmemLayout L;
     const size_t B2 = (size_t)bins * bins;
-    const bool u16 = (variant % HV_TEX) == HV_U16 || (variant % HV_TEX) == HV_U16_MATCH;
+    const int kind = hv_kind(variant);
+    const bool u16 = kind == HV_U16 || kind == HV_U16_MATCH;
     const size_t S = (size_t)bins + 1, H = ((size_t)bins + 1) / 2;
     size_t o = 0;
     L.hist = o;
-    o += u16 ? H * S * 4 : (size_t)bins * S * 4;
+    if (kind == HV_ROWS)
+        o += (size_t)rows_words * 4;
+    else
+        o += u16 ? H * S * 4 : (size_t)bins * S * 4;
     L.okey = o;
     if (u16) o += (size_t)kOvfSlots * 4;
     L.ocnt = o;
     if (u16) o += (size_t)kOvfSlots * 4;
     L.bmap = o;
     if (u16) o += ((B2 + 31) / 32) * 4;
+    L.rinfo = o;
+    if (kind == HV_ROWS) o += (size_t)bins * 4;
     L.rows = o;
     o += (size_t)bins * 4;
     L.cols = o;
@@ -383,6 +422,7 @@ __host__ __device__ inline SmemLayout smem_layout(int variant, int bins, int thr
     L.red = o;
     o += (size_t)(3 * 32 + 3 * kMaxQ + 1) * 8;
     L.total = o;
+    (void)threads;
     return L;
 }
 
@@ -396,9 +436,12 @@ template <>
 struct HistOf<HV_U16> { using T = HistU16<false>; };
 template <>
 struct HistOf<HV_U16_MATCH> { using T = HistU16<true>; };
+template <>
+struct HistOf<HV_ROWS> { using T = HistRows; };
 
 template <int HV>
-__device__ typename HistOf<HV>::T make_hist(unsigned char *smem, const SmemLayout &L, int B, int *flags) {
+__device__ typename HistOf<HV>::T make_hist(unsigned char *smem, const SmemLayout &L, int B, int *flags,
+                                            int rows_words = 0) {
     typename HistOf<HV>::T H;
     H.B = B;
     H.S = B + 1;
@@ -409,8 +452,15 @@ __device__ typename HistOf<HV>::T make_hist(unsigned char *smem, const SmemLayou
         H.ocnt = (uint32_t *)(smem + L.ocnt);
         H.bmap = (uint32_t *)(smem + L.bmap);
         H.flags = flags;
+    } else if constexpr (HV == HV_ROWS) {
+        H.w = (uint32_t *)(smem + L.hist);
+        H.info = (uint32_t *)(smem + L.rinfo);
+        H.nwords = rows_words;
+        (void)flags;
     } else {
         H.h = (uint32_t *)(smem + L.hist);
+        (void)flags;
+        (void)rows_words;
     }
     return H;
 }
@@ -616,12 +666,11 @@ __global__ void __launch_bounds__(1024, 1)
     const PairDev P = pairs[0];
     const int t = blockIdx.y;
     const int B = P.bins;
-    const SmemLayout L = smem_layout(HV, B, blockDim.x);
+    const SmemLayout L = smem_layout(HV, B, blockDim.x, P.rows_words);
     __shared__ int q[12];
-    __shared__ int s_next;
     if (threadIdx.x < 12) q[threadIdx.x] = aff[(size_t)t * 12 + threadIdx.x];
-    if (threadIdx.x == 0) s_next = 0;
-    auto H = make_hist<HV>(smem, L, B, flags);
+    auto H = make_hist<HV>(smem, L, B, flags, P.rows_words);
+    H.load_info(P.rowinfo);
     H.zero();
     __syncthreads();
     const int nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
@@ -657,12 +706,11 @@ __global__ void __launch_bounds__(1024, 1)
 template <int HV, bool TEX>
 __global__ void __launch_bounds__(1024, 1)
     k_batched(const PairDev *__restrict__ pairs, const int32_t *__restrict__ aff, const Item *__restrict__ items,
-              int nitems, int *ticket, int max_bins, QSet Q, Outputs O) {
+              int nitems, int *ticket, int max_bins, int rows_words, QSet Q, Outputs O) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item;
-    __shared__ int s_next;
     __shared__ int q[12];
-    const SmemLayout L = smem_layout(HV, max_bins, blockDim.x);
+    const SmemLayout L = smem_layout(HV, max_bins, blockDim.x, rows_words);
     const int nwarps = blockDim.x >> 5;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(ticket, 1);
@@ -673,8 +721,8 @@ __global__ void __launch_bounds__(1024, 1)
         const PairDev P = pairs[I.pair];
         const int B = P.bins;
         if (threadIdx.x < 12) q[threadIdx.x] = aff[(size_t)I.t * 12 + threadIdx.x];
-        if (threadIdx.x == 0) s_next = 0;
-        auto H = make_hist<HV>(smem, L, B, O.flags);
+        auto H = make_hist<HV>(smem, L, B, O.flags, P.rows_words);
+        H.load_info(P.rowinfo);
         H.zero();
         __syncthreads();
         if (P.mdtype == 0)
@@ -730,7 +778,29 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 
 }  // namespace
 
-size_t hard_smem_bytes(int variant, int bins, int threads) { return smem_layout(variant, bins, threads).total; }
+size_t hard_smem_bytes(int variant, int bins, int threads, int rows_words) {
+    return smem_layout(variant, bins, threads, rows_words).total;
+}
+
+__global__ void k_fixed_hist(const uint8_t *__restrict__ fb, long long n, int bins, unsigned long long *__restrict__ out) {
+    __shared__ unsigned int h[256];
+    for (int c = threadIdx.x; c < 256; c += blockDim.x) h[c] = 0;
+    __syncthreads();
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x)
+        atomicAdd(&h[fb[x]], 1u);
+    __syncthreads();
+    for (int c = threadIdx.x; c < bins; c += blockDim.x)
+        if (h[c]) atomicAdd(out + c, (unsigned long long)h[c]);
+}
+
+cudaError_t launch_fixed_hist(const uint8_t *fbins, long long n, int bins, unsigned long long *out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, (size_t)bins * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    long long g = (n + 255) / 256;
+    if (g > 1024) g = 1024;
+    k_fixed_hist<<<(int)(g < 1 ? 1 : g), 256, 0, s>>>(fbins, n, bins, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_f32_to_u16(const float *in, long long n, uint16_t *out, cudaStream_t s) {
     k_f32_to_u16<<<grid_for(n, 256), 256, 0, s>>>(in, n, out);
@@ -779,7 +849,7 @@ cudaError_t launch_plain_hist(const PairDev *d_pair, const PairDev &h_pair, cons
     const size_t B2 = (size_t)h_pair.bins * h_pair.bins;
     cudaError_t e = cudaMemsetAsync(d_hist, 0, (size_t)n * B2 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    const size_t smem = smem_layout(variant, h_pair.bins, threads).total;
+    const size_t smem = smem_layout(variant, h_pair.bins, threads, h_pair.rows_words).total;
     dim3 grid(ctas, n);
 #define MI_LAUNCH_PLAIN(MT, HVV, TX)                                                     \
     do {                                                                                 \
@@ -792,16 +862,17 @@ cudaError_t launch_plain_hist(const PairDev *d_pair, const PairDev &h_pair, cons
         if (h_pair.mdtype == 0) MI_LAUNCH_PLAIN(uint16_t, HVV, TX); \
         else MI_LAUNCH_PLAIN(uint32_t, HVV, TX);                   \
     } while (0)
-    const bool tex = variant >= HV_TEX;
-    switch (variant % HV_TEX) {
+    const bool tex = hv_tex(variant);
+    switch (hv_kind(variant)) {
         case HV_U32: if (tex) MI_LAUNCH_PLAIN_MT(HV_U32, true); else MI_LAUNCH_PLAIN_MT(HV_U32, false); break;
         case HV_U32_MATCH:
             if (tex) MI_LAUNCH_PLAIN_MT(HV_U32_MATCH, true); else MI_LAUNCH_PLAIN_MT(HV_U32_MATCH, false);
             break;
         case HV_U16: if (tex) MI_LAUNCH_PLAIN_MT(HV_U16, true); else MI_LAUNCH_PLAIN_MT(HV_U16, false); break;
-        default:
+        case HV_U16_MATCH:
             if (tex) MI_LAUNCH_PLAIN_MT(HV_U16_MATCH, true); else MI_LAUNCH_PLAIN_MT(HV_U16_MATCH, false);
             break;
+        default: if (tex) MI_LAUNCH_PLAIN_MT(HV_ROWS, true); else MI_LAUNCH_PLAIN_MT(HV_ROWS, false); break;
     }
 #undef MI_LAUNCH_PLAIN_MT
 #undef MI_LAUNCH_PLAIN
@@ -826,12 +897,14 @@ static const void *batched_fn(int variant) {
         case HV_TEX + HV_U32: return (const void *)k_batched<HV_U32, true>;
         case HV_TEX + HV_U32_MATCH: return (const void *)k_batched<HV_U32_MATCH, true>;
         case HV_TEX + HV_U16: return (const void *)k_batched<HV_U16, true>;
-        default: return (const void *)k_batched<HV_U16_MATCH, true>;
+        case HV_TEX + HV_U16_MATCH: return (const void *)k_batched<HV_U16_MATCH, true>;
+        case HV_ROWS: return (const void *)k_batched<HV_ROWS, false>;
+        default: return (const void *)k_batched<HV_ROWS, true>;
     }
 }
 
-int batched_ctas_per_sm(int variant, int max_bins, int threads) {
-    const size_t smem = smem_layout(variant, max_bins, threads).total;
+int batched_ctas_per_sm(int variant, int max_bins, int threads, int rows_words) {
+    const size_t smem = smem_layout(variant, max_bins, threads, rows_words).total;
     const void *fn = batched_fn(variant);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     int nb = 0;
@@ -840,14 +913,14 @@ int batched_ctas_per_sm(int variant, int max_bins, int threads) {
 }
 
 cudaError_t launch_batched(const PairDev *d_pairs, const int32_t *d_aff, const Item *d_items, int nitems,
-                           int *d_ticket, int max_bins, int variant, int threads, int ctas, const QSet &Q,
-                           const Outputs &O, cudaStream_t s) {
-    const size_t smem = smem_layout(variant, max_bins, threads).total;
+                           int *d_ticket, int max_bins, int rows_words, int variant, int threads, int ctas,
+                           const QSet &Q, const Outputs &O, cudaStream_t s) {
+    const size_t smem = smem_layout(variant, max_bins, threads, rows_words).total;
     const void *fn = batched_fn(variant);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&d_pairs, (void *)&d_aff, (void *)&d_items, (void *)&nitems, (void *)&d_ticket,
-                    (void *)&max_bins, (void *)&Q, (void *)&O};
+                    (void *)&max_bins, (void *)&rows_words, (void *)&Q, (void *)&O};
     return cudaLaunchKernel(fn, dim3(ctas), dim3(threads), args, smem, s);
 }
 
@@ -932,7 +1005,7 @@ template <typename FixT, typename MovT>
 __global__ void __launch_bounds__(1024, 1) k_hist_raw(RawPair P, Q12 A, uint32_t *__restrict__ ghist, int *flags) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int B = P.bins;
-    const SmemLayout L = smem_layout(HV_U16_MATCH, B, blockDim.x);
+    const SmemLayout L = smem_layout(HV_U16_MATCH, B, blockDim.x, 0);
     __shared__ int q[12];
     if (threadIdx.x < 12) q[threadIdx.x] = A.q[threadIdx.x];
     auto H = make_hist<HV_U16_MATCH>(smem, L, B, flags);
@@ -1058,7 +1131,7 @@ cudaError_t launch_noalloc_eval(const void *fix, int fdtype, int fdepth, const v
     Q12 A;
     for (int e = 0; e < 12; ++e) A.q[e] = q16[e];
     const int threads = 1024;
-    const size_t smem = smem_layout(HV_U16_MATCH, bins, threads).total;
+    const size_t smem = smem_layout(HV_U16_MATCH, bins, threads, 0).total;
     cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)bins * bins * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(flags, 0, 2 * sizeof(int), s)) != cudaSuccess) return e;

@@ -18,12 +18,13 @@ struct PairDev {
     const void *mov;       // moving volume, uint8 or uint16, clamped to its bit depth
     const void *movp;      // x-paired copy (v[x], v[x+1]), uint16 / uint32, dims (nx, ny + 1, nz + 1)
     unsigned long long texp;  // the same pairs as a 3D texture (point sampling, clamped), dims (nx, ny, nz)
+    const uint32_t *rowinfo;  // row-bound layout: per fixed bin, word offset | shift << 24 | wide << 31
     int nf[3];             // fixed dims (x, y, z)
     int nm[3];             // moving dims
     int bins;
     int mdepth;            // moving bit depth
     int mdtype;            // 0 = uint8, 1 = uint16
-    int pad;
+    int rows_words;        // words of the row-bound layout of this pair
 };
 
 // q values of one call with their count-indexed FP64 tables
@@ -52,12 +53,19 @@ struct Item {
     int t;   // transform index (row of the affine array and of the outputs)
 };
 
-// Histogram variants (match the public MI_HV_* values); + HV_TEX = the same
-// histogram with the moving pairs fetched through the texture path.
-enum { HV_U32 = 0, HV_U32_MATCH = 1, HV_U16 = 2, HV_U16_MATCH = 3, HV_TEX = 4, HV_COUNT = 8 };
+// Histogram variants (match the public MI_HV_* values).  0..3: counter kinds
+// with LDG gathers, 4..7: the same with texture-path gathers, 8 / 9: the
+// row-bound layout with LDG / texture gathers.
+enum { HV_U32 = 0, HV_U32_MATCH = 1, HV_U16 = 2, HV_U16_MATCH = 3, HV_TEX = 4, HV_ROWS = 8, HV_ROWS_TEX = 9,
+       HV_COUNT = 10 };
+__host__ __device__ inline int hv_kind(int v) { return v < HV_ROWS ? v % HV_TEX : HV_ROWS; }
+__host__ __device__ inline bool hv_tex(int v) { return (v >= HV_TEX && v < HV_ROWS) || v == HV_ROWS_TEX; }
 
-// Shared memory needed by a hard-path CTA of `threads` threads for `bins` bins.
-size_t hard_smem_bytes(int variant, int bins, int threads);
+// Shared memory needed by a hard-path CTA of `threads` threads for `bins` bins
+// (rows_words: words of the row-bound layout, used by HV_ROWS*).
+size_t hard_smem_bytes(int variant, int bins, int threads, int rows_words);
+// Per-bin voxel counts of a binned fixed volume (bins u64, zeroed here).
+cudaError_t launch_fixed_hist(const uint8_t *fbins, long long n, int bins, unsigned long long *out, cudaStream_t s);
 
 // ---- launchers (all asynchronous on `s`) ---------------------------------
 cudaError_t launch_f32_to_u16(const float *in, long long n, uint16_t *out, cudaStream_t s);
@@ -74,9 +82,9 @@ cudaError_t launch_entropy(const uint32_t *d_hist, int n, int bins, const QSet &
                            cudaStream_t s);
 // Batched path: persistent CTAs pull items from *d_ticket (reset by the caller).
 cudaError_t launch_batched(const PairDev *d_pairs, const int32_t *d_aff, const Item *d_items, int nitems,
-                           int *d_ticket, int max_bins, int variant, int threads, int ctas, const QSet &Q,
-                           const Outputs &O, cudaStream_t s);
-int batched_ctas_per_sm(int variant, int max_bins, int threads);
+                           int *d_ticket, int max_bins, int rows_words, int variant, int threads, int ctas,
+                           const QSet &Q, const Outputs &O, cudaStream_t s);
+int batched_ctas_per_sm(int variant, int max_bins, int threads, int rows_words);
 cudaError_t launch_resample(const PairDev *d_pair, const PairDev &h_pair, const int32_t *d_aff, void *out,
                             cudaStream_t s);
 

@@ -16,7 +16,7 @@ from paper_1909_10690_gb300 import phantoms
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-6
-VARIANTS = [0, 1, 2, 3, 4, 5, 6, 7]
+VARIANTS = [0, 1, 2, 3, 4, 5, 6, 7, 8, 9]
 IDENT = np.array([65536, 0, 0, 0, 0, 65536, 0, 0, 0, 0, 65536, 0], dtype=np.int32)
 
 
@@ -116,7 +116,7 @@ def test_ragged_sizes_all_variants(cuda_lib, variant, bins):
     assert_mi_close(mi, mi_o, h_o)
 
 
-@pytest.mark.parametrize("variant", [2, 3, 6, 7])
+@pytest.mark.parametrize("variant", [2, 3, 6, 7, 8, 9])
 def test_u16_counter_drains_exact(cuda_lib, variant):
     # a large uniform background makes the (0, 0) cell pass 2^14 many times inside one CTA
     f = np.zeros((64, 96, 100), np.uint16)
@@ -288,3 +288,19 @@ def test_full_size_batched_256_cubed_sampled(cuda_lib):
         q16 = oracle.affine_q16(oracle.affine(prm[t], f.shape, (1, 1, 1), m.shape, (1, 1, 1)))
         ho, _ = oracle.joint_hist(f, m, q16, 256, 12, 12)
         np.testing.assert_array_equal(H[k], ho.astype(np.uint32))
+
+
+@pytest.mark.parametrize("n_a", [65535, 65536])
+def test_row_bound_layout_at_the_16_bit_limit(cuda_lib, n_a):
+    # a fixed bin holding exactly 65535 voxels keeps 16-bit counters; one more makes it a 32-bit row;
+    # at identity with u = v its diagonal cell reaches the bin's full count
+    shape = (40, 50, 70)
+    f = np.full(shape, 3000, dtype=np.uint16)
+    f.ravel()[:n_a] = 1000
+    for variant in (8, 9):
+        ctx = cuda_lib.Context(f, f, bins=64, fixed_depth=12, moving_depth=12, hist_variant=variant)
+        for path in (cuda_lib.PATH_PLAIN, cuda_lib.PATH_BATCHED):
+            H = ctx.hist(affines=IDENT, path=path)
+            ho, _ = oracle.joint_hist(f, f, IDENT, 64, 12, 12)
+            np.testing.assert_array_equal(H[0], ho.astype(np.uint32))
+            assert H[0, 1000 * 64 >> 12, 1000 * 64 >> 12] == n_a

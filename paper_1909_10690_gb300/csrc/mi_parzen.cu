@@ -143,16 +143,26 @@ __device__ __forceinline__ bool inside_u(long long Ux, long long Uy, long long U
 
 // Weights are quantised to 2^-32 with the largest one absorbing the rounding
 // residue, so every voxel adds exactly 2^32 (the B-spline partition of unity)
-// and the 64-bit integer sums are exact and independent of the order of the
-// atomics: the soft histogram, MI and gradient are bitwise reproducible.
+// and the integer sums are exact and independent of the order of the atomics:
+// the soft histogram, MI and gradient are bitwise reproducible.  Each shared
+// cell is a 64-bit count kept as two 32-bit words (64-bit shared atomics are
+// several times slower): a weight (< 2^32) is added to the low word, and the
+// add that wraps it -- detected exactly once, from the returned old value --
+// adds 1 to the high word.
+__device__ __forceinline__ void add64(uint32_t *lo, uint32_t *hi, int c, uint32_t w) {
+    const uint32_t old = atomicAdd(lo + c, w);
+    if (old + w < old) atomicAdd(hi + c, 1u);
+}
+
 __global__ void __launch_bounds__(256)
     k_parzen_hist(ParzenPair P, const ParzenAffine *__restrict__ aff, unsigned long long *__restrict__ ghist,
                   unsigned long long *__restrict__ gcount) {
-    extern __shared__ unsigned long long sh[];
+    extern __shared__ uint32_t sh32[];  // low words [B^2], then high words [B^2]
     const int t = blockIdx.y, B = P.B, B2 = B * B;
+    uint32_t *lo = sh32, *hi = sh32 + B2;
     __shared__ long long A[12];
     if (threadIdx.x < 12) A[threadIdx.x] = aff[t].A[threadIdx.x];
-    for (int c = threadIdx.x; c < B2; c += blockDim.x) sh[c] = 0ull;
+    for (int c = threadIdx.x; c < 2 * B2; c += blockDim.x) sh32[c] = 0u;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int nf0 = P.nf[0], nf1 = P.nf[1];
@@ -175,21 +185,22 @@ __global__ void __launch_bounds__(256)
             const int k0 = (int)mt;
             float w[4];
             bspline_w(mt - (float)k0, w);
-            const unsigned long long q0 = __float2ull_rn(w[0] * 4294967296.0f);
-            const unsigned long long q2 = __float2ull_rn(w[2] * 4294967296.0f);
-            const unsigned long long q3 = __float2ull_rn(w[3] * 4294967296.0f);
-            const unsigned long long q1 = 4294967296ull - q0 - q2 - q3;
-            unsigned long long *row = sh + (int)__ldg(frow + i) * B + (k0 - 1);
-            atomicAdd(row + 0, q0);
-            atomicAdd(row + 1, q1);
-            atomicAdd(row + 2, q2);
-            if (q3) atomicAdd(row + 3, q3);  // q3 == 0 whenever k0 + 3 > B (t = 0 there)
+            // every quantised weight is at most (2/3) 2^32, so it fits the 32-bit low word
+            const uint32_t q0 = (uint32_t)__float2ull_rn(w[0] * 4294967296.0f);
+            const uint32_t q2 = (uint32_t)__float2ull_rn(w[2] * 4294967296.0f);
+            const uint32_t q3 = (uint32_t)__float2ull_rn(w[3] * 4294967296.0f);
+            const uint32_t q1 = (uint32_t)(4294967296ull - q0 - q2 - q3);
+            const int c = (int)__ldg(frow + i) * B + (k0 - 1);
+            add64(lo, hi, c + 0, q0);
+            add64(lo, hi, c + 1, q1);
+            add64(lo, hi, c + 2, q2);
+            if (q3) add64(lo, hi, c + 3, q3);  // q3 == 0 whenever k0 + 3 > B (t = 0 there)
         }
     }
     __syncthreads();
     unsigned long long *gh = ghist + (size_t)t * B2;
     for (int c = threadIdx.x; c < B2; c += blockDim.x) {
-        const unsigned long long v = sh[c];
+        const unsigned long long v = ((unsigned long long)hi[c] << 32) | lo[c];
         if (v) atomicAdd(gh + c, v);
     }
 #pragma unroll
@@ -481,7 +492,7 @@ cudaError_t launch_parzen_hist(const ParzenPair &P, const ParzenAffine *d_aff, i
     cudaError_t e = cudaMemsetAsync(d_hist, 0, (size_t)n * B2 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(d_count, 0, (size_t)n * sizeof(unsigned long long), s)) != cudaSuccess) return e;
-    const size_t smem = B2 * sizeof(unsigned long long);
+    const size_t smem = 2 * B2 * sizeof(uint32_t);
     if ((e = cudaFuncSetAttribute(k_parzen_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
     dim3 grid(ctas, n);

@@ -305,6 +305,27 @@ def run_profile(args):
                       "kernel_ms": ms, "voxel_transforms_per_s": args.profile * nvox / (np.mean(ms) / 1e3)}))
 
 
+def run_profile_parzen(args):
+    """Only the Parzen MI + gradient of ``args.profile_parzen`` poses on the 192x192x128 pair, for ncu."""
+    import torch
+
+    import paper_1909_10690_gb300 as mi
+    from paper_1909_10690_gb300 import phantoms
+
+    fp, mp = phantoms.head_pair(shape=PARZEN_SHAPE, spacing=PARZEN_SPACING, seed=50, dtype=np.float32)
+    ctx = mi.Context(fp, mp, bins=PARZEN_BINS, kernel="parzen", fixed_spacing=PARZEN_SPACING,
+                     moving_spacing=PARZEN_SPACING)
+    pp = torch.from_numpy(phantoms.random_transforms(args.profile_parzen, seed=51, t_mm=10, r_deg=15,
+                                                     s_range=(0.9, 1.1))).cuda()
+    for _ in range(args.warmup):
+        ctx.grad(pp, PARZEN_QS)
+    ms = []
+    for _ in range(args.steps):
+        ctx.grad(pp, PARZEN_QS)
+        ms.append(ctx.last_kernel_ms()[0])
+    print(json.dumps({"profile": "parzen", "poses": args.profile_parzen, "kernel_ms": ms}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -314,11 +335,15 @@ def main():
     ap.add_argument("--skip-extras", action="store_true", help="skip the plain and Parzen lines")
     ap.add_argument("--skip-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--profile", type=int, default=0, help="profile mode: batched kernel only, on this many transforms")
-    ap.add_argument("--variant", type=int, default=2, help="histogram variant in profile mode (MI_HV_*)")
+    ap.add_argument("--variant", type=int, default=9, help="histogram variant in profile mode (MI_HV_*)")
     ap.add_argument("--threads", type=int, default=1024, help="CTA size in profile mode (512 or 1024)")
+    ap.add_argument("--profile-parzen", type=int, default=0, help="profile mode: Parzen MI + gradient of this many poses")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
+        return
+    if args.profile_parzen:
+        run_profile_parzen(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -157,12 +157,14 @@ __device__ __forceinline__ void add64(uint32_t *lo, uint32_t *hi, int c, uint32_
 __global__ void __launch_bounds__(256)
     k_parzen_hist(ParzenPair P, const ParzenAffine *__restrict__ aff, unsigned long long *__restrict__ ghist,
                   unsigned long long *__restrict__ gcount) {
-    extern __shared__ uint32_t sh32[];  // low words [B^2], then high words [B^2]
-    const int t = blockIdx.y, B = P.B, B2 = B * B;
-    uint32_t *lo = sh32, *hi = sh32 + B2;
+    // low words [B x (B + 1)], then high words: rows padded by one word so the
+    // bank is (fixed bin + moving bin) mod 32 rather than the moving bin alone
+    extern __shared__ uint32_t sh32[];
+    const int t = blockIdx.y, B = P.B, B2 = B * B, SB = B + 1, NP = B * SB;
+    uint32_t *lo = sh32, *hi = sh32 + NP;
     __shared__ long long A[12];
     if (threadIdx.x < 12) A[threadIdx.x] = aff[t].A[threadIdx.x];
-    for (int c = threadIdx.x; c < 2 * B2; c += blockDim.x) sh32[c] = 0u;
+    for (int c = threadIdx.x; c < 2 * NP; c += blockDim.x) sh32[c] = 0u;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int nf0 = P.nf[0], nf1 = P.nf[1];
@@ -190,7 +192,7 @@ __global__ void __launch_bounds__(256)
             const uint32_t q2 = (uint32_t)__float2ull_rn(w[2] * 4294967296.0f);
             const uint32_t q3 = (uint32_t)__float2ull_rn(w[3] * 4294967296.0f);
             const uint32_t q1 = (uint32_t)(4294967296ull - q0 - q2 - q3);
-            const int c = (int)__ldg(frow + i) * B + (k0 - 1);
+            const int c = (int)__ldg(frow + i) * SB + (k0 - 1);
             add64(lo, hi, c + 0, q0);
             add64(lo, hi, c + 1, q1);
             add64(lo, hi, c + 2, q2);
@@ -200,7 +202,8 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     unsigned long long *gh = ghist + (size_t)t * B2;
     for (int c = threadIdx.x; c < B2; c += blockDim.x) {
-        const unsigned long long v = ((unsigned long long)hi[c] << 32) | lo[c];
+        const int cp = (c / B) * SB + c % B;
+        const unsigned long long v = ((unsigned long long)hi[cp] << 32) | lo[cp];
         if (v) atomicAdd(gh + c, v);
     }
 #pragma unroll
@@ -349,15 +352,21 @@ __global__ void __launch_bounds__(256)
     k_parzen_adj(ParzenPair P, const ParzenAffine *__restrict__ aff, int nq_total, int q0,
                  const float *__restrict__ wtab, int w_in_smem, double *__restrict__ mom) {
     // mom: n x nq_total x gridDim.x x 12 per-CTA partial moments (no atomics: fixed-order reduction later)
-    extern __shared__ float sw[];  // NQ x B^2 weights when they fit
+    extern __shared__ float sw[];  // NQ x B x (B + 1) weights (rows padded by one word) when they fit
     const int t = blockIdx.y, B = P.B, B2 = B * B;
     __shared__ long long A[12];
     __shared__ float s_red[8][NQ * 12];
     if (threadIdx.x < 12) A[threadIdx.x] = aff[t].A[threadIdx.x];
     const float *W = wtab + ((size_t)t * nq_total + q0) * B2;
+    int RS = B, QS = B2;  // row stride and per-q stride of the table in use
     if (w_in_smem) {
-        for (int c = threadIdx.x; c < NQ * B2; c += blockDim.x) sw[c] = W[c];
+        for (int c = threadIdx.x; c < NQ * B2; c += blockDim.x) {
+            const int qq = c / B2, cc = c % B2;
+            sw[qq * B * (B + 1) + (cc / B) * (B + 1) + cc % B] = W[c];
+        }
         W = sw;
+        RS = B + 1;
+        QS = B * (B + 1);
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -390,11 +399,11 @@ __global__ void __launch_bounds__(256)
             float d[4];
             bspline_dw(mt - (float)k0, d);
             if (k0 + 2 >= B) d[3] = 0.0f;
-            const int base = (int)__ldg(frow + i) * B + (k0 - 1);
+            const int base = (int)__ldg(frow + i) * RS + (k0 - 1);
             const int i3 = k0 + 2 < B ? base + 3 : base;  // in range; weight 0 when clamped
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
-                const float *Wq = W + (size_t)q * B2;
+                const float *Wq = W + (size_t)q * QS;
                 const float s = Wq[base] * d[0] + Wq[base + 1] * d[1] + Wq[base + 2] * d[2] + Wq[i3] * d[3];
                 const float sx = s * g.gx, sy = s * g.gy, sz = s * g.gz;
                 M[q][0] = fmaf(sx, ic, M[q][0]);
@@ -492,7 +501,7 @@ cudaError_t launch_parzen_hist(const ParzenPair &P, const ParzenAffine *d_aff, i
     cudaError_t e = cudaMemsetAsync(d_hist, 0, (size_t)n * B2 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(d_count, 0, (size_t)n * sizeof(unsigned long long), s)) != cudaSuccess) return e;
-    const size_t smem = 2 * B2 * sizeof(uint32_t);
+    const size_t smem = 2 * (size_t)P.B * (P.B + 1) * sizeof(uint32_t);
     if ((e = cudaFuncSetAttribute(k_parzen_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
     dim3 grid(ctas, n);
@@ -522,7 +531,7 @@ cudaError_t launch_parzen_adjoint(const ParzenPair &P, const ParzenAffine *d_aff
     dim3 grid(ctas, n);
     for (int q0 = 0; q0 < nq; q0 += 4) {
         const int g = nq - q0 < 4 ? nq - q0 : 4;
-        const size_t wbytes = (size_t)g * B2 * sizeof(float);
+        const size_t wbytes = (size_t)g * P.B * (P.B + 1) * sizeof(float);
         const int in_smem = wbytes <= 96 * 1024;
         const size_t smem = in_smem ? wbytes : 0;
 #define MI_ADJ(NQV)                                                                                         \

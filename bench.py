@@ -38,6 +38,14 @@ QS = [0.5, 1.0, 1.5, 2.0]
 # 3 coordinate adds, 6 index/weight extractions, 9 address operations, 7 lerps x 4,
 # 2 for the moving bin, 1 for the joint index, 1 increment
 ALG_OPS_PER_VOXT = 50
+# DRAM bytes (read + write) of one full k_batched launch, from the ncu capture summarised in
+# profiles/k_batched_rows_tex_256cubed_256bins.md; reported only while the kernel source and the
+# selected variant are the ones measured
+K_BATCHED_TRAFFIC = {"variant": 9, "source_sha16": "11bb587497c37227", "bytes_per_launch": 14.49e9 + 29.1e6}
+# algorithmic FP32 operations per voxel x transform of the Parzen MI + gradient at 3 q values:
+# forward 31 (trilinear 14, bin coordinate 1, B-spline weights 12, 4 increments),
+# adjoint 89 (trilinear value and gradient 23, bin coordinate 1, B-spline derivatives 8, 3 q x 19)
+PARZEN_OPS_PER_VOXT = 120
 PARZEN_SHAPE = (128, 192, 192)
 PARZEN_SPACING = (1.0, 1.0, 1.2)
 PARZEN_BINS = 64
@@ -51,6 +59,13 @@ def workload_config():
             "volume": list(SHAPE[::-1]), "bits": DEPTH, "bins": BINS, "transforms_per_step": N_T, "q": QS,
             "transform_dist": "t U(+-15 mm), r U(+-20 deg), s U(0.85, 1.15)",
             "l2": "flushed (256 MiB write) between timed steps"}
+
+
+def kernel_source_sha16(name="mi_hard.cu"):
+    import hashlib
+
+    p = os.path.join(ROOT, "paper_1909_10690_gb300", "csrc", name)
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 
 def peaks():
@@ -212,8 +227,11 @@ def run_ours(args, rank, world, local_rank):
     alu_peak = props.multi_processor_count * 128 * sm_mhz * 1e6 / 1e12  # int32 lane-ops/s, Tops/s
     kms = float(np.mean(kern_ms))
     achieved = ALG_OPS_PER_VOXT * N_T * nvox / (kms / 1e3) / 1e12
+    traffic = None
+    if variant == K_BATCHED_TRAFFIC["variant"] and kernel_source_sha16() == K_BATCHED_TRAFFIC["source_sha16"]:
+        traffic = K_BATCHED_TRAFFIC["bytes_per_launch"]
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak,
-                "traffic": None, "kernel": "k_batched", "kernel_ms": kms,
+                "traffic": traffic, "kernel": "k_batched", "kernel_ms": kms,
                 "peak_source": f"{props.multi_processor_count} SMs x 128 int32 lanes x {sm_mhz:.0f} MHz ({src} clock)"}
     # --- end to end through the C ABI with host buffers ----------------------------
     prm_pinned = torch.from_numpy(prm).pin_memory()
@@ -261,10 +279,16 @@ def run_ours(args, rank, world, local_rank):
             zk.append(zctx.last_kernel_ms()[0])
         z_s = time.perf_counter() - t0
         pv = int(np.prod(PARZEN_SHAPE))
+        zms = float(np.mean(zk))
+        z_ach = PARZEN_OPS_PER_VOXT * PARZEN_N * pv / (zms / 1e3) / 1e12
         extra["mi_grad"] = {"value": args.steps * PARZEN_N / z_s, "unit": "(MI+grad over 9 params, 3 q)/s",
                             "voxel_transforms_per_s": args.steps * PARZEN_N * pv / z_s,
-                            "kernel_ms_per_call": float(np.mean(zk)), "poses_per_call": PARZEN_N,
-                            "volume": list(PARZEN_SHAPE[::-1]), "bins": PARZEN_BINS, "q": PARZEN_QS}
+                            "kernel_ms_per_call": zms, "poses_per_call": PARZEN_N,
+                            "volume": list(PARZEN_SHAPE[::-1]), "bins": PARZEN_BINS, "q": PARZEN_QS,
+                            "roofline": {"bound": "alu", "achieved": z_ach, "peak": alu_peak, "unit": "Tops/s",
+                                         "frac": z_ach / alu_peak, "traffic": None,
+                                         "kernel": "k_parzen_hist + k_parzen_cells + k_parzen_adj",
+                                         "note": "FP32 lane-ops per voxel x transform over the whole MI+grad call"}}
         del zctx
     line = {"metric": METRIC, "value": value, "unit": "voxel*transforms/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,

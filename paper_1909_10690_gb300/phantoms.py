@@ -57,28 +57,25 @@ class Ellipsoid:
         return e
 
 
-def _grid(shape, spacing):
-    nz, ny, nx = shape
-    sx, sy, sz = spacing
-    x = (np.arange(nx, dtype=np.float32) * np.float32(sx))[None, None, :]
-    y = (np.arange(ny, dtype=np.float32) * np.float32(sy))[None, :, None]
-    z = (np.arange(nz, dtype=np.float32) * np.float32(sz))[:, None, None]
-    return x, y, z
-
-
 def _paint(label: np.ndarray, ell: Ellipsoid, value: int, spacing) -> None:
-    """label[inside ell] = value, evaluated slab by slab to bound memory."""
+    """label[inside ell] = value, evaluated over the ellipsoid's bounding box, slab by slab."""
     nz, ny, nx = label.shape
-    x, y, _ = _grid(label.shape, spacing)
+    half = np.sqrt(np.diag(np.linalg.inv(ell.Q)))  # half-extent of the bounding box along x, y, z (mm)
+    lo = np.floor((ell.c - half) / np.asarray(spacing)).astype(int) - 1
+    hi = np.ceil((ell.c + half) / np.asarray(spacing)).astype(int) + 2
+    x0, y0, z0 = (max(0, v) for v in lo)
+    x1, y1, z1 = min(nx, hi[0]), min(ny, hi[1]), min(nz, hi[2])
+    if x0 >= x1 or y0 >= y1 or z0 >= z1:
+        return
     Q = ell.Q.astype(np.float32)
-    dx = x - np.float32(ell.c[0])
-    dy = y - np.float32(ell.c[1])
-    for z0 in range(0, nz, 16):
-        z1 = min(nz, z0 + 16)
-        dz = (np.arange(z0, z1, dtype=np.float32) * np.float32(spacing[2]) - np.float32(ell.c[2]))[:, None, None]
+    dx = (np.arange(x0, x1, dtype=np.float32) * np.float32(spacing[0]) - np.float32(ell.c[0]))[None, None, :]
+    dy = (np.arange(y0, y1, dtype=np.float32) * np.float32(spacing[1]) - np.float32(ell.c[1]))[None, :, None]
+    for zs in range(z0, z1, 16):
+        ze = min(z1, zs + 16)
+        dz = (np.arange(zs, ze, dtype=np.float32) * np.float32(spacing[2]) - np.float32(ell.c[2]))[:, None, None]
         f = (Q[0, 0] * dx * dx + Q[1, 1] * dy * dy + Q[2, 2] * dz * dz
              + 2 * Q[0, 1] * dx * dy + 2 * Q[0, 2] * dx * dz + 2 * Q[1, 2] * dy * dz)
-        label[z0:z1][f <= 1.0] = value
+        label[zs:ze, y0:y1, x0:x1][f <= 1.0] = value
 
 
 def _centre(shape, spacing) -> np.ndarray:
@@ -160,9 +157,17 @@ def _head_labels(shape, spacing, rng, motion=None):
 
 
 def _rician(mean: np.ndarray, sigma: float, rng) -> np.ndarray:
-    a = mean.astype(np.float32) + rng.normal(0.0, sigma, size=mean.shape).astype(np.float32)
-    b = rng.normal(0.0, sigma, size=mean.shape).astype(np.float32)
-    return np.sqrt(a * a + b * b)
+    """Magnitude of a complex Gaussian around ``mean`` (float32 draws)."""
+    s = np.float32(sigma)
+    a = rng.standard_normal(size=mean.shape, dtype=np.float32)
+    a *= s
+    a += mean.astype(np.float32, copy=False)
+    b = rng.standard_normal(size=mean.shape, dtype=np.float32)
+    b *= s
+    a *= a
+    b *= b
+    a += b
+    return np.sqrt(a, out=a)
 
 
 def head_pair(shape=(160, 256, 256), spacing=(1.0, 1.0, 1.2), depth=12, seed=2, motion=HEAD_MOTION,
@@ -185,7 +190,7 @@ def head_pair(shape=(160, 256, 256), spacing=(1.0, 1.0, 1.2), depth=12, seed=2, 
                    rng.uniform(0.30, 0.38)]) * full
     out = []
     for lab, means in ((lab_f, t1), (lab_m, t2)):
-        vol = _rician(means[lab], noise * full, rng)
+        vol = _rician(means.astype(np.float32)[lab], noise * full, rng)
         if dtype == np.float32:
             out.append(np.clip(vol / full, 0.0, 1.0).astype(np.float32))
         else:

@@ -304,3 +304,75 @@ def test_row_bound_layout_at_the_16_bit_limit(cuda_lib, n_a):
             ho, _ = oracle.joint_hist(f, f, IDENT, 64, 12, 12)
             np.testing.assert_array_equal(H[0], ho.astype(np.uint32))
             assert H[0, 1000 * 64 >> 12, 1000 * 64 >> 12] == n_a
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("bins", [64, 128])
+def test_head_sweeps_full_size(cuda_lib, bins):
+    # the multimodal head-like workload: 256x256x160 12-bit, 1 x 1 x 1.2 mm, nine one-parameter sweeps of
+    # 81 steps (729 transforms) about the known motion, six q values; sampled transforms against the oracle
+    sp = (1.0, 1.0, 1.2)
+    f, m = phantoms.head_pair(shape=(160, 256, 256), spacing=sp, seed=60)
+    truth = np.asarray(phantoms.HEAD_MOTION, np.float32)
+    prm = []
+    for k, half in enumerate([20.0] * 3 + [30.0] * 3 + [0.2] * 3):
+        prm.append(phantoms.sweep(k, truth[k] - half, truth[k] + half, 81, base=truth))
+    prm = np.concatenate(prm)
+    qs = [0.2, 0.5, 0.8, 1.0, 1.5, 2.0]
+    ctx = cuda_lib.Context(f, m, bins=bins, fixed_depth=12, moving_depth=12, fixed_spacing=sp, moving_spacing=sp)
+    mi, h, cnt = ctx.eval(prm, qs, with_entropies=True)
+    assert np.all(np.isfinite(mi))
+    sample = np.array([0, 40, 121, 283, 364, 500, 688, 728])
+    mi_o, h_o, cnt_o = oracle.mi_eval(f, m, bins, prm[sample], qs, fixed_spacing=sp, moving_spacing=sp,
+                                      fixed_depth=12, moving_depth=12, nthreads=16)
+    np.testing.assert_array_equal(cnt[sample], cnt_o)
+    assert_mi_close(mi[sample], mi_o, h_o)
+    H = ctx.hist(transforms=prm[sample[:2]])
+    for k, t in enumerate(sample[:2]):
+        q16 = oracle.affine_q16(oracle.affine(prm[t], f.shape, sp, m.shape, sp))
+        ho, _ = oracle.joint_hist(f, m, q16, bins, 12, 12)
+        np.testing.assert_array_equal(H[k], ho.astype(np.uint32))
+    # Eq. 3: along every sweep the Shannon MI peaks at the known motion (the sweep's centre) within one step
+    peak = mi[:, qs.index(1.0)].reshape(9, 81).argmax(1)
+    assert np.all(np.abs(peak - 40) <= 1), peak
+
+
+@pytest.mark.slow
+def test_uneven_batch_full_size(cuda_lib):
+    # 48 pairs from 96^3 up to 320x320x200, mixed uint8/uint16, bins in {32, 64, 128}, 256 transforms each,
+    # all in one persistent launch; two sampled transforms per pair against the oracle
+    specs = phantoms.uneven_specs(48, seed=5)
+    pairs, vols = [], []
+    for s in specs:
+        f, m = phantoms.head_pair(shape=s["shape"], spacing=(1, 1, 1), depth=s["depth"], seed=s["seed"], dtype=s["dtype"])
+        vols.append((f, m, s["depth"], s["bins"]))
+        pairs.append(dict(fixed=f, moving=m, bins=s["bins"], fixed_depth=s["depth"], moving_depth=s["depth"]))
+    ctx = cuda_lib.Context(pairs=pairs)
+    n_per = 256
+    prm = phantoms.random_transforms(n_per * len(specs), seed=61)
+    pair_of = np.repeat(np.arange(len(specs), dtype=np.int32), n_per)
+    perm = np.random.default_rng(62).permutation(len(prm))
+    prm, pair_of = prm[perm], pair_of[perm]
+    qs = [1.0, 0.5, 1.5, 2.0]
+    mi, h, cnt = ctx.batch_eval(pair_of, prm, qs, with_entropies=True)
+    for p, (f, m, depth, bins) in enumerate(vols):
+        sel = np.nonzero(pair_of == p)[0]
+        assert len(sel) == n_per
+        chk = sel[[0, n_per - 1]]
+        mi_o, h_o, cnt_o = oracle.mi_eval(f, m, bins, prm[chk], qs, fixed_depth=depth, moving_depth=depth, nthreads=16)
+        np.testing.assert_array_equal(cnt[chk], cnt_o)
+        ok = cnt_o > 0
+        assert_mi_close(mi[chk][ok], mi_o[ok], h_o[ok])
+    # the Parzen MI and gradient of the 8 largest pairs (float volumes normalised from the same data)
+    big = np.argsort([np.prod(s["shape"]) for s in specs])[-8:]
+    for p in big:
+        f, m, depth, bins = vols[p]
+        pctx = cuda_lib.Context(f, m, bins=64, kernel="parzen", fixed_depth=depth, moving_depth=depth)
+        sel = np.nonzero(pair_of == p)[0][:64]
+        mi_p, g_p = pctx.grad(prm[sel], [1.0, 0.7, 1.3])
+        t = sel[0]
+        aff, J = oracle.affine(prm[t], f.shape, (1, 1, 1), m.shape, (1, 1, 1), with_jacobian=True)
+        mi_o, g_o, n = oracle.parzen(f, m, aff, 64, [1.0, 0.7, 1.3], daff=J, fixed_depth=depth, moving_depth=depth)
+        assert np.all(np.abs(mi_p[0] - mi_o) <= 1e-6 * np.maximum(np.abs(mi_o), 1.0)), (p, mi_p[0], mi_o)
+        for iq in range(3):
+            assert np.abs(g_p[0, iq] - g_o[iq]).max() <= 1e-4 * np.abs(g_o[iq]).max(), (p, iq)

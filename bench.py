@@ -125,6 +125,31 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows), "samples_under_load": len(load)}
 
 
+def rank_transforms(rank):
+    """The transforms one rank evaluates per step: a seed of its own, so ranks share no
+    work and add up (weak scaling; no collective on the data path)."""
+    from paper_1909_10690_gb300 import phantoms
+
+    return phantoms.random_transforms(N_T, seed=31 + rank)
+
+
+def max_over_ranks(x, world):
+    """Largest value of a host scalar over all ranks (the job's time is its slowest rank's)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as tdist
+
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps, units_per_rank_step, seconds):
+    """Units all ranks processed over the slowest rank's time."""
+    return world * steps * units_per_rank_step / seconds
+
+
 def oracle_rate(f, m, prm, cores):
     """Oracle vox.T/s on the given transforms (all host cores, parallel across transforms)."""
     import oracle
@@ -142,7 +167,7 @@ def run_reference(args, rank, world):
 
     cores = os.cpu_count() or 1
     f, m = phantoms.head_pair(shape=SHAPE, spacing=(1, 1, 1), seed=30)
-    prm = phantoms.random_transforms(N_T, seed=31)
+    prm = rank_transforms(0)
     per_step = cores  # one transform per core per step: a bounded sample of the step's 4096
     for w in range(args.warmup):
         oracle_rate(f, m, prm[w * per_step:(w + 1) * per_step], cores)
@@ -180,15 +205,8 @@ def run_ours(args, rank, world, local_rank):
         if dist:
             tdist.barrier()
 
-    def allmax(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        return float(t.item())
-
     f, m = phantoms.head_pair(shape=SHAPE, spacing=(1, 1, 1), seed=30)
-    prm = phantoms.random_transforms(N_T, seed=31 + rank)
+    prm = rank_transforms(rank)
     stream = torch.cuda.Stream(device=dev)
     ctx = mi.Context(f, m, bins=BINS, fixed_depth=DEPTH, moving_depth=DEPTH, path="batched", device=local_rank)
     ctx.set_stream(stream)
@@ -217,9 +235,9 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    total_s = allmax(sum(step_ms) / 1e3)
+    total_s = max_over_ranks(sum(step_ms) / 1e3, world)
     assert torch.isfinite(out).all()
-    value = world * args.steps * N_T * nvox / total_s
+    value = whole_job_rate(world, args.steps, N_T * nvox, total_s)
     # --- roofline of the main kernel ----------------------------------------------
     pk, src = peaks()
     props = torch.cuda.get_device_properties(dev)
@@ -240,9 +258,9 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.steps):
         res = ctx.eval(prm_pinned, QS)  # host in, host out
     barrier()
-    e2e_s = allmax(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     assert np.isfinite(res).all()
-    e2e = {"value": world * args.steps * N_T * nvox / e2e_s, "unit": "voxel*transforms/s",
+    e2e = {"value": whole_job_rate(world, args.steps, N_T * nvox, e2e_s), "unit": "voxel*transforms/s",
            "h2d_bytes_per_step": N_T * 48 + N_T * 8, "d2h_bytes_per_step": N_T * len(QS) * 8 + 8}
     extra = {}
     if rank == 0 and not args.skip_extras:

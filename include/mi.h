@@ -99,7 +99,12 @@ enum {
        65535 fixed voxels, 16-bit halves for the rest (provably never overflow);
        fits when those rows are few */
     MI_HV_ROWS = 8,
-    MI_HV_ROWS_TEX = 9
+    MI_HV_ROWS_TEX = 9,
+    /* the moving volume as 2 x 2 (x, y) quads read through the texture path:
+       two fetches per voxel instead of four, twice the moving-volume memory */
+    MI_HV_ROWS_QUAD = 10,
+    MI_HV_U32_QUAD = 11,
+    MI_HV_U16_QUAD = 12
 };
 /* Evaluation path of mi_eval. */
 enum { MI_PATH_AUTO = 0, MI_PATH_PLAIN = 1, MI_PATH_BATCHED = 2 };

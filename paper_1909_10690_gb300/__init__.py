@@ -23,6 +23,7 @@ MI_OK, MI_EINVAL, MI_ENOMEM, MI_ECUDA, MI_EEMPTY, MI_EUNSUPPORTED, MI_ERANGE = r
 HV_AUTO, HV_U32, HV_U32_MATCH, HV_U16, HV_U16_MATCH = -1, 0, 1, 2, 3
 HV_U32_TEX, HV_U32_MATCH_TEX, HV_U16_TEX, HV_U16_MATCH_TEX = 4, 5, 6, 7
 HV_ROWS, HV_ROWS_TEX = 8, 9
+HV_ROWS_QUAD, HV_U32_QUAD, HV_U16_QUAD = 10, 11, 12
 PATH_AUTO, PATH_PLAIN, PATH_BATCHED = 0, 1, 2
 _DT = {np.dtype(np.uint8): 0, np.dtype(np.uint16): 1, np.dtype(np.float32): 2}
 

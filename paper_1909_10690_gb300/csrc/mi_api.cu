@@ -189,12 +189,16 @@ struct Pair {
     DevBuf fbins, mov, movp;    // hard path (movp: x-paired moving volume)
     cudaArray_t arr = nullptr;  // the pairs as a 3D array, read through tex
     cudaTextureObject_t tex = 0;
+    cudaArray_t arrq = nullptr;  // 2 x 2 quads as a 3D array (one extra z plane), read through texq
+    cudaTextureObject_t texq = 0;
     DevBuf rowinfo;             // row-bound layout table (bins entries)
     int rows_words = 0;
     DevBuf pfbins, pmov;        // Parzen path
     ~Pair() {
         if (tex) cudaDestroyTextureObject(tex);
         if (arr) cudaFreeArray(arr);
+        if (texq) cudaDestroyTextureObject(texq);
+        if (arrq) cudaFreeArray(arrq);
     }
 };
 
@@ -390,13 +394,13 @@ mi_status add_pair(mi_ctx *ctx, const mi_volume *fx, const mi_volume *mv, int bi
             uint32_t off = 0;
             for (int r = 0; r < bins; ++r)
                 if (F[r] > 65535) {
-                    info[r] = off | (1u << 31);
+                    info[r] = off << 6 | 32u;
                     off += S;
                 }
             int k = 0;
             for (int r = 0; r < bins; ++r)
                 if (F[r] <= 65535) {
-                    info[r] = (off + (uint32_t)(k / 2) * S) | ((uint32_t)(k % 2 ? 16 : 0) << 24);
+                    info[r] = (off + (uint32_t)(k / 2) * S) << 6 | (uint32_t)(k % 2 ? 16 : 0);
                     ++k;
                 }
             off += (uint32_t)((k + 1) / 2) * S;
@@ -441,6 +445,27 @@ mi_status add_pair(mi_ctx *ctx, const mi_volume *fx, const mi_volume *mv, int bi
         td.readMode = cudaReadModeElementType;
         td.normalizedCoords = 0;
         MI_CU(cudaCreateTextureObject(&P->tex, &rd, &td, nullptr), "creating the texture object");
+        // 2 x 2 quads (uchar4 / ushort4) with the last z plane repeated, read at integer texel coordinates
+        {
+            const int cb = P->mdtype == 0 ? 8 : 16;
+            const size_t qsz = (size_t)cb / 2;  // bytes per quad
+            DevBuf quads;
+            MI_CU(quads.ensure((size_t)P->nm[0] * P->nm[1] * (P->nm[2] + 1) * qsz), "allocating the quads");
+            MI_CU(launch_make_quads(P->mov.p, P->mdtype, P->nm, quads.p, s), "building the quads");
+            cudaChannelFormatDesc cq = cudaCreateChannelDesc(cb, cb, cb, cb, cudaChannelFormatKindUnsigned);
+            MI_CU(cudaMalloc3DArray(&P->arrq, &cq, make_cudaExtent(P->nm[0], P->nm[1], P->nm[2] + 1)),
+                  "allocating the quad array");
+            cudaMemcpy3DParms cq3;
+            memset(&cq3, 0, sizeof cq3);
+            cq3.srcPtr = make_cudaPitchedPtr(quads.p, (size_t)P->nm[0] * qsz, P->nm[0], P->nm[1]);
+            cq3.dstArray = P->arrq;
+            cq3.extent = make_cudaExtent(P->nm[0], P->nm[1], P->nm[2] + 1);
+            cq3.kind = cudaMemcpyDeviceToDevice;
+            MI_CU(cudaMemcpy3DAsync(&cq3, s), "filling the quad array");
+            rd.res.array.array = P->arrq;
+            MI_CU(cudaCreateTextureObject(&P->texq, &rd, &td, nullptr), "creating the quad texture object");
+            MI_CU(cudaStreamSynchronize(s), "building the quads");
+        }
     }
     MI_CU(cudaStreamSynchronize(s), "preparing the volumes");
     ctx->max_bins = std::max(ctx->max_bins, bins);
@@ -459,6 +484,7 @@ mi_status upload_pairs(mi_ctx *ctx) {
         d.mov = P.mov.p;
         d.movp = P.movp.p;
         d.texp = P.tex;
+        d.texq = P.texq;
         d.rowinfo = P.rowinfo.as<uint32_t>();
         d.rows_words = P.rows_words;
         for (int a = 0; a < 3; ++a) {
@@ -482,6 +508,7 @@ PairDev host_pairdev(const Pair &P) {
     d.mov = P.mov.p;
     d.movp = P.movp.p;
     d.texp = P.tex;
+    d.texq = P.texq;
     d.rowinfo = P.rowinfo.as<uint32_t>();
     d.rows_words = P.rows_words;
     for (int a = 0; a < 3; ++a) {
@@ -518,7 +545,7 @@ mi_status create_common(mi_ctx **out, const mi_volume *fixed, const mi_volume *m
         g_create_error = "the Parzen form takes one pair per context";
         return MI_EINVAL;
     }
-    if (ctx->opt.hist_variant < MI_HV_AUTO || ctx->opt.hist_variant > MI_HV_ROWS_TEX) {
+    if (ctx->opt.hist_variant < MI_HV_AUTO || ctx->opt.hist_variant > MI_HV_U16_QUAD) {
         g_create_error = "opt.hist_variant out of range";
         return MI_EINVAL;
     }
@@ -566,7 +593,7 @@ mi_status create_common(mi_ctx **out, const mi_volume *fixed, const mi_volume *m
             return st;
         }
         MI_CU(ctx->d_flags.ensure(2 * sizeof(int)), "allocating flags");
-        MI_CU(ctx->d_ticket.ensure(sizeof(int)), "allocating the ticket");
+        MI_CU(ctx->d_ticket.ensure(2 * sizeof(int)), "allocating the ticket");  // ticket, sweep phase
     }
     *out = ctx.release();
     return MI_OK;
@@ -741,7 +768,7 @@ cudaError_t record_event(cudaEvent_t ev, cudaStream_t s) {
 
 mi_status launch_batched_once(mi_ctx *ctx, int nitems, const QSet &Q, const Outputs &O, const Choice &ch,
                               bool record = false) {
-    MI_CU(cudaMemsetAsync(ctx->d_ticket.p, 0, sizeof(int), ctx->stream), "resetting the work queue");
+    MI_CU(cudaMemsetAsync(ctx->d_ticket.p, 0, 2 * sizeof(int), ctx->stream), "resetting the work queue");
     if (record) MI_CU(record_event(ctx->ev0, ctx->stream), "event");
     MI_CU(launch_batched(ctx->d_pairs.as<PairDev>(), ctx->d_aff.as<int32_t>(), ctx->d_items.as<Item>(), nitems,
                          ctx->d_ticket.as<int>(), ctx->max_bins, ctx->max_rows_words, ch.variant, ch.threads, ch.ctas,
@@ -751,7 +778,9 @@ mi_status launch_batched_once(mi_ctx *ctx, int nitems, const QSet &Q, const Outp
     return MI_OK;
 }
 
-// Autotune: time every candidate on the first items of this call (one wave).
+// Autotune: time every candidate on the first items of this call (up to three
+// waves, so that effects that build up across waves, such as CTAs drifting to
+// different parts of the volumes, show in the timing).
 mi_status autotune(mi_ctx *ctx, int nitems, const QSet &Q, const Outputs &O, Choice &best,
                    const std::vector<Choice> &cands) {
     if (cands.empty()) return ctx->fail(MI_EUNSUPPORTED, "no histogram variant fits this bin count and volume size");
@@ -770,12 +799,12 @@ mi_status autotune(mi_ctx *ctx, int nitems, const QSet &Q, const Outputs &O, Cho
     Outputs Ot = O;
     Ot.dump = nullptr;
     for (const Choice &c : cands) {
-        const int items = std::min(nitems, c.ctas);
+        const int items = std::min(nitems, 3 * c.ctas);
         Choice cc = c;
-        mi_status st = launch_batched_once(ctx, items, Q, Ot, cc);  // warm-up
+        mi_status st = launch_batched_once(ctx, std::min(items, c.ctas), Q, Ot, cc);  // warm-up
         if (st != MI_OK) break;
         cudaEventRecord(e0, ctx->stream);
-        for (int rep = 0; rep < 2; ++rep) launch_batched_once(ctx, items, Q, Ot, cc);
+        launch_batched_once(ctx, items, Q, Ot, cc);
         cudaEventRecord(e1, ctx->stream);
         cudaError_t e = cudaEventSynchronize(e1);
         if (e != cudaSuccess) {
@@ -785,7 +814,6 @@ mi_status autotune(mi_ctx *ctx, int nitems, const QSet &Q, const Outputs &O, Cho
         }
         float ms = 0;
         cudaEventElapsedTime(&ms, e0, e1);
-        // per item on a full wave
         ms = ms / (float)items;
         if (ms < best_ms) {
             best_ms = ms;

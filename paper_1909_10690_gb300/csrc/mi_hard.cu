@@ -32,6 +32,7 @@ namespace mi {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kSlabs = 8;  // slabs per sweep in the batched kernel
 constexpr uint32_t kEmptyKey = 0xffffffffu;
 
 // ---------------------------------------------------------------------------
@@ -147,6 +148,57 @@ __device__ __forceinline__ int sample_hard_tex(unsigned long long tex, int ux, i
     const int e10 = lerp8g((int)(c & LO), (int)(c >> HB), fx, gx), e11 = lerp8g((int)(d & LO), (int)(d >> HB), fx, gx);
     const int g0 = lerp8g(e00, e01, fy, gy), g1 = lerp8g(e10, e11, fy, gy);
     return lerp8g(g0, g1, fz, gz);
+}
+
+// The same resample from 2 x 2 quads through the texture path.  A fetch at
+// integer texel coordinates (ix, iy, iz) returns v(ix, iy), v(ix + 1, iy),
+// v(ix, iy + 1), v(ix + 1, iy + 1) of plane iz in four registers, already
+// unpacked, so a voxel takes two fetches (planes iz and iz + 1; the array
+// repeats the last plane once, so iz + 1 is always in range).
+__device__ __forceinline__ void tex_quad(unsigned long long tex, int x, int y, int z, uint32_t &a, uint32_t &b,
+                                         uint32_t &c, uint32_t &d) {
+    asm("tex.3d.v4.u32.s32 {%0, %1, %2, %3}, [%4, {%5, %6, %7, %7}];"
+        : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
+        : "l"(tex), "r"(x), "r"(y), "r"(z));
+}
+
+// The 8 neighbours of the sample at 16.16 index (ux, uy, uz): t[0..3] from
+// plane iz, t[4..7] from plane iz + 1.
+__device__ __forceinline__ void quad_fetch(unsigned long long tex, unsigned ux, unsigned uy, unsigned uz,
+                                           uint32_t (&t)[8]) {
+    const int ix = (int)(ux >> 16), iy = (int)(uy >> 16), iz = (int)(uz >> 16);
+    tex_quad(tex, ix, iy, iz, t[0], t[1], t[2], t[3]);
+    tex_quad(tex, ix, iy, iz + 1, t[4], t[5], t[6], t[7]);
+}
+
+// Trilinear value from the 8 neighbours: x, then y, then z stages.
+__device__ __forceinline__ int quad_lerp(unsigned ux, unsigned uy, unsigned uz, const uint32_t (&t)[8]) {
+    const int fx = (int)__byte_perm(ux, 0u, 0x4441), fy = (int)__byte_perm(uy, 0u, 0x4441),
+              fz = (int)__byte_perm(uz, 0u, 0x4441);
+    const int gx = 256 - fx, gy = 256 - fy, gz = 256 - fz;
+    const int e00 = lerp8g((int)t[0], (int)t[1], fx, gx), e01 = lerp8g((int)t[2], (int)t[3], fx, gx);
+    const int e10 = lerp8g((int)t[4], (int)t[5], fx, gx), e11 = lerp8g((int)t[6], (int)t[7], fx, gx);
+    const int g0 = lerp8g(e00, e01, fy, gy), g1 = lerp8g(e10, e11, fy, gy);
+    return lerp8g(g0, g1, fz, gz);
+}
+
+// Builds the 2 x 2 quads: out has dims (n0, n1, n2 + 1), the last plane repeated.
+template <typename T, typename QT>
+__global__ void k_make_quads(const T *__restrict__ in, int n0, int n1, int n2, QT *__restrict__ out) {
+    const long long plane = (long long)n0 * n1, n = plane * (n2 + 1);
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n; o += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(o % n0);
+        const int y = (int)((o / n0) % n1);
+        const int z = min((int)(o / plane), n2 - 1);
+        const int x1 = min(x + 1, n0 - 1), y1 = min(y + 1, n1 - 1);
+        const T *p = in + plane * z;
+        QT q;
+        q.x = p[(long long)y * n0 + x];
+        q.y = p[(long long)y * n0 + x1];
+        q.z = p[(long long)y1 * n0 + x];
+        q.w = p[(long long)y1 * n0 + x1];
+        out[o] = q;
+    }
 }
 
 // Builds the padded x-paired volume: out has dims (n0, n1 + 1, n2 + 1).
@@ -355,8 +407,8 @@ struct HistU16 {
 // F[r] <= 65535 ("narrow") share words two at a time as 16-bit halves; the
 // others ("wide") get 32-bit words.  No counter can overflow, so increments
 // are fire-and-forget atomics with no return value and no drain.  rowinfo[r]
-// = word offset of row r | shift << 24 | wide << 31; rows are padded to
-// S = B + 1 words.
+// = word offset of row r << 6 | wide << 5 | shift (0 or 16: the half of a
+// narrow row); rows are padded to S = B + 1 words.
 struct HistRows {
     uint32_t *w;
     uint32_t *info;  // B entries, copied into shared memory per item
@@ -370,13 +422,14 @@ struct HistRows {
     __device__ __forceinline__ void add(int bf, int bm, bool valid) {
         if (valid) {
             const uint32_t inf = info[bf];
-            atomicAdd(&w[(inf & 0xffffffu) + bm], 1u << ((inf >> 24) & 31u));
+            // 1 << (inf & 31): the funnel shift takes its count modulo 32
+            atomicAdd(&w[(inf >> 6) + bm], __funnelshift_l(0u, 1u, inf));
         }
     }
     __device__ __forceinline__ uint32_t count(int bf, int bm) const {
         const uint32_t inf = info[bf];
-        const uint32_t v = w[(inf & 0xffffffu) + bm] >> ((inf >> 24) & 31u);
-        return (inf >> 31) ? v : (v & 0xffffu);
+        const uint32_t v = w[(inf >> 6) + bm] >> (inf & 31u);
+        return (inf & 32u) ? v : (v & 0xffffu);
     }
 };
 
@@ -477,9 +530,11 @@ __device__ typename HistOf<HV>::T make_hist(unsigned char *smem, const SmemLayou
 // block_stride, n = 0, 1, ...  A warp clips its next 32 rows at once (lane l
 // takes the warp's l-th upcoming row, exactly in 64 bits), then walks them one
 // by one, 32 voxels at a time, with each row's interval broadcast by shuffles.
-template <typename PairT, bool TEX, class Hist>
+// Blocks first_block + n * block_stride, n = 0, 1, ..., below n_end are
+// visited (the batched kernel passes one slab of blocks at a time).
+template <typename PairT, int FM, class Hist>
 __device__ void accumulate_rows(const PairDev &P, const int *q, long long first_block, long long block_stride,
-                                Hist &H) {
+                                long long n_end, Hist &H) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int nf0 = P.nf[0], nf1 = P.nf[1];
     const long long R = (long long)nf1 * P.nf[2];
@@ -488,18 +543,22 @@ __device__ void accumulate_rows(const PairDev &P, const int *q, long long first_
     const int bins = P.bins, mdepth = P.mdepth;
     const PairT *__restrict__ movp = (const PairT *)P.movp;
     for (long long n0b = 0;; n0b += 32) {
-        // rows of this group: lane l gets block first_block + (n0b + l) * block_stride
-        const long long first_row = (first_block + n0b * block_stride) * nwarps + warp;
-        if (first_row >= R) break;
+        // blocks of this group: lane l gets block first_block + (n0b + l) * block_stride
+        if (first_block + n0b * block_stride >= n_end) break;
         RowClip mine;
         mine.lo = 0;
         mine.hi = -1;
         mine.u0 = mine.u1 = mine.u2 = 0;
-        const long long rl = (first_block + (n0b + lane) * block_stride) * nwarps + warp;
-        if (rl < R) mine = clip_row(q, (int)(rl % nf1), (int)(rl / nf1), nf0, P.nm);
+        const long long nl = first_block + (n0b + lane) * block_stride;
+        if (nl < n_end) {
+            const long long rl = nl * nwarps + warp;
+            if (rl < R) mine = clip_row(q, (int)(rl % nf1), (int)(rl / nf1), nf0, P.nm);
+        }
         for (int s = 0; s < 32; ++s) {
-            const long long r = (first_block + (n0b + s) * block_stride) * nwarps + warp;
-            if (r >= R) break;  // warp-uniform
+            const long long n = first_block + (n0b + s) * block_stride;
+            if (n >= n_end) break;  // warp-uniform
+            const long long r = n * nwarps + warp;
+            if (r >= R) break;  // warp-uniform: only the last block may be partial
             const int lo = __shfl_sync(kFull, mine.lo, s), hi = __shfl_sync(kFull, mine.hi, s);
             if (lo > hi) continue;
             // unsigned: lanes past the row end may step outside the int range; only in-range lanes use them
@@ -507,12 +566,47 @@ __device__ void accumulate_rows(const PairDev &P, const int *q, long long first_
                      U1 = (unsigned)__shfl_sync(kFull, mine.u1, s) + (unsigned)st1 * lane,
                      U2 = (unsigned)__shfl_sync(kFull, mine.u2, s) + (unsigned)st2 * lane;
             const uint8_t *__restrict__ frow = P.fbins + (size_t)r * nf0;
+            if constexpr (FM == FM_QUAD) {
+                // full steps (all 32 lanes inside the interval) without predicates; the fixed bin of
+                // the next step is loaded one step ahead, so its L2 latency overlaps a whole step
+                const unsigned d0 = 32u * (unsigned)st0, d1 = 32u * (unsigned)st1, d2 = 32u * (unsigned)st2;
+                int base = lo;
+                const uint8_t *__restrict__ fp = frow + lo + lane;
+                int bf_next = base + 31 <= hi ? (int)__ldg(fp) : 0;
+#pragma unroll 2
+                for (; base + 31 <= hi; base += 32) {
+                    const int bf = bf_next;
+                    fp += 32;
+                    if (base + 63 <= hi) bf_next = (int)__ldg(fp);
+                    uint32_t t[8];
+                    quad_fetch(P.texq, U0, U1, U2, t);
+                    H.add(bf, (quad_lerp(U0, U1, U2, t) * bins) >> mdepth, true);
+                    U0 += d0;
+                    U1 += d1;
+                    U2 += d2;
+                }
+                if (base <= hi) {  // the tail: lanes up to hi - base
+                    const bool valid = base + lane <= hi;
+                    int bf = 0, bm = 0;
+                    if (valid) {
+                        uint32_t t[8];
+                        quad_fetch(P.texq, U0, U1, U2, t);
+                        bm = (quad_lerp(U0, U1, U2, t) * bins) >> mdepth;
+                        bf = (int)__ldg(frow + base + lane);
+                    }
+                    H.add(bf, bm, valid);
+                }
+                continue;
+            }
             for (int i = lo + lane; i - lane <= hi; i += 32) {
                 const bool valid = i <= hi;
                 int bf = 0, bm = 0;
                 if (valid) {
-                    const int v = TEX ? sample_hard_tex<PairT>(P.texp, (int)U0, (int)U1, (int)U2)
-                                      : sample_hard_pair<PairT>(movp, sy, sz, n0, sz, (int)U0, (int)U1, (int)U2);
+                    int v;
+                    if constexpr (FM == FM_TEX)
+                        v = sample_hard_tex<PairT>(P.texp, (int)U0, (int)U1, (int)U2);
+                    else
+                        v = sample_hard_pair<PairT>(movp, sy, sz, n0, sz, (int)U0, (int)U1, (int)U2);
                     bm = (v * bins) >> mdepth;
                     bf = (int)__ldg(frow + i);
                 }
@@ -658,7 +752,7 @@ __device__ void reduce_entropies(const Hist &H, int B, const QSet &Q, uint32_t *
 // Plain form
 // ---------------------------------------------------------------------------
 
-template <typename PairT, int HV, bool TEX>
+template <typename PairT, int HV, int FM>
 __global__ void __launch_bounds__(1024, 1)
     k_hist(const PairDev *__restrict__ pairs, const int32_t *__restrict__ aff, uint32_t *__restrict__ ghist,
            int *flags) {
@@ -674,7 +768,7 @@ __global__ void __launch_bounds__(1024, 1)
     H.zero();
     __syncthreads();
     const int nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
-    accumulate_rows<PairT, TEX>(P, q, blockIdx.x, gridDim.x, H);
+    accumulate_rows<PairT, FM>(P, q, blockIdx.x, gridDim.x, ((long long)P.nf[1] * P.nf[2] + nwarps - 1) / nwarps, H);
     __syncthreads();
     uint32_t *gh = ghist + (size_t)t * B * B;
     for (int r = threadIdx.x >> 5; r < B; r += nwarps)
@@ -703,15 +797,16 @@ __global__ void __launch_bounds__(1024, 1)
 // Batched form: persistent CTAs, one (pair, transform) item per CTA at a time
 // ---------------------------------------------------------------------------
 
-template <int HV, bool TEX>
+template <int HV, int FM>
 __global__ void __launch_bounds__(1024, 1)
     k_batched(const PairDev *__restrict__ pairs, const int32_t *__restrict__ aff, const Item *__restrict__ items,
               int nitems, int *ticket, int max_bins, int rows_words, QSet Q, Outputs O) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_item;
+    __shared__ int s_item, s_slab;
     __shared__ int q[12];
     const SmemLayout L = smem_layout(HV, max_bins, blockDim.x, rows_words);
     const int nwarps = blockDim.x >> 5;
+    int *phase = ticket + 1;  // the slab most recently started by any CTA
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(ticket, 1);
         __syncthreads();
@@ -725,10 +820,33 @@ __global__ void __launch_bounds__(1024, 1)
         H.load_info(P.rowinfo);
         H.zero();
         __syncthreads();
-        if (P.mdtype == 0)
-            accumulate_rows<uint16_t, TEX>(P, q, 0, 1, H);
-        else
-            accumulate_rows<uint32_t, TEX>(P, q, 0, 1, H);
+        // The sweep is cut into kSlabs slabs of row blocks, done in any order (counts do not depend
+        // on it).  Each slab goes to the first remaining one at or after the slab most recently
+        // started by any CTA, so CTAs working on different transforms keep to neighbouring slabs
+        // of the volumes and their working set stays in L2.  No CTA waits for another.
+        const long long NB = ((long long)P.nf[1] * P.nf[2] + nwarps - 1) / nwarps;
+        const long long SB = (NB + kSlabs - 1) / kSlabs;
+        unsigned left = (1u << kSlabs) - 1u;
+        while (left) {
+            if (threadIdx.x == 0) {
+                int k = *(volatile int *)phase;
+                k = k < 0 || k >= kSlabs ? 0 : k;
+                while (!((left >> k) & 1u)) k = k + 1 == kSlabs ? 0 : k + 1;
+                s_slab = k;
+                *(volatile int *)phase = k;
+            }
+            __syncthreads();
+            const int k = s_slab;
+            left &= ~(1u << k);
+            const long long b0 = (long long)k * SB, b1 = b0 + SB < NB ? b0 + SB : NB;
+            if (b0 < b1) {
+                if (FM == FM_QUAD || P.mdtype == 1)  // quads are unpacked by the texture unit: one instance
+                    accumulate_rows<uint32_t, FM>(P, q, b0, 1, b1, H);
+                else
+                    accumulate_rows<uint16_t, FM>(P, q, b0, 1, b1, H);
+            }
+            __syncthreads();  // s_slab is rewritten for the next slab
+        }
         __syncthreads();
         if (O.dump) {
             uint32_t *dh = O.dump + (size_t)I.t * B * B;
@@ -830,6 +948,17 @@ cudaError_t launch_make_pairs(const void *mov, int dtype, const int nm[3], void 
     return cudaGetLastError();
 }
 
+cudaError_t launch_make_quads(const void *mov, int dtype, const int nm[3], void *out, cudaStream_t s) {
+    const long long n = (long long)nm[0] * nm[1] * (nm[2] + 1);
+    if (dtype == 0)
+        k_make_quads<uint8_t, uchar4><<<grid_for(n, 256), 256, 0, s>>>((const uint8_t *)mov, nm[0], nm[1], nm[2],
+                                                                        (uchar4 *)out);
+    else
+        k_make_quads<uint16_t, ushort4><<<grid_for(n, 256), 256, 0, s>>>((const uint16_t *)mov, nm[0], nm[1], nm[2],
+                                                                          (ushort4 *)out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bin_fixed(const void *data, int dtype, int depth, long long n, int bins, uint8_t *out,
                              cudaStream_t s) {
     if (dtype == 0)
@@ -844,39 +973,42 @@ cudaError_t launch_table(double *tab, float q, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Every variant as (public value, counter kind, fetch mode).
+#define MI_VARIANTS(X)                                                                              \
+    X(HV_U32, HV_U32, FM_LDG) X(HV_U32_MATCH, HV_U32_MATCH, FM_LDG) X(HV_U16, HV_U16, FM_LDG)        \
+    X(HV_U16_MATCH, HV_U16_MATCH, FM_LDG) X(HV_TEX + HV_U32, HV_U32, FM_TEX)                        \
+    X(HV_TEX + HV_U32_MATCH, HV_U32_MATCH, FM_TEX) X(HV_TEX + HV_U16, HV_U16, FM_TEX)                \
+    X(HV_TEX + HV_U16_MATCH, HV_U16_MATCH, FM_TEX) X(HV_ROWS, HV_ROWS, FM_LDG)                      \
+    X(HV_ROWS_TEX, HV_ROWS, FM_TEX) X(HV_ROWS_QUAD, HV_ROWS, FM_QUAD) X(HV_U32_QUAD, HV_U32, FM_QUAD) \
+    X(HV_U16_QUAD, HV_U16, FM_QUAD)
+
+template <typename MT>
+static const void *plain_fn_of(int variant) {
+    switch (variant) {
+#define MI_PLAIN_CASE(V, K, F) \
+    case V: return (const void *)k_hist<MT, K, F>;
+        MI_VARIANTS(MI_PLAIN_CASE)
+#undef MI_PLAIN_CASE
+        default: return nullptr;
+    }
+}
+
+static const void *plain_fn(int variant, int mdtype) {
+    return mdtype == 0 ? plain_fn_of<uint16_t>(variant) : plain_fn_of<uint32_t>(variant);
+}
+
 cudaError_t launch_plain_hist(const PairDev *d_pair, const PairDev &h_pair, const int32_t *d_aff, int n,
                               uint32_t *d_hist, int variant, int threads, int ctas, int *d_flags, cudaStream_t s) {
     const size_t B2 = (size_t)h_pair.bins * h_pair.bins;
     cudaError_t e = cudaMemsetAsync(d_hist, 0, (size_t)n * B2 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     const size_t smem = smem_layout(variant, h_pair.bins, threads, h_pair.rows_words).total;
-    dim3 grid(ctas, n);
-#define MI_LAUNCH_PLAIN(MT, HVV, TX)                                                     \
-    do {                                                                                 \
-        auto kf = k_hist<MT, HVV, TX>;                                                   \
-        if ((e = set_smem(kf, smem)) != cudaSuccess) return e;                           \
-        kf<<<grid, threads, smem, s>>>(d_pair, d_aff, d_hist, d_flags);                  \
-    } while (0)
-#define MI_LAUNCH_PLAIN_MT(HVV, TX)                                \
-    do {                                                           \
-        if (h_pair.mdtype == 0) MI_LAUNCH_PLAIN(uint16_t, HVV, TX); \
-        else MI_LAUNCH_PLAIN(uint32_t, HVV, TX);                   \
-    } while (0)
-    const bool tex = hv_tex(variant);
-    switch (hv_kind(variant)) {
-        case HV_U32: if (tex) MI_LAUNCH_PLAIN_MT(HV_U32, true); else MI_LAUNCH_PLAIN_MT(HV_U32, false); break;
-        case HV_U32_MATCH:
-            if (tex) MI_LAUNCH_PLAIN_MT(HV_U32_MATCH, true); else MI_LAUNCH_PLAIN_MT(HV_U32_MATCH, false);
-            break;
-        case HV_U16: if (tex) MI_LAUNCH_PLAIN_MT(HV_U16, true); else MI_LAUNCH_PLAIN_MT(HV_U16, false); break;
-        case HV_U16_MATCH:
-            if (tex) MI_LAUNCH_PLAIN_MT(HV_U16_MATCH, true); else MI_LAUNCH_PLAIN_MT(HV_U16_MATCH, false);
-            break;
-        default: if (tex) MI_LAUNCH_PLAIN_MT(HV_ROWS, true); else MI_LAUNCH_PLAIN_MT(HV_ROWS, false); break;
-    }
-#undef MI_LAUNCH_PLAIN_MT
-#undef MI_LAUNCH_PLAIN
-    return cudaGetLastError();
+    const void *fn = plain_fn(variant, h_pair.mdtype);
+    if (!fn) return cudaErrorInvalidValue;
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return e;
+    void *args[] = {(void *)&d_pair, (void *)&d_aff, (void *)&d_hist, (void *)&d_flags};
+    return cudaLaunchKernel(fn, dim3(ctas, n), dim3(threads), args, smem, s);
 }
 
 cudaError_t launch_entropy(const uint32_t *d_hist, int n, int bins, const QSet &Q, const Outputs &O, cudaStream_t s) {
@@ -890,22 +1022,18 @@ cudaError_t launch_entropy(const uint32_t *d_hist, int n, int bins, const QSet &
 
 static const void *batched_fn(int variant) {
     switch (variant) {
-        case HV_U32: return (const void *)k_batched<HV_U32, false>;
-        case HV_U32_MATCH: return (const void *)k_batched<HV_U32_MATCH, false>;
-        case HV_U16: return (const void *)k_batched<HV_U16, false>;
-        case HV_U16_MATCH: return (const void *)k_batched<HV_U16_MATCH, false>;
-        case HV_TEX + HV_U32: return (const void *)k_batched<HV_U32, true>;
-        case HV_TEX + HV_U32_MATCH: return (const void *)k_batched<HV_U32_MATCH, true>;
-        case HV_TEX + HV_U16: return (const void *)k_batched<HV_U16, true>;
-        case HV_TEX + HV_U16_MATCH: return (const void *)k_batched<HV_U16_MATCH, true>;
-        case HV_ROWS: return (const void *)k_batched<HV_ROWS, false>;
-        default: return (const void *)k_batched<HV_ROWS, true>;
+#define MI_BATCHED_CASE(V, K, F) \
+    case V: return (const void *)k_batched<K, F>;
+        MI_VARIANTS(MI_BATCHED_CASE)
+#undef MI_BATCHED_CASE
+        default: return nullptr;
     }
 }
 
 int batched_ctas_per_sm(int variant, int max_bins, int threads, int rows_words) {
     const size_t smem = smem_layout(variant, max_bins, threads, rows_words).total;
     const void *fn = batched_fn(variant);
+    if (!fn) return 0;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess) return 0;
@@ -917,6 +1045,7 @@ cudaError_t launch_batched(const PairDev *d_pairs, const int32_t *d_aff, const I
                            const QSet &Q, const Outputs &O, cudaStream_t s) {
     const size_t smem = smem_layout(variant, max_bins, threads, rows_words).total;
     const void *fn = batched_fn(variant);
+    if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&d_pairs, (void *)&d_aff, (void *)&d_items, (void *)&nitems, (void *)&d_ticket,

@@ -18,7 +18,8 @@ struct PairDev {
     const void *mov;       // moving volume, uint8 or uint16, clamped to its bit depth
     const void *movp;      // x-paired copy (v[x], v[x+1]), uint16 / uint32, dims (nx, ny + 1, nz + 1)
     unsigned long long texp;  // the same pairs as a 3D texture (point sampling, clamped), dims (nx, ny, nz)
-    const uint32_t *rowinfo;  // row-bound layout: per fixed bin, word offset | shift << 24 | wide << 31
+    unsigned long long texq;  // 2 x 2 quads (x, y), (x + 1, y), (x, y + 1), (x + 1, y + 1) as a 3D texture
+    const uint32_t *rowinfo;  // row-bound layout: per fixed bin, word offset << 6 | wide << 5 | shift (0 or 16)
     int nf[3];             // fixed dims (x, y, z)
     int nm[3];             // moving dims
     int bins;
@@ -54,12 +55,19 @@ struct Item {
 };
 
 // Histogram variants (match the public MI_HV_* values).  0..3: counter kinds
-// with LDG gathers, 4..7: the same with texture-path gathers, 8 / 9: the
-// row-bound layout with LDG / texture gathers.
+// with LDG gathers of x-pairs, 4..7: the same with texture-path gathers of
+// x-pairs, 8 / 9: the row-bound layout with LDG / texture x-pairs, 10..12:
+// the row-bound, 32-bit and 16-bit kinds with texture gathers of 2 x 2 quads.
 enum { HV_U32 = 0, HV_U32_MATCH = 1, HV_U16 = 2, HV_U16_MATCH = 3, HV_TEX = 4, HV_ROWS = 8, HV_ROWS_TEX = 9,
-       HV_COUNT = 10 };
-__host__ __device__ inline int hv_kind(int v) { return v < HV_ROWS ? v % HV_TEX : HV_ROWS; }
-__host__ __device__ inline bool hv_tex(int v) { return (v >= HV_TEX && v < HV_ROWS) || v == HV_ROWS_TEX; }
+       HV_ROWS_QUAD = 10, HV_U32_QUAD = 11, HV_U16_QUAD = 12, HV_COUNT = 13 };
+// How a variant fetches the moving volume.
+enum { FM_LDG = 0, FM_TEX = 1, FM_QUAD = 2 };
+__host__ __device__ inline int hv_kind(int v) {
+    return v < HV_ROWS ? v % HV_TEX : v == HV_U32_QUAD ? HV_U32 : v == HV_U16_QUAD ? HV_U16 : HV_ROWS;
+}
+__host__ __device__ inline int hv_fetch(int v) {
+    return v >= HV_ROWS_QUAD ? FM_QUAD : ((v >= HV_TEX && v < HV_ROWS) || v == HV_ROWS_TEX) ? FM_TEX : FM_LDG;
+}
 
 // Shared memory needed by a hard-path CTA of `threads` threads for `bins` bins
 // (rows_words: words of the row-bound layout, used by HV_ROWS*).
@@ -72,6 +80,10 @@ cudaError_t launch_f32_to_u16(const float *in, long long n, uint16_t *out, cudaS
 cudaError_t launch_clamp_depth(void *data, int dtype, int depth, long long n, cudaStream_t s);
 // Padded x-paired moving volume, dims (n0, n1 + 1, n2 + 1).
 cudaError_t launch_make_pairs(const void *mov, int dtype, const int nm[3], void *out, cudaStream_t s);
+// 2 x 2 quads of the moving volume, dims (n0, n1, n2): element (x, y, z) holds
+// v(x, y), v(x + 1, y), v(x, y + 1), v(x + 1, y + 1) of plane z, upper indices
+// clamped to the last ones (uchar4 for uint8, ushort4 for uint16 volumes).
+cudaError_t launch_make_quads(const void *mov, int dtype, const int nm[3], void *out, cudaStream_t s);
 cudaError_t launch_bin_fixed(const void *data, int dtype, int depth, long long n, int bins, uint8_t *out,
                              cudaStream_t s);
 cudaError_t launch_table(double *tab, float q, cudaStream_t s);

@@ -113,6 +113,7 @@ enum { MI_PATH_AUTO = 0, MI_PATH_PLAIN = 1, MI_PATH_BATCHED = 2 };
 #define MI_MAX_BINS 256
 #define MI_MIN_BINS 2
 #define MI_MIN_PARZEN_BINS 8
+#define MI_MAX_PARZEN_NX 65536  /* longest fixed row of a MI_PARZEN context */
 
 typedef struct {
     int kernel;        /* MI_HARD (default) or MI_PARZEN                            */
@@ -136,7 +137,8 @@ const char *mi_version(void);
 
 /*
  * Creates a context for one (fixed, moving) pair and a bin count
- * (MI_MIN_BINS..MI_MAX_BINS; MI_MIN_PARZEN_BINS.. for MI_PARZEN).  The metric
+ * (MI_MIN_BINS..MI_MAX_BINS; MI_MIN_PARZEN_BINS..128 for MI_PARZEN, whose
+ * fixed volume must have nx <= MI_MAX_PARZEN_NX, else MI_EUNSUPPORTED).  The metric
  * is F_m(u(x), v(T(x))) of Fig. 1; the pair's geometry (dims, spacing) fixes
  * the parameter-to-affine map.  opt may be NULL (defaults).  On success *out
  * owns device copies of both volumes (the fixed one pre-binned) and must be

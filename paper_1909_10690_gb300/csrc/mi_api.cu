@@ -193,12 +193,16 @@ struct Pair {
     cudaTextureObject_t texq = 0;
     DevBuf rowinfo;             // row-bound layout table (bins entries)
     int rows_words = 0;
-    DevBuf pfbins, pmov;        // Parzen path
+    DevBuf pfbins, pmov, pmovx;  // Parzen path (pmovx: pmov extended by one plane per axis)
+    cudaArray_t parr = nullptr;  // float4 quads of pmovx as a 3D array, read through ptex
+    cudaTextureObject_t ptex = 0;
     ~Pair() {
         if (tex) cudaDestroyTextureObject(tex);
         if (arr) cudaFreeArray(arr);
         if (texq) cudaDestroyTextureObject(texq);
         if (arrq) cudaFreeArray(arrq);
+        if (ptex) cudaDestroyTextureObject(ptex);
+        if (parr) cudaFreeArray(parr);
     }
 };
 
@@ -232,7 +236,7 @@ struct mi_ctx {
     DevBuf d_aff, d_items, d_mi, d_h, d_cnt, d_hist, d_flags, d_ticket, d_dump;
     HostBuf h_aff, h_items, h_out;
     // Parzen scratch
-    DevBuf p_aff, p_jac, p_hist, p_cnt, p_marg, p_ment, p_jsum, p_w, p_mom, p_grad;
+    DevBuf p_aff, p_jac, p_hist, p_cnt, p_marg, p_ment, p_mterm, p_jsum, p_w, p_mom, p_grad;
     // autotune and graph caches
     std::map<std::tuple<int, int, int>, Choice> tuned;  // (path, pair-or--1, n bucket)
     std::map<std::string, std::unique_ptr<GraphEntry>> graphs;
@@ -341,6 +345,9 @@ mi_status add_pair(mi_ctx *ctx, const mi_volume *fx, const mi_volume *mv, int bi
     if (parzen) {
         if (bins < MI_MIN_PARZEN_BINS || bins > 128)
             return ctx->fail(MI_EINVAL, "Parzen bins must be in " + std::to_string(MI_MIN_PARZEN_BINS) + "..128");
+        if (fx->dims[0] > MI_MAX_PARZEN_NX)
+            return ctx->fail(MI_EUNSUPPORTED, "Parzen fixed rows are limited to " + std::to_string(MI_MAX_PARZEN_NX) +
+                                                  " voxels (nx)");
     } else if (bins < MI_MIN_BINS || bins > MI_MAX_BINS) {
         return ctx->fail(MI_EINVAL, "bins must be in 2..256, got " + std::to_string(bins));
     }
@@ -367,6 +374,36 @@ mi_status add_pair(mi_ctx *ctx, const mi_volume *fx, const mi_volume *mv, int bi
         MI_CU(P->pmov.ensure((size_t)P->nvm * 4), "allocating the normalised moving volume");
         MI_CU(launch_parzen_prep_moving(rawm.p, mv->dtype, P->mdepth, P->nvm, P->pmov.as<float>(), s),
               "normalising the moving volume");
+        MI_CU(P->pmovx.ensure((size_t)(P->nm[0] + 1) * (P->nm[1] + 1) * (P->nm[2] + 1) * 4),
+              "allocating the extended moving volume");
+        MI_CU(launch_parzen_extend(P->pmov.as<float>(), P->nm, P->pmovx.as<float>(), s), "extending the moving volume");
+        {
+            const cudaExtent ext = make_cudaExtent(P->nm[0], P->nm[1], P->nm[2] + 1);
+            DevBuf quads;
+            MI_CU(quads.ensure(ext.width * ext.height * ext.depth * 16), "allocating the Parzen quads");
+            MI_CU(launch_parzen_quads(P->pmovx.as<float>(), P->nm, quads.p, s), "building the Parzen quads");
+            cudaChannelFormatDesc cd = cudaCreateChannelDesc(32, 32, 32, 32, cudaChannelFormatKindFloat);
+            MI_CU(cudaMalloc3DArray(&P->parr, &cd, ext), "allocating the Parzen quad array");
+            cudaMemcpy3DParms cp;
+            memset(&cp, 0, sizeof cp);
+            cp.srcPtr = make_cudaPitchedPtr(quads.p, ext.width * 16, ext.width, ext.height);
+            cp.dstArray = P->parr;
+            cp.extent = ext;
+            cp.kind = cudaMemcpyDeviceToDevice;
+            MI_CU(cudaMemcpy3DAsync(&cp, s), "filling the Parzen quad array");
+            cudaResourceDesc rd;
+            memset(&rd, 0, sizeof rd);
+            rd.resType = cudaResourceTypeArray;
+            rd.res.array.array = P->parr;
+            cudaTextureDesc td;
+            memset(&td, 0, sizeof td);
+            td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
+            td.filterMode = cudaFilterModePoint;
+            td.readMode = cudaReadModeElementType;
+            td.normalizedCoords = 0;
+            MI_CU(cudaCreateTextureObject(&P->ptex, &rd, &td, nullptr), "creating the Parzen quad texture");
+            MI_CU(cudaStreamSynchronize(s), "building the Parzen quads");
+        }
         P->mdtype = 1;
     } else {
         // fixed: float -> 16-bit first, then bins
@@ -1015,6 +1052,8 @@ mi_status parzen_core(mi_ctx *ctx, const std::vector<float> &prm, int n, const f
     memset(&pp, 0, sizeof pp);
     pp.fbins = P.pfbins.as<uint8_t>();
     pp.mov = P.pmov.as<float>();
+    pp.movx = P.pmovx.as<float>();
+    pp.texq = P.ptex;
     for (int a = 0; a < 3; ++a) {
         pp.nf[a] = P.nf[a];
         pp.nm[a] = P.nm[a];
@@ -1028,6 +1067,7 @@ mi_status parzen_core(mi_ctx *ctx, const std::vector<float> &prm, int n, const f
     MI_CU(ctx->p_cnt.ensure((size_t)n * 8), "alloc");
     MI_CU(ctx->p_marg.ensure((size_t)n * 2 * B * 8), "alloc");
     MI_CU(ctx->p_ment.ensure((size_t)n * nq * 2 * 8), "alloc");
+    MI_CU(ctx->p_mterm.ensure((size_t)n * nq * 2 * B * 8), "alloc");
     MI_CU(ctx->p_jsum.ensure((size_t)n * nq * cblocks * 8), "alloc");
     MI_CU(ctx->p_w.ensure((size_t)n * nq * B2 * 4), "alloc");
     MI_CU(ctx->p_mom.ensure((size_t)n * nq * ctas * 12 * 8), "alloc");
@@ -1041,7 +1081,8 @@ mi_status parzen_core(mi_ctx *ctx, const std::vector<float> &prm, int n, const f
     MI_CU(cudaEventRecord(ctx->ev0, s), "event");
     MI_CU(launch_parzen_hist(pp, d_aff, n, ctas, hist, cnt, s), "Parzen histogram");
     MI_CU(launch_parzen_weights(hist, cnt, n, B, Q, ctx->p_marg.as<double>(), ctx->p_ment.as<double>(),
-                                ctx->p_jsum.as<double>(), ctx->d_mi.as<double>(), ctx->p_w.as<float>(), s),
+                                ctx->p_mterm.as<double>(), ctx->p_jsum.as<double>(), ctx->d_mi.as<double>(),
+                                ctx->p_w.as<float>(), s),
           "Parzen entropies");
     if (out_grad)
         MI_CU(launch_parzen_adjoint(pp, d_aff, ctx->p_jac.as<double>(), n, nq, ctas, ctx->p_w.as<float>(), cnt,

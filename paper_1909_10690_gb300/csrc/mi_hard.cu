@@ -32,7 +32,7 @@ namespace mi {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kSlabs = 8;  // slabs per sweep in the batched kernel
+constexpr int kSlabs = 4;  // slabs per sweep in the batched kernel
 constexpr uint32_t kEmptyKey = 0xffffffffu;
 
 // ---------------------------------------------------------------------------

@@ -104,6 +104,8 @@ cudaError_t launch_resample(const PairDev *d_pair, const PairDev &h_pair, const 
 struct ParzenPair {
     const uint8_t *fbins;   // Parzen fixed bins floor(f (B-4)) + 2
     const float *mov;       // normalised moving intensities in [0, 1]
+    const float *movx;      // the same extended by one plane per axis, dims (n0 + 1, n1 + 1, n2 + 1)
+    unsigned long long texq;  // 2 x 2 (x, y) quads of movx as a float4 3D texture, dims (n0, n1, n2 + 1)
     int nf[3];
     int nm[3];
     int B;
@@ -120,15 +122,23 @@ cudaError_t launch_parzen_prep_moving(const void *data, int dtype, int depth, lo
                                       cudaStream_t s);
 // CTAs per transform of the Parzen voxel kernels, and blocks of the per-cell kernel.
 int parzen_ctas(const ParzenPair &P, int n, int sms);
+// The extended moving volume: out has dims (n0 + 1, n1 + 1, n2 + 1); on the extra planes each axis
+// continues linearly (v[n] = 2 v[n - 1] - v[n - 2]), so that the trilinear cell of an index on the
+// last plane can be its integer part: the value there is v[n - 1] and the derivative along the axis
+// is v[n - 1] - v[n - 2], those of the last cell.
+cudaError_t launch_parzen_extend(const float *mov, const int nm[3], float *out, cudaStream_t s);
+// Quads of the extended volume: out (float4) has dims (n0, n1, n2 + 1); element (x, y, z) holds
+// movx at (x, y), (x + 1, y), (x, y + 1), (x + 1, y + 1) of plane z.
+cudaError_t launch_parzen_quads(const float *movx, const int nm[3], void *out, cudaStream_t s);
 int parzen_cell_blocks(int B);
 // Soft histograms (n x B^2 u64 sums of 2^-32-quantised weights, zeroed here) and overlap counts (n).
 cudaError_t launch_parzen_hist(const ParzenPair &P, const ParzenAffine *d_aff, int n, int ctas,
                                unsigned long long *d_hist, unsigned long long *d_count, cudaStream_t s);
 // MI per q (n x nq) and the weight tables W (n x nq x B^2, FP32) from the soft histograms.
-// Scratch: marg (n x 2B), ment (n x nq x 2), jpart (n x nq x parzen_cell_blocks(B)) FP64.
+// Scratch: marg (n x 2B), ment (n x nq x 2), mterm (n x nq x 2B), jpart (n x nq x parzen_cell_blocks(B)) FP64.
 cudaError_t launch_parzen_weights(const unsigned long long *d_hist, const unsigned long long *d_count, int n, int B,
-                                  const QSet &Q, double *marg, double *ment, double *jpart, double *d_mi, float *d_w,
-                                  cudaStream_t s);
+                                  const QSet &Q, double *marg, double *ment, double *mterm, double *jpart, double *d_mi,
+                                  float *d_w, cudaStream_t s);
 // Gradient: per-CTA moments (scratch n x nq x ctas x 12 FP64) and dMI/dtheta (n x nq x 9 FP64);
 // d_jac is n x 12 x 9 FP64 taken about the fixed-volume centre.
 cudaError_t launch_parzen_adjoint(const ParzenPair &P, const ParzenAffine *d_aff, const double *d_jac, int n, int nq,

@@ -74,28 +74,26 @@ __global__ void k_pmov_f32(const float *__restrict__ in, long long n, float *__r
     }
 }
 
-// FP32 trilinear value and gradient (w.r.t. the moving index) at u inside
-// [0, n-1]^3; cell c = min(floor(u), n - 2), weight u - c.
+// FP32 trilinear value and gradient (w.r.t. the moving index) at a 32.32
+// index u inside [0, n-1]^3, read from the extended volume (dims n + 1 per
+// axis): the cell is the integer part of u and the weight its fraction, also
+// on the last plane, where the extension makes the value v[n-1] and the
+// derivative v[n-1] - v[n-2] (those of the last cell of the volume).
 struct MG {
     float m, gx, gy, gz;
 };
 
-// Cell and weight of a 32.32 fixed-point coordinate U in [0, (n - 1) 2^32].
-__device__ __forceinline__ int cell_of(long long U, int n, float &w) {
-    const int c = min((int)(U >> 32), n - 2);
-    w = (float)(U - ((long long)c << 32)) * 2.3283064365386963e-10f;  // 2^-32
-    return c;
-}
-
 template <bool GRAD>
-__device__ __forceinline__ MG trilinear(const float *__restrict__ mov, int n0, int n1, int n2, long long Ux,
-                                        long long Uy, long long Uz) {
-    float wx, wy, wz;
-    const int cx = cell_of(Ux, n0, wx), cy = cell_of(Uy, n1, wy), cz = cell_of(Uz, n2, wz);
-    const int sy = n0, sz = n0 * n1;
-    const float *p = mov + (cx + n0 * (cy + n1 * cz));
-    const float v000 = __ldg(p), v001 = __ldg(p + 1), v010 = __ldg(p + sy), v011 = __ldg(p + sy + 1);
-    const float v100 = __ldg(p + sz), v101 = __ldg(p + sz + 1), v110 = __ldg(p + sz + sy), v111 = __ldg(p + sz + sy + 1);
+__device__ __forceinline__ MG trilinear_x(const float *__restrict__ movx, int m0, size_t m01, long long Ux,
+                                          long long Uy, long long Uz) {
+    constexpr float k2m32 = 2.3283064365386963e-10f;  // 2^-32
+    const int cx = (int)(Ux >> 32), cy = (int)(Uy >> 32), cz = (int)(Uz >> 32);
+    const float wx = __uint2float_rn((unsigned)Ux) * k2m32, wy = __uint2float_rn((unsigned)Uy) * k2m32,
+                wz = __uint2float_rn((unsigned)Uz) * k2m32;
+    const float *p = movx + ((size_t)cx + (size_t)m0 * cy + m01 * cz);
+    const float v000 = __ldg(p), v001 = __ldg(p + 1), v010 = __ldg(p + m0), v011 = __ldg(p + m0 + 1);
+    const float v100 = __ldg(p + m01), v101 = __ldg(p + m01 + 1), v110 = __ldg(p + m01 + m0),
+                v111 = __ldg(p + m01 + m0 + 1);
     const float d00 = v001 - v000, d01 = v011 - v010, d10 = v101 - v100, d11 = v111 - v110;
     const float a00 = fmaf(wx, d00, v000), a01 = fmaf(wx, d01, v010);
     const float a10 = fmaf(wx, d10, v100), a11 = fmaf(wx, d11, v110);
@@ -112,6 +110,86 @@ __device__ __forceinline__ MG trilinear(const float *__restrict__ mov, int n0, i
         r.gx = r.gy = r.gz = 0.0f;
     }
     return r;
+}
+
+// The same through the quad texture: two fetches at integer texel coordinates
+// (planes cz and cz + 1) return the eight neighbours, so the results are identical.
+template <bool GRAD>
+__device__ __forceinline__ MG trilinear_q(unsigned long long tex, long long Ux, long long Uy, long long Uz) {
+    constexpr float k2m32 = 2.3283064365386963e-10f;  // 2^-32
+    const int cx = (int)(Ux >> 32), cy = (int)(Uy >> 32), cz = (int)(Uz >> 32);
+    const float wx = __uint2float_rn((unsigned)Ux) * k2m32, wy = __uint2float_rn((unsigned)Uy) * k2m32,
+                wz = __uint2float_rn((unsigned)Uz) * k2m32;
+    float v000, v001, v010, v011, v100, v101, v110, v111;
+    asm("tex.3d.v4.f32.s32 {%0, %1, %2, %3}, [%4, {%5, %6, %7, %7}];"
+        : "=f"(v000), "=f"(v001), "=f"(v010), "=f"(v011)
+        : "l"(tex), "r"(cx), "r"(cy), "r"(cz));
+    asm("tex.3d.v4.f32.s32 {%0, %1, %2, %3}, [%4, {%5, %6, %7, %7}];"
+        : "=f"(v100), "=f"(v101), "=f"(v110), "=f"(v111)
+        : "l"(tex), "r"(cx), "r"(cy), "r"(cz + 1));
+    const float d00 = v001 - v000, d01 = v011 - v010, d10 = v101 - v100, d11 = v111 - v110;
+    const float a00 = fmaf(wx, d00, v000), a01 = fmaf(wx, d01, v010);
+    const float a10 = fmaf(wx, d10, v100), a11 = fmaf(wx, d11, v110);
+    const float b0 = fmaf(wy, a01 - a00, a00), b1 = fmaf(wy, a11 - a10, a10);
+    MG r;
+    r.m = fmaf(wz, b1 - b0, b0);
+    if (GRAD) {
+        r.gz = b1 - b0;
+        const float y0 = a01 - a00, y1 = a11 - a10;
+        r.gy = fmaf(wz, y1 - y0, y0);
+        const float e0 = fmaf(wy, d01 - d00, d00), e1 = fmaf(wy, d11 - d10, d10);
+        r.gx = fmaf(wz, e1 - e0, e0);
+    } else {
+        r.gx = r.gy = r.gz = 0.0f;
+    }
+    return r;
+}
+
+// Overlap interval of one fixed row, exactly: the i in [lo, hi] with
+// 0 <= U_a(i) <= (n_a - 1) 2^32 for a = x, y, z, where U_a(i) = A[4a] i +
+// A[4a+1] j + A[4a+2] k + A[4a+3] (32.32 integers), and U at i = lo.
+struct Clip64 {
+    int lo, hi;
+    long long u0, u1, u2;
+};
+
+__device__ __forceinline__ long long floor_div(long long a, long long b) {
+    long long q = a / b;
+    if (a % b != 0 && ((a < 0) != (b < 0))) --q;
+    return q;
+}
+
+__device__ __forceinline__ long long ceil_div(long long a, long long b) { return -floor_div(-a, b); }
+
+__device__ Clip64 clip_row64(const long long *A, long long j, long long k, int nf0, int n0, int n1, int n2) {
+    long long lo = 0, hi = nf0 - 1, b[3];
+    const int nm[3] = {n0, n1, n2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        b[a] = A[4 * a + 1] * j + A[4 * a + 2] * k + A[4 * a + 3];
+        const long long st = A[4 * a], umax = (long long)(nm[a] - 1) << 32;
+        if (st > 0) {
+            lo = max(lo, ceil_div(-b[a], st));
+            hi = min(hi, floor_div(umax - b[a], st));
+        } else if (st < 0) {
+            lo = max(lo, ceil_div(umax - b[a], st));
+            hi = min(hi, floor_div(-b[a], st));
+        } else if (b[a] < 0 || b[a] > umax) {
+            hi = -1;
+        }
+    }
+    Clip64 c;
+    c.lo = 1;
+    c.hi = 0;
+    c.u0 = c.u1 = c.u2 = 0;
+    if (lo <= hi) {
+        c.lo = (int)lo;
+        c.hi = (int)hi;
+        c.u0 = b[0] + A[0] * lo;
+        c.u1 = b[1] + A[4] * lo;
+        c.u2 = b[2] + A[8] * lo;
+    }
+    return c;
 }
 
 // Cubic B-spline weights of the four bins k0-1 .. k0+2 around m~ = k0 + t.
@@ -132,11 +210,6 @@ __device__ __forceinline__ void bspline_dw(float t, float d[4]) {
     d[3] = -0.5f * t * t;
 }
 
-__device__ __forceinline__ bool inside_u(long long Ux, long long Uy, long long Uz, int n0, int n1, int n2) {
-    return Ux >= 0 && Uy >= 0 && Uz >= 0 && Ux <= ((long long)(n0 - 1) << 32) && Uy <= ((long long)(n1 - 1) << 32) &&
-           Uz <= ((long long)(n2 - 1) << 32);
-}
-
 // ---------------------------------------------------------------------------
 // Forward: soft histogram (unnormalised sums of weights) and overlap count
 // ---------------------------------------------------------------------------
@@ -144,71 +217,151 @@ __device__ __forceinline__ bool inside_u(long long Ux, long long Uy, long long U
 // Weights are quantised to 2^-32 with the largest one absorbing the rounding
 // residue, so every voxel adds exactly 2^32 (the B-spline partition of unity)
 // and the integer sums are exact and independent of the order of the atomics:
-// the soft histogram, MI and gradient are bitwise reproducible.  Each shared
-// cell is a 64-bit count kept as two 32-bit words (64-bit shared atomics are
-// several times slower): a weight (< 2^32) is added to the low word, and the
-// add that wraps it -- detected exactly once, from the returned old value --
-// adds 1 to the high word.
-__device__ __forceinline__ void add64(uint32_t *lo, uint32_t *hi, int c, uint32_t w) {
-    const uint32_t old = atomicAdd(lo + c, w);
-    if (old + w < old) atomicAdd(hi + c, 1u);
+// the soft histogram, MI and gradient are bitwise reproducible.  A weight is
+// added as its two 16-bit halves into two 32-bit shared words per cell, with
+// fire-and-forget atomics (no returned value, so no latency on the voxel's
+// path).  A CTA covers at most 2^16 voxels, each adding at most once to a
+// cell, so neither word can overflow (2^16 x (2^16 - 1) < 2^32); at the end
+// the cell's 64-bit count, low + (high << 16), goes to the global histogram.
+constexpr int kParzenMaxVox = 65536;  // also the longest fixed row (MI_MAX_PARZEN_NX)
+constexpr int kParzenBankSkew = 7;    // row stride of the forward's shared histogram, mod 32
+constexpr bool kParzenFwdTex = true;   // forward gathers through the quad texture
+constexpr bool kParzenAdjTex = false;  // adjoint gathers with loads from the extended volume
+constexpr int kParzenRowsPerStep = 1;  // rows a warp of the forward works on at a time
+
+// Row stride of the shared tables: the least SB >= B + 1 with SB = kParzenBankSkew (mod 32).
+__host__ __device__ inline int parzen_stride(int B) { return B + 1 + ((kParzenBankSkew - (B + 1)) % 32 + 32) % 32; }
+
+// Shared words of one histogram copy: low-half sums [B x SB], then high-half sums, rounded up to
+// whole bank rows plus 32 / ncopy words, so that copy c starts c * 32 / ncopy banks further on.
+__host__ __device__ inline int parzen_copy_words(int B, int SB, int ncopy) {
+    return ((2 * B * SB + 31) / 32) * 32 + 32 / ncopy;
 }
 
+template <int RPW, int NCOPY>
 __global__ void __launch_bounds__(256)
-    k_parzen_hist(ParzenPair P, const ParzenAffine *__restrict__ aff, unsigned long long *__restrict__ ghist,
-                  unsigned long long *__restrict__ gcount) {
-    // low words [B x (B + 1)], then high words: rows padded by one word so the
-    // bank is (fixed bin + moving bin) mod 32 rather than the moving bin alone
+    k_parzen_hist(ParzenPair P, const ParzenAffine *__restrict__ aff, int rows_per_cta, int SB,
+                  unsigned long long *__restrict__ ghist, unsigned long long *__restrict__ gcount) {
+    // NCOPY copies of the low-half sums [B x SB] and the high-half sums.  The row stride SB >= B + 1
+    // is 7 mod 32, so the bank of cell (fixed bin b, moving bin k) is (k + 7 b) mod 32: the cells of
+    // neighbouring voxels, which differ by a bin or two on either axis, fall in different banks.
+    // Lane l adds to copy l mod NCOPY; the copies are shifted by 32 / NCOPY banks, so neighbouring
+    // lanes adding to the same cell (the common case) use different banks.  Column B absorbs the
+    // zero weight of bin B (m~ = B - 2 exactly).
     extern __shared__ uint32_t sh32[];
-    const int t = blockIdx.y, B = P.B, B2 = B * B, SB = B + 1, NP = B * SB;
-    uint32_t *lo = sh32, *hi = sh32 + NP;
+    const int t = blockIdx.y, B = P.B, B2 = B * B, NP = B * SB;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int CS = parzen_copy_words(B, SB, NCOPY);
+    uint32_t *lo16 = sh32 + (size_t)(lane % NCOPY) * CS, *hi16 = lo16 + NP;
     __shared__ long long A[12];
     if (threadIdx.x < 12) A[threadIdx.x] = aff[t].A[threadIdx.x];
-    for (int c = threadIdx.x; c < 2 * NP; c += blockDim.x) sh32[c] = 0u;
+    for (int c = threadIdx.x; c < NCOPY * CS; c += blockDim.x) sh32[c] = 0u;
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int nf0 = P.nf[0], nf1 = P.nf[1];
     const int n0 = P.nm[0], n1 = P.nm[1], n2 = P.nm[2];
     const long long R = (long long)nf1 * P.nf[2];
+    const long long r0 = (long long)blockIdx.x * rows_per_cta;
+    const long long r1 = r0 + rows_per_cta < R ? r0 + rows_per_cta : R;
     const float Bm4 = (float)(B - 4);
-    unsigned int cnt = 0;
-    for (long long r = (long long)blockIdx.x * nwarps + warp; r < R; r += (long long)gridDim.x * nwarps) {
-        const long long j = r % nf1, k = r / nf1;
-        const long long b0 = A[1] * j + A[2] * k + A[3];
-        const long long b1 = A[5] * j + A[6] * k + A[7];
-        const long long b2 = A[9] * j + A[10] * k + A[11];
-        const uint8_t *__restrict__ frow = P.fbins + (size_t)r * nf0;
-        for (int i = lane; i < nf0; i += 32) {
-            const long long ux = b0 + A[0] * i, uy = b1 + A[4] * i, uz = b2 + A[8] * i;
-            if (!inside_u(ux, uy, uz, n0, n1, n2)) continue;
-            ++cnt;
-            const MG g = trilinear<false>(P.mov, n0, n1, n2, ux, uy, uz);
-            const float mt = fmaf(fminf(fmaxf(g.m, 0.0f), 1.0f), Bm4, 2.0f);
-            const int k0 = (int)mt;
-            float w[4];
-            bspline_w(mt - (float)k0, w);
-            // every quantised weight is at most (2/3) 2^32, so it fits the 32-bit low word
-            const uint32_t q0 = (uint32_t)__float2ull_rn(w[0] * 4294967296.0f);
-            const uint32_t q2 = (uint32_t)__float2ull_rn(w[2] * 4294967296.0f);
-            const uint32_t q3 = (uint32_t)__float2ull_rn(w[3] * 4294967296.0f);
-            const uint32_t q1 = (uint32_t)(4294967296ull - q0 - q2 - q3);
-            const int c = (int)__ldg(frow + i) * SB + (k0 - 1);
-            add64(lo, hi, c + 0, q0);
-            add64(lo, hi, c + 1, q1);
-            add64(lo, hi, c + 2, q2);
-            if (q3) add64(lo, hi, c + 3, q3);  // q3 == 0 whenever k0 + 3 > B (t = 0 there)
+    // a warp works on RPW rows at a time, G = 32 / RPW neighbouring voxels of each: the lanes that
+    // add to one cell at once are then at most the G of a row (neighbouring voxels mostly share
+    // cells, and same-address shared atomics queue), while each row's gathers stay coalesced
+    constexpr int G = 32 / RPW;
+    const int sub = lane / G, pos = lane % G;
+    const long long DG0 = G * A[0], DG1 = G * A[4], DG2 = G * A[8];
+    unsigned int cnt = 0;  // overlap voxels counted by this lane (one lane per row)
+    // warp w takes rows r0 + w + nwarps n; a group of 32 of them is clipped at once (lane l: row l)
+    for (long long g = r0 + warp; g < r1; g += 32LL * nwarps) {
+        Clip64 mine;
+        mine.lo = 1;
+        mine.hi = 0;
+        mine.u0 = mine.u1 = mine.u2 = 0;
+        const long long rl = g + (long long)nwarps * lane;
+        if (rl < r1) mine = clip_row64(A, rl % nf1, rl / nf1, nf0, n0, n1, n2);
+        for (int s = 0; s < 32; s += RPW) {
+            if (g + (long long)nwarps * s >= r1) break;  // warp-uniform: the rest of the group is past r1
+            const int src = s + sub;
+            const long long r = g + (long long)nwarps * src;
+            int lo = __shfl_sync(kFull, mine.lo, src), hi = __shfl_sync(kFull, mine.hi, src);
+            if (r >= r1) hi = lo - 1;
+            const int len = hi - lo + 1 > 0 ? hi - lo + 1 : 0;
+            if (pos == 0) cnt += (unsigned)len;
+            const int nsteps = __reduce_max_sync(kFull, (unsigned)((len + G - 1) / G));
+            long long U0 = __shfl_sync(kFull, mine.u0, src) + A[0] * pos;
+            long long U1 = __shfl_sync(kFull, mine.u1, src) + A[4] * pos;
+            long long U2 = __shfl_sync(kFull, mine.u2, src) + A[8] * pos;
+            const uint8_t *__restrict__ frow = P.fbins + (size_t)(r < r1 ? r : r0) * nf0;
+            for (int k = 0; k < nsteps; ++k) {
+                const int i = lo + k * G + pos;
+                if (i <= hi) {
+                    const MG g3 = kParzenFwdTex ? trilinear_q<false>(P.texq, U0, U1, U2)
+                                                : trilinear_x<false>(P.movx, P.nm[0] + 1, (size_t)(P.nm[0] + 1) * (P.nm[1] + 1), U0, U1, U2);
+                    const float mt = fmaf(fminf(fmaxf(g3.m, 0.0f), 1.0f), Bm4, 2.0f);
+                    const int k0 = (int)mt;
+                    float w[4];
+                    bspline_w(mt - (float)k0, w);
+                    // every quantised weight is below 2^32 (at most (2/3) 2^32)
+                    const uint32_t q0 = __float2uint_rn(w[0] * 4294967296.0f);
+                    const uint32_t q2 = __float2uint_rn(w[2] * 4294967296.0f);
+                    const uint32_t q3 = __float2uint_rn(w[3] * 4294967296.0f);
+                    const uint32_t q1 = 0u - q0 - q2 - q3;  // 2^32 - (q0 + q2 + q3)
+                    const int c = (int)__ldg(frow + i) * SB + (k0 - 1);
+                    atomicAdd(lo16 + c, q0 & 0xffffu);
+                    atomicAdd(hi16 + c, q0 >> 16);
+                    atomicAdd(lo16 + c + 1, q1 & 0xffffu);
+                    atomicAdd(hi16 + c + 1, q1 >> 16);
+                    atomicAdd(lo16 + c + 2, q2 & 0xffffu);
+                    atomicAdd(hi16 + c + 2, q2 >> 16);
+                    atomicAdd(lo16 + c + 3, q3 & 0xffffu);
+                    atomicAdd(hi16 + c + 3, q3 >> 16);
+                }
+                U0 += DG0;
+                U1 += DG1;
+                U2 += DG2;
+            }
         }
     }
+    cnt = __reduce_add_sync(kFull, cnt);
     __syncthreads();
     unsigned long long *gh = ghist + (size_t)t * B2;
     for (int c = threadIdx.x; c < B2; c += blockDim.x) {
         const int cp = (c / B) * SB + c % B;
-        const unsigned long long v = ((unsigned long long)hi[cp] << 32) | lo[cp];
+        unsigned long long v = 0;
+#pragma unroll
+        for (int k = 0; k < NCOPY; ++k)
+            v += (unsigned long long)sh32[(size_t)k * CS + cp] + ((unsigned long long)sh32[(size_t)k * CS + NP + cp] << 16);
         if (v) atomicAdd(gh + c, v);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
     if (lane == 0 && cnt) atomicAdd(gcount + t, (unsigned long long)cnt);
+}
+
+__global__ void k_parzen_quads(const float *__restrict__ movx, int n0, int n1, int n2, float4 *__restrict__ out) {
+    const long long m0 = n0 + 1, m01 = m0 * (n1 + 1), n = (long long)n0 * n1 * (n2 + 1);
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n; o += (long long)gridDim.x * blockDim.x) {
+        const long long x = o % n0, y = (o / n0) % n1, z = o / ((long long)n0 * n1);
+        const float *p = movx + x + m0 * y + m01 * z;
+        out[o] = make_float4(p[0], p[1], p[m0], p[m0 + 1]);
+    }
+}
+
+__global__ void k_parzen_extend(const float *__restrict__ mov, int n0, int n1, int n2, float *__restrict__ out) {
+    const long long m0 = n0 + 1, m1 = n1 + 1, n = m0 * m1 * (n2 + 1);
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n; o += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(o % m0), y = (int)((o / m0) % m1), z = (int)(o / (m0 * m1));
+        // per axis: an index inside the volume, or the linear continuation 2 v[n-1] - v[n-2]
+        int xi[2], yi[2], zi[2];
+        double xc[2], yc[2], zc[2];
+        const int nx = x < n0 ? 1 : 2, ny = y < n1 ? 1 : 2, nz = z < n2 ? 1 : 2;
+        xi[0] = x < n0 ? x : n0 - 1, xc[0] = x < n0 ? 1.0 : 2.0, xi[1] = n0 - 2, xc[1] = -1.0;
+        yi[0] = y < n1 ? y : n1 - 1, yc[0] = y < n1 ? 1.0 : 2.0, yi[1] = n1 - 2, yc[1] = -1.0;
+        zi[0] = z < n2 ? z : n2 - 1, zc[0] = z < n2 ? 1.0 : 2.0, zi[1] = n2 - 2, zc[1] = -1.0;
+        double v = 0.0;
+        for (int c = 0; c < nz; ++c)
+            for (int b = 0; b < ny; ++b)
+                for (int a = 0; a < nx; ++a)
+                    v += xc[a] * yc[b] * zc[c] * (double)mov[xi[a] + (long long)n0 * (yi[b] + (long long)n1 * zi[c])];
+        out[o] = (float)v;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -243,10 +396,12 @@ __device__ __forceinline__ double finish_entropy(double sum, float qf, int bits)
     return (1.0 - sum) / ((double)qf - 1.0);
 }
 
-// One CTA per transform: marginals P_F (rows), P_M (cols) and their entropies per q.
-// marg: n x 2B (P_F then P_M); ment: n x nq x 2 (S_F, S_M).
+// One CTA per transform: marginals P_F (rows), P_M (cols), their entropies per q, and the row and
+// column factors of W per q (mterm: n x nq x 2B): ln P for q = 1, dS_q/dP = -q P^(q-1) / (q - 1)
+// otherwise.  marg: n x 2B (P_F then P_M); ment: n x nq x 2 (S_F, S_M).
 __global__ void k_parzen_marg(const unsigned long long *__restrict__ ghist, const unsigned long long *__restrict__ gcount,
-                              int B, QSet Q, double *__restrict__ marg, double *__restrict__ ment) {
+                              int B, QSet Q, double *__restrict__ marg, double *__restrict__ ment,
+                              double *__restrict__ mterm) {
     __shared__ double s_tmp[32];
     const int t = blockIdx.x;
     const double N = (double)gcount[t] * 4294967296.0;  // total weight: 2^32 per overlap voxel
@@ -263,10 +418,17 @@ __global__ void k_parzen_marg(const unsigned long long *__restrict__ ghist, cons
     }
     __syncthreads();
     for (int iq = 0; iq < Q.nq; ++iq) {
+        const float qf = Q.q[iq];
+        const double q = (double)qf;
+        double *mt = mterm + ((size_t)t * Q.nq + iq) * 2 * B;
         double a = 0.0, b = 0.0;
         for (int r = threadIdx.x; r < B; r += blockDim.x) {
-            if (pf[r] > 0.0) a += ent_term(pf[r], Q.q[iq]);
-            if (pm[r] > 0.0) b += ent_term(pm[r], Q.q[iq]);
+            if (pf[r] > 0.0) a += ent_term(pf[r], qf);
+            if (pm[r] > 0.0) b += ent_term(pm[r], qf);
+            for (int h = 0; h < 2; ++h) {
+                const double v = h ? pm[r] : pf[r];
+                mt[h * B + r] = !(v > 0.0) ? 0.0 : qf == 1.0f ? log(v) : -q * pow(v, q - 1.0) / (q - 1.0);
+            }
         }
         a = block_sum(a, s_tmp);
         b = block_sum(b, s_tmp);
@@ -278,42 +440,44 @@ __global__ void k_parzen_marg(const unsigned long long *__restrict__ ghist, cons
 }
 
 // Grid (cells / 256, n): per-block joint entropy partial sums (jpart: n x nq x
-// gridDim.x, reduced in a fixed order later) and W (n x nq x B^2, FP32).
+// gridDim.x, reduced in a fixed order later) and W (n x nq x B^2, FP32).  One
+// ln p per cell serves every q: the Shannon term -p ln p, p^q = exp(q ln p)
+// for the Tsallis ones, and dS_q/dp = -q p^q / (p (q - 1)).
 __global__ void __launch_bounds__(256)
     k_parzen_cells(const unsigned long long *__restrict__ ghist, const unsigned long long *__restrict__ gcount, int B,
-                   QSet Q, const double *__restrict__ marg, const double *__restrict__ ment, double *__restrict__ jpart,
+                   QSet Q, const double *__restrict__ mterm, const double *__restrict__ ment, double *__restrict__ jpart,
                    float *__restrict__ wout) {
     __shared__ double s_tmp[32];
     const int t = blockIdx.y, B2 = B * B;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const double N = (double)gcount[t] * 4294967296.0;
     const double lnb = Q.bits ? log(2.0) : 1.0;
-    double p = 0.0, pfr = 0.0, pmc = 0.0;
+    double p = 0.0, lp = 0.0;
     if (c < B2 && N > 0) {
         p = (double)ghist[(size_t)t * B2 + c] / N;
-        pfr = marg[(size_t)t * 2 * B + c / B];
-        pmc = marg[(size_t)t * 2 * B + B + c % B];
+        if (p > 0.0) lp = log(p);
     }
     for (int iq = 0; iq < Q.nq; ++iq) {
         const float qf = Q.q[iq];
-        double e = p > 0.0 ? ent_term(p, qf) : 0.0;
+        const double q = (double)qf;
+        const double pq = p > 0.0 && qf != 1.0f ? exp(q * lp) : 0.0;
+        double e = p > 0.0 ? (qf == 1.0f ? -p * lp : pq) : 0.0;
         e = block_sum(e, s_tmp);
         if (threadIdx.x == 0) jpart[((size_t)t * Q.nq + iq) * gridDim.x + blockIdx.x] = e;
         if (c < B2) {
             double w = 0.0;
             if (p > 0.0) {
+                const double *mt = mterm + ((size_t)t * Q.nq + iq) * 2 * B;
+                const double fr = mt[c / B], mc = mt[B + c % B];
                 if (qf == 1.0f) {
-                    w = (log(p) - log(pfr) - log(pmc) - 1.0) / lnb;
+                    w = (lp - fr - mc - 1.0) / lnb;
                 } else {
-                    const double q = (double)qf;
-                    const double dSF = -q * pow(pfr, q - 1.0) / (q - 1.0);
-                    const double dSM = -q * pow(pmc, q - 1.0) / (q - 1.0);
-                    const double dSJ = -q * pow(p, q - 1.0) / (q - 1.0);
-                    w = dSF + dSM - dSJ;
+                    const double dSJ = -q * pq / (p * (q - 1.0));
+                    w = fr + mc - dSJ;
                     if (Q.form == 1) {
                         const double SF = ment[((size_t)t * Q.nq + iq) * 2 + 0];
                         const double SM = ment[((size_t)t * Q.nq + iq) * 2 + 1];
-                        w += (1.0 - q) * (dSF * SM + SF * dSM);
+                        w += (1.0 - q) * (fr * SM + SF * mc);
                     }
                 }
             }
@@ -348,12 +512,14 @@ __global__ void k_parzen_final(int n, const unsigned long long *__restrict__ gco
 // ---------------------------------------------------------------------------
 
 template <int NQ>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
     k_parzen_adj(ParzenPair P, const ParzenAffine *__restrict__ aff, int nq_total, int q0,
                  const float *__restrict__ wtab, int w_in_smem, double *__restrict__ mom) {
     // mom: n x nq_total x gridDim.x x 12 per-CTA partial moments (no atomics: fixed-order reduction later)
-    extern __shared__ float sw[];  // NQ x B x (B + 1) weights (rows padded by one word) when they fit
-    const int t = blockIdx.y, B = P.B, B2 = B * B;
+    // NQ x B x SB weights when they fit; the row stride SB >= B + 1 is 7 mod 32, so neighbouring
+    // voxels' cells, a bin or two apart on either axis, are read from different banks
+    extern __shared__ float sw[];
+    const int t = blockIdx.y, B = P.B, B2 = B * B, SB = parzen_stride(B);
     __shared__ long long A[12];
     __shared__ float s_red[8][NQ * 12];
     if (threadIdx.x < 12) A[threadIdx.x] = aff[t].A[threadIdx.x];
@@ -362,11 +528,11 @@ __global__ void __launch_bounds__(256)
     if (w_in_smem) {
         for (int c = threadIdx.x; c < NQ * B2; c += blockDim.x) {
             const int qq = c / B2, cc = c % B2;
-            sw[qq * B * (B + 1) + (cc / B) * (B + 1) + cc % B] = W[c];
+            sw[qq * B * SB + (cc / B) * SB + cc % B] = W[c];
         }
         W = sw;
-        RS = B + 1;
-        QS = B * (B + 1);
+        RS = SB;
+        QS = B * SB;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -374,6 +540,7 @@ __global__ void __launch_bounds__(256)
     const int n0 = P.nm[0], n1 = P.nm[1], n2 = P.nm[2];
     const long long R = (long long)nf1 * P.nf[2];
     const float Bm4 = (float)(B - 4);
+    const long long D0 = 32 * A[0], D1 = 32 * A[4], D2 = 32 * A[8];
     // moments are taken about the fixed-volume centre, where the rotation and
     // scale columns of du/dtheta have no constant part (no cancellation)
     const float ci = 0.5f * (float)(nf0 - 1), cj = 0.5f * (float)(nf1 - 1), ck = 0.5f * (float)(P.nf[2] - 1);
@@ -382,43 +549,71 @@ __global__ void __launch_bounds__(256)
     for (int q = 0; q < NQ; ++q)
 #pragma unroll
         for (int e = 0; e < 12; ++e) M[q][e] = 0.0f;
-    for (long long r = (long long)blockIdx.x * nwarps + warp; r < R; r += (long long)gridDim.x * nwarps) {
-        const long long jl = r % nf1, kl = r / nf1;
-        const long long b0 = A[1] * jl + A[2] * kl + A[3];
-        const long long b1 = A[5] * jl + A[6] * kl + A[7];
-        const long long b2 = A[9] * jl + A[10] * kl + A[11];
-        const float j = (float)jl - cj, k = (float)kl - ck;
-        const uint8_t *__restrict__ frow = P.fbins + (size_t)r * nf0;
-        for (int i = lane; i < nf0; i += 32) {
-            const long long ux = b0 + A[0] * i, uy = b1 + A[4] * i, uz = b2 + A[8] * i;
-            if (!inside_u(ux, uy, uz, n0, n1, n2)) continue;
-            const MG g = trilinear<true>(P.mov, n0, n1, n2, ux, uy, uz);
-            const float ic = (float)i - ci;
-            const float mt = fmaf(fminf(fmaxf(g.m, 0.0f), 1.0f), Bm4, 2.0f);
-            const int k0 = (int)mt;
-            float d[4];
-            bspline_dw(mt - (float)k0, d);
-            if (k0 + 2 >= B) d[3] = 0.0f;
-            const int base = (int)__ldg(frow + i) * RS + (k0 - 1);
-            const int i3 = k0 + 2 < B ? base + 3 : base;  // in range; weight 0 when clamped
+    // warp w of CTA b takes rows (b nwarps + w) + gridDim.x nwarps n; a group of 32 is clipped at once
+    const long long rstep = (long long)gridDim.x * nwarps;
+    for (long long g = (long long)blockIdx.x * nwarps + warp; g < R; g += 32 * rstep) {
+        Clip64 mine;
+        mine.lo = 1;
+        mine.hi = 0;
+        mine.u0 = mine.u1 = mine.u2 = 0;
+        const long long rl = g + rstep * lane;
+        if (rl < R) mine = clip_row64(A, rl % nf1, rl / nf1, nf0, n0, n1, n2);
+        for (int s = 0; s < 32; ++s) {
+            const long long r = g + rstep * s;
+            if (r >= R) break;  // warp-uniform
+            const int lo = __shfl_sync(kFull, mine.lo, s), hi = __shfl_sync(kFull, mine.hi, s);
+            if (lo > hi) continue;
+            long long U0 = __shfl_sync(kFull, mine.u0, s) + A[0] * lane;
+            long long U1 = __shfl_sync(kFull, mine.u1, s) + A[4] * lane;
+            long long U2 = __shfl_sync(kFull, mine.u2, s) + A[8] * lane;
+            const float j = (float)(r % nf1) - cj, k = (float)(r / nf1) - ck;
+            const uint8_t *__restrict__ frow = P.fbins + (size_t)r * nf0;
+            // along the row j and k are constant: per row, S0[q][a] = sum s d_a m and
+            // S1[q][a] = sum s d_a m (i - ci); the 12 moments follow at the row's end
+            float S0[NQ][3], S1[NQ][3];
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const float *Wq = W + (size_t)q * QS;
-                const float s = Wq[base] * d[0] + Wq[base + 1] * d[1] + Wq[base + 2] * d[2] + Wq[i3] * d[3];
-                const float sx = s * g.gx, sy = s * g.gy, sz = s * g.gz;
-                M[q][0] = fmaf(sx, ic, M[q][0]);
-                M[q][1] = fmaf(sx, j, M[q][1]);
-                M[q][2] = fmaf(sx, k, M[q][2]);
-                M[q][3] += sx;
-                M[q][4] = fmaf(sy, ic, M[q][4]);
-                M[q][5] = fmaf(sy, j, M[q][5]);
-                M[q][6] = fmaf(sy, k, M[q][6]);
-                M[q][7] += sy;
-                M[q][8] = fmaf(sz, ic, M[q][8]);
-                M[q][9] = fmaf(sz, j, M[q][9]);
-                M[q][10] = fmaf(sz, k, M[q][10]);
-                M[q][11] += sz;
+            for (int q = 0; q < NQ; ++q)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) S0[q][a] = S1[q][a] = 0.0f;
+            for (int base = lo; base <= hi; base += 32) {
+                const int i = base + lane;
+                if (i <= hi) {
+                    const MG g3 = kParzenAdjTex ? trilinear_q<true>(P.texq, U0, U1, U2)
+                                                : trilinear_x<true>(P.movx, P.nm[0] + 1, (size_t)(P.nm[0] + 1) * (P.nm[1] + 1), U0, U1, U2);
+                    const float ic = (float)i - ci;
+                    const float mt = fmaf(fminf(fmaxf(g3.m, 0.0f), 1.0f), Bm4, 2.0f);
+                    const int k0 = (int)mt;
+                    float d[4];
+                    bspline_dw(mt - (float)k0, d);
+                    if (k0 + 2 >= B) d[3] = 0.0f;
+                    const int cb = (int)__ldg(frow + i) * RS + (k0 - 1);
+                    const int i3 = k0 + 2 < B ? cb + 3 : cb;  // in range; weight 0 when clamped
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) {
+                        const float *Wq = W + (size_t)q * QS;
+                        const float sv = Wq[cb] * d[0] + Wq[cb + 1] * d[1] + Wq[cb + 2] * d[2] + Wq[i3] * d[3];
+                        const float sx = sv * g3.gx, sy = sv * g3.gy, sz = sv * g3.gz;
+                        S1[q][0] = fmaf(sx, ic, S1[q][0]);
+                        S0[q][0] += sx;
+                        S1[q][1] = fmaf(sy, ic, S1[q][1]);
+                        S0[q][1] += sy;
+                        S1[q][2] = fmaf(sz, ic, S1[q][2]);
+                        S0[q][2] += sz;
+                    }
+                }
+                U0 += D0;
+                U1 += D1;
+                U2 += D2;
             }
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    M[q][4 * a + 0] += S1[q][a];
+                    M[q][4 * a + 1] = fmaf(S0[q][a], j, M[q][4 * a + 1]);
+                    M[q][4 * a + 2] = fmaf(S0[q][a], k, M[q][4 * a + 2]);
+                    M[q][4 * a + 3] += S0[q][a];
+                }
         }
     }
     // warp reduction in FP32, then the 8 warps in FP64 into global memory
@@ -495,29 +690,54 @@ int parzen_ctas(const ParzenPair &P, int n, int sms) {
 
 int parzen_cell_blocks(int B) { return (B * B + 255) / 256; }
 
+cudaError_t launch_parzen_extend(const float *mov, const int nm[3], float *out, cudaStream_t s) {
+    const long long n = (long long)(nm[0] + 1) * (nm[1] + 1) * (nm[2] + 1);
+    k_parzen_extend<<<grid_for(n, 256), 256, 0, s>>>(mov, nm[0], nm[1], nm[2], out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_parzen_quads(const float *movx, const int nm[3], void *out, cudaStream_t s) {
+    const long long n = (long long)nm[0] * nm[1] * (nm[2] + 1);
+    k_parzen_quads<<<grid_for(n, 256), 256, 0, s>>>(movx, nm[0], nm[1], nm[2], (float4 *)out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_parzen_hist(const ParzenPair &P, const ParzenAffine *d_aff, int n, int ctas,
                                unsigned long long *d_hist, unsigned long long *d_count, cudaStream_t s) {
     const size_t B2 = (size_t)P.B * P.B;
     cudaError_t e = cudaMemsetAsync(d_hist, 0, (size_t)n * B2 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(d_count, 0, (size_t)n * sizeof(unsigned long long), s)) != cudaSuccess) return e;
-    const size_t smem = 2 * (size_t)P.B * (P.B + 1) * sizeof(uint32_t);
-    if ((e = cudaFuncSetAttribute(k_parzen_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    const int SB = parzen_stride(P.B);
+    // two copies while they fit 100 KB (three CTAs per SM), else one
+    const int ncopy = (size_t)2 * parzen_copy_words(P.B, SB, 2) * 4 <= 100 * 1024 ? 2 : 1;
+    const size_t smem = (size_t)ncopy * parzen_copy_words(P.B, SB, ncopy) * sizeof(uint32_t);
+    const void *fn = ncopy == 2 ? (const void *)k_parzen_hist<kParzenRowsPerStep, 2>
+                                : (const void *)k_parzen_hist<kParzenRowsPerStep, 1>;
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
-    dim3 grid(ctas, n);
-    k_parzen_hist<<<grid, 256, smem, s>>>(P, d_aff, d_hist, d_count);
-    return cudaGetLastError();
+    // rows per CTA: at most kParzenMaxVox voxels (the 16-bit halves cannot overflow), and about
+    // `ctas` CTAs per transform when that is finer
+    const long long R = (long long)P.nf[1] * P.nf[2];
+    long long rpc = kParzenMaxVox / P.nf[0];
+    const long long want = (R + ctas - 1) / ctas;
+    if (want < rpc) rpc = want;
+    if (rpc < 1) rpc = 1;
+    dim3 grid((unsigned)((R + rpc - 1) / rpc), n);
+    int rpci = (int)rpc, sb = SB;
+    void *args[] = {(void *)&P, (void *)&d_aff, (void *)&rpci, (void *)&sb, (void *)&d_hist, (void *)&d_count};
+    return cudaLaunchKernel(fn, grid, dim3(256), args, smem, s);
 }
 
 cudaError_t launch_parzen_weights(const unsigned long long *d_hist, const unsigned long long *d_count, int n, int B,
-                                  const QSet &Q, double *marg, double *ment, double *jpart, double *d_mi, float *d_w,
-                                  cudaStream_t s) {
+                                  const QSet &Q, double *marg, double *ment, double *mterm, double *jpart, double *d_mi,
+                                  float *d_w, cudaStream_t s) {
     cudaError_t e;
-    k_parzen_marg<<<n, 256, 0, s>>>(d_hist, d_count, B, Q, marg, ment);
+    k_parzen_marg<<<n, 256, 0, s>>>(d_hist, d_count, B, Q, marg, ment, mterm);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int nb = parzen_cell_blocks(B);
     dim3 grid(nb, n);
-    k_parzen_cells<<<grid, 256, 0, s>>>(d_hist, d_count, B, Q, marg, ment, jpart, d_w);
+    k_parzen_cells<<<grid, 256, 0, s>>>(d_hist, d_count, B, Q, mterm, ment, jpart, d_w);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_parzen_final<<<(n * Q.nq + 127) / 128, 128, 0, s>>>(n, d_count, Q, ment, jpart, nb, d_mi);
     return cudaGetLastError();
@@ -527,11 +747,10 @@ cudaError_t launch_parzen_adjoint(const ParzenPair &P, const ParzenAffine *d_aff
                                   int ctas, const float *d_w, const unsigned long long *d_count, double *d_mom,
                                   double *d_grad, cudaStream_t s) {
     cudaError_t e;
-    const size_t B2 = (size_t)P.B * P.B;
     dim3 grid(ctas, n);
     for (int q0 = 0; q0 < nq; q0 += 4) {
         const int g = nq - q0 < 4 ? nq - q0 : 4;
-        const size_t wbytes = (size_t)g * P.B * (P.B + 1) * sizeof(float);
+        const size_t wbytes = (size_t)g * P.B * parzen_stride(P.B) * sizeof(float);
         const int in_smem = wbytes <= 96 * 1024;
         const size_t smem = in_smem ? wbytes : 0;
 #define MI_ADJ(NQV)                                                                                         \

@@ -34,15 +34,15 @@ BINS = 256
 DEPTH = 12
 N_T = 4096
 QS = [0.5, 1.0, 1.5, 2.0]
-# algorithmic integer operations per voxel x transform of the hard path (see DESIGN.md):
+# algorithmic integer operations per voxel x transform of the hard path:
 # 3 coordinate adds, 6 index/weight extractions, 9 address operations, 7 lerps x 4,
 # 2 for the moving bin, 1 for the joint index, 1 increment
 ALG_OPS_PER_VOXT = 50
-# DRAM bytes (read + write) of one full k_batched launch, from the ncu capture summarised in
-# profiles/k_batched_rows_tex_256cubed_256bins.md; reported only while the kernel source and the
+# DRAM bytes (read + write) of one full k_batched launch (4096 transforms), from one ncu capture of
+# dram__bytes_read.sum + dram__bytes_write.sum; reported only while the kernel source and the
 # selected variant are the ones measured
-K_BATCHED_TRAFFIC = {"variant": 9, "source_sha16": "11bb587497c37227", "bytes_per_launch": 14.49e9 + 29.1e6}
-# algorithmic FP32 operations per voxel x transform of the Parzen MI + gradient at 3 q values (see DESIGN.md):
+K_BATCHED_TRAFFIC = {"variant": 10, "source_sha16": "17bada66fbf63a9e", "bytes_per_launch": 414.06e9 + 30.2e6}
+# algorithmic FP32 operations per voxel x transform of the Parzen MI + gradient at 3 q values:
 # forward 31 (trilinear 14, bin coordinate 1, B-spline weights 12, 4 increments),
 # adjoint 89 (trilinear value and gradient 23, bin coordinate 1, B-spline derivatives 8, 3 q x 19)
 PARZEN_OPS_PER_VOXT = 120

@@ -59,6 +59,8 @@ def _load():
             lib.orc_f32_to_u16.argtypes = [P, I64, P]
             lib.orc_affine.restype = None
             lib.orc_affine.argtypes = [P, P, P, P, P, P, P]
+            lib.orc_affine_mode.restype = None
+            lib.orc_affine_mode.argtypes = [P, P, P, P, P, I, I, P, P]
             lib.orc_affine_q16.restype = I
             lib.orc_affine_q16.argtypes = [P, P]
             lib.orc_resample.restype = None
@@ -134,13 +136,17 @@ def bin_volume(vol: np.ndarray, bins: int, depth: int | None = None) -> np.ndarr
     return out
 
 
-def affine(params, fixed_shape, fixed_spacing, moving_shape, moving_spacing, with_jacobian=False):
+def affine(params, fixed_shape, fixed_spacing, moving_shape, moving_spacing, with_jacobian=False,
+           rotation="euler", scale="factor"):
     """R2 (Fig. 1 Transform block; Introduction's translation/rotation/scale families).
 
     ``params`` = (tx, ty, tz mm, rx, ry, rz degrees, sx, sy, sz).  Shapes are
     numpy shapes (nz, ny, nx); spacings are (sx, sy, sz) in mm.  Returns the
     3x4 FP64 matrix [A | b] mapping a fixed index (i, j, k) to a moving index,
     and optionally its 12x9 Jacobian with respect to the parameters.
+    rotation="versor": the rotation parameters are the unit-ball versor of
+    R14 (the Results' rotation maps); scale="offset": zero-centred scale
+    parameters s, sigma = 1 + s (R15, the Results' scale maps).
     """
     lib = _load()
     prm = np.ascontiguousarray(params, dtype=np.float32).reshape(9)
@@ -150,7 +156,10 @@ def affine(params, fixed_shape, fixed_spacing, moving_shape, moving_spacing, wit
     sm = np.ascontiguousarray(moving_spacing, dtype=np.float32)
     out = np.empty(12, dtype=np.float64)
     dout = np.empty(12 * 9, dtype=np.float64) if with_jacobian else None
-    lib.orc_affine(_p(prm), _p(nf), _p(sf), _p(nm), _p(sm), _p(out), _p(dout) if with_jacobian else None)
+    if rotation not in ("euler", "versor") or scale not in ("factor", "offset"):
+        raise ValueError("rotation is 'euler' or 'versor', scale is 'factor' or 'offset'")
+    lib.orc_affine_mode(_p(prm), _p(nf), _p(sf), _p(nm), _p(sm), int(rotation == "versor"), int(scale == "offset"),
+                        _p(out), _p(dout) if with_jacobian else None)
     if with_jacobian:
         return out.reshape(3, 4), dout.reshape(12, 9)
     return out.reshape(3, 4)

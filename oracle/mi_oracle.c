@@ -16,12 +16,13 @@
  * and Eq. (3) (registration as argmax over T); it names Tsallis entropy and
  * the translation / rotation / scale families (Introduction) and a full,
  * all-voxel histogram (Discussion) but leaves the rest open.  The readings
- * used here are tagged R1..R9 where they are applied:
+ * used here are tagged R1..R15 where they are applied:
  *   R1 binning (v * bins) >> depth               R2 parameter -> affine
  *   R3 16.16 fixed-point coordinate, overlap     R4 integer trilinear
  *   R5 counts over the overlap only              R6 natural logarithm
  *   R7 Tsallis entropy and Tsallis MI forms      R8 Parzen soft histogram
- *   R9 Parzen gradient (adjoint of R8)
+ *   R9 Parzen gradient (adjoint of R8)           R14 unit-ball (versor) rotation
+ *   R15 zero-centred scale parameters
  *
  * Every function here is pinned by tests that do not re-type its formula:
  * hand-enumerated 4x4x4 cases, exact permutations, closed forms, limits,
@@ -160,24 +161,90 @@ static void orc_rot_z(double a, int d, double m[9]) {
  * b[a] = ((c_m[a] + t[a]) - sum_c (R[a][c]*sigma[c]) * c_f[c]) / s_m[a] with
  * the same summation order; no fused multiply-add anywhere.
  */
+/*
+ * R14, the unit-ball rotation (the rotation maps of the Results, whose points
+ * outside radius 1 land on the sphere): the three rotation parameters are the
+ * vector part v of a unit quaternion (w, v), w = sqrt(1 - |v|^2); |v| >= 1 is
+ * first normalised onto the sphere (w = 0, a half turn).  R is the rotation
+ * matrix of that quaternion (a turn by 2 asin|v| about v).  Order of
+ * operations: n2 = (x*x + y*y) + z*z; outside, x = x / sqrt(n2) and so on;
+ * R[0] = 1 - 2*(y*y + z*z), R[1] = 2*(x*y - w*z), R[2] = 2*(x*z + w*y),
+ * R[3] = 2*(x*y + w*z), R[4] = 1 - 2*(x*x + z*z), R[5] = 2*(y*z - w*x),
+ * R[6] = 2*(x*z - w*y), R[7] = 2*(y*z + w*x), R[8] = 1 - 2*(x*x + y*y).
+ * dR (may be NULL) receives dR/dv_p at dR[9*p + e].
+ */
+static void orc_versor(const double v[3], double R[9], double *dR) {
+    double x = v[0], y = v[1], z = v[2], w;
+    const double n2 = x * x + y * y + z * z;
+    const int outside = n2 >= 1.0;
+    const double nrm = outside ? sqrt(n2) : 1.0;
+    if (outside) {
+        x = x / nrm;
+        y = y / nrm;
+        z = z / nrm;
+        w = 0.0;
+    } else {
+        w = sqrt(1.0 - n2);
+    }
+    R[0] = 1.0 - 2.0 * (y * y + z * z);
+    R[1] = 2.0 * (x * y - w * z);
+    R[2] = 2.0 * (x * z + w * y);
+    R[3] = 2.0 * (x * y + w * z);
+    R[4] = 1.0 - 2.0 * (x * x + z * z);
+    R[5] = 2.0 * (y * z - w * x);
+    R[6] = 2.0 * (x * z - w * y);
+    R[7] = 2.0 * (y * z + w * x);
+    R[8] = 1.0 - 2.0 * (x * x + y * y);
+    if (!dR) return;
+    /* partial derivatives of the nine entries with respect to x, y, z, w */
+    const double Dx[9] = {0, 2 * y, 2 * z, 2 * y, -4 * x, -2 * w, 2 * z, 2 * w, -4 * x};
+    const double Dy[9] = {-4 * y, 2 * x, 2 * w, 2 * x, 0, 2 * z, -2 * w, 2 * z, -4 * y};
+    const double Dz[9] = {-4 * z, -2 * w, 2 * x, 2 * w, -4 * z, 2 * y, 2 * x, 2 * y, 0};
+    const double Dw[9] = {0, -2 * z, 2 * y, 2 * z, 0, -2 * x, -2 * y, 2 * x, 0};
+    const double q[3] = {x, y, z};
+    for (int p = 0; p < 3; p++) {
+        /* d(x, y, z, w)/d v_p: inside (e_p, -v_p / w); outside (e_p - q q_p) / |v| and 0 */
+        double dq[3], dw = 0.0;
+        for (int c = 0; c < 3; c++) dq[c] = outside ? ((c == p) - q[c] * q[p]) / nrm : (double)(c == p);
+        if (!outside) dw = -v[p] / w;
+        for (int e = 0; e < 9; e++) dR[9 * p + e] = Dx[e] * dq[0] + Dy[e] * dq[1] + Dz[e] * dq[2] + Dw[e] * dw;
+    }
+}
+
+void orc_affine_mode(const float prm[9], const int nf[3], const float sf_in[3], const int nm[3],
+                     const float sm_in[3], int rot_mode, int scale_mode, double out[12], double *dout);
+
 void orc_affine(const float prm[9], const int nf[3], const float sf_in[3], const int nm[3],
                 const float sm_in[3], double out[12], double *dout) {
-    double t[3], ang[3], sig[3], sf[3], sm[3], cf[3], cm[3];
+    orc_affine_mode(prm, nf, sf_in, nm, sm_in, 0, 0, out, dout);
+}
+
+/* The same with the rotation parameters as Euler angles in degrees (rot_mode
+ * 0) or the unit-ball versor of R14 (1), and the scale parameters as factors
+ * sigma (scale_mode 0) or zero-centred offsets s, sigma = 1 + s (1, R15). */
+void orc_affine_mode(const float prm[9], const int nf[3], const float sf_in[3], const int nm[3],
+                     const float sm_in[3], int rot_mode, int scale_mode, double out[12], double *dout) {
+    double t[3], ang[3], sig[3], sf[3], sm[3], cf[3], cm[3], vv[3];
     for (int a = 0; a < 3; a++) {
         t[a] = (double)prm[a];
         ang[a] = orc_deg2rad((double)prm[3 + a]);
-        sig[a] = (double)prm[6 + a];
+        vv[a] = (double)prm[3 + a];
+        sig[a] = scale_mode ? 1.0 + (double)prm[6 + a] : (double)prm[6 + a];
         sf[a] = (double)sf_in[a];
         sm[a] = (double)sm_in[a];
         cf[a] = sf[a] * ((double)(nf[a] - 1) * 0.5);
         cm[a] = sm[a] * ((double)(nm[a] - 1) * 0.5);
     }
-    double Rx[9], Ry[9], Rz[9], Rzy[9], R[9];
-    orc_rot_x(ang[0], 0, Rx);
-    orc_rot_y(ang[1], 0, Ry);
-    orc_rot_z(ang[2], 0, Rz);
-    orc_mat3_mul(Rz, Ry, Rzy);
-    orc_mat3_mul(Rzy, Rx, R);
+    double Rx[9], Ry[9], Rz[9], Rzy[9], R[9], dRv[27];
+    if (rot_mode) {
+        orc_versor(vv, R, dout ? dRv : NULL);
+    } else {
+        orc_rot_x(ang[0], 0, Rx);
+        orc_rot_y(ang[1], 0, Ry);
+        orc_rot_z(ang[2], 0, Rz);
+        orc_mat3_mul(Rz, Ry, Rzy);
+        orc_mat3_mul(Rzy, Rx, R);
+    }
     for (int a = 0; a < 3; a++) {
         double s = 0.0;
         for (int c = 0; c < 3; c++) {
@@ -191,15 +258,21 @@ void orc_affine(const float prm[9], const int nf[3], const float sf_in[3], const
     memset(dout, 0, sizeof(double) * 12 * 9);
     /* translation: d b_a / d t_a = 1 / s_m[a] */
     for (int a = 0; a < 3; a++) dout[9 * (4 * a + 3) + a] = 1.0 / sm[a];
-    /* rotation: dR/d(deg) = (pi/180) * (Rz Ry Rx with one factor differentiated) */
+    /* rotation: dR/d(deg) = (pi/180) * (Rz Ry Rx with one factor differentiated),
+     * or the versor's dR/dv_p */
     for (int p = 0; p < 3; p++) {
         double dX[9], dY[9], dZ[9], M1[9], dR[9];
-        orc_rot_x(ang[0], p == 0, dX);
-        orc_rot_y(ang[1], p == 1, dY);
-        orc_rot_z(ang[2], p == 2, dZ);
-        orc_mat3_mul(dZ, dY, M1);
-        orc_mat3_mul(M1, dX, dR);
         double k = orc_deg2rad(1.0);
+        if (rot_mode) {
+            memcpy(dR, dRv + 9 * p, sizeof dR);
+            k = 1.0;
+        } else {
+            orc_rot_x(ang[0], p == 0, dX);
+            orc_rot_y(ang[1], p == 1, dY);
+            orc_rot_z(ang[2], p == 2, dZ);
+            orc_mat3_mul(dZ, dY, M1);
+            orc_mat3_mul(M1, dX, dR);
+        }
         for (int a = 0; a < 3; a++) {
             double s = 0.0;
             for (int c = 0; c < 3; c++) {

@@ -167,3 +167,79 @@ def test_q16_rounding_and_range():
     a[2, 3] = 40000.0  # 40000 * 65536 > 2^31
     with pytest.raises(OverflowError):
         oracle.affine_q16(a)
+
+
+# --- R14 unit-ball (versor) rotation and R15 zero-centred scale -------------------------------------------------
+
+def _rot_of(p, rotation="versor", scale="factor"):
+    # with equal unit spacings, equal shapes and unit scale, A is the rotation matrix itself
+    return oracle.affine(p, (9, 9, 9), (1, 1, 1), (9, 9, 9), (1, 1, 1), rotation=rotation, scale=scale)[:, :3]
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_versor_on_an_axis_is_the_euler_rotation(axis):
+    # v = sin(theta / 2) e_axis is the turn by theta about that axis: compare with the Euler builder at the
+    # angle the float32 parameter actually represents
+    for theta_deg in (-150.0, -33.0, 5.0, 90.0, 171.0):
+        s = np.float32(np.sin(np.radians(theta_deg) / 2))
+        v = np.zeros(9, np.float32)
+        v[6:] = 1
+        v[3 + axis] = s
+        e = np.zeros(9, np.float32)
+        e[6:] = 1
+        e[3 + axis] = np.float32(np.degrees(2 * np.arcsin(np.float64(s))))
+        np.testing.assert_allclose(_rot_of(v), _rot_of(e, rotation="euler"), atol=2e-7)
+
+
+def test_versor_rotations_are_proper_with_the_unit_ball_angle():
+    rng = np.random.default_rng(21)
+    for _ in range(200):
+        v = rng.uniform(-1, 1, 3)
+        p = np.concatenate([[0, 0, 0], v, [1, 1, 1]]).astype(np.float32)
+        R = _rot_of(p)
+        np.testing.assert_allclose(R @ R.T, np.eye(3), atol=1e-12)
+        assert abs(np.linalg.det(R) - 1) < 1e-12
+        n = min(np.linalg.norm(p[3:6].astype(np.float64)), 1.0)
+        # trace = 1 + 2 cos(angle), angle = 2 asin |v| (a half turn on and outside the sphere)
+        assert abs(np.trace(R) - (1 + 2 * np.cos(2 * np.arcsin(n)))) < 1e-9
+        axis = p[3:6].astype(np.float64)
+        np.testing.assert_allclose(R @ axis, axis, atol=1e-9)  # the axis is fixed
+
+
+def test_versor_outside_the_ball_lands_on_the_sphere():
+    for v in ([0, 0, 2.0], [0.9, -0.9, 0.4], [1.0, 0, 0]):
+        p = np.concatenate([[0, 0, 0], v, [1, 1, 1]]).astype(np.float32)
+        R = _rot_of(p)
+        np.testing.assert_allclose(R @ R, np.eye(3), atol=1e-12)  # a half turn
+        q = p.copy()
+        q[3:6] = p[3:6] * np.float32(3.0)  # further out along the same ray: the same point of the sphere
+        np.testing.assert_allclose(_rot_of(q), R, atol=1e-7)
+
+
+def test_zero_centred_scale_is_one_plus_offset():
+    fs, ms, sf, sm = (20, 22, 18), (19, 21, 23), (1.0, 0.8, 1.25), (1.0, 1.0, 0.5)
+    for s in ([0.25, -0.5, 0.125], [0, 0, 0], [-0.75, 0.5, 1.0]):
+        off = np.array([1, -2, 3, 10, -20, 5, *s], np.float32)
+        fac = off.copy()
+        fac[6:] = 1 + np.array(s, np.float32)  # exact in float32 for these offsets
+        np.testing.assert_array_equal(oracle.affine(off, fs, sf, ms, sm, scale="offset"), oracle.affine(fac, fs, sf, ms, sm))
+
+
+@pytest.mark.parametrize("inside", [True, False])
+def test_versor_and_offset_jacobian_match_finite_differences(inside):
+    rng = np.random.default_rng(5 if inside else 6)
+    fs, ms, sf, sm = (30, 24, 20), (26, 28, 22), (1.0, 0.9, 1.2), (1.1, 1.0, 1.3)
+    for _ in range(5):
+        v = rng.normal(size=3)
+        v *= (rng.uniform(0.1, 0.8) if inside else rng.uniform(1.2, 2.0)) / np.linalg.norm(v)
+        p = np.concatenate([rng.uniform(-5, 5, 3), v, rng.uniform(-0.2, 0.2, 3)]).astype(np.float32)
+        _, J = oracle.affine(p, fs, sf, ms, sm, with_jacobian=True, rotation="versor", scale="offset")
+        for k in range(9):
+            h = np.float32(2.0 ** -12)
+            pp, pm = p.copy(), p.copy()
+            pp[k] += h
+            pm[k] -= h
+            ap = oracle.affine(pp, fs, sf, ms, sm, rotation="versor", scale="offset").ravel()
+            am = oracle.affine(pm, fs, sf, ms, sm, rotation="versor", scale="offset").ravel()
+            fd = (ap - am) / float(pp[k] - pm[k])
+            np.testing.assert_allclose(J[:, k], fd, rtol=1e-4, atol=1e-5)

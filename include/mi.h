@@ -18,7 +18,8 @@
  *    once to 16-bit integers (round-half-even of v * 65535, depth 16).
  *  - Binning: an integer value v of depth d lies in bin (v * bins) >> d.
  *  - Transform parameters, 9 floats per transform: tx ty tz (mm), rx ry rz
- *    (degrees), sx sy sz (scale factors, 1 = identity).  A fixed physical
+ *    (degrees; or a unit-ball versor, mi_options.rotation), sx sy sz (scale
+ *    factors, 1 = identity; or zero-centred offsets, mi_options.scale).  A fixed physical
  *    point p = s_f * i (i the voxel index) maps to
  *    p_m = R diag(s) (p - c_f) + c_m + t, R = Rz(rz) Ry(ry) Rx(rx), c the
  *    volume centres s * (n - 1) / 2; the moving index is p_m / s_m.  In index
@@ -106,6 +107,21 @@ enum {
     MI_HV_U32_QUAD = 11,
     MI_HV_U16_QUAD = 12
 };
+/* Meaning of the rotation parameters (transform[3..5]):
+ *  MI_ROT_EULER_DEG  R = Rz(rz) Ry(ry) Rx(rx), right-handed, degrees;
+ *  MI_ROT_VERSOR     the unit-ball parameterisation of the paper's rotation
+ *                    maps (Results): v = (v1, v2, v3) is the vector part of
+ *                    the unit quaternion (sqrt(1 - |v|^2), v), a turn by
+ *                    2 asin|v| about v; |v| >= 1 is normalised onto the sphere
+ *                    (a half turn).  Gradients are d/dv (the normalised
+ *                    direction's outside the ball).
+ * Meaning of the scale parameters (transform[6..8]):
+ *  MI_SCALE_FACTOR   sigma = s (1 = identity);
+ *  MI_SCALE_OFFSET   sigma = 1 + s (0 = identity), the paper's zero-centred
+ *                    scale maps (Results). */
+enum { MI_ROT_EULER_DEG = 0, MI_ROT_VERSOR = 1 };
+enum { MI_SCALE_FACTOR = 0, MI_SCALE_OFFSET = 1 };
+
 /* Evaluation path of mi_eval. */
 enum { MI_PATH_AUTO = 0, MI_PATH_PLAIN = 1, MI_PATH_BATCHED = 2 };
 
@@ -125,6 +141,8 @@ typedef struct {
     int autotune;      /* 1 (default): time the variants once per shape and cache  */
     int device;        /* CUDA device ordinal; -1 (default) = the current device   */
     int block_threads; /* hard-path CTA size: 0 (default) = autotuned, or 512 / 1024 */
+    int rotation;      /* MI_ROT_EULER_DEG (default) or MI_ROT_VERSOR               */
+    int scale;         /* MI_SCALE_FACTOR (default) or MI_SCALE_OFFSET              */
 } mi_options;
 
 typedef struct mi_ctx mi_ctx;
@@ -248,7 +266,8 @@ mi_status mi_last_kernel_ms(mi_ctx *ctx, float *ms, int *launches);
  * (cudaMalloc is not allowed then), plug-ins inside a framework whose caching
  * allocator owns the device memory, services that fix their GPU memory budget
  * up front.  It computes the same hard-binned MI as mi_eval (plain path) for
- * ONE transform (9 parameters, host memory) and nq q values (host memory)
+ * ONE transform (9 parameters in the default conventions -- Euler degrees,
+ * scale factors -- host memory) and nq q values (host memory)
  * without creating a context and without calling cudaMalloc, cudaFree or any
  * allocating routine.
  *  - fixed, moving: uint8 or uint16 volumes already in device memory of the

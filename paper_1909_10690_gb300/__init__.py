@@ -101,7 +101,8 @@ def _volume(x, spacing, depth):
     return v, arg
 
 
-def _options(kernel, tsallis_form, bits, hist_variant, path, use_graphs, autotune, device, block_threads=0):
+def _options(kernel, tsallis_form, bits, hist_variant, path, use_graphs, autotune, device, block_threads=0,
+             rotation="euler", scale="factor"):
     o = _lib.MiOptions()
     load().mi_options_default(ctypes.byref(o))
     o.kernel = {"hard": 0, "parzen": 1}[kernel]
@@ -113,6 +114,8 @@ def _options(kernel, tsallis_form, bits, hist_variant, path, use_graphs, autotun
     o.autotune = int(bool(autotune))
     o.device = -1 if device is None else int(device)
     o.block_threads = int(block_threads)
+    o.rotation = {"euler": 0, "versor": 1}[rotation]
+    o.scale = {"factor": 0, "offset": 1}[scale]
     return o
 
 
@@ -133,16 +136,21 @@ class Context:
     """One (fixed, moving) pair, or several pairs (``pairs=[...]``) for the uneven batch.
 
     kernel: "hard" (exact joint histogram, default) or "parzen" (differentiable).
+    rotation: "euler" (rx, ry, rz in degrees, default) or "versor" (the unit-ball
+    parameterisation of the paper's rotation maps); scale: "factor" (1 =
+    identity, default) or "offset" (zero-centred, sigma = 1 + s).
     """
 
     def __init__(self, fixed=None, moving=None, bins=64, fixed_spacing=(1.0, 1.0, 1.0),
                  moving_spacing=(1.0, 1.0, 1.0), fixed_depth=None, moving_depth=None, kernel="hard",
                  tsallis_form="additive", bits=False, hist_variant=HV_AUTO, path="auto", use_graphs=True,
-                 autotune=True, device=None, pairs=None, block_threads=0):
+                 autotune=True, device=None, pairs=None, block_threads=0, rotation="euler", scale="factor"):
         self._lib = load()
         self._h = ctypes.c_void_p()
         self.kernel = kernel
-        opt = _options(kernel, tsallis_form, bits, hist_variant, path, use_graphs, autotune, device, block_threads)
+        self.rotation, self.scale = rotation, scale
+        opt = _options(kernel, tsallis_form, bits, hist_variant, path, use_graphs, autotune, device, block_threads,
+                       rotation, scale)
         if pairs is None:
             pairs = [dict(fixed=fixed, moving=moving, bins=bins, fixed_spacing=fixed_spacing,
                           moving_spacing=moving_spacing, fixed_depth=fixed_depth, moving_depth=moving_depth)]

@@ -109,25 +109,77 @@ void elem_rot(int axis, double rad, bool deriv, double m[9]) {
 
 const double kRadPerDeg = 3.14159265358979323846 / 180.0;
 
+// Rotation of the unit quaternion (w, x, y, z) whose vector part is the parameter v; |v| >= 1 is
+// first scaled onto the unit sphere (w = 0).  Expressions written in the order the quantised
+// matrix depends on.  dR (optional, 3 x 9): dR/dv_p through w = sqrt(1 - |v|^2) inside the ball,
+// through the normalisation v / |v| outside.
+void versor_rotation(const double v[3], double R[9], double *dR) {
+    double x = v[0], y = v[1], z = v[2];
+    const double n2 = x * x + y * y + z * z;
+    const bool on_sphere = n2 >= 1.0;
+    const double len = on_sphere ? sqrt(n2) : 1.0;
+    double w = 0.0;
+    if (on_sphere) {
+        x = x / len;
+        y = y / len;
+        z = z / len;
+    } else {
+        w = sqrt(1.0 - n2);
+    }
+    R[0] = 1.0 - 2.0 * (y * y + z * z);
+    R[1] = 2.0 * (x * y - w * z);
+    R[2] = 2.0 * (x * z + w * y);
+    R[3] = 2.0 * (x * y + w * z);
+    R[4] = 1.0 - 2.0 * (x * x + z * z);
+    R[5] = 2.0 * (y * z - w * x);
+    R[6] = 2.0 * (x * z - w * y);
+    R[7] = 2.0 * (y * z + w * x);
+    R[8] = 1.0 - 2.0 * (x * x + y * y);
+    if (!dR) return;
+    const double u[3] = {x, y, z};
+    for (int p = 0; p < 3; ++p) {
+        // the quaternion's change per unit change of v_p
+        double d[3];
+        for (int c = 0; c < 3; ++c) d[c] = on_sphere ? ((c == p ? 1.0 : 0.0) - u[c] * u[p]) / len : (c == p ? 1.0 : 0.0);
+        const double dw = on_sphere ? 0.0 : -v[p] / w;
+        double *g = dR + 9 * p;
+        g[0] = -4.0 * (y * d[1] + z * d[2]);
+        g[1] = 2.0 * (x * d[1] + y * d[0] - w * d[2] - z * dw);
+        g[2] = 2.0 * (x * d[2] + z * d[0] + w * d[1] + y * dw);
+        g[3] = 2.0 * (x * d[1] + y * d[0] + w * d[2] + z * dw);
+        g[4] = -4.0 * (x * d[0] + z * d[2]);
+        g[5] = 2.0 * (y * d[2] + z * d[1] - w * d[0] - x * dw);
+        g[6] = 2.0 * (x * d[2] + z * d[0] - w * d[1] - y * dw);
+        g[7] = 2.0 * (y * d[2] + z * d[1] + w * d[0] + x * dw);
+        g[8] = -4.0 * (x * d[0] + y * d[1]);
+    }
+}
+
 // [A | b] (row-major 3x4) for one transform, and optionally J = d[A|b]/dparam (12 x 9).
+// rot: MI_ROT_EULER_DEG or MI_ROT_VERSOR; scale: MI_SCALE_FACTOR or MI_SCALE_OFFSET (sigma = 1 + s).
 void build_affine(const float prm[9], const int nf[3], const float sfp[3], const int nm[3], const float smp[3],
-                  double out[12], double *jac) {
-    double tr[3], rad[3], sc[3], sf[3], sm[3], cf[3], cm[3];
+                  double out[12], double *jac, int rot = MI_ROT_EULER_DEG, int scale = MI_SCALE_FACTOR) {
+    double tr[3], rad[3], sc[3], sf[3], sm[3], cf[3], cm[3], vq[3];
     for (int a = 0; a < 3; ++a) {
         tr[a] = (double)prm[a];
         rad[a] = (double)prm[3 + a] * kRadPerDeg;
-        sc[a] = (double)prm[6 + a];
+        vq[a] = (double)prm[3 + a];
+        sc[a] = scale == MI_SCALE_OFFSET ? 1.0 + (double)prm[6 + a] : (double)prm[6 + a];
         sf[a] = (double)sfp[a];
         sm[a] = (double)smp[a];
         cf[a] = sf[a] * ((double)(nf[a] - 1) * 0.5);
         cm[a] = sm[a] * ((double)(nm[a] - 1) * 0.5);
     }
-    double rx[9], ry[9], rz[9], rzy[9], R[9];
-    elem_rot(0, rad[0], false, rx);
-    elem_rot(1, rad[1], false, ry);
-    elem_rot(2, rad[2], false, rz);
-    mul3(rz, ry, rzy);
-    mul3(rzy, rx, R);
+    double rx[9], ry[9], rz[9], rzy[9], R[9], dRv[27];
+    if (rot == MI_ROT_VERSOR) {
+        versor_rotation(vq, R, jac ? dRv : nullptr);
+    } else {
+        elem_rot(0, rad[0], false, rx);
+        elem_rot(1, rad[1], false, ry);
+        elem_rot(2, rad[2], false, rz);
+        mul3(rz, ry, rzy);
+        mul3(rzy, rx, R);
+    }
     for (int a = 0; a < 3; ++a) {
         double acc = 0.0;
         for (int c = 0; c < 3; ++c) {
@@ -142,15 +194,21 @@ void build_affine(const float prm[9], const int nf[3], const float sfp[3], const
     for (int a = 0; a < 3; ++a) jac[9 * (4 * a + 3) + a] = 1.0 / sm[a];
     for (int p = 0; p < 3; ++p) {
         double dx[9], dy[9], dz[9], t1[9], dR[9];
-        elem_rot(0, rad[0], p == 0, dx);
-        elem_rot(1, rad[1], p == 1, dy);
-        elem_rot(2, rad[2], p == 2, dz);
-        mul3(dz, dy, t1);
-        mul3(t1, dx, dR);
+        double unit = kRadPerDeg;  // Euler angles are differentiated per degree
+        if (rot == MI_ROT_VERSOR) {
+            for (int e = 0; e < 9; ++e) dR[e] = dRv[9 * p + e];
+            unit = 1.0;
+        } else {
+            elem_rot(0, rad[0], p == 0, dx);
+            elem_rot(1, rad[1], p == 1, dy);
+            elem_rot(2, rad[2], p == 2, dz);
+            mul3(dz, dy, t1);
+            mul3(t1, dx, dR);
+        }
         for (int a = 0; a < 3; ++a) {
             double acc = 0.0;
             for (int c = 0; c < 3; ++c) {
-                const double d = dR[3 * a + c] * kRadPerDeg * sc[c];
+                const double d = dR[3 * a + c] * unit * sc[c];
                 jac[9 * (4 * a + c) + 3 + p] = d * sf[c] / sm[a];
                 acc += d * cf[c];
             }
@@ -582,6 +640,11 @@ mi_status create_common(mi_ctx **out, const mi_volume *fixed, const mi_volume *m
         g_create_error = "the Parzen form takes one pair per context";
         return MI_EINVAL;
     }
+    if ((ctx->opt.rotation != MI_ROT_EULER_DEG && ctx->opt.rotation != MI_ROT_VERSOR) ||
+        (ctx->opt.scale != MI_SCALE_FACTOR && ctx->opt.scale != MI_SCALE_OFFSET)) {
+        g_create_error = "opt.rotation / opt.scale out of range";
+        return MI_EINVAL;
+    }
     if (ctx->opt.hist_variant < MI_HV_AUTO || ctx->opt.hist_variant > MI_HV_U16_QUAD) {
         g_create_error = "opt.hist_variant out of range";
         return MI_EINVAL;
@@ -699,7 +762,7 @@ mi_status read_transforms(mi_ctx *ctx, const float *tr, int n, std::vector<float
 
 mi_status build_q16(mi_ctx *ctx, const Pair &P, const float *prm, int32_t *q16, int t) {
     double aff[12];
-    build_affine(prm, P.nf, P.sf, P.nm, P.sm, aff, nullptr);
+    build_affine(prm, P.nf, P.sf, P.nm, P.sm, aff, nullptr, ctx->opt.rotation, ctx->opt.scale);
     if (!quantise_q16(aff, q16))
         return ctx->fail(MI_ERANGE, "transform " + std::to_string(t) + ": affine does not fit 16.16 fixed point");
     return MI_OK;
@@ -1032,7 +1095,7 @@ mi_status parzen_core(mi_ctx *ctx, const std::vector<float> &prm, int n, const f
     for (int t = 0; t < n; ++t) {
         double aff[12];
         double *J = &jac[(size_t)t * 108];
-        build_affine(&prm[(size_t)t * 9], P.nf, P.sf, P.nm, P.sm, aff, J);
+        build_affine(&prm[(size_t)t * 9], P.nf, P.sf, P.nm, P.sm, aff, J, ctx->opt.rotation, ctx->opt.scale);
         for (int e = 0; e < 12; ++e) {
             const double s = aff[e] * 4294967296.0;
             if (!(fabs(s) < 4503599627370496.0))  // |x| < 2^20 keeps every int64 product below 2^63
@@ -1120,6 +1183,8 @@ void mi_options_default(mi_options *opt) {
     opt->autotune = 1;
     opt->device = -1;
     opt->block_threads = 0;
+    opt->rotation = MI_ROT_EULER_DEG;
+    opt->scale = MI_SCALE_FACTOR;
 }
 
 const char *mi_version(void) { return "gb300-mi 0.1 (sm_103a)"; }
@@ -1313,7 +1378,8 @@ mi_status mi_affine(mi_ctx *ctx, int pair, const float *transforms, int n, doubl
     mi_status st = MI_OK;
     for (int t = 0; t < n; ++t) {
         double aff[12], jac[108];
-        build_affine(transforms + (size_t)t * 9, P.nf, P.sf, P.nm, P.sm, aff, out_jacobian ? jac : nullptr);
+        build_affine(transforms + (size_t)t * 9, P.nf, P.sf, P.nm, P.sm, aff, out_jacobian ? jac : nullptr,
+                     ctx->opt.rotation, ctx->opt.scale);
         if (out_affine) memcpy(out_affine + (size_t)t * 12, aff, sizeof aff);
         if (out_jacobian) memcpy(out_jacobian + (size_t)t * 108, jac, sizeof jac);
         if (out_q16) {

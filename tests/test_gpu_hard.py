@@ -59,6 +59,38 @@ def test_affine_builder_matches_oracle_bit_for_bit(cuda_lib):
         np.testing.assert_allclose(j[t], jo, rtol=1e-12, atol=1e-12)
 
 
+def test_versor_and_offset_builder_matches_oracle_bit_for_bit(cuda_lib):
+    # the unit-ball rotation (inside and outside the ball) and zero-centred scale parameters
+    f = np.zeros((20, 24, 30), np.uint16)
+    m = np.zeros((22, 28, 26), np.uint16)
+    sf, sm = (1.0, 0.875, 1.25), (1.125, 1.0, 1.375)
+    ctx = cuda_lib.Context(f, m, bins=16, fixed_spacing=sf, moving_spacing=sm, rotation="versor", scale="offset")
+    rng = np.random.default_rng(8)
+    n = 2000
+    prm = np.concatenate([rng.uniform(-30, 30, (n, 3)), rng.uniform(-1.2, 1.2, (n, 3)),
+                          rng.uniform(-0.5, 0.5, (n, 3))], 1).astype(np.float32)
+    a, q, j = ctx.affine(prm)
+    for t in range(n):
+        ao, jo = oracle.affine(prm[t], f.shape, sf, m.shape, sm, with_jacobian=True, rotation="versor", scale="offset")
+        np.testing.assert_array_equal(a[t], ao)
+        np.testing.assert_array_equal(q[t], oracle.affine_q16(ao))
+        np.testing.assert_allclose(j[t], jo, rtol=1e-12, atol=1e-12)
+
+
+def test_versor_and_offset_mi_parity(cuda_lib):
+    f, m = phantoms.head_pair(shape=(40, 44, 48), spacing=(1, 1, 1), seed=9)
+    ctx = cuda_lib.Context(f, m, bins=64, fixed_depth=12, moving_depth=12, rotation="versor", scale="offset")
+    rng = np.random.default_rng(10)
+    prm = np.concatenate([rng.uniform(-4, 4, (12, 3)), rng.uniform(-0.15, 0.15, (12, 3)),
+                          rng.uniform(-0.1, 0.1, (12, 3))], 1).astype(np.float32)
+    mi, h, cnt = ctx.eval(prm, [1.0, 1.5], with_entropies=True)
+    q16 = np.stack([oracle.affine_q16(oracle.affine(p, f.shape, (1, 1, 1), m.shape, (1, 1, 1), rotation="versor",
+                                                    scale="offset")) for p in prm])
+    mi_o, h_o, cnt_o = oracle.mi_eval_q16(f, m, 64, q16, [1.0, 1.5], fixed_depth=12, moving_depth=12, nthreads=8)
+    np.testing.assert_array_equal(cnt, cnt_o)
+    assert_mi_close(mi, mi_o, h_o)
+
+
 def test_hand_enumerated_cases_on_gpu(cuda_lib):
     cases = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hand_4x4x4.json")))["cases"]
     z, y, x = np.meshgrid(np.arange(4), np.arange(4), np.arange(4), indexing="ij")

@@ -51,6 +51,25 @@ def test_parzen_integer_pair_and_bin_counts(cuda_lib, B):
     check(ctx, f, m, prm, [1.0, 1.5], B, depth=12)
 
 
+def test_parzen_versor_and_offset_gradient(cuda_lib):
+    # d MI / d(versor, zero-centred scale): the Jacobian of the unit-ball parameterisation
+    f, m = phantoms.head_pair(shape=(30, 34, 38), spacing=(1, 1, 1), seed=46, dtype=np.float32)
+    B = 32
+    ctx = cuda_lib.Context(f, m, bins=B, kernel="parzen", rotation="versor", scale="offset")
+    rng = np.random.default_rng(47)
+    prm = np.concatenate([rng.uniform(-3, 3, (4, 3)), rng.uniform(-0.08, 0.08, (4, 3)),
+                          rng.uniform(-0.05, 0.05, (4, 3))], 1).astype(np.float32)
+    qs = [1.0, 1.3]
+    mi, g = ctx.grad(prm, qs)
+    for t in range(len(prm)):
+        aff, J = oracle.affine(prm[t], f.shape, (1, 1, 1), m.shape, (1, 1, 1), with_jacobian=True, rotation="versor",
+                               scale="offset")
+        mi_o, g_o, n = oracle.parzen(f, m, aff, B, qs, daff=J)
+        assert np.all(np.abs(mi[t] - mi_o) <= MI_TOL * np.maximum(np.abs(mi_o), 1.0)), (t, mi[t], mi_o)
+        for iq in range(len(qs)):
+            assert np.abs(g[t, iq] - g_o[iq]).max() <= G_TOL * np.abs(g_o[iq]).max(), (t, iq)
+
+
 def test_parzen_pseudo_additive_and_many_q(cuda_lib):
     f, m = phantoms.head_pair(shape=(28, 30, 32), spacing=(1, 1, 1), seed=44, dtype=np.float32)
     B = 24

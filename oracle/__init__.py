@@ -73,6 +73,15 @@ def _load():
             lib.orc_mi_eval.argtypes = [P, P, P, P, I, I, P, P, I, P, I, P, I, I, I, I, P, P, P]
             lib.orc_mi_eval_q16.restype = I
             lib.orc_mi_eval_q16.argtypes = [P, P, P, I, I, P, I, P, I, P, I, I, I, I, P, P, P]
+            U32 = ctypes.c_uint32
+            lib.orc_mi_eval_q16_s.restype = I
+            lib.orc_mi_eval_q16_s.argtypes = [P, P, P, I, I, P, I, P, I, P, I, I, I, I, U32, U32, P, P, P]
+            lib.orc_fmix32.restype = U32
+            lib.orc_fmix32.argtypes = [U32]
+            lib.orc_sampled.restype = I
+            lib.orc_sampled.argtypes = [I64, U32, U32]
+            lib.orc_sample_threshold.restype = U32
+            lib.orc_sample_threshold.argtypes = [ctypes.c_double]
             lib.orc_beta3.restype = ctypes.c_double
             lib.orc_beta3.argtypes = [ctypes.c_double]
             lib.orc_dbeta3.restype = ctypes.c_double
@@ -239,8 +248,25 @@ def mi_eval(fixed, moving, bins, params, q, fixed_spacing=(1, 1, 1), moving_spac
     return mi, hh, cnt
 
 
-def mi_eval_q16(fixed, moving, bins, q16, q, form=0, bits=False, fixed_depth=None, moving_depth=None, nthreads=1):
-    """Hard-binned MI from 16.16 affines (n x 12 int32) given directly."""
+def fmix32(k: int) -> int:
+    """R16: the MurmurHash3 32-bit finalizer."""
+    return int(_load().orc_fmix32(int(k) & 0xFFFFFFFF))
+
+
+def sample_threshold(fraction: float) -> int:
+    """R16: floor(fraction * 2^32) for 0 < fraction < 1, else 0 (every voxel)."""
+    return int(_load().orc_sample_threshold(float(fraction)))
+
+
+def sampled(index: int, seed: int, threshold: int) -> bool:
+    """R16: whether the fixed voxel with this linear index takes part."""
+    return bool(_load().orc_sampled(int(index), int(seed) & 0xFFFFFFFF, int(threshold)))
+
+
+def mi_eval_q16(fixed, moving, bins, q16, q, form=0, bits=False, fixed_depth=None, moving_depth=None, nthreads=1,
+                sample_fraction=0.0, sample_seed=0):
+    """Hard-binned MI from 16.16 affines (n x 12 int32) given directly; with
+    0 < sample_fraction < 1, over the randomly sampled fixed voxels (R16)."""
     fb = bin_volume(fixed, bins, fixed_depth)
     mv, md = _as_int(moving, moving_depth)
     qa = np.ascontiguousarray(q16, dtype=np.int32).reshape(-1, 12)
@@ -250,8 +276,10 @@ def mi_eval_q16(fixed, moving, bins, q16, q, form=0, bits=False, fixed_depth=Non
     mi = np.empty((n, nq), dtype=np.float64)
     hh = np.empty((n, nq, 3), dtype=np.float64)
     cnt = np.empty(n, dtype=np.int64)
-    rc = _load().orc_mi_eval_q16(_p(fb), _p(_dims(fb)), _p(mv), _dtype_code(mv), md, _p(_dims(mv)), int(bins), _p(qa),
-                                 n, _p(qs), nq, int(form), int(bool(bits)), int(nthreads), _p(mi), _p(hh), _p(cnt))
+    thr = sample_threshold(sample_fraction)
+    rc = _load().orc_mi_eval_q16_s(_p(fb), _p(_dims(fb)), _p(mv), _dtype_code(mv), md, _p(_dims(mv)), int(bins),
+                                   _p(qa), n, _p(qs), nq, int(form), int(bool(bits)), int(nthreads),
+                                   int(sample_seed) & 0xFFFFFFFF, thr, _p(mi), _p(hh), _p(cnt))
     if rc != 0:
         raise RuntimeError(f"oracle mi_eval_q16 failed ({rc})")
     return mi, hh, cnt

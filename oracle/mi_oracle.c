@@ -16,13 +16,13 @@
  * and Eq. (3) (registration as argmax over T); it names Tsallis entropy and
  * the translation / rotation / scale families (Introduction) and a full,
  * all-voxel histogram (Discussion) but leaves the rest open.  The readings
- * used here are tagged R1..R15 where they are applied:
+ * used here are tagged R1..R16 where they are applied:
  *   R1 binning (v * bins) >> depth               R2 parameter -> affine
  *   R3 16.16 fixed-point coordinate, overlap     R4 integer trilinear
  *   R5 counts over the overlap only              R6 natural logarithm
  *   R7 Tsallis entropy and Tsallis MI forms      R8 Parzen soft histogram
  *   R9 Parzen gradient (adjoint of R8)           R14 unit-ball (versor) rotation
- *   R15 zero-centred scale parameters
+ *   R15 zero-centred scale parameters            R16 random voxel sampling
  *
  * Every function here is pinned by tests that do not re-type its formula:
  * hand-enumerated 4x4x4 cases, exact permutations, closed forms, limits,
@@ -371,14 +371,55 @@ void orc_resample(const void *mov, int mdtype, int mdepth, const int nm[3], cons
  * voxels inside the overlap -- the paper's "full histogram" over all voxels
  * (Discussion).  Row = fixed bin.  Returns the overlap count N.
  */
+/*
+ * R16, random sampling (the Discussion's open question: ITK Mattes samples
+ * the image at random, MICUDA uses every voxel): a fixed voxel with linear
+ * index x takes part iff fmix32((uint32) x ^ fmix32(seed)) < threshold, where
+ * fmix32 is the 32-bit finalizer of MurmurHash3 (xor-shift by 16, multiply by
+ * 0x85ebca6b, xor-shift by 13, multiply by 0xc2b2ae35, xor-shift by 16, all
+ * mod 2^32) and threshold = floor(fraction * 2^32) for 0 < fraction < 1.  The
+ * subset is fixed per seed (a property of the fixed volume, as in Mattes'
+ * method), so the metric stays a deterministic function of the transform.
+ */
+uint32_t orc_fmix32(uint32_t k) {
+    k ^= k >> 16;
+    k *= 0x85ebca6bu;
+    k ^= k >> 13;
+    k *= 0xc2b2ae35u;
+    k ^= k >> 16;
+    return k;
+}
+
+int orc_sampled(int64_t x, uint32_t seed, uint32_t threshold) {
+    return orc_fmix32((uint32_t)x ^ orc_fmix32(seed)) < threshold;
+}
+
+uint32_t orc_sample_threshold(double fraction) {
+    if (!(fraction > 0.0 && fraction < 1.0)) return 0;
+    return (uint32_t)floor(fraction * 4294967296.0);
+}
+
+/* Joint histogram over the overlap, restricted to the sampled fixed voxels
+ * when threshold > 0 (R16); every voxel when threshold == 0. */
+int64_t orc_joint_hist_s(const uint8_t *fbins, const int nf[3], const void *mov, int mdtype, int mdepth,
+                         const int nm[3], const int32_t q[12], int bins, uint32_t seed, uint32_t threshold,
+                         uint64_t *hist);
+
 int64_t orc_joint_hist(const uint8_t *fbins, const int nf[3], const void *mov, int mdtype, int mdepth,
                        const int nm[3], const int32_t q[12], int bins, uint64_t *hist) {
+    return orc_joint_hist_s(fbins, nf, mov, mdtype, mdepth, nm, q, bins, 0u, 0u, hist);
+}
+
+int64_t orc_joint_hist_s(const uint8_t *fbins, const int nf[3], const void *mov, int mdtype, int mdepth,
+                         const int nm[3], const int32_t q[12], int bins, uint32_t seed, uint32_t threshold,
+                         uint64_t *hist) {
     memset(hist, 0, sizeof(uint64_t) * (size_t)bins * (size_t)bins);
     int64_t n = 0;
     for (int64_t k = 0; k < nf[2]; k++)
         for (int64_t j = 0; j < nf[1]; j++)
             for (int64_t i = 0; i < nf[0]; i++) {
                 uint32_t val;
+                if (threshold && !orc_sampled(orc_index(nf, i, j, k), seed, threshold)) continue;
                 if (!orc_sample_hard(mov, mdtype, mdepth, nm, q, i, j, k, &val)) continue;
                 int bf = fbins[orc_index(nf, i, j, k)];
                 int bm = orc_bin_of(val, bins, mdepth);
@@ -520,10 +561,24 @@ int orc_mi_eval(const uint8_t *fbins, const int nf[3], const float sf[3], const 
     return err;
 }
 
-/* Same, from 16.16 affines given directly (n x 12 int32). */
+/* Same, from 16.16 affines given directly (n x 12 int32), over the sampled
+ * fixed voxels (R16) when threshold > 0. */
+int orc_mi_eval_q16_s(const uint8_t *fbins, const int nf[3], const void *mov, int mdtype, int mdepth,
+                      const int nm[3], int bins, const int32_t *q, int n, const double *qs, int nq, int form,
+                      int bits, int nthreads, uint32_t seed, uint32_t threshold, double *mi, double *h,
+                      int64_t *count);
+
 int orc_mi_eval_q16(const uint8_t *fbins, const int nf[3], const void *mov, int mdtype, int mdepth,
                     const int nm[3], int bins, const int32_t *q, int n, const double *qs, int nq, int form,
                     int bits, int nthreads, double *mi, double *h, int64_t *count) {
+    return orc_mi_eval_q16_s(fbins, nf, mov, mdtype, mdepth, nm, bins, q, n, qs, nq, form, bits, nthreads, 0u, 0u,
+                             mi, h, count);
+}
+
+int orc_mi_eval_q16_s(const uint8_t *fbins, const int nf[3], const void *mov, int mdtype, int mdepth,
+                      const int nm[3], int bins, const int32_t *q, int n, const double *qs, int nq, int form,
+                      int bits, int nthreads, uint32_t seed, uint32_t threshold, double *mi, double *h,
+                      int64_t *count) {
     int err = ORC_OK;
     (void)nthreads;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
@@ -538,7 +593,7 @@ int orc_mi_eval_q16(const uint8_t *fbins, const int nf[3], const void *mov, int 
             err = ORC_ENOMEM;
             continue;
         }
-        int64_t N = orc_joint_hist(fbins, nf, mov, mdtype, mdepth, nm, q + 12 * (size_t)t, bins, hh);
+        int64_t N = orc_joint_hist_s(fbins, nf, mov, mdtype, mdepth, nm, q + 12 * (size_t)t, bins, seed, threshold, hh);
         for (size_t x = 0; x < B2; x++) hd[x] = (double)hh[x];
         orc_entropies(hd, bins, qs, nq, form, bits, mi + (size_t)t * nq, h ? h + (size_t)t * nq * 3 : NULL);
         if (count) count[t] = N;

@@ -76,6 +76,8 @@ def _load():
             U32 = ctypes.c_uint32
             lib.orc_mi_eval_q16_s.restype = I
             lib.orc_mi_eval_q16_s.argtypes = [P, P, P, I, I, P, I, P, I, P, I, I, I, I, U32, U32, P, P, P]
+            lib.orc_joint_hist_s.restype = I64
+            lib.orc_joint_hist_s.argtypes = [P, P, P, I, I, P, P, I, U32, U32, P]
             lib.orc_fmix32.restype = U32
             lib.orc_fmix32.argtypes = [U32]
             lib.orc_sampled.restype = I
@@ -193,14 +195,16 @@ def resample(moving: np.ndarray, q16, fixed_shape, depth: int | None = None) -> 
     return out
 
 
-def joint_hist(fixed: np.ndarray, moving: np.ndarray, q16, bins: int, fixed_depth=None, moving_depth=None):
-    """R5 joint histogram (row = fixed bin) over the overlap; returns (hist uint64, N)."""
+def joint_hist(fixed: np.ndarray, moving: np.ndarray, q16, bins: int, fixed_depth=None, moving_depth=None,
+               sample_fraction=0.0, sample_seed=0):
+    """R5 joint histogram (row = fixed bin) over the overlap -- over the randomly
+    sampled fixed voxels (R16) when 0 < sample_fraction < 1; returns (hist uint64, N)."""
     fb = bin_volume(fixed, bins, fixed_depth)
     mv, md = _as_int(moving, moving_depth)
     q = np.ascontiguousarray(q16, dtype=np.int32).reshape(12)
     h = np.empty((bins, bins), dtype=np.uint64)
-    n = _load().orc_joint_hist(_p(fb), _p(_dims(fb)), _p(mv), _dtype_code(mv), md, _p(_dims(mv)), _p(q),
-                               int(bins), _p(h))
+    n = _load().orc_joint_hist_s(_p(fb), _p(_dims(fb)), _p(mv), _dtype_code(mv), md, _p(_dims(mv)), _p(q),
+                                 int(bins), int(sample_seed) & 0xFFFFFFFF, sample_threshold(sample_fraction), _p(h))
     return h, int(n)
 
 

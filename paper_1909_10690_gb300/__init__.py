@@ -102,7 +102,7 @@ def _volume(x, spacing, depth):
 
 
 def _options(kernel, tsallis_form, bits, hist_variant, path, use_graphs, autotune, device, block_threads=0,
-             rotation="euler", scale="factor"):
+             rotation="euler", scale="factor", sample_fraction=0.0, sample_seed=0):
     o = _lib.MiOptions()
     load().mi_options_default(ctypes.byref(o))
     o.kernel = {"hard": 0, "parzen": 1}[kernel]
@@ -116,6 +116,8 @@ def _options(kernel, tsallis_form, bits, hist_variant, path, use_graphs, autotun
     o.block_threads = int(block_threads)
     o.rotation = {"euler": 0, "versor": 1}[rotation]
     o.scale = {"factor": 0, "offset": 1}[scale]
+    o.sample_fraction = float(sample_fraction)
+    o.sample_seed = int(sample_seed) & 0xFFFFFFFF
     return o
 
 
@@ -139,18 +141,21 @@ class Context:
     rotation: "euler" (rx, ry, rz in degrees, default) or "versor" (the unit-ball
     parameterisation of the paper's rotation maps); scale: "factor" (1 =
     identity, default) or "offset" (zero-centred, sigma = 1 + s).
+    sample_fraction in (0, 1): the hard-path metric over a random subset of the
+    fixed voxels of that fraction, fixed by sample_seed (0: every voxel).
     """
 
     def __init__(self, fixed=None, moving=None, bins=64, fixed_spacing=(1.0, 1.0, 1.0),
                  moving_spacing=(1.0, 1.0, 1.0), fixed_depth=None, moving_depth=None, kernel="hard",
                  tsallis_form="additive", bits=False, hist_variant=HV_AUTO, path="auto", use_graphs=True,
-                 autotune=True, device=None, pairs=None, block_threads=0, rotation="euler", scale="factor"):
+                 autotune=True, device=None, pairs=None, block_threads=0, rotation="euler", scale="factor",
+                 sample_fraction=0.0, sample_seed=0):
         self._lib = load()
         self._h = ctypes.c_void_p()
         self.kernel = kernel
         self.rotation, self.scale = rotation, scale
         opt = _options(kernel, tsallis_form, bits, hist_variant, path, use_graphs, autotune, device, block_threads,
-                       rotation, scale)
+                       rotation, scale, sample_fraction, sample_seed)
         if pairs is None:
             pairs = [dict(fixed=fixed, moving=moving, bins=bins, fixed_spacing=fixed_spacing,
                           moving_spacing=moving_spacing, fixed_depth=fixed_depth, moving_depth=moving_depth)]

@@ -81,7 +81,8 @@ class MiOptions(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("tsallis_form", ctypes.c_int), ("log_bits", ctypes.c_int),
                 ("hist_variant", ctypes.c_int), ("path", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("device", ctypes.c_int), ("block_threads", ctypes.c_int),
-                ("rotation", ctypes.c_int), ("scale", ctypes.c_int)]
+                ("rotation", ctypes.c_int), ("scale", ctypes.c_int), ("sample_fraction", ctypes.c_float),
+                ("sample_seed", ctypes.c_uint)]
 
 
 # Symbols declared in include/mi.h, with their ctypes signatures.

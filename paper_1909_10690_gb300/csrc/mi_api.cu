@@ -250,6 +250,7 @@ struct Pair {
     cudaArray_t arrq = nullptr;  // 2 x 2 quads as a 3D array (one extra z plane), read through texq
     cudaTextureObject_t texq = 0;
     DevBuf rowinfo;             // row-bound layout table (bins entries)
+    DevBuf srow, scol, sbin;    // random sampling: per-row lists of the sampled fixed voxels
     int rows_words = 0;
     DevBuf pfbins, pmov, pmovx;  // Parzen path (pmovx: pmov extended by one plane per axis)
     cudaArray_t parr = nullptr;  // float4 quads of pmovx as a 3D array, read through ptex
@@ -504,6 +505,34 @@ mi_status add_pair(mi_ctx *ctx, const mi_volume *fx, const mi_volume *mv, int bi
             MI_CU(cudaMemcpyAsync(P->rowinfo.p, info.data(), (size_t)bins * 4, cudaMemcpyHostToDevice, s), "row table");
             MI_CU(cudaStreamSynchronize(s), "row table");
         }
+        // random sampling: per fixed row, the x indices and bins of its sampled voxels (CSR)
+        const double frac = (double)ctx->opt.sample_fraction;
+        if (frac > 0.0 && frac < 1.0) {
+            if (P->nf[0] > 65536)
+                return ctx->fail(MI_EUNSUPPORTED, "random sampling needs fixed rows of at most 65536 voxels");
+            const uint32_t thr = (uint32_t)floor(frac * 4294967296.0);
+            const long long R = (long long)P->nf[1] * P->nf[2];
+            DevBuf dcnt;
+            MI_CU(dcnt.ensure((size_t)R * 4), "allocating sample counts");
+            MI_CU(launch_sample_count(P->nf[0], R, ctx->opt.sample_seed, thr, dcnt.as<uint32_t>(), s), "sample counts");
+            std::vector<uint32_t> cnt((size_t)R), ptr((size_t)R + 1);
+            MI_CU(cudaMemcpyAsync(cnt.data(), dcnt.p, (size_t)R * 4, cudaMemcpyDeviceToHost, s), "sample counts D2H");
+            MI_CU(cudaStreamSynchronize(s), "sample counts");
+            unsigned long long acc = 0;
+            for (long long r = 0; r < R; ++r) {
+                ptr[(size_t)r] = (uint32_t)acc;
+                acc += cnt[(size_t)r];
+            }
+            ptr[(size_t)R] = (uint32_t)acc;
+            MI_CU(P->srow.ensure(((size_t)R + 1) * 4), "allocating sample rows");
+            MI_CU(P->scol.ensure(std::max<size_t>((size_t)acc * 2, 2)), "allocating sample columns");
+            MI_CU(P->sbin.ensure(std::max<size_t>((size_t)acc, 1)), "allocating sample bins");
+            MI_CU(cudaMemcpyAsync(P->srow.p, ptr.data(), ((size_t)R + 1) * 4, cudaMemcpyHostToDevice, s), "sample rows");
+            MI_CU(launch_sample_fill(P->nf[0], R, ctx->opt.sample_seed, thr, P->fbins.as<uint8_t>(), P->srow.as<uint32_t>(),
+                                     P->scol.as<uint16_t>(), P->sbin.as<uint8_t>(), s),
+                  "sample lists");
+            MI_CU(cudaStreamSynchronize(s), "sample lists");
+        }
         if (mv->dtype == MI_F32) {
             MI_CU(P->mov.ensure((size_t)P->nvm * 2), "allocating the moving volume");
             MI_CU(launch_f32_to_u16(rawm.as<float>(), P->nvm, P->mov.as<uint16_t>(), s), "converting the moving volume");
@@ -581,6 +610,9 @@ mi_status upload_pairs(mi_ctx *ctx) {
         d.texp = P.tex;
         d.texq = P.texq;
         d.rowinfo = P.rowinfo.as<uint32_t>();
+        d.srow = P.srow.p ? P.srow.as<uint32_t>() : nullptr;
+        d.scol = P.scol.as<uint16_t>();
+        d.sbin = P.sbin.as<uint8_t>();
         d.rows_words = P.rows_words;
         for (int a = 0; a < 3; ++a) {
             d.nf[a] = P.nf[a];
@@ -605,6 +637,9 @@ PairDev host_pairdev(const Pair &P) {
     d.texp = P.tex;
     d.texq = P.texq;
     d.rowinfo = P.rowinfo.as<uint32_t>();
+    d.srow = P.srow.p ? P.srow.as<uint32_t>() : nullptr;
+    d.scol = P.scol.as<uint16_t>();
+    d.sbin = P.sbin.as<uint8_t>();
     d.rows_words = P.rows_words;
     for (int a = 0; a < 3; ++a) {
         d.nf[a] = P.nf[a];
@@ -639,6 +674,14 @@ mi_status create_common(mi_ctx **out, const mi_volume *fixed, const mi_volume *m
     if (ctx->opt.kernel == MI_PARZEN && npairs != 1) {
         g_create_error = "the Parzen form takes one pair per context";
         return MI_EINVAL;
+    }
+    if (!(ctx->opt.sample_fraction >= 0.0f && ctx->opt.sample_fraction <= 1.0f)) {
+        g_create_error = "opt.sample_fraction must lie in [0, 1]";
+        return MI_EINVAL;
+    }
+    if (ctx->opt.sample_fraction > 0.0f && ctx->opt.sample_fraction < 1.0f && ctx->opt.kernel == MI_PARZEN) {
+        g_create_error = "random sampling is a hard-path option";
+        return MI_EUNSUPPORTED;
     }
     if ((ctx->opt.rotation != MI_ROT_EULER_DEG && ctx->opt.rotation != MI_ROT_VERSOR) ||
         (ctx->opt.scale != MI_SCALE_FACTOR && ctx->opt.scale != MI_SCALE_OFFSET)) {
@@ -1185,6 +1228,8 @@ void mi_options_default(mi_options *opt) {
     opt->block_threads = 0;
     opt->rotation = MI_ROT_EULER_DEG;
     opt->scale = MI_SCALE_FACTOR;
+    opt->sample_fraction = 0.0f;
+    opt->sample_seed = 0u;
 }
 
 const char *mi_version(void) { return "gb300-mi 0.1 (sm_103a)"; }

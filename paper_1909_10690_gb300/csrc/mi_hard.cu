@@ -532,6 +532,49 @@ __device__ typename HistOf<HV>::T make_hist(unsigned char *smem, const SmemLayou
 // by one, 32 voxels at a time, with each row's interval broadcast by shuffles.
 // Blocks first_block + n * block_stride, n = 0, 1, ..., below n_end are
 // visited (the batched kernel passes one slab of blocks at a time).
+// The interpolated moving value at a 16.16 index, through the variant's fetch path.
+template <int FM, typename PairT>
+__device__ __forceinline__ int sample_value(const PairDev &P, unsigned U0, unsigned U1, unsigned U2) {
+    if constexpr (FM == FM_QUAD) {
+        uint32_t t[8];
+        quad_fetch(P.texq, U0, U1, U2, t);
+        return quad_lerp(U0, U1, U2, t);
+    } else if constexpr (FM == FM_TEX) {
+        return sample_hard_tex<PairT>(P.texp, (int)U0, (int)U1, (int)U2);
+    } else {
+        const int n0 = P.nm[0], sz = n0 * (P.nm[1] + 1);
+        return sample_hard_pair<PairT>((const PairT *)P.movp, n0, sz, n0, sz, (int)U0, (int)U1, (int)U2);
+    }
+}
+
+// A clipped row [lo, hi] under random sampling: its sampled voxels only, 32 at a time; U at an
+// entry's x index i is u_lo + st (i - lo), exact inside the interval.
+template <int FM, typename PairT, class Hist>
+__device__ __forceinline__ void sampled_row(const PairDev &P, long long r, int lo, int hi, unsigned ub0, unsigned ub1,
+                                            unsigned ub2, int st0, int st1, int st2, Hist &H) {
+    const int lane = threadIdx.x & 31;
+    const int bins = P.bins, mdepth = P.mdepth;
+    const uint32_t k0 = __ldg(P.srow + r), k1 = __ldg(P.srow + r + 1);
+    for (uint32_t kb = k0; kb < k1; kb += 32) {
+        const uint32_t k = kb + lane;
+        int i = 0;
+        bool valid = false;
+        if (k < k1) {
+            i = (int)__ldg(P.scol + k);
+            valid = i >= lo && i <= hi;
+        }
+        int bf = 0, bm = 0;
+        if (valid) {
+            const unsigned d = (unsigned)(i - lo);
+            const int v = sample_value<FM, PairT>(P, ub0 + (unsigned)st0 * d, ub1 + (unsigned)st1 * d,
+                                                  ub2 + (unsigned)st2 * d);
+            bm = (v * bins) >> mdepth;
+            bf = (int)__ldg(P.sbin + k);
+        }
+        H.add(bf, bm, valid);
+    }
+}
+
 template <typename PairT, int FM, class Hist>
 __device__ void accumulate_rows(const PairDev &P, const int *q, long long first_block, long long block_stride,
                                 long long n_end, Hist &H) {
@@ -561,10 +604,14 @@ __device__ void accumulate_rows(const PairDev &P, const int *q, long long first_
             if (r >= R) break;  // warp-uniform: only the last block may be partial
             const int lo = __shfl_sync(kFull, mine.lo, s), hi = __shfl_sync(kFull, mine.hi, s);
             if (lo > hi) continue;
+            const unsigned ub0 = (unsigned)__shfl_sync(kFull, mine.u0, s), ub1 = (unsigned)__shfl_sync(kFull, mine.u1, s),
+                           ub2 = (unsigned)__shfl_sync(kFull, mine.u2, s);
+            if (P.srow != nullptr) {  // random sampling: the row's sampled voxels only
+                sampled_row<FM, PairT>(P, r, lo, hi, ub0, ub1, ub2, st0, st1, st2, H);
+                continue;
+            }
             // unsigned: lanes past the row end may step outside the int range; only in-range lanes use them
-            unsigned U0 = (unsigned)__shfl_sync(kFull, mine.u0, s) + (unsigned)st0 * lane,
-                     U1 = (unsigned)__shfl_sync(kFull, mine.u1, s) + (unsigned)st1 * lane,
-                     U2 = (unsigned)__shfl_sync(kFull, mine.u2, s) + (unsigned)st2 * lane;
+            unsigned U0 = ub0 + (unsigned)st0 * lane, U1 = ub1 + (unsigned)st1 * lane, U2 = ub2 + (unsigned)st2 * lane;
             const uint8_t *__restrict__ frow = P.fbins + (size_t)r * nf0;
             if constexpr (FM == FM_QUAD) {
                 // full steps (all 32 lanes inside the interval) without predicates; the fixed bin of
@@ -900,6 +947,43 @@ size_t hard_smem_bytes(int variant, int bins, int threads, int rows_words) {
     return smem_layout(variant, bins, threads, rows_words).total;
 }
 
+// MurmurHash3's 32-bit finalizer: xor-shift 16, multiply 0x85ebca6b, xor-shift 13, multiply 0xc2b2ae35,
+// xor-shift 16 (mod 2^32).
+__host__ __device__ inline uint32_t fmix32(uint32_t k) {
+    k ^= k >> 16;
+    k *= 0x85ebca6bu;
+    k ^= k >> 13;
+    k *= 0xc2b2ae35u;
+    k ^= k >> 16;
+    return k;
+}
+
+// One thread per fixed row: how many of its voxels are sampled (hseed = fmix32(seed)).
+__global__ void k_sample_count(int n0, long long R, uint32_t hseed, uint32_t thr, uint32_t *__restrict__ counts) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < R; r += (long long)gridDim.x * blockDim.x) {
+        uint32_t c = 0;
+        const uint32_t x0 = (uint32_t)(r * n0);
+        for (int i = 0; i < n0; ++i) c += fmix32((x0 + (uint32_t)i) ^ hseed) < thr ? 1u : 0u;
+        counts[r] = c;
+    }
+}
+
+// One thread per fixed row: its sampled voxels' x indices (ascending) and fixed bins.
+__global__ void k_sample_fill(int n0, long long R, uint32_t hseed, uint32_t thr, const uint8_t *__restrict__ fbins,
+                              const uint32_t *__restrict__ row_ptr, uint16_t *__restrict__ cols,
+                              uint8_t *__restrict__ bins) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < R; r += (long long)gridDim.x * blockDim.x) {
+        uint32_t o = row_ptr[r];
+        const uint32_t x0 = (uint32_t)(r * n0);
+        for (int i = 0; i < n0; ++i)
+            if (fmix32((x0 + (uint32_t)i) ^ hseed) < thr) {
+                cols[o] = (uint16_t)i;
+                bins[o] = fbins[(size_t)r * n0 + i];
+                ++o;
+            }
+    }
+}
+
 __global__ void k_fixed_hist(const uint8_t *__restrict__ fb, long long n, int bins, unsigned long long *__restrict__ out) {
     __shared__ unsigned int h[256];
     for (int c = threadIdx.x; c < 256; c += blockDim.x) h[c] = 0;
@@ -909,6 +993,18 @@ __global__ void k_fixed_hist(const uint8_t *__restrict__ fb, long long n, int bi
     __syncthreads();
     for (int c = threadIdx.x; c < bins; c += blockDim.x)
         if (h[c]) atomicAdd(out + c, (unsigned long long)h[c]);
+}
+
+cudaError_t launch_sample_count(int n0, long long R, uint32_t seed, uint32_t threshold, uint32_t *counts,
+                                cudaStream_t s) {
+    k_sample_count<<<grid_for(R, 256), 256, 0, s>>>(n0, R, fmix32(seed), threshold, counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_fill(int n0, long long R, uint32_t seed, uint32_t threshold, const uint8_t *fbins,
+                               const uint32_t *row_ptr, uint16_t *cols, uint8_t *bins, cudaStream_t s) {
+    k_sample_fill<<<grid_for(R, 256), 256, 0, s>>>(n0, R, fmix32(seed), threshold, fbins, row_ptr, cols, bins);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fixed_hist(const uint8_t *fbins, long long n, int bins, unsigned long long *out, cudaStream_t s) {

@@ -20,6 +20,9 @@ struct PairDev {
     unsigned long long texp;  // the same pairs as a 3D texture (point sampling, clamped), dims (nx, ny, nz)
     unsigned long long texq;  // 2 x 2 quads (x, y), (x + 1, y), (x, y + 1), (x + 1, y + 1) as a 3D texture
     const uint32_t *rowinfo;  // row-bound layout: per fixed bin, word offset << 6 | wide << 5 | shift (0 or 16)
+    const uint32_t *srow;     // random sampling (else null): row r's sampled voxels are entries srow[r]..srow[r+1]-1
+    const uint16_t *scol;     //   of scol (their x index, ascending)
+    const uint8_t *sbin;      //   and sbin (their fixed bin)
     int nf[3];             // fixed dims (x, y, z)
     int nm[3];             // moving dims
     int bins;
@@ -72,6 +75,13 @@ __host__ __device__ inline int hv_fetch(int v) {
 // Shared memory needed by a hard-path CTA of `threads` threads for `bins` bins
 // (rows_words: words of the row-bound layout, used by HV_ROWS*).
 size_t hard_smem_bytes(int variant, int bins, int threads, int rows_words);
+// Random voxel sampling: voxel x takes part iff fmix32(x ^ fmix32(seed)) < threshold.
+// Per fixed row, the number of sampled voxels (counts: R entries), then the lists themselves
+// (row_ptr: the exclusive prefix sums, R + 1 entries; cols / bins: row_ptr[R] entries).
+cudaError_t launch_sample_count(int n0, long long R, uint32_t seed, uint32_t threshold, uint32_t *counts,
+                                cudaStream_t s);
+cudaError_t launch_sample_fill(int n0, long long R, uint32_t seed, uint32_t threshold, const uint8_t *fbins,
+                               const uint32_t *row_ptr, uint16_t *cols, uint8_t *bins, cudaStream_t s);
 // Per-bin voxel counts of a binned fixed volume (bins u64, zeroed here).
 cudaError_t launch_fixed_hist(const uint8_t *fbins, long long n, int bins, unsigned long long *out, cudaStream_t s);
 

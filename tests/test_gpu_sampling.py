@@ -1,0 +1,56 @@
+"""GPU parity of random voxel sampling (R16: the fixed voxels whose hashed index falls below
+floor(fraction 2^32)), every histogram variant, plain and batched paths."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_10690_gb300 import phantoms
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = list(range(13))
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_sampled_histograms_bit_exact(cuda_lib, variant):
+    f, m = phantoms.head_pair(shape=(29, 41, 75), spacing=(1, 1, 1), seed=80)
+    m = np.ascontiguousarray(m[:, :37, :71])
+    bins, frac, seed = 64, 0.3, 1234
+    ctx = cuda_lib.Context(f, m, bins=bins, fixed_depth=12, moving_depth=12, hist_variant=variant,
+                           sample_fraction=frac, sample_seed=seed)
+    prm = phantoms.random_transforms(12, seed=81, t_mm=4, r_deg=10, s_range=(0.9, 1.1))
+    q16 = np.stack([oracle.affine_q16(oracle.affine(p, f.shape, (1, 1, 1), m.shape, (1, 1, 1))) for p in prm])
+    for path in (cuda_lib.PATH_PLAIN, cuda_lib.PATH_BATCHED):
+        H = ctx.hist(affines=q16, path=path)
+        for t in range(0, len(q16), 4):
+            ho, n = oracle.joint_hist(f, m, q16[t], bins, 12, 12, sample_fraction=frac, sample_seed=seed)
+            np.testing.assert_array_equal(H[t], ho.astype(np.uint32))
+
+
+def test_sampled_mi_counts_and_seeds(cuda_lib):
+    f, m = phantoms.head_pair(shape=(48, 56, 60), spacing=(1, 1, 1), seed=82)
+    prm = phantoms.random_transforms(20, seed=83, t_mm=5, r_deg=10, s_range=(0.9, 1.1))
+    q16 = np.stack([oracle.affine_q16(oracle.affine(p, f.shape, (1, 1, 1), m.shape, (1, 1, 1))) for p in prm])
+    qs = [1.0, 0.5, 2.0]
+    counts = {}
+    for frac, seed in ((0.1, 1), (0.5, 1), (0.5, 2)):
+        ctx = cuda_lib.Context(f, m, bins=128, fixed_depth=12, moving_depth=12, sample_fraction=frac, sample_seed=seed)
+        mi, h, cnt = ctx.eval(prm, qs, with_entropies=True)
+        mi_o, h_o, cnt_o = oracle.mi_eval_q16(f, m, 128, q16, qs, fixed_depth=12, moving_depth=12, nthreads=8,
+                                              sample_fraction=frac, sample_seed=seed)
+        np.testing.assert_array_equal(cnt, cnt_o)
+        scale = np.maximum(np.abs(mi_o), h_o[..., 2])
+        assert np.all(np.abs(mi - mi_o) <= 1e-6 * scale)
+        counts[(frac, seed)] = cnt
+    full = cuda_lib.Context(f, m, bins=128, fixed_depth=12, moving_depth=12).eval(prm, qs, with_entropies=True)[2]
+    for (frac, seed), c in counts.items():
+        assert np.all(np.abs(c / full - frac) < 0.05)  # about that fraction of the overlap
+    assert not np.array_equal(counts[(0.5, 1)], counts[(0.5, 2)])
+
+
+def test_sampling_is_a_hard_path_option(cuda_lib):
+    f, m = phantoms.head_pair(shape=(16, 18, 20), spacing=(1, 1, 1), seed=84, dtype=np.float32)
+    with pytest.raises(cuda_lib.MIError):
+        cuda_lib.Context(f, m, bins=16, kernel="parzen", sample_fraction=0.5)
+    with pytest.raises(cuda_lib.MIError):
+        cuda_lib.Context(f, m, bins=16, sample_fraction=1.5)

@@ -368,6 +368,38 @@ def run_profile_parzen(args):
     print(json.dumps({"profile": "parzen", "poses": args.profile_parzen, "kernel_ms": ms}))
 
 
+def run_maps(args):
+    """The Methodology's parameter-space map: args.maps^3 translations over +-25 mm of the 256x256x160 12-bit
+    head-like pair (no motion, so the true pose is the grid centre), 64 bins, Shannon and Tsallis q = 1.5,
+    through the batched path; then the ascent analysis of the Results on the Shannon map."""
+    import torch
+
+    import paper_1909_10690_gb300 as mi
+    from paper_1909_10690_gb300 import maps, phantoms
+
+    sp = (1.0, 1.0, 1.2)
+    f, m = phantoms.head_pair(shape=(160, 256, 256), spacing=sp, seed=60, motion=(0, 0, 0, 0, 0, 0, 1, 1, 1))
+    ctx = mi.Context(f, m, bins=64, fixed_depth=12, moving_depth=12, fixed_spacing=sp, moving_spacing=sp,
+                     path="batched")
+    n = args.maps
+    maps.param_map(ctx, "translation", -25, 25, 3, q=[1.0, 1.5])  # warm-up: autotune, graph
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mp = maps.param_map(ctx, "translation", -25, 25, n, q=[1.0, 1.5])
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    c = (n - 1) // 2
+    frac = maps.capture_fraction(mp[..., 0], (c, c, c))
+    _, maxima = maps.ascent_sinks(mp[..., 0])
+    da = time.perf_counter() - t1
+    print(json.dumps({"maps": "translation", "grid": [n, n, n], "range_mm": [-25, 25], "transforms": n ** 3,
+                      "voxels": int(f.size), "seconds": dt, "voxel_transforms_per_s": n ** 3 * f.size / dt,
+                      "peak_at_centre": bool(np.unravel_index(np.argmax(mp[..., 0]), mp.shape[:3]) == (c, c, c)),
+                      "capture_fraction_shannon": frac, "local_maxima_shannon": int(len(maxima)),
+                      "ascent_analysis_seconds": da}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -380,7 +412,11 @@ def main():
     ap.add_argument("--variant", type=int, default=9, help="histogram variant in profile mode (MI_HV_*)")
     ap.add_argument("--threads", type=int, default=1024, help="CTA size in profile mode (512 or 1024)")
     ap.add_argument("--profile-parzen", type=int, default=0, help="profile mode: Parzen MI + gradient of this many poses")
+    ap.add_argument("--maps", type=int, default=0, help="time an N^3 translation map of the head-like pair")
     args = ap.parse_args()
+    if args.maps:
+        run_maps(args)
+        return
     if args.profile:
         run_profile(args)
         return

@@ -408,3 +408,16 @@ def test_uneven_batch_full_size(cuda_lib):
         assert np.all(np.abs(mi_p[0] - mi_o) <= 1e-6 * np.maximum(np.abs(mi_o), 1.0)), (p, mi_p[0], mi_o)
         for iq in range(3):
             assert np.abs(g_p[0, iq] - g_o[iq]).max() <= 1e-4 * np.abs(g_o[iq]).max(), (p, iq)
+
+
+def test_versor_on_the_sphere_is_a_half_turn(cuda_lib):
+    # |v| = 1 exactly and |v| > 1: the same half turn (the sphere surface of the unit-ball maps)
+    f, m = phantoms.head_pair(shape=(30, 30, 30), spacing=(1, 1, 1), seed=12)
+    ctx = cuda_lib.Context(f, m, bins=32, fixed_depth=12, moving_depth=12, rotation="versor")
+    prm = np.array([[0, 0, 0, 0, 0, 1.0, 1, 1, 1], [0, 0, 0, 0, 0, 3.0, 1, 1, 1],
+                    [0, 0, 0, 0.6, 0.8, 0, 1, 1, 1], [0, 0, 0, 1.2, 1.6, 0, 1, 1, 1]], np.float32)
+    a, q, _ = ctx.affine(prm)
+    np.testing.assert_array_equal(q[0], q[1])
+    np.testing.assert_array_equal(q[2], q[3])
+    mi = ctx.eval(prm, [1.0])
+    assert mi[0, 0] == mi[1, 0] and mi[2, 0] == mi[3, 0]

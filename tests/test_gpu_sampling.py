@@ -54,3 +54,34 @@ def test_sampling_is_a_hard_path_option(cuda_lib):
         cuda_lib.Context(f, m, bins=16, kernel="parzen", sample_fraction=0.5)
     with pytest.raises(cuda_lib.MIError):
         cuda_lib.Context(f, m, bins=16, sample_fraction=1.5)
+
+
+def test_sampled_empty_overlap_and_uneven_pairs(cuda_lib):
+    # a transform with no overlap gives NaN and MI_EEMPTY after the rest of the batch is done
+    f, m = phantoms.head_pair(shape=(24, 26, 28), spacing=(1, 1, 1), seed=85)
+    ctx = cuda_lib.Context(f, m, bins=32, fixed_depth=12, moving_depth=12, sample_fraction=0.4, sample_seed=9)
+    prm = phantoms.random_transforms(3, seed=86, t_mm=2, r_deg=3, s_range=(0.98, 1.02))
+    prm[1, :3] = 500.0
+    with pytest.raises(cuda_lib.MIError) as e:
+        ctx.eval(prm, [1.0], allow_empty=False)
+    assert e.value.status == cuda_lib.MI_EEMPTY
+    mi = ctx.eval(prm, [1.0])
+    assert np.isnan(mi[1, 0]) and np.all(np.isfinite(mi[[0, 2], 0]))
+    # each pair of an uneven batch has its own sampled subset
+    specs = [((20, 22, 24), np.uint8, 8, 32), ((26, 18, 30), np.uint16, 12, 64)]
+    pairs, vols = [], []
+    for i, (shape, dt, depth, bins) in enumerate(specs):
+        fi, mi_ = phantoms.head_pair(shape=shape, spacing=(1, 1, 1), depth=depth, seed=90 + i, dtype=dt)
+        vols.append((fi, mi_, depth, bins))
+        pairs.append(dict(fixed=fi, moving=mi_, bins=bins, fixed_depth=depth, moving_depth=depth))
+    bctx = cuda_lib.Context(pairs=pairs, sample_fraction=0.6, sample_seed=17)
+    prm = phantoms.random_transforms(8, seed=92, t_mm=3, r_deg=6, s_range=(0.95, 1.05))
+    pair_of = np.array([0, 1] * 4, np.int32)
+    got, h, cnt = bctx.batch_eval(pair_of, prm, [1.0, 2.0], with_entropies=True)
+    for p, (fi, mi_, depth, bins) in enumerate(vols):
+        sel = np.nonzero(pair_of == p)[0]
+        q16 = np.stack([oracle.affine_q16(oracle.affine(prm[t], fi.shape, (1, 1, 1), mi_.shape, (1, 1, 1))) for t in sel])
+        mo, ho, co = oracle.mi_eval_q16(fi, mi_, bins, q16, [1.0, 2.0], fixed_depth=depth, moving_depth=depth,
+                                        sample_fraction=0.6, sample_seed=17)
+        np.testing.assert_array_equal(cnt[sel], co)
+        assert np.all(np.abs(got[sel] - mo) <= 1e-6 * np.maximum(np.abs(mo), ho[..., 2]))

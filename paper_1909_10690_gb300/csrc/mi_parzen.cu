@@ -516,8 +516,8 @@ __global__ void __launch_bounds__(256, 2)
     k_parzen_adj(ParzenPair P, const ParzenAffine *__restrict__ aff, int nq_total, int q0,
                  const float *__restrict__ wtab, int w_in_smem, double *__restrict__ mom) {
     // mom: n x nq_total x gridDim.x x 12 per-CTA partial moments (no atomics: fixed-order reduction later)
-    // NQ x B x SB weights when they fit; the row stride SB >= B + 1 is 7 mod 32, so neighbouring
-    // voxels' cells, a bin or two apart on either axis, are read from different banks
+    // NQ x B x SB weight pairs (W[k], W[k + 1]) when they fit; the row stride SB >= B + 1 is 7 mod 32,
+    // so neighbouring voxels' cells, a bin or two apart on either axis, are read from different banks
     extern __shared__ float sw[];
     const int t = blockIdx.y, B = P.B, B2 = B * B, SB = parzen_stride(B);
     __shared__ long long A[12];
@@ -525,12 +525,13 @@ __global__ void __launch_bounds__(256, 2)
     if (threadIdx.x < 12) A[threadIdx.x] = aff[t].A[threadIdx.x];
     const float *W = wtab + ((size_t)t * nq_total + q0) * B2;
     int RS = B, QS = B2;  // row stride and per-q stride of the table in use
-    if (w_in_smem) {
+    float2 *sw2 = reinterpret_cast<float2 *>(sw);
+    if (w_in_smem) {  // pairs (W[k], W[k + 1]), W[B] = 0: two 8-byte reads give a cell's four weights
         for (int c = threadIdx.x; c < NQ * B2; c += blockDim.x) {
-            const int qq = c / B2, cc = c % B2;
-            sw[qq * B * SB + (cc / B) * SB + cc % B] = W[c];
+            const int qq = c / B2, cc = c % B2, k = cc % B;
+            const float nxt = k + 1 < B ? W[c + 1] : 0.0f;
+            sw2[qq * B * SB + (cc / B) * SB + k] = make_float2(W[c], nxt);
         }
-        W = sw;
         RS = SB;
         QS = B * SB;
     }
@@ -590,8 +591,15 @@ __global__ void __launch_bounds__(256, 2)
                     const int i3 = k0 + 2 < B ? cb + 3 : cb;  // in range; weight 0 when clamped
 #pragma unroll
                     for (int q = 0; q < NQ; ++q) {
-                        const float *Wq = W + (size_t)q * QS;
-                        const float sv = Wq[cb] * d[0] + Wq[cb + 1] * d[1] + Wq[cb + 2] * d[2] + Wq[i3] * d[3];
+                        float sv;
+                        if (w_in_smem) {
+                            const float2 *Wq = sw2 + (size_t)q * QS;
+                            const float2 a = Wq[cb], b = Wq[cb + 2];
+                            sv = a.x * d[0] + a.y * d[1] + b.x * d[2] + b.y * d[3];
+                        } else {
+                            const float *Wq = W + (size_t)q * QS;
+                            sv = Wq[cb] * d[0] + Wq[cb + 1] * d[1] + Wq[cb + 2] * d[2] + Wq[i3] * d[3];
+                        }
                         const float sx = sv * g3.gx, sy = sv * g3.gy, sz = sv * g3.gz;
                         S1[q][0] = fmaf(sx, ic, S1[q][0]);
                         S0[q][0] += sx;
@@ -750,8 +758,8 @@ cudaError_t launch_parzen_adjoint(const ParzenPair &P, const ParzenAffine *d_aff
     dim3 grid(ctas, n);
     for (int q0 = 0; q0 < nq; q0 += 4) {
         const int g = nq - q0 < 4 ? nq - q0 : 4;
-        const size_t wbytes = (size_t)g * P.B * parzen_stride(P.B) * sizeof(float);
-        const int in_smem = wbytes <= 96 * 1024;
+        const size_t wbytes = (size_t)g * P.B * parzen_stride(P.B) * sizeof(float2);
+        const int in_smem = wbytes <= 110 * 1024;
         const size_t smem = in_smem ? wbytes : 0;
 #define MI_ADJ(NQV)                                                                                         \
     do {                                                                                                    \

@@ -232,30 +232,21 @@ constexpr int kParzenRowsPerStep = 1;  // rows a warp of the forward works on at
 // Row stride of the shared tables: the least SB >= B + 1 with SB = kParzenBankSkew (mod 32).
 __host__ __device__ inline int parzen_stride(int B) { return B + 1 + ((kParzenBankSkew - (B + 1)) % 32 + 32) % 32; }
 
-// Shared words of one histogram copy: low-half sums [B x SB], then high-half sums, rounded up to
-// whole bank rows plus 32 / ncopy words, so that copy c starts c * 32 / ncopy banks further on.
-__host__ __device__ inline int parzen_copy_words(int B, int SB, int ncopy) {
-    return ((2 * B * SB + 31) / 32) * 32 + 32 / ncopy;
-}
-
-template <int RPW, int NCOPY>
+template <int RPW>
 __global__ void __launch_bounds__(256)
     k_parzen_hist(ParzenPair P, const ParzenAffine *__restrict__ aff, int rows_per_cta, int SB,
                   unsigned long long *__restrict__ ghist, unsigned long long *__restrict__ gcount) {
-    // NCOPY copies of the low-half sums [B x SB] and the high-half sums.  The row stride SB >= B + 1
-    // is 7 mod 32, so the bank of cell (fixed bin b, moving bin k) is (k + 7 b) mod 32: the cells of
-    // neighbouring voxels, which differ by a bin or two on either axis, fall in different banks.
-    // Lane l adds to copy l mod NCOPY; the copies are shifted by 32 / NCOPY banks, so neighbouring
-    // lanes adding to the same cell (the common case) use different banks.  Column B absorbs the
+    // Low-half sums [B x SB], then high-half sums.  The row stride SB >= B + 1 is 7 mod 32, so the
+    // bank of cell (fixed bin b, moving bin k) is (k + 7 b) mod 32: the cells of neighbouring voxels,
+    // which differ by a bin or two on either axis, fall in different banks.  Column B absorbs the
     // zero weight of bin B (m~ = B - 2 exactly).
     extern __shared__ uint32_t sh32[];
     const int t = blockIdx.y, B = P.B, B2 = B * B, NP = B * SB;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int CS = parzen_copy_words(B, SB, NCOPY);
-    uint32_t *lo16 = sh32 + (size_t)(lane % NCOPY) * CS, *hi16 = lo16 + NP;
+    uint32_t *lo16 = sh32, *hi16 = sh32 + NP;
     __shared__ long long A[12];
     if (threadIdx.x < 12) A[threadIdx.x] = aff[t].A[threadIdx.x];
-    for (int c = threadIdx.x; c < NCOPY * CS; c += blockDim.x) sh32[c] = 0u;
+    for (int c = threadIdx.x; c < 2 * NP; c += blockDim.x) sh32[c] = 0u;
     __syncthreads();
     const int nf0 = P.nf[0], nf1 = P.nf[1];
     const int n0 = P.nm[0], n1 = P.nm[1], n2 = P.nm[2];
@@ -326,10 +317,7 @@ __global__ void __launch_bounds__(256)
     unsigned long long *gh = ghist + (size_t)t * B2;
     for (int c = threadIdx.x; c < B2; c += blockDim.x) {
         const int cp = (c / B) * SB + c % B;
-        unsigned long long v = 0;
-#pragma unroll
-        for (int k = 0; k < NCOPY; ++k)
-            v += (unsigned long long)sh32[(size_t)k * CS + cp] + ((unsigned long long)sh32[(size_t)k * CS + NP + cp] << 16);
+        const unsigned long long v = (unsigned long long)lo16[cp] + ((unsigned long long)hi16[cp] << 16);
         if (v) atomicAdd(gh + c, v);
     }
     if (lane == 0 && cnt) atomicAdd(gcount + t, (unsigned long long)cnt);
@@ -717,11 +705,8 @@ cudaError_t launch_parzen_hist(const ParzenPair &P, const ParzenAffine *d_aff, i
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(d_count, 0, (size_t)n * sizeof(unsigned long long), s)) != cudaSuccess) return e;
     const int SB = parzen_stride(P.B);
-    // two copies while they fit 100 KB (three CTAs per SM), else one
-    const int ncopy = (size_t)2 * parzen_copy_words(P.B, SB, 2) * 4 <= 100 * 1024 ? 2 : 1;
-    const size_t smem = (size_t)ncopy * parzen_copy_words(P.B, SB, ncopy) * sizeof(uint32_t);
-    const void *fn = ncopy == 2 ? (const void *)k_parzen_hist<kParzenRowsPerStep, 2>
-                                : (const void *)k_parzen_hist<kParzenRowsPerStep, 1>;
+    const size_t smem = 2 * (size_t)P.B * SB * sizeof(uint32_t);
+    const void *fn = (const void *)k_parzen_hist<kParzenRowsPerStep>;
     if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
     // rows per CTA: at most kParzenMaxVox voxels (the 16-bit halves cannot overflow), and about

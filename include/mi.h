@@ -143,19 +143,19 @@ typedef struct {
     int block_threads; /* hard-path CTA size: 0 (default) = autotuned, or 512 / 1024 */
     int rotation;      /* MI_ROT_EULER_DEG (default) or MI_ROT_VERSOR               */
     int scale;         /* MI_SCALE_FACTOR (default) or MI_SCALE_OFFSET              */
-    float sample_fraction;    /* hard path: 0 (default) = every fixed voxel; in (0, 1) =
-                                 a random subset of that fraction (see below)          */
+    float sample_fraction;    /* 0 (default) = every fixed voxel; in (0, 1) = a random
+                                 subset of that fraction (see below)                   */
     unsigned int sample_seed; /* seed of that subset                                    */
 } mi_options;
 
-/* Random voxel sampling (mi_options.sample_fraction in (0, 1), hard path
- * only; the Discussion's comparison with ITK Mattes, which samples the image
- * at random, against MICUDA's every-voxel histogram).  A fixed voxel with
+/* Random voxel sampling (mi_options.sample_fraction in (0, 1), hard and
+ * Parzen forms; the Discussion's comparison with ITK Mattes, which samples the
+ * image at random, against MICUDA's every-voxel histogram).  A fixed voxel with
  * linear index x takes part iff fmix32(x ^ fmix32(seed)) < floor(fraction *
  * 2^32), fmix32 being the 32-bit finalizer of MurmurHash3.  The subset is
  * fixed when the context is created, so the metric stays a deterministic
  * function of the transform, and only the sampled voxels are visited.
- * Requires nx <= 65536 (MI_EUNSUPPORTED otherwise, and with MI_PARZEN). */
+ * Requires nx <= 65536 (MI_EUNSUPPORTED otherwise). */
 
 typedef struct mi_ctx mi_ctx;
 

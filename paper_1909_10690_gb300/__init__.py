@@ -141,8 +141,8 @@ class Context:
     rotation: "euler" (rx, ry, rz in degrees, default) or "versor" (the unit-ball
     parameterisation of the paper's rotation maps); scale: "factor" (1 =
     identity, default) or "offset" (zero-centred, sigma = 1 + s).
-    sample_fraction in (0, 1): the hard-path metric over a random subset of the
-    fixed voxels of that fraction, fixed by sample_seed (0: every voxel).
+    sample_fraction in (0, 1): the metric (hard or Parzen) over a random subset
+    of the fixed voxels of that fraction, fixed by sample_seed (0: every voxel).
     """
 
     def __init__(self, fixed=None, moving=None, bins=64, fixed_spacing=(1.0, 1.0, 1.0),

@@ -395,6 +395,37 @@ mi_status upload_volume(mi_ctx *ctx, const mi_volume *v, DevBuf &dst) {
     return MI_OK;
 }
 
+// Random sampling (mi_options.sample_fraction in (0, 1)): per fixed row, the x indices and fixed
+// bins (fb: the hard or the Parzen bins) of its sampled voxels, as row offsets + lists.
+mi_status build_samples(mi_ctx *ctx, Pair &P, const uint8_t *fb, cudaStream_t s) {
+    const double frac = (double)ctx->opt.sample_fraction;
+    if (!(frac > 0.0 && frac < 1.0)) return MI_OK;
+    if (P.nf[0] > 65536) return ctx->fail(MI_EUNSUPPORTED, "random sampling needs fixed rows of at most 65536 voxels");
+    const uint32_t thr = (uint32_t)floor(frac * 4294967296.0);
+    const long long R = (long long)P.nf[1] * P.nf[2];
+    DevBuf dcnt;
+    MI_CU(dcnt.ensure((size_t)R * 4), "allocating sample counts");
+    MI_CU(launch_sample_count(P.nf[0], R, ctx->opt.sample_seed, thr, dcnt.as<uint32_t>(), s), "sample counts");
+    std::vector<uint32_t> cnt((size_t)R), ptr((size_t)R + 1);
+    MI_CU(cudaMemcpyAsync(cnt.data(), dcnt.p, (size_t)R * 4, cudaMemcpyDeviceToHost, s), "sample counts D2H");
+    MI_CU(cudaStreamSynchronize(s), "sample counts");
+    unsigned long long acc = 0;
+    for (long long r = 0; r < R; ++r) {
+        ptr[(size_t)r] = (uint32_t)acc;
+        acc += cnt[(size_t)r];
+    }
+    ptr[(size_t)R] = (uint32_t)acc;
+    MI_CU(P.srow.ensure(((size_t)R + 1) * 4), "allocating sample rows");
+    MI_CU(P.scol.ensure(std::max<size_t>((size_t)acc * 2, 2)), "allocating sample columns");
+    MI_CU(P.sbin.ensure(std::max<size_t>((size_t)acc, 1)), "allocating sample bins");
+    MI_CU(cudaMemcpyAsync(P.srow.p, ptr.data(), ((size_t)R + 1) * 4, cudaMemcpyHostToDevice, s), "sample rows");
+    MI_CU(launch_sample_fill(P.nf[0], R, ctx->opt.sample_seed, thr, fb, P.srow.as<uint32_t>(), P.scol.as<uint16_t>(),
+                             P.sbin.as<uint8_t>(), s),
+          "sample lists");
+    MI_CU(cudaStreamSynchronize(s), "sample lists");
+    return MI_OK;
+}
+
 mi_status add_pair(mi_ctx *ctx, const mi_volume *fx, const mi_volume *mv, int bins) {
     std::string e;
     const bool parzen = ctx->opt.kernel == MI_PARZEN;
@@ -436,6 +467,7 @@ mi_status add_pair(mi_ctx *ctx, const mi_volume *fx, const mi_volume *mv, int bi
         MI_CU(P->pmovx.ensure((size_t)(P->nm[0] + 1) * (P->nm[1] + 1) * (P->nm[2] + 1) * 4),
               "allocating the extended moving volume");
         MI_CU(launch_parzen_extend(P->pmov.as<float>(), P->nm, P->pmovx.as<float>(), s), "extending the moving volume");
+        if ((st = build_samples(ctx, *P, P->pfbins.as<uint8_t>(), s)) != MI_OK) return st;
         {
             const cudaExtent ext = make_cudaExtent(P->nm[0], P->nm[1], P->nm[2] + 1);
             DevBuf quads;
@@ -505,34 +537,7 @@ mi_status add_pair(mi_ctx *ctx, const mi_volume *fx, const mi_volume *mv, int bi
             MI_CU(cudaMemcpyAsync(P->rowinfo.p, info.data(), (size_t)bins * 4, cudaMemcpyHostToDevice, s), "row table");
             MI_CU(cudaStreamSynchronize(s), "row table");
         }
-        // random sampling: per fixed row, the x indices and bins of its sampled voxels (CSR)
-        const double frac = (double)ctx->opt.sample_fraction;
-        if (frac > 0.0 && frac < 1.0) {
-            if (P->nf[0] > 65536)
-                return ctx->fail(MI_EUNSUPPORTED, "random sampling needs fixed rows of at most 65536 voxels");
-            const uint32_t thr = (uint32_t)floor(frac * 4294967296.0);
-            const long long R = (long long)P->nf[1] * P->nf[2];
-            DevBuf dcnt;
-            MI_CU(dcnt.ensure((size_t)R * 4), "allocating sample counts");
-            MI_CU(launch_sample_count(P->nf[0], R, ctx->opt.sample_seed, thr, dcnt.as<uint32_t>(), s), "sample counts");
-            std::vector<uint32_t> cnt((size_t)R), ptr((size_t)R + 1);
-            MI_CU(cudaMemcpyAsync(cnt.data(), dcnt.p, (size_t)R * 4, cudaMemcpyDeviceToHost, s), "sample counts D2H");
-            MI_CU(cudaStreamSynchronize(s), "sample counts");
-            unsigned long long acc = 0;
-            for (long long r = 0; r < R; ++r) {
-                ptr[(size_t)r] = (uint32_t)acc;
-                acc += cnt[(size_t)r];
-            }
-            ptr[(size_t)R] = (uint32_t)acc;
-            MI_CU(P->srow.ensure(((size_t)R + 1) * 4), "allocating sample rows");
-            MI_CU(P->scol.ensure(std::max<size_t>((size_t)acc * 2, 2)), "allocating sample columns");
-            MI_CU(P->sbin.ensure(std::max<size_t>((size_t)acc, 1)), "allocating sample bins");
-            MI_CU(cudaMemcpyAsync(P->srow.p, ptr.data(), ((size_t)R + 1) * 4, cudaMemcpyHostToDevice, s), "sample rows");
-            MI_CU(launch_sample_fill(P->nf[0], R, ctx->opt.sample_seed, thr, P->fbins.as<uint8_t>(), P->srow.as<uint32_t>(),
-                                     P->scol.as<uint16_t>(), P->sbin.as<uint8_t>(), s),
-                  "sample lists");
-            MI_CU(cudaStreamSynchronize(s), "sample lists");
-        }
+        if ((st = build_samples(ctx, *P, P->fbins.as<uint8_t>(), s)) != MI_OK) return st;
         if (mv->dtype == MI_F32) {
             MI_CU(P->mov.ensure((size_t)P->nvm * 2), "allocating the moving volume");
             MI_CU(launch_f32_to_u16(rawm.as<float>(), P->nvm, P->mov.as<uint16_t>(), s), "converting the moving volume");
@@ -678,10 +683,6 @@ mi_status create_common(mi_ctx **out, const mi_volume *fixed, const mi_volume *m
     if (!(ctx->opt.sample_fraction >= 0.0f && ctx->opt.sample_fraction <= 1.0f)) {
         g_create_error = "opt.sample_fraction must lie in [0, 1]";
         return MI_EINVAL;
-    }
-    if (ctx->opt.sample_fraction > 0.0f && ctx->opt.sample_fraction < 1.0f && ctx->opt.kernel == MI_PARZEN) {
-        g_create_error = "random sampling is a hard-path option";
-        return MI_EUNSUPPORTED;
     }
     if ((ctx->opt.rotation != MI_ROT_EULER_DEG && ctx->opt.rotation != MI_ROT_VERSOR) ||
         (ctx->opt.scale != MI_SCALE_FACTOR && ctx->opt.scale != MI_SCALE_OFFSET)) {
@@ -1160,6 +1161,9 @@ mi_status parzen_core(mi_ctx *ctx, const std::vector<float> &prm, int n, const f
     pp.mov = P.pmov.as<float>();
     pp.movx = P.pmovx.as<float>();
     pp.texq = P.ptex;
+    pp.srow = P.srow.p ? P.srow.as<uint32_t>() : nullptr;
+    pp.scol = P.scol.as<uint16_t>();
+    pp.sbin = P.sbin.as<uint8_t>();
     for (int a = 0; a < 3; ++a) {
         pp.nf[a] = P.nf[a];
         pp.nm[a] = P.nm[a];

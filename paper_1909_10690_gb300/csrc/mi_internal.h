@@ -116,6 +116,9 @@ struct ParzenPair {
     const float *mov;       // normalised moving intensities in [0, 1]
     const float *movx;      // the same extended by one plane per axis, dims (n0 + 1, n1 + 1, n2 + 1)
     unsigned long long texq;  // 2 x 2 (x, y) quads of movx as a float4 3D texture, dims (n0, n1, n2 + 1)
+    const uint32_t *srow;   // random sampling (else null): row r's sampled voxels are entries srow[r]..srow[r+1]-1
+    const uint16_t *scol;   //   of scol (their x index, ascending)
+    const uint8_t *sbin;    //   and sbin (their Parzen fixed bin)
     int nf[3];
     int nm[3];
     int B;

@@ -232,7 +232,7 @@ constexpr int kParzenRowsPerStep = 1;  // rows a warp of the forward works on at
 // Row stride of the shared tables: the least SB >= B + 1 with SB = kParzenBankSkew (mod 32).
 __host__ __device__ inline int parzen_stride(int B) { return B + 1 + ((kParzenBankSkew - (B + 1)) % 32 + 32) % 32; }
 
-template <int RPW>
+template <int RPW, bool SAMPLED>
 __global__ void __launch_bounds__(256)
     k_parzen_hist(ParzenPair P, const ParzenAffine *__restrict__ aff, int rows_per_cta, int SB,
                   unsigned long long *__restrict__ ghist, unsigned long long *__restrict__ gcount) {
@@ -260,7 +260,31 @@ __global__ void __launch_bounds__(256)
     constexpr int G = 32 / RPW;
     const int sub = lane / G, pos = lane % G;
     const long long DG0 = G * A[0], DG1 = G * A[4], DG2 = G * A[8];
-    unsigned int cnt = 0;  // overlap voxels counted by this lane (one lane per row)
+    unsigned int cnt = 0;  // overlap voxels counted by this lane
+    // one voxel at 32.32 index U with fixed bin bf: its four quantised B-spline weights
+    auto add_voxel = [&](long long U0, long long U1, long long U2, int bf) {
+        const MG g3 = kParzenFwdTex ? trilinear_q<false>(P.texq, U0, U1, U2)
+                                    : trilinear_x<false>(P.movx, P.nm[0] + 1, (size_t)(P.nm[0] + 1) * (P.nm[1] + 1),
+                                                         U0, U1, U2);
+        const float mt = fmaf(fminf(fmaxf(g3.m, 0.0f), 1.0f), Bm4, 2.0f);
+        const int k0 = (int)mt;
+        float w[4];
+        bspline_w(mt - (float)k0, w);
+        // every quantised weight is below 2^32 (at most (2/3) 2^32)
+        const uint32_t q0 = __float2uint_rn(w[0] * 4294967296.0f);
+        const uint32_t q2 = __float2uint_rn(w[2] * 4294967296.0f);
+        const uint32_t q3 = __float2uint_rn(w[3] * 4294967296.0f);
+        const uint32_t q1 = 0u - q0 - q2 - q3;  // 2^32 - (q0 + q2 + q3)
+        const int c = bf * SB + (k0 - 1);
+        atomicAdd(lo16 + c, q0 & 0xffffu);
+        atomicAdd(hi16 + c, q0 >> 16);
+        atomicAdd(lo16 + c + 1, q1 & 0xffffu);
+        atomicAdd(hi16 + c + 1, q1 >> 16);
+        atomicAdd(lo16 + c + 2, q2 & 0xffffu);
+        atomicAdd(hi16 + c + 2, q2 >> 16);
+        atomicAdd(lo16 + c + 3, q3 & 0xffffu);
+        atomicAdd(hi16 + c + 3, q3 >> 16);
+    };
     // warp w takes rows r0 + w + nwarps n; a group of 32 of them is clipped at once (lane l: row l)
     for (long long g = r0 + warp; g < r1; g += 32LL * nwarps) {
         Clip64 mine;
@@ -269,6 +293,27 @@ __global__ void __launch_bounds__(256)
         mine.u0 = mine.u1 = mine.u2 = 0;
         const long long rl = g + (long long)nwarps * lane;
         if (rl < r1) mine = clip_row64(A, rl % nf1, rl / nf1, nf0, n0, n1, n2);
+        if constexpr (SAMPLED) {  // random sampling: each row's sampled voxels inside its interval
+            for (int s = 0; s < 32; ++s) {
+                const long long r = g + (long long)nwarps * s;
+                if (r >= r1) break;  // warp-uniform
+                const int lo = __shfl_sync(kFull, mine.lo, s), hi = __shfl_sync(kFull, mine.hi, s);
+                if (lo > hi) continue;
+                const long long ub0 = __shfl_sync(kFull, mine.u0, s), ub1 = __shfl_sync(kFull, mine.u1, s),
+                                ub2 = __shfl_sync(kFull, mine.u2, s);
+                const uint32_t e0 = __ldg(P.srow + r), e1 = __ldg(P.srow + r + 1);
+                for (uint32_t eb = e0; eb < e1; eb += 32) {
+                    const uint32_t e = eb + lane;
+                    const int i = e < e1 ? (int)__ldg(P.scol + e) : -1;
+                    if (e < e1 && i >= lo && i <= hi) {
+                        const long long d = i - lo;
+                        add_voxel(ub0 + A[0] * d, ub1 + A[4] * d, ub2 + A[8] * d, (int)__ldg(P.sbin + e));
+                        ++cnt;
+                    }
+                }
+            }
+            continue;
+        }
         for (int s = 0; s < 32; s += RPW) {
             if (g + (long long)nwarps * s >= r1) break;  // warp-uniform: the rest of the group is past r1
             const int src = s + sub;
@@ -284,28 +329,7 @@ __global__ void __launch_bounds__(256)
             const uint8_t *__restrict__ frow = P.fbins + (size_t)(r < r1 ? r : r0) * nf0;
             for (int k = 0; k < nsteps; ++k) {
                 const int i = lo + k * G + pos;
-                if (i <= hi) {
-                    const MG g3 = kParzenFwdTex ? trilinear_q<false>(P.texq, U0, U1, U2)
-                                                : trilinear_x<false>(P.movx, P.nm[0] + 1, (size_t)(P.nm[0] + 1) * (P.nm[1] + 1), U0, U1, U2);
-                    const float mt = fmaf(fminf(fmaxf(g3.m, 0.0f), 1.0f), Bm4, 2.0f);
-                    const int k0 = (int)mt;
-                    float w[4];
-                    bspline_w(mt - (float)k0, w);
-                    // every quantised weight is below 2^32 (at most (2/3) 2^32)
-                    const uint32_t q0 = __float2uint_rn(w[0] * 4294967296.0f);
-                    const uint32_t q2 = __float2uint_rn(w[2] * 4294967296.0f);
-                    const uint32_t q3 = __float2uint_rn(w[3] * 4294967296.0f);
-                    const uint32_t q1 = 0u - q0 - q2 - q3;  // 2^32 - (q0 + q2 + q3)
-                    const int c = (int)__ldg(frow + i) * SB + (k0 - 1);
-                    atomicAdd(lo16 + c, q0 & 0xffffu);
-                    atomicAdd(hi16 + c, q0 >> 16);
-                    atomicAdd(lo16 + c + 1, q1 & 0xffffu);
-                    atomicAdd(hi16 + c + 1, q1 >> 16);
-                    atomicAdd(lo16 + c + 2, q2 & 0xffffu);
-                    atomicAdd(hi16 + c + 2, q2 >> 16);
-                    atomicAdd(lo16 + c + 3, q3 & 0xffffu);
-                    atomicAdd(hi16 + c + 3, q3 >> 16);
-                }
+                if (i <= hi) add_voxel(U0, U1, U2, (int)__ldg(frow + i));
                 U0 += DG0;
                 U1 += DG1;
                 U2 += DG2;
@@ -499,7 +523,7 @@ __global__ void k_parzen_final(int n, const unsigned long long *__restrict__ gco
 // Adjoint: moments M[q][a][c] = sum_x s_q(x) d_a m(u_x) x_c, x = (i - ci, j - cj, k - ck, 1)
 // ---------------------------------------------------------------------------
 
-template <int NQ>
+template <int NQ, bool SAMPLED>
 __global__ void __launch_bounds__(256, 2)
     k_parzen_adj(ParzenPair P, const ParzenAffine *__restrict__ aff, int nq_total, int q0,
                  const float *__restrict__ wtab, int w_in_smem, double *__restrict__ mom) {
@@ -564,42 +588,58 @@ __global__ void __launch_bounds__(256, 2)
             for (int q = 0; q < NQ; ++q)
 #pragma unroll
                 for (int a = 0; a < 3; ++a) S0[q][a] = S1[q][a] = 0.0f;
-            for (int base = lo; base <= hi; base += 32) {
-                const int i = base + lane;
-                if (i <= hi) {
-                    const MG g3 = kParzenAdjTex ? trilinear_q<true>(P.texq, U0, U1, U2)
-                                                : trilinear_x<true>(P.movx, P.nm[0] + 1, (size_t)(P.nm[0] + 1) * (P.nm[1] + 1), U0, U1, U2);
-                    const float ic = (float)i - ci;
-                    const float mt = fmaf(fminf(fmaxf(g3.m, 0.0f), 1.0f), Bm4, 2.0f);
-                    const int k0 = (int)mt;
-                    float d[4];
-                    bspline_dw(mt - (float)k0, d);
-                    if (k0 + 2 >= B) d[3] = 0.0f;
-                    const int cb = (int)__ldg(frow + i) * RS + (k0 - 1);
-                    const int i3 = k0 + 2 < B ? cb + 3 : cb;  // in range; weight 0 when clamped
+            // one voxel (x index i, fixed bin bf) at 32.32 index U: its share of S0 and S1
+            auto acc_voxel = [&](long long V0, long long V1, long long V2, int i, int bf) {
+                const MG g3 = kParzenAdjTex ? trilinear_q<true>(P.texq, V0, V1, V2)
+                                            : trilinear_x<true>(P.movx, P.nm[0] + 1,
+                                                                (size_t)(P.nm[0] + 1) * (P.nm[1] + 1), V0, V1, V2);
+                const float ic = (float)i - ci;
+                const float mt = fmaf(fminf(fmaxf(g3.m, 0.0f), 1.0f), Bm4, 2.0f);
+                const int k0 = (int)mt;
+                float d[4];
+                bspline_dw(mt - (float)k0, d);
+                if (k0 + 2 >= B) d[3] = 0.0f;
+                const int cb = bf * RS + (k0 - 1);
+                const int i3 = k0 + 2 < B ? cb + 3 : cb;  // in range; weight 0 when clamped
 #pragma unroll
-                    for (int q = 0; q < NQ; ++q) {
-                        float sv;
-                        if (w_in_smem) {
-                            const float2 *Wq = sw2 + (size_t)q * QS;
-                            const float2 a = Wq[cb], b = Wq[cb + 2];
-                            sv = a.x * d[0] + a.y * d[1] + b.x * d[2] + b.y * d[3];
-                        } else {
-                            const float *Wq = W + (size_t)q * QS;
-                            sv = Wq[cb] * d[0] + Wq[cb + 1] * d[1] + Wq[cb + 2] * d[2] + Wq[i3] * d[3];
-                        }
-                        const float sx = sv * g3.gx, sy = sv * g3.gy, sz = sv * g3.gz;
-                        S1[q][0] = fmaf(sx, ic, S1[q][0]);
-                        S0[q][0] += sx;
-                        S1[q][1] = fmaf(sy, ic, S1[q][1]);
-                        S0[q][1] += sy;
-                        S1[q][2] = fmaf(sz, ic, S1[q][2]);
-                        S0[q][2] += sz;
+                for (int q = 0; q < NQ; ++q) {
+                    float sv;
+                    if (w_in_smem) {
+                        const float2 *Wq = sw2 + (size_t)q * QS;
+                        const float2 a = Wq[cb], b = Wq[cb + 2];
+                        sv = a.x * d[0] + a.y * d[1] + b.x * d[2] + b.y * d[3];
+                    } else {
+                        const float *Wq = W + (size_t)q * QS;
+                        sv = Wq[cb] * d[0] + Wq[cb + 1] * d[1] + Wq[cb + 2] * d[2] + Wq[i3] * d[3];
+                    }
+                    const float sx = sv * g3.gx, sy = sv * g3.gy, sz = sv * g3.gz;
+                    S1[q][0] = fmaf(sx, ic, S1[q][0]);
+                    S0[q][0] += sx;
+                    S1[q][1] = fmaf(sy, ic, S1[q][1]);
+                    S0[q][1] += sy;
+                    S1[q][2] = fmaf(sz, ic, S1[q][2]);
+                    S0[q][2] += sz;
+                }
+            };
+            if constexpr (SAMPLED) {  // random sampling: the row's sampled voxels inside [lo, hi]
+                const long long ub0 = U0 - A[0] * lane, ub1 = U1 - A[4] * lane, ub2 = U2 - A[8] * lane;
+                const uint32_t e0 = __ldg(P.srow + r), e1 = __ldg(P.srow + r + 1);
+                for (uint32_t eb = e0; eb < e1; eb += 32) {
+                    const uint32_t e = eb + lane;
+                    const int i = e < e1 ? (int)__ldg(P.scol + e) : -1;
+                    if (e < e1 && i >= lo && i <= hi) {
+                        const long long dd = i - lo;
+                        acc_voxel(ub0 + A[0] * dd, ub1 + A[4] * dd, ub2 + A[8] * dd, i, (int)__ldg(P.sbin + e));
                     }
                 }
-                U0 += D0;
-                U1 += D1;
-                U2 += D2;
+            } else {
+                for (int base = lo; base <= hi; base += 32) {
+                    const int i = base + lane;
+                    if (i <= hi) acc_voxel(U0, U1, U2, i, (int)__ldg(frow + i));
+                    U0 += D0;
+                    U1 += D1;
+                    U2 += D2;
+                }
             }
 #pragma unroll
             for (int q = 0; q < NQ; ++q)
@@ -706,7 +746,8 @@ cudaError_t launch_parzen_hist(const ParzenPair &P, const ParzenAffine *d_aff, i
     if ((e = cudaMemsetAsync(d_count, 0, (size_t)n * sizeof(unsigned long long), s)) != cudaSuccess) return e;
     const int SB = parzen_stride(P.B);
     const size_t smem = 2 * (size_t)P.B * SB * sizeof(uint32_t);
-    const void *fn = (const void *)k_parzen_hist<kParzenRowsPerStep>;
+    const void *fn = P.srow ? (const void *)k_parzen_hist<kParzenRowsPerStep, true>
+                            : (const void *)k_parzen_hist<kParzenRowsPerStep, false>;
     if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
     // rows per CTA: at most kParzenMaxVox voxels (the 16-bit halves cannot overflow), and about
@@ -746,12 +787,19 @@ cudaError_t launch_parzen_adjoint(const ParzenPair &P, const ParzenAffine *d_aff
         const size_t wbytes = (size_t)g * P.B * parzen_stride(P.B) * sizeof(float2);
         const int in_smem = wbytes <= 110 * 1024;
         const size_t smem = in_smem ? wbytes : 0;
-#define MI_ADJ(NQV)                                                                                         \
+#define MI_ADJ_S(NQV, SV)                                                                                   \
     do {                                                                                                    \
-        if ((e = cudaFuncSetAttribute(k_parzen_adj<NQV>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+        if ((e = cudaFuncSetAttribute(k_parzen_adj<NQV, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                                       (int)smem)) != cudaSuccess)                                           \
             return e;                                                                                       \
-        k_parzen_adj<NQV><<<grid, 256, smem, s>>>(P, d_aff, nq, q0, d_w, in_smem, d_mom);                   \
+        k_parzen_adj<NQV, SV><<<grid, 256, smem, s>>>(P, d_aff, nq, q0, d_w, in_smem, d_mom);               \
+    } while (0)
+#define MI_ADJ(NQV)                 \
+    do {                            \
+        if (P.srow)                 \
+            MI_ADJ_S(NQV, true);    \
+        else                        \
+            MI_ADJ_S(NQV, false);   \
     } while (0)
         switch (g) {
             case 1: MI_ADJ(1); break;
@@ -760,6 +808,7 @@ cudaError_t launch_parzen_adjoint(const ParzenPair &P, const ParzenAffine *d_aff
             default: MI_ADJ(4); break;
         }
 #undef MI_ADJ
+#undef MI_ADJ_S
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     k_parzen_grad<<<(n * nq * 9 + 127) / 128, 128, 0, s>>>(n, nq, P.B, ctas, d_count, d_mom, d_jac, d_grad);

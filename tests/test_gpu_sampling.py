@@ -48,10 +48,24 @@ def test_sampled_mi_counts_and_seeds(cuda_lib):
     assert not np.array_equal(counts[(0.5, 1)], counts[(0.5, 2)])
 
 
-def test_sampling_is_a_hard_path_option(cuda_lib):
-    f, m = phantoms.head_pair(shape=(16, 18, 20), spacing=(1, 1, 1), seed=84, dtype=np.float32)
-    with pytest.raises(cuda_lib.MIError):
-        cuda_lib.Context(f, m, bins=16, kernel="parzen", sample_fraction=0.5)
+def test_sampled_parzen_mi_and_gradient(cuda_lib):
+    # the Mattes-like combination: a Parzen soft histogram over a random voxel subset; the oracle's
+    # voxel set is the mask (sampled and inside the overlap)
+    f, m = phantoms.head_pair(shape=(30, 34, 38), spacing=(1, 1, 1), seed=87, dtype=np.float32)
+    B, frac, seed, qs = 32, 0.35, 21, [1.0, 1.3]
+    ctx = cuda_lib.Context(f, m, bins=B, kernel="parzen", sample_fraction=frac, sample_seed=seed)
+    thr = oracle.sample_threshold(frac)
+    keep = np.array([oracle.sampled(x, seed, thr) for x in range(f.size)], np.uint8).reshape(f.shape)
+    prm = phantoms.random_transforms(3, seed=88, t_mm=4, r_deg=8, s_range=(0.95, 1.05))
+    mi, g = ctx.grad(prm, qs)
+    for t in range(len(prm)):
+        aff, J = oracle.affine(prm[t], f.shape, (1, 1, 1), m.shape, (1, 1, 1), with_jacobian=True)
+        mask = keep & oracle.overlap_mask(f.shape, m.shape, aff)
+        mi_o, g_o, n = oracle.parzen(f, m, aff, B, qs, daff=J, mask=mask)
+        assert n == int(mask.sum()) and 0.25 * f.size < n < 0.45 * f.size
+        assert np.all(np.abs(mi[t] - mi_o) <= 1e-6 * np.maximum(np.abs(mi_o), 1.0)), (t, mi[t], mi_o)
+        for iq in range(len(qs)):
+            assert np.abs(g[t, iq] - g_o[iq]).max() <= 1e-4 * np.abs(g_o[iq]).max(), (t, iq)
     with pytest.raises(cuda_lib.MIError):
         cuda_lib.Context(f, m, bins=16, sample_fraction=1.5)
 

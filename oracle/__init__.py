@@ -5,10 +5,11 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 FP64 entropies, exact integer fixed-point resampling) through ctypes and
 shares no code with the CUDA library.
 
-Each wrapper cites the passage of the paper it follows; the readings R1..R9
-(binning, transform convention, fixed point, integer trilinear, overlap-only
-counts, natural log, Tsallis forms, Parzen soft histogram and its adjoint)
-are stated in ``mi_oracle.c``.
+Each wrapper cites the passage of the paper it follows; the readings R1..R17
+(binning, transform conventions, fixed point, integer trilinear, overlap-only
+counts, natural log, Tsallis forms, Parzen soft histogram and its adjoint,
+unit-ball rotation, zero-centred scale, random sampling, general affine) are
+stated in ``mi_oracle.c``.
 """
 from __future__ import annotations
 
@@ -91,7 +92,9 @@ def _load():
             lib.orc_parzen_fixed_bin.restype = I
             lib.orc_parzen_fixed_bin.argtypes = [P, I, I, I64, I]
             lib.orc_parzen.restype = I
-            lib.orc_parzen.argtypes = [P, I, I, P, P, I, I, P, P, P, I, P, I, I, I, P, P, P, P, P]
+            lib.orc_parzen.argtypes = [P, I, I, P, P, I, I, P, P, P, I, I, P, I, I, I, P, P, P, P, P]
+            lib.orc_affine_matrix.restype = None
+            lib.orc_affine_matrix.argtypes = [P, P, P, P, P, P, P]
             lib.orc_overlap_mask.restype = None
             lib.orc_overlap_mask.argtypes = [P, P, P, P]
             _lib = lib
@@ -148,7 +151,7 @@ def bin_volume(vol: np.ndarray, bins: int, depth: int | None = None) -> np.ndarr
 
 
 def affine(params, fixed_shape, fixed_spacing, moving_shape, moving_spacing, with_jacobian=False,
-           rotation="euler", scale="factor"):
+           rotation="euler", scale="factor", transform="params"):
     """R2 (Fig. 1 Transform block; Introduction's translation/rotation/scale families).
 
     ``params`` = (tx, ty, tz mm, rx, ry, rz degrees, sx, sy, sz).  Shapes are
@@ -158,14 +161,26 @@ def affine(params, fixed_shape, fixed_spacing, moving_shape, moving_spacing, wit
     rotation="versor": the rotation parameters are the unit-ball versor of
     R14 (the Results' rotation maps); scale="offset": zero-centred scale
     parameters s, sigma = 1 + s (R15, the Results' scale maps).
+    transform="affine": ``params`` is the general affine [M | t] (12 values,
+    row-major; R17, the Methodology's 12 degrees of freedom) and the Jacobian
+    is 12 x 12; rotation and scale do not apply.
     """
     lib = _load()
-    prm = np.ascontiguousarray(params, dtype=np.float32).reshape(9)
     nf = np.array(fixed_shape[::-1], dtype=np.int32)
     nm = np.array(moving_shape[::-1], dtype=np.int32)
     sf = np.ascontiguousarray(fixed_spacing, dtype=np.float32)
     sm = np.ascontiguousarray(moving_spacing, dtype=np.float32)
     out = np.empty(12, dtype=np.float64)
+    if transform == "affine":
+        prm = np.ascontiguousarray(params, dtype=np.float32).reshape(12)
+        dout = np.empty(12 * 12, dtype=np.float64) if with_jacobian else None
+        lib.orc_affine_matrix(_p(prm), _p(nf), _p(sf), _p(nm), _p(sm), _p(out), _p(dout) if with_jacobian else None)
+        if with_jacobian:
+            return out.reshape(3, 4), dout.reshape(12, 12)
+        return out.reshape(3, 4)
+    if transform != "params":
+        raise ValueError("transform is 'params' or 'affine'")
+    prm = np.ascontiguousarray(params, dtype=np.float32).reshape(9)
     dout = np.empty(12 * 9, dtype=np.float64) if with_jacobian else None
     if rotation not in ("euler", "versor") or scale not in ("factor", "offset"):
         raise ValueError("rotation is 'euler' or 'versor', scale is 'factor' or 'offset'")
@@ -312,8 +327,9 @@ def parzen(fixed, moving, aff, B, q, daff=None, form=0, bits=False, mask=None, f
            want_hist=False):
     """R8/R9 Parzen MI (and gradient if ``daff`` is given) at one FP64 affine.
 
-    ``aff`` is the 3x4 [A | b]; ``daff`` the 12x9 Jacobian from :func:`affine`.
-    Returns (mi[nq], grad[nq, 9] or None, N[, P]).
+    ``aff`` is the 3x4 [A | b]; ``daff`` the 12 x npar Jacobian from
+    :func:`affine` (npar = 9 parameters, or 12 for the general affine).
+    Returns (mi[nq], grad[nq, npar] or None, N[, P]).
     """
     fx = np.ascontiguousarray(fixed)
     mv = np.ascontiguousarray(moving)
@@ -321,14 +337,15 @@ def parzen(fixed, moving, aff, B, q, daff=None, form=0, bits=False, mask=None, f
     qs = _q_as_double(q)
     nq = len(qs)
     mi = np.empty(nq, dtype=np.float64)
-    grad = np.empty((nq, 9), dtype=np.float64) if daff is not None else None
-    da = np.ascontiguousarray(daff, dtype=np.float64).reshape(108) if daff is not None else None
+    npar = int(np.asarray(daff).size // 12) if daff is not None else 9
+    grad = np.empty((nq, npar), dtype=np.float64) if daff is not None else None
+    da = np.ascontiguousarray(daff, dtype=np.float64).reshape(12 * npar) if daff is not None else None
     cnt = np.zeros(1, dtype=np.int64)
     ph = np.empty((B, B), dtype=np.float64) if want_hist else None
     mk = np.ascontiguousarray(mask, dtype=np.uint8) if mask is not None else None
     rc = _load().orc_parzen(_p(fx), _dtype_code(fx), _depth(fx, fixed_depth), _p(_dims(fx)), _p(mv), _dtype_code(mv),
                             _depth(mv, moving_depth), _p(_dims(mv)), _p(a), _p(da) if da is not None else None,
-                            int(B), _p(qs), nq, int(form), int(bool(bits)), _p(mk) if mk is not None else None,
+                            npar, int(B), _p(qs), nq, int(form), int(bool(bits)), _p(mk) if mk is not None else None,
                             _p(mi), _p(grad) if grad is not None else None, _p(cnt), _p(ph) if ph is not None else None)
     if rc != 0:
         raise RuntimeError(f"oracle parzen failed ({rc})")

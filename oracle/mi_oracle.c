@@ -1,7 +1,8 @@
 /*
  * mi_oracle.c -- plain, slow, obviously correct CPU reference for Shannon and
  * Tsallis mutual information between a fixed 3D volume and a moving volume
- * resampled under a 9-parameter transform (translation, rotation, scale).
+ * resampled under a 9-parameter transform (translation, rotation, scale) or
+ * a general 12-parameter affine.
  *
  * TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the
  * benchmark's CPU-baseline leg load this library.  The CUDA library shares no
@@ -16,13 +17,14 @@
  * and Eq. (3) (registration as argmax over T); it names Tsallis entropy and
  * the translation / rotation / scale families (Introduction) and a full,
  * all-voxel histogram (Discussion) but leaves the rest open.  The readings
- * used here are tagged R1..R16 where they are applied:
+ * used here are tagged R1..R17 where they are applied:
  *   R1 binning (v * bins) >> depth               R2 parameter -> affine
  *   R3 16.16 fixed-point coordinate, overlap     R4 integer trilinear
  *   R5 counts over the overlap only              R6 natural logarithm
  *   R7 Tsallis entropy and Tsallis MI forms      R8 Parzen soft histogram
  *   R9 Parzen gradient (adjoint of R8)           R14 unit-ball (versor) rotation
  *   R15 zero-centred scale parameters            R16 random voxel sampling
+ *   R17 general affine [M | t] (12 parameters)
  *
  * Every function here is pinned by tests that do not re-type its formula:
  * hand-enumerated 4x4x4 cases, exact permutations, closed forms, limits,
@@ -289,6 +291,43 @@ void orc_affine_mode(const float prm[9], const int nf[3], const float sf_in[3], 
             dout[9 * (4 * a + p) + 6 + p] = R[3 * a + p] * sf[p] / sm[a];
             dout[9 * (4 * a + 3) + 6 + p] = -R[3 * a + p] * cf[p] / sm[a];
         }
+}
+
+/* R17: the general affine of the Methodology's 12 degrees of freedom (the
+ * affine family of the Introduction: translation, rotation, scale and skew).
+ * prm = [M | t] row-major, M 3x3 and t in mm; the moving physical point is
+ * M (p - c_f) + c_m + t, the 9-parameter form's R diag(sigma) replaced by M.
+ * Index space: A = diag(1/s_m) M diag(s_f), b = diag(1/s_m) (c_m + t - M c_f),
+ * evaluated in the same order as orc_affine_mode.  dout (12 x 12) is
+ * d[A|b]/dprm, prm index 4a + c as in [M | t]. */
+void orc_affine_matrix(const float prm[12], const int nf[3], const float sf_in[3], const int nm[3],
+                       const float sm_in[3], double out[12], double *dout) {
+    double sf[3], sm[3], cf[3], cm[3];
+    for (int a = 0; a < 3; a++) {
+        sf[a] = (double)sf_in[a];
+        sm[a] = (double)sm_in[a];
+        cf[a] = sf[a] * ((double)(nf[a] - 1) * 0.5);
+        cm[a] = sm[a] * ((double)(nm[a] - 1) * 0.5);
+    }
+    for (int a = 0; a < 3; a++) {
+        double s = 0.0;
+        for (int c = 0; c < 3; c++) {
+            double m = (double)prm[4 * a + c];
+            out[4 * a + c] = (m * sf[c]) / sm[a];
+            s = s + m * cf[c];
+        }
+        out[4 * a + 3] = ((cm[a] + (double)prm[4 * a + 3]) - s) / sm[a];
+    }
+    if (!dout) return;
+    memset(dout, 0, sizeof(double) * 12 * 12);
+    for (int a = 0; a < 3; a++) {
+        /* row a of [A | b] depends on row a of [M | t] only */
+        for (int c = 0; c < 3; c++) {
+            dout[12 * (4 * a + c) + 4 * a + c] = sf[c] / sm[a];
+            dout[12 * (4 * a + 3) + 4 * a + c] = -cf[c] / sm[a];
+        }
+        dout[12 * (4 * a + 3) + 4 * a + 3] = 1.0 / sm[a];
+    }
 }
 
 /* R3: each of the 12 entries of [A | b] is quantised to 16.16 fixed point as
@@ -717,16 +756,17 @@ static double orc_entropy_p(const double *p, int64_t m, double q) {
  *     Tsallis: dS(F) + dS(M) [+ (1-q)(dS(F) S(M) + S(F) dS(M)) if form 1] - dS(FM),
  *              dS(X) = -q X^(q-1) / (q - 1) at the cell's X,
  *   and W = 0 on cells with P = 0 (no voxel moves them: beta3' vanishes there).
- * du/dtheta comes from daff (12 x 9, d [A|b] / d theta, see orc_affine).
+ * du/dtheta comes from daff (12 x npar, d [A|b] / d theta: npar = 9 from
+ * orc_affine / orc_affine_mode, 12 from orc_affine_matrix).
  * If mask is not NULL, the voxel set is the mask (instead of the overlap)
  * and sample coordinates are clamped into the volume: this is the function
  * the gradient differentiates, used for finite-difference checks.
- * Outputs: mi[nq], grad[nq*9] (NULL ok), count (NULL ok), phist (B*B, NULL ok).
+ * Outputs: mi[nq], grad[nq*npar] (NULL ok), count (NULL ok), phist (B*B, NULL ok).
  */
 int orc_parzen(const void *fix, int fdtype, int fdepth, const int nf[3], const void *mov, int mdtype, int mdepth,
-               const int nm[3], const double aff[12], const double *daff, int B, const double *qs, int nq, int form,
-               int bits, const uint8_t *mask, double *mi, double *grad, int64_t *count, double *phist) {
-    if (B < 8) return ORC_EINVAL;
+               const int nm[3], const double aff[12], const double *daff, int npar, int B, const double *qs, int nq,
+               int form, int bits, const uint8_t *mask, double *mi, double *grad, int64_t *count, double *phist) {
+    if (B < 8 || npar < 1 || npar > 12) return ORC_EINVAL;
     size_t BB = (size_t)B * (size_t)B;
     int64_t nvf = orc_nvox(nf);
     double *P = calloc(BB, sizeof(double));
@@ -772,7 +812,7 @@ int orc_parzen(const void *fix, int fdtype, int fdepth, const int nf[3], const v
         for (int iq = 0; iq < nq; iq++) {
             mi[iq] = NAN;
             if (grad)
-                for (int p = 0; p < 9; p++) grad[9 * iq + p] = NAN;
+                for (int p = 0; p < npar; p++) grad[npar * iq + p] = NAN;
         }
         free(P); free(PF); free(PM); free(W);
         return ORC_OK;
@@ -810,7 +850,7 @@ int orc_parzen(const void *fix, int fdtype, int fdepth, const int nf[3], const v
                 W[(size_t)r * B + c] = w;
             }
         /* pass 2: adjoint */
-        double G[9] = {0};
+        double G[12] = {0};
         for (int64_t k = 0; k < nf[2]; k++)
             for (int64_t j = 0; j < nf[1]; j++)
                 for (int64_t i = 0; i < nf[0]; i++) {
@@ -838,17 +878,17 @@ int orc_parzen(const void *fix, int fdtype, int fdepth, const int nf[3], const v
                         if (kk >= 0 && kk < B) s += W[(size_t)fb * B + kk] * orc_dbeta3((double)kk - mt);
                     double dmt = -s / (double)N * (double)(B - 4);
                     double x4[4] = {(double)i, (double)j, (double)k, 1.0};
-                    for (int p = 0; p < 9; p++) {
+                    for (int p = 0; p < npar; p++) {
                         double d = 0.0;
                         for (int a = 0; a < 3; a++) {
                             double du = 0.0;
-                            for (int c = 0; c < 4; c++) du += daff[9 * (4 * a + c) + p] * x4[c];
+                            for (int c = 0; c < 4; c++) du += daff[npar * (4 * a + c) + p] * x4[c];
                             d += g[a] * du;
                         }
                         G[p] += dmt * d;
                     }
                 }
-        for (int p = 0; p < 9; p++) grad[9 * iq + p] = G[p];
+        for (int p = 0; p < npar; p++) grad[npar * iq + p] = G[p];
     }
     free(P); free(PF); free(PM); free(W);
     (void)nvf;

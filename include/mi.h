@@ -8,7 +8,7 @@
  * under a transform, v(T(x)) (Fig. 1 block diagram; the metric F_m whose
  * argmax over T is the registration, Eq. (3)).  T has 9 parameters from the
  * three families the paper studies (Introduction): translation, rotation,
- * scale.  All voxels contribute to one full joint histogram (Discussion),
+ * scale; or, optionally, the 12 of a general affine (Methodology).  All voxels contribute to one full joint histogram (Discussion),
  * and one histogram serves Shannon and every Tsallis q (Discussion).
  *
  * Conventions that the paper leaves open and this library fixes:
@@ -22,7 +22,8 @@
  *    factors, 1 = identity; or zero-centred offsets, mi_options.scale).  A fixed physical
  *    point p = s_f * i (i the voxel index) maps to
  *    p_m = R diag(s) (p - c_f) + c_m + t, R = Rz(rz) Ry(ry) Rx(rx), c the
- *    volume centres s * (n - 1) / 2; the moving index is p_m / s_m.  In index
+ *    volume centres s * (n - 1) / 2; the moving index is p_m / s_m (a general
+ *    affine replaces R diag(s) by its matrix M, MI_TRANSFORM_AFFINE).  In index
  *    space u = A i + b; [A | b] is quantised to 16.16 fixed point as
  *    llround(x * 65536) (computed in FP64 on the host with the order of
  *    operations fixed, so the quantised matrix is reproducible).
@@ -122,6 +123,24 @@ enum {
 enum { MI_ROT_EULER_DEG = 0, MI_ROT_VERSOR = 1 };
 enum { MI_SCALE_FACTOR = 0, MI_SCALE_OFFSET = 1 };
 
+/* What a transform's floats are (mi_options.transform):
+ *  MI_TRANSFORM_PARAMS  9 parameters: tx, ty, tz (mm), three rotation and
+ *                       three scale parameters as above.
+ *  MI_TRANSFORM_AFFINE  12 parameters, the general affine of the
+ *                       Methodology's 12 degrees of freedom (the affine
+ *                       family of the Introduction adds skew to translation,
+ *                       rotation and scale): [M | t] row-major
+ *                       (M00 M01 M02 t0 M10 M11 M12 t1 M20 M21 M22 t2), M
+ *                       dimensionless and t in mm.  The moving physical point
+ *                       is M (p - c_f) + c_m + t, p the fixed physical point
+ *                       and c_f, c_m the volume centres, exactly as the
+ *                       9-parameter form with R diag(sigma) replaced by M;
+ *                       identity: M = I, t = 0.  mi.rotation and mi.scale do
+ *                       not apply.  Gradients are d MI / d [M | t] in the
+ *                       same order.
+ * P below is the count (9 or 12); mi_transform_size returns it. */
+enum { MI_TRANSFORM_PARAMS = 0, MI_TRANSFORM_AFFINE = 1 };
+
 /* Evaluation path of mi_eval. */
 enum { MI_PATH_AUTO = 0, MI_PATH_PLAIN = 1, MI_PATH_BATCHED = 2 };
 
@@ -146,6 +165,7 @@ typedef struct {
     float sample_fraction;    /* 0 (default) = every fixed voxel; in (0, 1) = a random
                                  subset of that fraction (see below)                   */
     unsigned int sample_seed; /* seed of that subset                                    */
+    int transform;     /* MI_TRANSFORM_PARAMS (default) or MI_TRANSFORM_AFFINE       */
 } mi_options;
 
 /* Random voxel sampling (mi_options.sample_fraction in (0, 1), hard and
@@ -189,6 +209,10 @@ mi_status mi_batch_create(mi_ctx **out, const mi_volume *fixed, const mi_volume 
 /* Releases every resource of the context (NULL is ignored). */
 void mi_destroy(mi_ctx *ctx);
 
+/* P, the number of floats per transform of ctx (9, or 12 for
+ * MI_TRANSFORM_AFFINE); -1 if ctx is NULL. */
+int mi_transform_size(const mi_ctx *ctx);
+
 /* Message of the last failed call on ctx, or of the last failed create on
  * this thread when ctx is NULL.  Valid until the next call on ctx. */
 const char *mi_last_error(const mi_ctx *ctx);
@@ -199,7 +223,7 @@ const char *mi_last_error(const mi_ctx *ctx);
 mi_status mi_set_stream(mi_ctx *ctx, void *stream);
 
 /*
- * MI for n transforms (n x 9 floats, parameters above) and nq exponents q
+ * MI for n transforms (n x P floats, parameters above) and nq exponents q
  * (1 <= nq <= MI_MAX_Q; q > 0; q == 1 is Shannon, Eq. (1)-(2); other q are
  * Tsallis; q within 1e-6 of 1 but not 1 is rejected).  One joint histogram
  * per transform serves every q (Discussion).
@@ -220,19 +244,20 @@ mi_status mi_eval_q16(mi_ctx *ctx, const int32_t *affines, int n, const float *q
 
 /*
  * Batched evaluation over the pairs of a mi_batch_create context:
- * transform t (n x 9 parameters) is evaluated on pair pair_of_transform[t].
+ * transform t (n x P parameters) is evaluated on pair pair_of_transform[t].
  * Outputs as in mi_eval.
  */
 mi_status mi_batch_eval(mi_ctx *ctx, const int *pair_of_transform, const float *transforms, int n,
                         const float *q, int nq, double *out_mi, double *out_h, int64_t *out_count);
 
 /*
- * Parzen MI and its gradient dMI/dtheta over the 9 parameters (MI_PARZEN
+ * Parzen MI and its gradient dMI/dtheta over the P parameters (MI_PARZEN
  * contexts only): cubic-B-spline soft joint histogram of the moving
  * intensity against the box-binned fixed intensity, differentiated through
  * the trilinear resampling and the transform (the optimiser's gradient,
  * Introduction; registration as argmax, Eq. (3)).
- * out_mi: n x nq; out_grad: n x nq x 9 (d MI / d param, angles per degree).
+ * out_mi: n x nq; out_grad: n x nq x P (d MI / d param, Euler angles per
+ * degree).
  */
 mi_status mi_grad(mi_ctx *ctx, const float *transforms, int n, const float *q, int nq, double *out_mi,
                   double *out_grad);
@@ -241,15 +266,15 @@ mi_status mi_grad(mi_ctx *ctx, const float *transforms, int n, const float *q, i
  * Test hook: the joint histogram (row = fixed bin, bins x bins uint32 per
  * transform) of n transforms of pair `pair`, computed by the plain path
  * (path = MI_PATH_PLAIN) or copied out of the batched kernel's on-chip
- * histogram (MI_PATH_BATCHED).  Exactly one of transforms (n x 9) and
+ * histogram (MI_PATH_BATCHED).  Exactly one of transforms (n x P) and
  * affines (n x 12 16.16) is non-NULL.
  */
 mi_status mi_hist(mi_ctx *ctx, int pair, const float *transforms, const int32_t *affines, int n, int path,
                   uint32_t *out_counts);
 
 /* Test hook: the FP64 affine [A | b] (n x 12), its 16.16 quantisation (n x 12)
- * and its Jacobian d[A|b]/dparam (n x 12 x 9) for pair `pair`; any output may
- * be NULL.  Host computation only. */
+ * and its Jacobian d[A|b]/dparam (n x 12 x P) for pair `pair` and n x P
+ * transforms; any output may be NULL.  Host computation only. */
 mi_status mi_affine(mi_ctx *ctx, int pair, const float *transforms, int n, double *out_affine,
                     int32_t *out_q16, double *out_jacobian);
 

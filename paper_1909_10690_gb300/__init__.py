@@ -4,7 +4,8 @@ Python binding of the C ABI in ``include/mi.h`` (argument marshalling only;
 every step of the metric runs in the CUDA library).  Volumes are numpy arrays
 or torch tensors indexed [z, y, x] (x fastest), of dtype uint8, uint16 or
 float32; spacings are (x, y, z) in mm.  Transforms are n x 9 float32
-(tx, ty, tz mm; rx, ry, rz degrees; sx, sy, sz scale factors).
+(tx, ty, tz mm; rx, ry, rz degrees; sx, sy, sz scale factors), or n x 12
+for a general affine [M | t] (``transform="affine"``).
 
 The metric is the paper's F_m(u(x), v(T(x))) (Fig. 1): Shannon MI of
 Eq. (1)-(2), and Tsallis MI for q != 1, from one joint histogram per
@@ -102,7 +103,7 @@ def _volume(x, spacing, depth):
 
 
 def _options(kernel, tsallis_form, bits, hist_variant, path, use_graphs, autotune, device, block_threads=0,
-             rotation="euler", scale="factor", sample_fraction=0.0, sample_seed=0):
+             rotation="euler", scale="factor", sample_fraction=0.0, sample_seed=0, transform="params"):
     o = _lib.MiOptions()
     load().mi_options_default(ctypes.byref(o))
     o.kernel = {"hard": 0, "parzen": 1}[kernel]
@@ -118,6 +119,7 @@ def _options(kernel, tsallis_form, bits, hist_variant, path, use_graphs, autotun
     o.scale = {"factor": 0, "offset": 1}[scale]
     o.sample_fraction = float(sample_fraction)
     o.sample_seed = int(sample_seed) & 0xFFFFFFFF
+    o.transform = {"params": 0, "affine": 1}[transform]
     return o
 
 
@@ -143,19 +145,22 @@ class Context:
     identity, default) or "offset" (zero-centred, sigma = 1 + s).
     sample_fraction in (0, 1): the metric (hard or Parzen) over a random subset
     of the fixed voxels of that fraction, fixed by sample_seed (0: every voxel).
+    transform: "params" (9 parameters, default) or "affine" (12: the general
+    affine [M | t] row-major, M dimensionless, t in mm; gradients per entry).
+    ``nparams`` is the count.
     """
 
     def __init__(self, fixed=None, moving=None, bins=64, fixed_spacing=(1.0, 1.0, 1.0),
                  moving_spacing=(1.0, 1.0, 1.0), fixed_depth=None, moving_depth=None, kernel="hard",
                  tsallis_form="additive", bits=False, hist_variant=HV_AUTO, path="auto", use_graphs=True,
                  autotune=True, device=None, pairs=None, block_threads=0, rotation="euler", scale="factor",
-                 sample_fraction=0.0, sample_seed=0):
+                 sample_fraction=0.0, sample_seed=0, transform="params"):
         self._lib = load()
         self._h = ctypes.c_void_p()
         self.kernel = kernel
-        self.rotation, self.scale = rotation, scale
+        self.rotation, self.scale, self.transform = rotation, scale, transform
         opt = _options(kernel, tsallis_form, bits, hist_variant, path, use_graphs, autotune, device, block_threads,
-                       rotation, scale, sample_fraction, sample_seed)
+                       rotation, scale, sample_fraction, sample_seed, transform)
         if pairs is None:
             pairs = [dict(fixed=fixed, moving=moving, bins=bins, fixed_spacing=fixed_spacing,
                           moving_spacing=moving_spacing, fixed_depth=fixed_depth, moving_depth=moving_depth)]
@@ -185,6 +190,7 @@ class Context:
             st = self._lib.mi_create(ctypes.byref(self._h), fx, mv, bins_arr[0], ctypes.byref(opt))
         if st != MI_OK:
             raise MIError(st, self._lib.mi_last_error(None).decode())
+        self.nparams = self._lib.mi_transform_size(self._h)
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
@@ -211,7 +217,7 @@ class Context:
         """MI (n x nq) for n transforms; with_entropies adds (H_F, H_M, H_FM) per q and the overlap counts."""
         T = _Arg(transforms, np.float32)
         Q = _Arg(np.atleast_1d(np.asarray(q, dtype=np.float32)))
-        n = int(np.prod(T.obj.shape) // 9)
+        n = int(np.prod(T.obj.shape) // self.nparams)
         nq = int(np.asarray(q).size)
         gpu = T.on_gpu
         dev = T.obj.device if gpu else None
@@ -240,7 +246,7 @@ class Context:
         P = _Arg(pair_of_transform, np.int32)
         T = _Arg(transforms, np.float32)
         Q = _Arg(np.atleast_1d(np.asarray(q, dtype=np.float32)))
-        n = int(np.prod(T.obj.shape) // 9)
+        n = int(np.prod(T.obj.shape) // self.nparams)
         nq = int(np.asarray(q).size)
         gpu = T.on_gpu
         dev = T.obj.device if gpu else None
@@ -252,15 +258,15 @@ class Context:
         return (mi, h, cnt) if with_entropies else mi
 
     def grad(self, transforms, q=(1.0,), allow_empty=False):
-        """Parzen MI (n x nq) and dMI/dparam (n x nq x 9)."""
+        """Parzen MI (n x nq) and dMI/dparam (n x nq x nparams)."""
         T = _Arg(transforms, np.float32)
         Q = _Arg(np.atleast_1d(np.asarray(q, dtype=np.float32)))
-        n = int(np.prod(T.obj.shape) // 9)
+        n = int(np.prod(T.obj.shape) // self.nparams)
         nq = int(np.asarray(q).size)
         gpu = T.on_gpu
         dev = T.obj.device if gpu else None
         mi = _out((n, nq), gpu, np.float64, dev)
-        g = _out((n, nq, 9), gpu, np.float64, dev)
+        g = _out((n, nq, self.nparams), gpu, np.float64, dev)
         st = self._lib.mi_grad(self._h, T.ptr, n, Q.ptr, nq, _ptr(mi), _ptr(g))
         self._check(st, allow_empty)
         return mi, g
@@ -270,7 +276,7 @@ class Context:
         if (transforms is None) == (affines is None):
             raise ValueError("give exactly one of transforms and affines")
         src = _Arg(transforms, np.float32) if transforms is not None else _Arg(affines, np.int32)
-        n = int(np.prod(src.obj.shape) // (9 if transforms is not None else 12))
+        n = int(np.prod(src.obj.shape) // (self.nparams if transforms is not None else 12))
         B = self.bins[pair]
         out = np.empty((n, B, B), dtype=np.uint32)
         st = self._lib.mi_hist(self._h, pair, src.ptr if transforms is not None else None,
@@ -279,12 +285,12 @@ class Context:
         return out
 
     def affine(self, transforms, pair=0):
-        """(FP64 [A|b] n x 3 x 4, 16.16 n x 3 x 4, Jacobian n x 12 x 9) from the library's host builder."""
+        """(FP64 [A|b] n x 3 x 4, 16.16 n x 3 x 4, Jacobian n x 12 x nparams) from the library's host builder."""
         T = _Arg(transforms, np.float32)
-        n = int(np.prod(T.obj.shape) // 9)
+        n = int(np.prod(T.obj.shape) // self.nparams)
         a = np.empty((n, 3, 4), np.float64)
         q = np.empty((n, 3, 4), np.int32)
-        j = np.empty((n, 12, 9), np.float64)
+        j = np.empty((n, 12, self.nparams), np.float64)
         st = self._lib.mi_affine(self._h, pair, T.ptr, n, a.ctypes.data, q.ctypes.data, j.ctypes.data)
         self._check(st)
         return a, q, j
@@ -352,7 +358,7 @@ def mi_function():
         def backward(fctx, grad_out):
             (g,) = fctx.saved_tensors
             g = g.to(grad_out.device)
-            # (n, nq) x (n, nq, 9) -> (n, 9)
+            # (n, nq) x (n, nq, P) -> (n, P)
             gt = (grad_out.to(g.dtype).unsqueeze(-1) * g).sum(dim=1)
             return gt, None, None
 

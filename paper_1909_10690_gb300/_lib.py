@@ -82,7 +82,7 @@ class MiOptions(ctypes.Structure):
                 ("hist_variant", ctypes.c_int), ("path", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("device", ctypes.c_int), ("block_threads", ctypes.c_int),
                 ("rotation", ctypes.c_int), ("scale", ctypes.c_int), ("sample_fraction", ctypes.c_float),
-                ("sample_seed", ctypes.c_uint)]
+                ("sample_seed", ctypes.c_uint), ("transform", ctypes.c_int)]
 
 
 # Symbols declared in include/mi.h, with their ctypes signatures.
@@ -96,6 +96,7 @@ SIGNATURES = {
     "mi_batch_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(MiVolume), ctypes.POINTER(MiVolume), _P, _I,
                              ctypes.POINTER(MiOptions)]),
     "mi_destroy": (None, [_P]),
+    "mi_transform_size": (_I, [_P]),
     "mi_last_error": (ctypes.c_char_p, [_P]),
     "mi_set_stream": (_I, [_P, _P]),
     "mi_eval": (_I, [_P, _P, _I, _P, _I, _P, _P, _P]),

@@ -222,6 +222,46 @@ void build_affine(const float prm[9], const int nf[3], const float sfp[3], const
         }
 }
 
+// The general affine (12 parameters [M | t], row-major): R diag(sigma) of build_affine replaced by M, with the
+// same order of operations.  J (12 x 12, optional) = d[A|b]/d[M|t] is constant.
+void build_affine_matrix(const float prm[12], const int nf[3], const float sfp[3], const int nm[3],
+                         const float smp[3], double out[12], double *jac) {
+    double sf[3], sm[3], cf[3], cm[3];
+    for (int a = 0; a < 3; ++a) {
+        sf[a] = (double)sfp[a];
+        sm[a] = (double)smp[a];
+        cf[a] = sf[a] * ((double)(nf[a] - 1) * 0.5);
+        cm[a] = sm[a] * ((double)(nm[a] - 1) * 0.5);
+    }
+    for (int a = 0; a < 3; ++a) {
+        double acc = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            const double m = (double)prm[4 * a + c];
+            out[4 * a + c] = (m * sf[c]) / sm[a];
+            acc = acc + m * cf[c];
+        }
+        out[4 * a + 3] = ((cm[a] + (double)prm[4 * a + 3]) - acc) / sm[a];
+    }
+    if (!jac) return;
+    for (int e = 0; e < 144; ++e) jac[e] = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        for (int c = 0; c < 3; ++c) {
+            jac[12 * (4 * a + c) + 4 * a + c] = sf[c] / sm[a];
+            jac[12 * (4 * a + 3) + 4 * a + c] = -cf[c] / sm[a];
+        }
+        jac[12 * (4 * a + 3) + 4 * a + 3] = 1.0 / sm[a];
+    }
+}
+
+// [A | b] of one transform in the context's conventions; jac (12 x nparams) optional.
+void build_affine_opt(const mi_options &o, const float *prm, const int nf[3], const float sf[3], const int nm[3],
+                      const float sm[3], double out[12], double *jac) {
+    if (o.transform == MI_TRANSFORM_AFFINE)
+        build_affine_matrix(prm, nf, sf, nm, sm, out, jac);
+    else
+        build_affine(prm, nf, sf, nm, sm, out, jac, o.rotation, o.scale);
+}
+
 bool quantise_q16(const double aff[12], int32_t q[12]) {
     for (int e = 0; e < 12; ++e) {
         const double s = aff[e] * 65536.0;
@@ -303,6 +343,9 @@ struct mi_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int last_launches = 0;
     bool timed = false;
+
+    // floats per transform: 9 parameters, or the 12 of a general affine [M | t]
+    int nparams() const { return opt.transform == MI_TRANSFORM_AFFINE ? 12 : 9; }
 
     mi_status fail(mi_status st, const std::string &msg) {
         err = msg;
@@ -689,6 +732,10 @@ mi_status create_common(mi_ctx **out, const mi_volume *fixed, const mi_volume *m
         g_create_error = "opt.rotation / opt.scale out of range";
         return MI_EINVAL;
     }
+    if (ctx->opt.transform != MI_TRANSFORM_PARAMS && ctx->opt.transform != MI_TRANSFORM_AFFINE) {
+        g_create_error = "opt.transform must be MI_TRANSFORM_PARAMS or MI_TRANSFORM_AFFINE";
+        return MI_EINVAL;
+    }
     if (ctx->opt.hist_variant < MI_HV_AUTO || ctx->opt.hist_variant > MI_HV_U16_QUAD) {
         g_create_error = "opt.hist_variant out of range";
         return MI_EINVAL;
@@ -792,21 +839,22 @@ mi_status make_qset(mi_ctx *ctx, const float *qv, int nq, QSet &Q) {
 
 // Transforms from the caller (host or device) into a host vector.
 mi_status read_transforms(mi_ctx *ctx, const float *tr, int n, std::vector<float> &out) {
-    out.resize((size_t)n * 9);
+    const int np = ctx->nparams();
+    out.resize((size_t)n * np);
     if (n == 0) return MI_OK;
     if (!tr) return ctx->fail(MI_EINVAL, "transforms is NULL");
     if (is_device_ptr(tr))
-        MI_CU(cudaMemcpy(out.data(), tr, (size_t)n * 9 * sizeof(float), cudaMemcpyDeviceToHost), "reading transforms");
+        MI_CU(cudaMemcpy(out.data(), tr, (size_t)n * np * sizeof(float), cudaMemcpyDeviceToHost), "reading transforms");
     else
-        memcpy(out.data(), tr, (size_t)n * 9 * sizeof(float));
+        memcpy(out.data(), tr, (size_t)n * np * sizeof(float));
     for (size_t i = 0; i < out.size(); ++i)
-        if (!isfinite(out[i])) return ctx->fail(MI_EINVAL, "transform " + std::to_string(i / 9) + " is not finite");
+        if (!isfinite(out[i])) return ctx->fail(MI_EINVAL, "transform " + std::to_string(i / np) + " is not finite");
     return MI_OK;
 }
 
 mi_status build_q16(mi_ctx *ctx, const Pair &P, const float *prm, int32_t *q16, int t) {
     double aff[12];
-    build_affine(prm, P.nf, P.sf, P.nm, P.sm, aff, nullptr, ctx->opt.rotation, ctx->opt.scale);
+    build_affine_opt(ctx->opt, prm, P.nf, P.sf, P.nm, P.sm, aff, nullptr);
     if (!quantise_q16(aff, q16))
         return ctx->fail(MI_ERANGE, "transform " + std::to_string(t) + ": affine does not fit 16.16 fixed point");
     return MI_OK;
@@ -1134,12 +1182,13 @@ mi_status parzen_core(mi_ctx *ctx, const std::vector<float> &prm, int n, const f
     QSet Q;
     mi_status st = make_qset(ctx, qv, nq, Q);
     if (st != MI_OK) return st;
+    const int np = ctx->nparams();
     std::vector<ParzenAffine> pa(n);
-    std::vector<double> jac((size_t)n * 108);
+    std::vector<double> jac((size_t)n * 12 * np);
     for (int t = 0; t < n; ++t) {
         double aff[12];
-        double *J = &jac[(size_t)t * 108];
-        build_affine(&prm[(size_t)t * 9], P.nf, P.sf, P.nm, P.sm, aff, J, ctx->opt.rotation, ctx->opt.scale);
+        double *J = &jac[(size_t)t * 12 * np];
+        build_affine_opt(ctx->opt, &prm[(size_t)t * np], P.nf, P.sf, P.nm, P.sm, aff, J);
         for (int e = 0; e < 12; ++e) {
             const double s = aff[e] * 4294967296.0;
             if (!(fabs(s) < 4503599627370496.0))  // |x| < 2^20 keeps every int64 product below 2^63
@@ -1148,10 +1197,10 @@ mi_status parzen_core(mi_ctx *ctx, const std::vector<float> &prm, int n, const f
         }
         // re-centre: u = A (i - c) + (A c + b), so the constant row becomes dA c + db
         for (int a = 0; a < 3; ++a)
-            for (int p = 0; p < 9; ++p) {
-                double acc = J[9 * (4 * a + 3) + p];
-                for (int c = 0; c < 3; ++c) acc += J[9 * (4 * a + c) + p] * (0.5 * (double)(P.nf[c] - 1));
-                J[9 * (4 * a + 3) + p] = acc;
+            for (int p = 0; p < np; ++p) {
+                double acc = J[np * (4 * a + 3) + p];
+                for (int c = 0; c < 3; ++c) acc += J[np * (4 * a + c) + p] * (0.5 * (double)(P.nf[c] - 1));
+                J[np * (4 * a + 3) + p] = acc;
             }
     }
     cudaStream_t s = ctx->stream;
@@ -1172,7 +1221,7 @@ mi_status parzen_core(mi_ctx *ctx, const std::vector<float> &prm, int n, const f
     const int ctas = parzen_ctas(pp, n, ctx->sms);
     const int cblocks = parzen_cell_blocks(B);
     MI_CU(ctx->p_aff.ensure((size_t)n * sizeof(ParzenAffine)), "alloc");
-    MI_CU(ctx->p_jac.ensure((size_t)n * 108 * 8), "alloc");
+    MI_CU(ctx->p_jac.ensure((size_t)n * 12 * np * 8), "alloc");
     MI_CU(ctx->p_hist.ensure((size_t)n * B2 * 8), "alloc");
     MI_CU(ctx->p_cnt.ensure((size_t)n * 8), "alloc");
     MI_CU(ctx->p_marg.ensure((size_t)n * 2 * B * 8), "alloc");
@@ -1181,10 +1230,10 @@ mi_status parzen_core(mi_ctx *ctx, const std::vector<float> &prm, int n, const f
     MI_CU(ctx->p_jsum.ensure((size_t)n * nq * cblocks * 8), "alloc");
     MI_CU(ctx->p_w.ensure((size_t)n * nq * B2 * 4), "alloc");
     MI_CU(ctx->p_mom.ensure((size_t)n * nq * ctas * 12 * 8), "alloc");
-    MI_CU(ctx->p_grad.ensure((size_t)n * nq * 9 * 8), "alloc");
+    MI_CU(ctx->p_grad.ensure((size_t)n * nq * np * 8), "alloc");
     MI_CU(ctx->d_mi.ensure((size_t)n * nq * 8), "alloc");
     MI_CU(cudaMemcpyAsync(ctx->p_aff.p, pa.data(), (size_t)n * sizeof(ParzenAffine), cudaMemcpyHostToDevice, s), "H2D");
-    MI_CU(cudaMemcpyAsync(ctx->p_jac.p, jac.data(), (size_t)n * 108 * 8, cudaMemcpyHostToDevice, s), "H2D");
+    MI_CU(cudaMemcpyAsync(ctx->p_jac.p, jac.data(), (size_t)n * 12 * np * 8, cudaMemcpyHostToDevice, s), "H2D");
     const ParzenAffine *d_aff = ctx->p_aff.as<ParzenAffine>();
     auto *cnt = ctx->p_cnt.as<unsigned long long>();
     auto *hist = ctx->p_hist.as<unsigned long long>();
@@ -1195,14 +1244,14 @@ mi_status parzen_core(mi_ctx *ctx, const std::vector<float> &prm, int n, const f
                                 ctx->p_w.as<float>(), s),
           "Parzen entropies");
     if (out_grad)
-        MI_CU(launch_parzen_adjoint(pp, d_aff, ctx->p_jac.as<double>(), n, nq, ctas, ctx->p_w.as<float>(), cnt,
+        MI_CU(launch_parzen_adjoint(pp, d_aff, ctx->p_jac.as<double>(), np, n, nq, ctas, ctx->p_w.as<float>(), cnt,
                                     ctx->p_mom.as<double>(), ctx->p_grad.as<double>(), s),
               "Parzen adjoint");
     MI_CU(cudaEventRecord(ctx->ev1, s), "event");
     ctx->timed = true;
     ctx->last_launches = 4 + (out_grad ? (nq + 3) / 4 + 1 : 0);
     if ((st = deliver(ctx, out_mi, ctx->d_mi.p, (size_t)n * nq * 8)) != MI_OK) return st;
-    if (out_grad && (st = deliver(ctx, out_grad, ctx->p_grad.p, (size_t)n * nq * 9 * 8)) != MI_OK) return st;
+    if (out_grad && (st = deliver(ctx, out_grad, ctx->p_grad.p, (size_t)n * nq * np * 8)) != MI_OK) return st;
     std::vector<unsigned long long> hc(n);
     MI_CU(cudaMemcpyAsync(hc.data(), cnt, (size_t)n * 8, cudaMemcpyDeviceToHost, s), "reading counts");
     MI_CU(cudaStreamSynchronize(s), "Parzen evaluation");
@@ -1234,9 +1283,12 @@ void mi_options_default(mi_options *opt) {
     opt->scale = MI_SCALE_FACTOR;
     opt->sample_fraction = 0.0f;
     opt->sample_seed = 0u;
+    opt->transform = MI_TRANSFORM_PARAMS;
 }
 
 const char *mi_version(void) { return "gb300-mi 0.1 (sm_103a)"; }
+
+int mi_transform_size(const mi_ctx *ctx) { return ctx ? ctx->nparams() : -1; }
 
 mi_status mi_create(mi_ctx **out, const mi_volume *fixed, const mi_volume *moving, int bins, const mi_options *opt) {
     return create_common(out, fixed, moving, &bins, 1, opt);
@@ -1304,7 +1356,7 @@ mi_status mi_eval(mi_ctx *ctx, const float *transforms, int n, const float *q, i
     R.path = ctx->opt.path;
     R.q16.resize((size_t)n * 12);
     for (int t = 0; t < n; ++t)
-        if ((st = build_q16(ctx, *ctx->pairs[0], &prm[(size_t)t * 9], &R.q16[(size_t)t * 12], t)) != MI_OK) return st;
+        if ((st = build_q16(ctx, *ctx->pairs[0], &prm[(size_t)t * ctx->nparams()], &R.q16[(size_t)t * 12], t)) != MI_OK) return st;
     return eval_core(ctx, R, qv, nq, out_mi, out_h, out_count);
 }
 
@@ -1356,7 +1408,7 @@ mi_status mi_batch_eval(mi_ctx *ctx, const int *pair_of_transform, const float *
     for (int t = 0; t < n; ++t) {
         const int p = R.pair_of[t];
         if (p < 0 || p >= (int)ctx->pairs.size()) return ctx->fail(MI_EINVAL, "pair index out of range");
-        if ((st = build_q16(ctx, *ctx->pairs[p], &prm[(size_t)t * 9], &R.q16[(size_t)t * 12], t)) != MI_OK) return st;
+        if ((st = build_q16(ctx, *ctx->pairs[p], &prm[(size_t)t * ctx->nparams()], &R.q16[(size_t)t * 12], t)) != MI_OK) return st;
     }
     return eval_core(ctx, R, qv, nq, out_mi, out_h, out_count);
 }
@@ -1399,7 +1451,7 @@ mi_status mi_hist(mi_ctx *ctx, int pair, const float *transforms, const int32_t 
         std::vector<float> prm;
         if ((st = read_transforms(ctx, transforms, n, prm)) != MI_OK) return st;
         for (int t = 0; t < n; ++t)
-            if ((st = build_q16(ctx, P, &prm[(size_t)t * 9], &R.q16[(size_t)t * 12], t)) != MI_OK) return st;
+            if ((st = build_q16(ctx, P, &prm[(size_t)t * ctx->nparams()], &R.q16[(size_t)t * 12], t)) != MI_OK) return st;
     } else if (is_device_ptr(affines)) {
         MI_CU(cudaMemcpy(R.q16.data(), affines, (size_t)n * 48, cudaMemcpyDeviceToHost), "reading affines");
     } else {
@@ -1425,12 +1477,13 @@ mi_status mi_affine(mi_ctx *ctx, int pair, const float *transforms, int n, doubl
     if (n < 0 || (n > 0 && !transforms)) return ctx->fail(MI_EINVAL, "bad transforms");
     const Pair &P = *ctx->pairs[pair];
     mi_status st = MI_OK;
+    const int np = ctx->nparams();
     for (int t = 0; t < n; ++t) {
-        double aff[12], jac[108];
-        build_affine(transforms + (size_t)t * 9, P.nf, P.sf, P.nm, P.sm, aff, out_jacobian ? jac : nullptr,
-                     ctx->opt.rotation, ctx->opt.scale);
+        double aff[12], jac[144];
+        build_affine_opt(ctx->opt, transforms + (size_t)t * np, P.nf, P.sf, P.nm, P.sm, aff,
+                         out_jacobian ? jac : nullptr);
         if (out_affine) memcpy(out_affine + (size_t)t * 12, aff, sizeof aff);
-        if (out_jacobian) memcpy(out_jacobian + (size_t)t * 108, jac, sizeof jac);
+        if (out_jacobian) memcpy(out_jacobian + (size_t)t * 12 * np, jac, sizeof(double) * 12 * np);
         if (out_q16) {
             int32_t q[12];
             if (!quantise_q16(aff, q)) {

@@ -154,8 +154,9 @@ cudaError_t launch_parzen_weights(const unsigned long long *d_hist, const unsign
                                   float *d_w, cudaStream_t s);
 // Gradient: per-CTA moments (scratch n x nq x ctas x 12 FP64) and dMI/dtheta (n x nq x 9 FP64);
 // d_jac is n x 12 x 9 FP64 taken about the fixed-volume centre.
-cudaError_t launch_parzen_adjoint(const ParzenPair &P, const ParzenAffine *d_aff, const double *d_jac, int n, int nq,
-                                  int ctas, const float *d_w, const unsigned long long *d_count, double *d_mom,
+// d_jac: n x 12 x np (d[A|b]/dparam about the fixed centre), np = 9 or 12; d_grad: n x nq x np.
+cudaError_t launch_parzen_adjoint(const ParzenPair &P, const ParzenAffine *d_aff, const double *d_jac, int np, int n,
+                                  int nq, int ctas, const float *d_w, const unsigned long long *d_count, double *d_mom,
                                   double *d_grad, cudaStream_t s);
 
 // ---- allocation-free evaluation (mi_noalloc.cu) ---------------------------

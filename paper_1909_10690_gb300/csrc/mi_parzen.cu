@@ -671,12 +671,12 @@ __global__ void __launch_bounds__(256, 2)
     }
 }
 
-// grad[t][q][p] = -(B - 4) / N sum_e mom[t][q][e] J[t][e][p], J taken about the fixed centre
-__global__ void k_parzen_grad(int n, int nq, int B, int nparts, const unsigned long long *__restrict__ gcount,
+// grad[t][q][p] = -(B - 4) / N sum_e mom[t][q][e] J[t][e][p], J (12 x np) taken about the fixed centre
+__global__ void k_parzen_grad(int n, int nq, int np, int B, int nparts, const unsigned long long *__restrict__ gcount,
                               const double *__restrict__ mom, const double *__restrict__ jac, double *__restrict__ grad) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= n * nq * 9) return;
-    const int p = x % 9, tq = x / 9, t = tq / nq;
+    if (x >= n * nq * np) return;
+    const int p = x % np, tq = x / np, t = tq / nq;
     const double N = (double)gcount[t];
     if (N <= 0) {
         grad[x] = __longlong_as_double(0x7ff8000000000000ll);
@@ -686,7 +686,7 @@ __global__ void k_parzen_grad(int n, int nq, int B, int nparts, const unsigned l
     for (int e = 0; e < 12; ++e) {
         double me = 0.0;
         for (int b = 0; b < nparts; ++b) me += mom[((size_t)tq * nparts + b) * 12 + e];
-        s += me * jac[((size_t)t * 12 + e) * 9 + p];
+        s += me * jac[((size_t)t * 12 + e) * np + p];
     }
     grad[x] = -(double)(B - 4) / N * s;
 }
@@ -777,8 +777,8 @@ cudaError_t launch_parzen_weights(const unsigned long long *d_hist, const unsign
     return cudaGetLastError();
 }
 
-cudaError_t launch_parzen_adjoint(const ParzenPair &P, const ParzenAffine *d_aff, const double *d_jac, int n, int nq,
-                                  int ctas, const float *d_w, const unsigned long long *d_count, double *d_mom,
+cudaError_t launch_parzen_adjoint(const ParzenPair &P, const ParzenAffine *d_aff, const double *d_jac, int np, int n,
+                                  int nq, int ctas, const float *d_w, const unsigned long long *d_count, double *d_mom,
                                   double *d_grad, cudaStream_t s) {
     cudaError_t e;
     dim3 grid(ctas, n);
@@ -811,7 +811,7 @@ cudaError_t launch_parzen_adjoint(const ParzenPair &P, const ParzenAffine *d_aff
 #undef MI_ADJ_S
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    k_parzen_grad<<<(n * nq * 9 + 127) / 128, 128, 0, s>>>(n, nq, P.B, ctas, d_count, d_mom, d_jac, d_grad);
+    k_parzen_grad<<<(n * nq * np + 127) / 128, 128, 0, s>>>(n, nq, np, P.B, ctas, d_count, d_mom, d_jac, d_grad);
     return cudaGetLastError();
 }
 

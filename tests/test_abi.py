@@ -44,7 +44,9 @@ def test_options_default_and_error_without_device():
     o = _lib.MiOptions()
     lib.mi_options_default(ctypes.byref(o))
     assert (o.kernel, o.tsallis_form, o.log_bits, o.hist_variant, o.path, o.use_graphs, o.autotune, o.device,
-            o.block_threads, o.rotation, o.scale) == (0, 0, 0, -1, 0, 1, 1, -1, 0, 0, 0)
+            o.block_threads, o.rotation, o.scale, o.sample_fraction, o.sample_seed,
+            o.transform) == (0, 0, 0, -1, 0, 1, 1, -1, 0, 0, 0, 0.0, 0, 0)
+    assert lib.mi_transform_size(None) == -1
     # invalid arguments are rejected before any device work
     h = ctypes.c_void_p()
     st = lib.mi_create(ctypes.byref(h), None, None, 32, None)

@@ -481,6 +481,9 @@ mi_status add_pair(mi_ctx *ctx, const mi_volume *fx, const mi_volume *mv, int bi
         if (fx->dims[0] > MI_MAX_PARZEN_NX)
             return ctx->fail(MI_EUNSUPPORTED, "Parzen fixed rows are limited to " + std::to_string(MI_MAX_PARZEN_NX) +
                                                   " voxels (nx)");
+        // the moving volume extended by one plane per axis is indexed with 32-bit offsets
+        if ((long long)(mv->dims[0] + 1) * (mv->dims[1] + 1) * (mv->dims[2] + 1) >= (1LL << 31))
+            return ctx->fail(MI_EUNSUPPORTED, "the Parzen moving volume is limited to (nx+1)(ny+1)(nz+1) < 2^31");
     } else if (bins < MI_MIN_BINS || bins > MI_MAX_BINS) {
         return ctx->fail(MI_EINVAL, "bins must be in 2..256, got " + std::to_string(bins));
     }

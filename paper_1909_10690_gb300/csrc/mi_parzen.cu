@@ -83,14 +83,16 @@ struct MG {
     float m, gx, gy, gz;
 };
 
+// m0 = n0 + 1 and m01 = (n0 + 1)(n1 + 1): element offsets fit 32 bits (the extended volume holds fewer
+// than 2^31 elements, checked when the context is created).
 template <bool GRAD>
-__device__ __forceinline__ MG trilinear_x(const float *__restrict__ movx, int m0, size_t m01, long long Ux,
+__device__ __forceinline__ MG trilinear_x(const float *__restrict__ movx, int m0, int m01, long long Ux,
                                           long long Uy, long long Uz) {
     constexpr float k2m32 = 2.3283064365386963e-10f;  // 2^-32
     const int cx = (int)(Ux >> 32), cy = (int)(Uy >> 32), cz = (int)(Uz >> 32);
     const float wx = __uint2float_rn((unsigned)Ux) * k2m32, wy = __uint2float_rn((unsigned)Uy) * k2m32,
                 wz = __uint2float_rn((unsigned)Uz) * k2m32;
-    const float *p = movx + ((size_t)cx + (size_t)m0 * cy + m01 * cz);
+    const float *p = movx + (cx + m0 * cy + m01 * cz);
     const float v000 = __ldg(p), v001 = __ldg(p + 1), v010 = __ldg(p + m0), v011 = __ldg(p + m0 + 1);
     const float v100 = __ldg(p + m01), v101 = __ldg(p + m01 + 1), v110 = __ldg(p + m01 + m0),
                 v111 = __ldg(p + m01 + m0 + 1);
@@ -264,8 +266,8 @@ __global__ void __launch_bounds__(256)
     // one voxel at 32.32 index U with fixed bin bf: its four quantised B-spline weights
     auto add_voxel = [&](long long U0, long long U1, long long U2, int bf) {
         const MG g3 = kParzenFwdTex ? trilinear_q<false>(P.texq, U0, U1, U2)
-                                    : trilinear_x<false>(P.movx, P.nm[0] + 1, (size_t)(P.nm[0] + 1) * (P.nm[1] + 1),
-                                                         U0, U1, U2);
+                                    : trilinear_x<false>(P.movx, P.nm[0] + 1, (P.nm[0] + 1) * (P.nm[1] + 1), U0,
+                                                         U1, U2);
         const float mt = fmaf(fminf(fmaxf(g3.m, 0.0f), 1.0f), Bm4, 2.0f);
         const int k0 = (int)mt;
         float w[4];
@@ -581,19 +583,21 @@ __global__ void __launch_bounds__(256, 2)
             long long U2 = __shfl_sync(kFull, mine.u2, s) + A[8] * lane;
             const float j = (float)(r % nf1) - cj, k = (float)(r / nf1) - ck;
             const uint8_t *__restrict__ frow = P.fbins + (size_t)r * nf0;
-            // along the row j and k are constant: per row, S0[q][a] = sum s d_a m and
-            // S1[q][a] = sum s d_a m (i - ci); the 12 moments follow at the row's end
-            float S0[NQ][3], S1[NQ][3];
+            // along the row j and k are constant: per row, S0[q][a] = sum s d_a m, and the moments in
+            // j, k and 1 follow from it at the row's end; sum s d_a m (i - ci) goes to M directly
+            float S0[NQ][3];
 #pragma unroll
             for (int q = 0; q < NQ; ++q)
 #pragma unroll
-                for (int a = 0; a < 3; ++a) S0[q][a] = S1[q][a] = 0.0f;
-            // one voxel (x index i, fixed bin bf) at 32.32 index U: its share of S0 and S1
+                for (int a = 0; a < 3; ++a) S0[q][a] = 0.0f;
+            // one voxel (x index i, fixed bin bf) at 32.32 index U: its share of S0 and M
             auto acc_voxel = [&](long long V0, long long V1, long long V2, int i, int bf) {
                 const MG g3 = kParzenAdjTex ? trilinear_q<true>(P.texq, V0, V1, V2)
-                                            : trilinear_x<true>(P.movx, P.nm[0] + 1,
-                                                                (size_t)(P.nm[0] + 1) * (P.nm[1] + 1), V0, V1, V2);
+                                            : trilinear_x<true>(P.movx, P.nm[0] + 1, (P.nm[0] + 1) * (P.nm[1] + 1),
+                                                                V0, V1, V2);
                 const float ic = (float)i - ci;
+                // d_a m and d_a m (i - ci), shared by every q
+                const float hx = g3.gx * ic, hy = g3.gy * ic, hz = g3.gz * ic;
                 const float mt = fmaf(fminf(fmaxf(g3.m, 0.0f), 1.0f), Bm4, 2.0f);
                 const int k0 = (int)mt;
                 float d[4];
@@ -612,13 +616,12 @@ __global__ void __launch_bounds__(256, 2)
                         const float *Wq = W + (size_t)q * QS;
                         sv = Wq[cb] * d[0] + Wq[cb + 1] * d[1] + Wq[cb + 2] * d[2] + Wq[i3] * d[3];
                     }
-                    const float sx = sv * g3.gx, sy = sv * g3.gy, sz = sv * g3.gz;
-                    S1[q][0] = fmaf(sx, ic, S1[q][0]);
-                    S0[q][0] += sx;
-                    S1[q][1] = fmaf(sy, ic, S1[q][1]);
-                    S0[q][1] += sy;
-                    S1[q][2] = fmaf(sz, ic, S1[q][2]);
-                    S0[q][2] += sz;
+                    M[q][0] = fmaf(sv, hx, M[q][0]);
+                    S0[q][0] = fmaf(sv, g3.gx, S0[q][0]);
+                    M[q][4] = fmaf(sv, hy, M[q][4]);
+                    S0[q][1] = fmaf(sv, g3.gy, S0[q][1]);
+                    M[q][8] = fmaf(sv, hz, M[q][8]);
+                    S0[q][2] = fmaf(sv, g3.gz, S0[q][2]);
                 }
             };
             if constexpr (SAMPLED) {  // random sampling: the row's sampled voxels inside [lo, hi]
@@ -645,7 +648,6 @@ __global__ void __launch_bounds__(256, 2)
             for (int q = 0; q < NQ; ++q)
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    M[q][4 * a + 0] += S1[q][a];
                     M[q][4 * a + 1] = fmaf(S0[q][a], j, M[q][4 * a + 1]);
                     M[q][4 * a + 2] = fmaf(S0[q][a], k, M[q][4 * a + 2]);
                     M[q][4 * a + 3] += S0[q][a];

@@ -190,7 +190,11 @@ const char *mi_version(void);
  * (MI_MIN_BINS..MI_MAX_BINS; MI_MIN_PARZEN_BINS..128 for MI_PARZEN, whose
  * fixed volume must have nx <= MI_MAX_PARZEN_NX, else MI_EUNSUPPORTED).  The metric
  * is F_m(u(x), v(T(x))) of Fig. 1; the pair's geometry (dims, spacing) fixes
- * the parameter-to-affine map.  opt may be NULL (defaults).  On success *out
+ * the parameter-to-affine map.  The moving volume is gathered through 3D
+ * textures: its dims must fit the device's 3D texture extent
+ * (cudaDevAttrMaxTexture3DWidth / Height / Depth) with one spare z plane,
+ * else MI_EUNSUPPORTED.
+ * opt may be NULL (defaults).  On success *out
  * owns device copies of both volumes (the fixed one pre-binned) and must be
  * released with mi_destroy.  On failure *out is NULL and mi_last_error(NULL)
  * describes the error on this thread.

@@ -475,6 +475,17 @@ mi_status add_pair(mi_ctx *ctx, const mi_volume *fx, const mi_volume *mv, int bi
     mi_status st;
     if ((st = validate_volume(fx, "fixed", parzen, e)) != MI_OK) return ctx->fail(st, e);
     if ((st = validate_volume(mv, "moving", parzen, e)) != MI_OK) return ctx->fail(st, e);
+    {
+        // both paths gather the moving volume through 3D textures of dims (nx, ny, nz + 1)
+        int tw = 0, th = 0, td = 0;
+        cudaDeviceGetAttribute(&tw, cudaDevAttrMaxTexture3DWidth, ctx->device);
+        cudaDeviceGetAttribute(&th, cudaDevAttrMaxTexture3DHeight, ctx->device);
+        cudaDeviceGetAttribute(&td, cudaDevAttrMaxTexture3DDepth, ctx->device);
+        if (mv->dims[0] > tw || mv->dims[1] > th || mv->dims[2] + 1 > td)
+            return ctx->fail(MI_EUNSUPPORTED, "moving volume dims exceed the device's 3D texture extent (" +
+                                                  std::to_string(tw) + " x " + std::to_string(th) + " x " +
+                                                  std::to_string(td - 1) + ")");
+    }
     if (parzen) {
         if (bins < MI_MIN_PARZEN_BINS || bins > 128)
             return ctx->fail(MI_EINVAL, "Parzen bins must be in " + std::to_string(MI_MIN_PARZEN_BINS) + "..128");

@@ -234,8 +234,26 @@ constexpr int kParzenRowsPerStep = 1;  // rows a warp of the forward works on at
 // Row stride of the shared tables: the least SB >= B + 1 with SB = kParzenBankSkew (mod 32).
 __host__ __device__ inline int parzen_stride(int B) { return B + 1 + ((kParzenBankSkew - (B + 1)) % 32 + 32) % 32; }
 
-template <int RPW, bool SAMPLED>
-__global__ void __launch_bounds__(256)
+// Histogram copies per CTA of the forward: with C copies, lane l adds to copy l mod C (copy i shifted by
+// 32 i / C banks), which divides by C the lanes of a warp that hit one cell in one atomic instruction;
+// CTAs of 256 C threads keep the shared memory per SM of one copy per 256 threads.
+constexpr int kParzenFwdMaxCopies = 4;
+__host__ __device__ inline int parzen_copy_offset(int B, int copies) {
+    return 2 * B * parzen_stride(B) + (copies > 1 ? 32 / copies : 0);
+}
+__host__ inline size_t parzen_fwd_smem(int B, int copies) {
+    return (size_t)copies * parzen_copy_offset(B, copies) * sizeof(uint32_t);
+}
+// Copies for B bins: the most (up to kParzenFwdMaxCopies) whose CTAs still fill an SM's 2048 threads,
+// i.e. while four copies fit the SM's 228 KB; one copy otherwise.
+__host__ inline int parzen_fwd_copies(int B) {
+    int c = kParzenFwdMaxCopies;
+    while (c > 1 && 4 * parzen_fwd_smem(B, c) / c > 228 * 1024) c /= 2;
+    return c;
+}
+
+template <int RPW, bool SAMPLED, int COPIES>
+__global__ void __launch_bounds__(256 * COPIES)
     k_parzen_hist(ParzenPair P, const ParzenAffine *__restrict__ aff, int rows_per_cta, int SB,
                   unsigned long long *__restrict__ ghist, unsigned long long *__restrict__ gcount) {
     // Low-half sums [B x SB], then high-half sums.  The row stride SB >= B + 1 is 7 mod 32, so the
@@ -245,10 +263,11 @@ __global__ void __launch_bounds__(256)
     extern __shared__ uint32_t sh32[];
     const int t = blockIdx.y, B = P.B, B2 = B * B, NP = B * SB;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    uint32_t *lo16 = sh32, *hi16 = sh32 + NP;
+    const int CP = parzen_copy_offset(B, COPIES);  // offset between copies
+    uint32_t *lo16 = sh32 + (lane & (COPIES - 1)) * CP, *hi16 = lo16 + NP;
     __shared__ long long A[12];
     if (threadIdx.x < 12) A[threadIdx.x] = aff[t].A[threadIdx.x];
-    for (int c = threadIdx.x; c < 2 * NP; c += blockDim.x) sh32[c] = 0u;
+    for (int c = threadIdx.x; c < COPIES * CP; c += blockDim.x) sh32[c] = 0u;
     __syncthreads();
     const int nf0 = P.nf[0], nf1 = P.nf[1];
     const int n0 = P.nm[0], n1 = P.nm[1], n2 = P.nm[2];
@@ -343,7 +362,10 @@ __global__ void __launch_bounds__(256)
     unsigned long long *gh = ghist + (size_t)t * B2;
     for (int c = threadIdx.x; c < B2; c += blockDim.x) {
         const int cp = (c / B) * SB + c % B;
-        const unsigned long long v = (unsigned long long)lo16[cp] + ((unsigned long long)hi16[cp] << 16);
+        unsigned long long v = 0;
+#pragma unroll
+        for (int i = 0; i < COPIES; ++i)
+            v += (unsigned long long)sh32[i * CP + cp] + ((unsigned long long)sh32[i * CP + NP + cp] << 16);
         if (v) atomicAdd(gh + c, v);
     }
     if (lane == 0 && cnt) atomicAdd(gcount + t, (unsigned long long)cnt);
@@ -747,22 +769,34 @@ cudaError_t launch_parzen_hist(const ParzenPair &P, const ParzenAffine *d_aff, i
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(d_count, 0, (size_t)n * sizeof(unsigned long long), s)) != cudaSuccess) return e;
     const int SB = parzen_stride(P.B);
-    const size_t smem = 2 * (size_t)P.B * SB * sizeof(uint32_t);
-    const void *fn = P.srow ? (const void *)k_parzen_hist<kParzenRowsPerStep, true>
-                            : (const void *)k_parzen_hist<kParzenRowsPerStep, false>;
+    const int copies = parzen_fwd_copies(P.B);
+    const size_t smem = parzen_fwd_smem(P.B, copies);
+    const void *fn = nullptr;
+    switch (copies) {
+        case 4: fn = P.srow ? (const void *)k_parzen_hist<kParzenRowsPerStep, true, 4>
+                            : (const void *)k_parzen_hist<kParzenRowsPerStep, false, 4>;
+                break;
+        case 2: fn = P.srow ? (const void *)k_parzen_hist<kParzenRowsPerStep, true, 2>
+                            : (const void *)k_parzen_hist<kParzenRowsPerStep, false, 2>;
+                break;
+        default: fn = P.srow ? (const void *)k_parzen_hist<kParzenRowsPerStep, true, 1>
+                             : (const void *)k_parzen_hist<kParzenRowsPerStep, false, 1>;
+    }
     if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
-    // rows per CTA: at most kParzenMaxVox voxels (the 16-bit halves cannot overflow), and about
-    // `ctas` CTAs per transform when that is finer
+    // rows per CTA: at most kParzenMaxVox voxels per copy, so that the 16-bit halves cannot overflow
+    // (a row of nx voxels, or of at most nx sampled entries, is walked 32 lanes at a time, so copy i,
+    // fed by the lanes l = i mod C, takes at most 32 / C of every 32), and about `ctas` CTAs per
+    // transform when that is finer
     const long long R = (long long)P.nf[1] * P.nf[2];
-    long long rpc = kParzenMaxVox / P.nf[0];
+    long long rpc = kParzenMaxVox / ((32 / copies) * ((P.nf[0] + 31) / 32));
     const long long want = (R + ctas - 1) / ctas;
     if (want < rpc) rpc = want;
     if (rpc < 1) rpc = 1;
     dim3 grid((unsigned)((R + rpc - 1) / rpc), n);
     int rpci = (int)rpc, sb = SB;
     void *args[] = {(void *)&P, (void *)&d_aff, (void *)&rpci, (void *)&sb, (void *)&d_hist, (void *)&d_count};
-    return cudaLaunchKernel(fn, grid, dim3(256), args, smem, s);
+    return cudaLaunchKernel(fn, grid, dim3(256 * copies), args, smem, s);
 }
 
 cudaError_t launch_parzen_weights(const unsigned long long *d_hist, const unsigned long long *d_count, int n, int B,

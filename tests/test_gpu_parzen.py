@@ -121,3 +121,38 @@ def test_parzen_full_size_sampled(cuda_lib):
     mi, g = ctx.grad(prm, [1.0, 0.7, 1.3])
     assert np.all(np.isfinite(mi)) and np.all(np.isfinite(g))
     check(ctx, f, m, prm[:2], [1.0, 0.7, 1.3], B, shape_sp=((1, 1, 1.2), (1, 1, 1.2)))
+
+
+def test_parzen_forward_at_the_per_copy_voxel_cap(cuda_lib):
+    # rows of 16384 voxels, 208 rows, 50 poses: a forward CTA takes 16 rows, so at the identity each of
+    # its histogram copies (fed by every fourth lane) sums exactly 2^16 voxels' 16-bit weight halves,
+    # the most that fits
+    rng = np.random.default_rng(52)
+    nz, ny, nx = 52, 4, 16384
+    z = np.arange(nz)[:, None, None] / (nz - 1)
+    x = np.arange(nx)[None, None, :] / (nx - 1)
+    f = (0.25 + 0.5 * (z > 0.5) + 0.02 * rng.standard_normal((nz, ny, nx))).clip(0, 1).astype(np.float32)
+    m = (0.2 + 0.3 * z + 0.4 * x + 0.01 * rng.standard_normal((nz, ny, nx))).clip(0, 1).astype(np.float32)
+    B = 64
+    ctx = cuda_lib.Context(f, m, bins=B, kernel="parzen")
+    prm = np.tile(np.array([0, 0, 0, 0, 0, 0, 1, 1, 1], np.float32), (50, 1))
+    prm[25:, 0] = np.linspace(-4, 4, 25, dtype=np.float32)
+    qs = [1.0, 0.7, 1.3]
+    mi, g = ctx.grad(prm, qs)
+    for t in (0, 40):
+        aff, J = oracle.affine(prm[t], f.shape, (1, 1, 1), m.shape, (1, 1, 1), with_jacobian=True)
+        mi_o, g_o, n = oracle.parzen(f, m, aff, B, qs, daff=J)
+        assert np.all(np.abs(mi[t] - mi_o) <= MI_TOL * np.maximum(np.abs(mi_o), 1.0)), (t, mi[t], mi_o)
+        for iq in range(len(qs)):
+            assert np.abs(g[t, iq] - g_o[iq]).max() <= G_TOL * np.abs(g_o[iq]).max(), (t, iq, g[t, iq], g_o[iq])
+    # every identity pose gives the same soft histogram
+    assert np.all(mi[:25] == mi[0]) and np.all(g[:25] == g[0])
+
+
+@pytest.mark.parametrize("kernel", ["hard", "parzen"])
+def test_moving_volume_beyond_the_texture_extent_is_rejected(cuda_lib, kernel):
+    f = np.zeros((2, 2, 64), np.float32)
+    m = np.zeros((2, 2, 40000), np.float32)
+    with pytest.raises(cuda_lib.MIError) as e:
+        cuda_lib.Context(f, m, bins=16, kernel=kernel)
+    assert e.value.status == cuda_lib.MI_EUNSUPPORTED

@@ -293,6 +293,14 @@ mi_status mi_resample(mi_ctx *ctx, int pair, const int32_t *affine, void *out);
  * for the given number of transforms per call; -1 if none yet. */
 int mi_selected_variant(mi_ctx *ctx, int pair, int n);
 
+/* Test hook (failure handling): after `after` further successful device
+ * allocations by the library in this process, the next one fails as if the
+ * device were out of memory (the caller sees MI_ENOMEM), and the hook disarms
+ * itself; after < 0 disarms it.  It lets callers check that every entry point
+ * fails cleanly and leaves its context usable.  Host-side only: no GPU fault
+ * is raised. */
+void mi_fault_alloc(int after);
+
 /* Profiling hook: device time in milliseconds of the main histogram kernel(s)
  * of the last completed mi_eval / mi_eval_q16 / mi_batch_eval / mi_grad call,
  * measured with CUDA events recorded on the context's stream around those

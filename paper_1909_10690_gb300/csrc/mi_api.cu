@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <memory>
 #include <string>
@@ -27,6 +28,17 @@ thread_local std::string g_create_error;
 // Device / pinned buffers
 // ---------------------------------------------------------------------------
 
+// mi_fault_alloc: successful device allocations left before a simulated failure (-1: disarmed).
+std::atomic<int> g_fault_alloc{-1};
+
+// True if this allocation is the one to fail (and disarms the hook).
+bool fault_alloc_now() {
+    int v = g_fault_alloc.load();
+    while (v >= 0)
+        if (g_fault_alloc.compare_exchange_weak(v, v - 1)) return v == 0;
+    return false;
+}
+
 struct DevBuf {
     void *p = nullptr;
     size_t cap = 0;
@@ -39,6 +51,7 @@ struct DevBuf {
         p = nullptr;
         cap = 0;
         size_t want = std::max<size_t>(bytes, 256);
+        if (fault_alloc_now()) return cudaErrorMemoryAllocation;
         cudaError_t e = cudaMalloc(&p, want);
         if (e == cudaSuccess) cap = want;
         return e;
@@ -1303,6 +1316,8 @@ void mi_options_default(mi_options *opt) {
 const char *mi_version(void) { return "gb300-mi 0.1 (sm_103a)"; }
 
 int mi_transform_size(const mi_ctx *ctx) { return ctx ? ctx->nparams() : -1; }
+
+void mi_fault_alloc(int after) { g_fault_alloc.store(after < 0 ? -1 : after); }
 
 mi_status mi_create(mi_ctx **out, const mi_volume *fixed, const mi_volume *moving, int bins, const mi_options *opt) {
     return create_common(out, fixed, moving, &bins, 1, opt);

@@ -244,12 +244,22 @@ __host__ __device__ inline int parzen_copy_offset(int B, int copies) {
 __host__ inline size_t parzen_fwd_smem(int B, int copies) {
     return (size_t)copies * parzen_copy_offset(B, copies) * sizeof(uint32_t);
 }
-// Copies for B bins: the most (up to kParzenFwdMaxCopies) whose CTAs still fill an SM's 2048 threads,
-// i.e. while four copies fit the SM's 228 KB; one copy otherwise.
+// Copies for B bins: among the counts that keep the most threads resident per SM (at 64 registers a
+// thread at most 1024; 228 KB of shared memory per SM, 227 KB per CTA, 1 KB of it reserved per CTA),
+// the most copies.
 __host__ inline int parzen_fwd_copies(int B) {
-    int c = kParzenFwdMaxCopies;
-    while (c > 1 && 4 * parzen_fwd_smem(B, c) / c > 228 * 1024) c /= 2;
-    return c;
+    int best = 1, best_threads = 0;
+    for (int c = 1; c <= kParzenFwdMaxCopies; c *= 2) {
+        const size_t smem = parzen_fwd_smem(B, c);
+        if (smem > 227 * 1024) break;
+        const int by_smem = (int)((228 * 1024) / (smem + 1024)), by_regs = 1024 / (256 * c);
+        const int threads = (by_smem < by_regs ? by_smem : by_regs) * 256 * c;
+        if (threads >= best_threads) {
+            best = c;
+            best_threads = threads;
+        }
+    }
+    return best;
 }
 
 template <int RPW, bool SAMPLED, int COPIES>

@@ -42,7 +42,7 @@ def test_parzen_float_pair(cuda_lib):
     check(ctx, f, m, prm, [1.0, 0.7, 1.3], B)
 
 
-@pytest.mark.parametrize("B", [8, 64, 128])
+@pytest.mark.parametrize("B", [8, 64, 96, 128])  # forward with four, four, two and one histogram copies
 def test_parzen_integer_pair_and_bin_counts(cuda_lib, B):
     f, m = phantoms.head_pair(shape=(30, 34, 40), spacing=(1, 1, 1), seed=42)
     ctx = cuda_lib.Context(f, m, bins=B, kernel="parzen", fixed_depth=12, moving_depth=12)

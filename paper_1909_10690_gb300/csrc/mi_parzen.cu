@@ -222,9 +222,10 @@ __device__ __forceinline__ void bspline_dw(float t, float d[4]) {
 // the soft histogram, MI and gradient are bitwise reproducible.  A weight is
 // added as its two 16-bit halves into two 32-bit shared words per cell, with
 // fire-and-forget atomics (no returned value, so no latency on the voxel's
-// path).  A CTA covers at most 2^16 voxels, each adding at most once to a
-// cell, so neither word can overflow (2^16 x (2^16 - 1) < 2^32); at the end
-// the cell's 64-bit count, low + (high << 16), goes to the global histogram.
+// path).  A histogram copy sums at most 2^16 voxels, each adding at most once
+// to a cell, so neither word can overflow (2^16 x (2^16 - 1) < 2^32); at the
+// end the cell's 64-bit count, low + (high << 16) summed over the CTA's
+// copies, goes to the global histogram.
 constexpr int kParzenMaxVox = 65536;  // also the longest fixed row (MI_MAX_PARZEN_NX)
 constexpr int kParzenBankSkew = 7;    // row stride of the forward's shared histogram, mod 32
 constexpr bool kParzenFwdTex = true;   // forward gathers through the quad texture
@@ -234,9 +235,10 @@ constexpr int kParzenRowsPerStep = 1;  // rows a warp of the forward works on at
 // Row stride of the shared tables: the least SB >= B + 1 with SB = kParzenBankSkew (mod 32).
 __host__ __device__ inline int parzen_stride(int B) { return B + 1 + ((kParzenBankSkew - (B + 1)) % 32 + 32) % 32; }
 
-// Histogram copies per CTA of the forward: with C copies, lane l adds to copy l mod C (copy i shifted by
-// 32 i / C banks), which divides by C the lanes of a warp that hit one cell in one atomic instruction;
-// CTAs of 256 C threads keep the shared memory per SM of one copy per 256 threads.
+// Histogram copies per CTA of the forward: with C copies, lane l adds to copy l mod C (copy i starts
+// i (2 B SB + 32 / C) words in, so that one cell's copies fall in different banks), which divides by C
+// the lanes of a warp that hit one cell in one atomic instruction; CTAs of 256 C threads keep the
+// shared memory per SM of one copy per 256 threads.
 constexpr int kParzenFwdMaxCopies = 4;
 __host__ __device__ inline int parzen_copy_offset(int B, int copies) {
     return 2 * B * parzen_stride(B) + (copies > 1 ? 32 / copies : 0);

@@ -132,3 +132,28 @@ def test_affine12_autograd(cuda_lib):
     mi.sum().backward()
     _, g = ctx.grad(theta.detach(), [1.0])
     torch.testing.assert_close(theta.grad.double(), g[:, 0].double(), rtol=1e-6, atol=1e-9)
+
+
+def test_affine12_singular_and_reflection(cuda_lib):
+    rng = np.random.default_rng(72)
+    f = rng.integers(0, 4096, size=(21, 23, 25), dtype=np.uint16)
+    m = rng.integers(0, 4096, size=(21, 23, 25), dtype=np.uint16)
+    T = np.array([[0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0],              # M = 0: every voxel samples the centre
+                  [-1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0],             # mirror x
+                  [1, 0, 0, 0, 0, -1, 0, 0, 0, 0, -1, 0],            # half turn about x (det +1)
+                  [0, 0, 0, 2.5, 0, 1, 0, -1, 0, 0, 1, 0.5]], np.float32)  # rank 2, shifted
+    qs = [1.0, 0.5]
+    for path in ("plain", "batched"):
+        ctx = cuda_lib.Context(f, m, bins=32, fixed_depth=12, moving_depth=12, transform="affine", path=path)
+        mi, h, cnt = ctx.eval(T, qs, with_entropies=True)
+        q16 = np.stack([oracle.affine_q16(oracle.affine(p, f.shape, (1, 1, 1), m.shape, (1, 1, 1),
+                                                        transform="affine")) for p in T])
+        mi_o, h_o, cnt_o = oracle.mi_eval_q16(f, m, 32, q16, qs, fixed_depth=12, moving_depth=12)
+        np.testing.assert_array_equal(cnt, cnt_o)
+        assert np.all(np.abs(mi - mi_o) <= TOL * np.maximum(np.abs(mi_o), h_o[..., 2]))
+        H = ctx.hist(transforms=T, path=cuda_lib.PATH_BATCHED if path == "batched" else cuda_lib.PATH_PLAIN)
+        for k in range(len(T)):
+            ho, _ = oracle.joint_hist(f, m, q16[k], 32, 12, 12)
+            np.testing.assert_array_equal(H[k], ho.astype(np.uint32))
+    # M = 0: one moving bin, so the moving and joint entropies equal H(F) and H(M) = 0: MI = 0
+    np.testing.assert_allclose(mi[0], 0.0, atol=1e-12)

@@ -112,3 +112,28 @@ def test_affine12_parzen_gradient_matches_central_differences():
             fd[:, k] = (mp - mm) / (2 * h)
         for iq in range(3):
             assert np.abs(g[iq] - fd[iq]).max() / np.abs(fd[iq]).max() < 1e-6
+
+
+def test_affine12_singular_and_reflection_closed_forms():
+    # M = 0 sends every fixed voxel to the moving centre (an integer index for odd sizes): all counts fall
+    # in the centre value's bin, distributed like the fixed histogram.  M = diag(-1, 1, 1) mirrors x about
+    # the centre: fixed voxel (i, j, k) pairs with moving voxel (nx - 1 - i, j, k)
+    rng = np.random.default_rng(44)
+    f = rng.integers(0, 256, size=(5, 7, 9), dtype=np.uint8)
+    m = rng.integers(0, 256, size=(5, 7, 9), dtype=np.uint8)
+    bins = 16
+    bf = (f.astype(np.int64) * bins) >> 8
+    q = oracle.affine_q16(oracle.affine(_mt(np.zeros((3, 3)), [0, 0, 0]), f.shape, (1, 1, 1), m.shape, (1, 1, 1),
+                                        transform="affine"))
+    assert np.all(q[:, :3] == 0)
+    h, n = oracle.joint_hist(f, m, q, bins)
+    assert n == f.size
+    want = np.zeros((bins, bins), np.int64)
+    want[:, (int(m[2, 3, 4]) * bins) >> 8] = np.bincount(bf.ravel(), minlength=bins)
+    np.testing.assert_array_equal(h, want)
+    q = oracle.affine_q16(oracle.affine(_mt(np.diag([-1.0, 1.0, 1.0]), [0, 0, 0]), f.shape, (1, 1, 1), m.shape,
+                                        (1, 1, 1), transform="affine"))
+    h, n = oracle.joint_hist(f, m, q, bins)
+    bm = (m[:, :, ::-1].astype(np.int64) * bins) >> 8
+    assert n == f.size
+    np.testing.assert_array_equal(h, np.bincount((bf * bins + bm).ravel(), minlength=bins * bins).reshape(bins, bins))

@@ -1246,6 +1246,7 @@ mi_status parzen_core(mi_ctx *ctx, const std::vector<float> &prm, int n, const f
     }
     pp.B = B;
     const int ctas = parzen_ctas(pp, n, ctx->sms);
+    const int actas = out_grad ? parzen_adj_ctas(pp, n, nq, ctx->sms) : 1;
     const int cblocks = parzen_cell_blocks(B);
     MI_CU(ctx->p_aff.ensure((size_t)n * sizeof(ParzenAffine)), "alloc");
     MI_CU(ctx->p_jac.ensure((size_t)n * 12 * np * 8), "alloc");
@@ -1256,7 +1257,7 @@ mi_status parzen_core(mi_ctx *ctx, const std::vector<float> &prm, int n, const f
     MI_CU(ctx->p_mterm.ensure((size_t)n * nq * 2 * B * 8), "alloc");
     MI_CU(ctx->p_jsum.ensure((size_t)n * nq * cblocks * 8), "alloc");
     MI_CU(ctx->p_w.ensure((size_t)n * nq * B2 * 4), "alloc");
-    MI_CU(ctx->p_mom.ensure((size_t)n * nq * ctas * 12 * 8), "alloc");
+    MI_CU(ctx->p_mom.ensure((size_t)n * nq * actas * 12 * 8), "alloc");
     MI_CU(ctx->p_grad.ensure((size_t)n * nq * np * 8), "alloc");
     MI_CU(ctx->d_mi.ensure((size_t)n * nq * 8), "alloc");
     MI_CU(cudaMemcpyAsync(ctx->p_aff.p, pa.data(), (size_t)n * sizeof(ParzenAffine), cudaMemcpyHostToDevice, s), "H2D");
@@ -1271,7 +1272,7 @@ mi_status parzen_core(mi_ctx *ctx, const std::vector<float> &prm, int n, const f
                                 ctx->p_w.as<float>(), s),
           "Parzen entropies");
     if (out_grad)
-        MI_CU(launch_parzen_adjoint(pp, d_aff, ctx->p_jac.as<double>(), np, n, nq, ctas, ctx->p_w.as<float>(), cnt,
+        MI_CU(launch_parzen_adjoint(pp, d_aff, ctx->p_jac.as<double>(), np, n, nq, actas, ctx->p_w.as<float>(), cnt,
                                     ctx->p_mom.as<double>(), ctx->p_grad.as<double>(), s),
               "Parzen adjoint");
     MI_CU(cudaEventRecord(ctx->ev1, s), "event");

@@ -135,6 +135,8 @@ cudaError_t launch_parzen_prep_moving(const void *data, int dtype, int depth, lo
                                       cudaStream_t s);
 // CTAs per transform of the Parzen voxel kernels, and blocks of the per-cell kernel.
 int parzen_ctas(const ParzenPair &P, int n, int sms);
+// CTAs per transform of the adjoint for nq q values: whole waves of its resident CTAs.
+int parzen_adj_ctas(const ParzenPair &P, int n, int nq, int sms);
 // The extended moving volume: out has dims (n0 + 1, n1 + 1, n2 + 1); on the extra planes each axis
 // continues linearly (v[n] = 2 v[n - 1] - v[n - 2]), so that the trilinear cell of an index on the
 // last plane can be its integer part: the value there is v[n - 1] and the derivative along the axis

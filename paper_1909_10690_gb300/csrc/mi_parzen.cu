@@ -760,6 +760,47 @@ int parzen_ctas(const ParzenPair &P, int n, int sms) {
     return (int)per_t;
 }
 
+// Shared memory of an adjoint launch over g q values: the W pairs when they fit, else none.
+static size_t parzen_adj_smem(int B, int g) {
+    const size_t wbytes = (size_t)g * B * parzen_stride(B) * sizeof(float2);
+    return wbytes <= 110 * 1024 ? wbytes : 0;
+}
+
+template <int NQ, bool SAMPLED>
+static int adj_blocks_per_sm(size_t smem) {
+    int nb = 0;
+    if (cudaFuncSetAttribute(k_parzen_adj<NQ, SAMPLED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_parzen_adj<NQ, SAMPLED>, 256, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return nb > 0 ? nb : 1;
+}
+
+int parzen_adj_ctas(const ParzenPair &P, int n, int nq, int sms) {
+    // every CTA of the adjoint does about the same work, so the grid is cut to whole waves of the
+    // CTAs that fit at once (those of the first q group's instance): the nearest whole number of
+    // waves to the usual ~4 CTAs per SM, then the most CTAs per transform that fill it
+    const int g = nq < 4 ? nq : 4;
+    const size_t smem = parzen_adj_smem(P.B, g);
+    int per_sm = 1;
+    switch (g) {
+        case 1: per_sm = P.srow ? adj_blocks_per_sm<1, true>(smem) : adj_blocks_per_sm<1, false>(smem); break;
+        case 2: per_sm = P.srow ? adj_blocks_per_sm<2, true>(smem) : adj_blocks_per_sm<2, false>(smem); break;
+        case 3: per_sm = P.srow ? adj_blocks_per_sm<3, true>(smem) : adj_blocks_per_sm<3, false>(smem); break;
+        default: per_sm = P.srow ? adj_blocks_per_sm<4, true>(smem) : adj_blocks_per_sm<4, false>(smem);
+    }
+    const long long cap = (long long)per_sm * sms, c0 = parzen_ctas(P, n, sms);
+    long long waves = ((long long)n * c0 + cap / 2) / cap;
+    if (waves < 1) waves = 1;
+    long long c = waves * cap / n;
+    const long long max_c = ((long long)P.nf[1] * P.nf[2] + 7) / 8;  // at least a row per warp
+    if (c > max_c) c = max_c;
+    if (c < 1) c = 1;
+    return (int)c;
+}
+
 int parzen_cell_blocks(int B) { return (B * B + 255) / 256; }
 
 cudaError_t launch_parzen_extend(const float *mov, const int nm[3], float *out, cudaStream_t s) {
@@ -832,9 +873,8 @@ cudaError_t launch_parzen_adjoint(const ParzenPair &P, const ParzenAffine *d_aff
     dim3 grid(ctas, n);
     for (int q0 = 0; q0 < nq; q0 += 4) {
         const int g = nq - q0 < 4 ? nq - q0 : 4;
-        const size_t wbytes = (size_t)g * P.B * parzen_stride(P.B) * sizeof(float2);
-        const int in_smem = wbytes <= 110 * 1024;
-        const size_t smem = in_smem ? wbytes : 0;
+        const size_t smem = parzen_adj_smem(P.B, g);
+        const int in_smem = smem > 0;
 #define MI_ADJ_S(NQV, SV)                                                                                   \
     do {                                                                                                    \
         if ((e = cudaFuncSetAttribute(k_parzen_adj<NQV, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \

@@ -1245,7 +1245,6 @@ mi_status parzen_core(mi_ctx *ctx, const std::vector<float> &prm, int n, const f
         pp.nm[a] = P.nm[a];
     }
     pp.B = B;
-    const int ctas = parzen_ctas(pp, n, ctx->sms);
     const int actas = out_grad ? parzen_adj_ctas(pp, n, nq, ctx->sms) : 1;
     const int cblocks = parzen_cell_blocks(B);
     MI_CU(ctx->p_aff.ensure((size_t)n * sizeof(ParzenAffine)), "alloc");
@@ -1266,7 +1265,7 @@ mi_status parzen_core(mi_ctx *ctx, const std::vector<float> &prm, int n, const f
     auto *cnt = ctx->p_cnt.as<unsigned long long>();
     auto *hist = ctx->p_hist.as<unsigned long long>();
     MI_CU(cudaEventRecord(ctx->ev0, s), "event");
-    MI_CU(launch_parzen_hist(pp, d_aff, n, ctas, hist, cnt, s), "Parzen histogram");
+    MI_CU(launch_parzen_hist(pp, d_aff, n, ctx->sms, hist, cnt, s), "Parzen histogram");
     MI_CU(launch_parzen_weights(hist, cnt, n, B, Q, ctx->p_marg.as<double>(), ctx->p_ment.as<double>(),
                                 ctx->p_mterm.as<double>(), ctx->p_jsum.as<double>(), ctx->d_mi.as<double>(),
                                 ctx->p_w.as<float>(), s),

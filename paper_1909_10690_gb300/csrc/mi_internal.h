@@ -147,7 +147,8 @@ cudaError_t launch_parzen_extend(const float *mov, const int nm[3], float *out, 
 cudaError_t launch_parzen_quads(const float *movx, const int nm[3], void *out, cudaStream_t s);
 int parzen_cell_blocks(int B);
 // Soft histograms (n x B^2 u64 sums of 2^-32-quantised weights, zeroed here) and overlap counts (n).
-cudaError_t launch_parzen_hist(const ParzenPair &P, const ParzenAffine *d_aff, int n, int ctas,
+// sms: the device's SM count (the grid is sized in whole waves).
+cudaError_t launch_parzen_hist(const ParzenPair &P, const ParzenAffine *d_aff, int n, int sms,
                                unsigned long long *d_hist, unsigned long long *d_count, cudaStream_t s);
 // MI per q (n x nq) and the weight tables W (n x nq x B^2, FP32) from the soft histograms.
 // Scratch: marg (n x 2B), ment (n x nq x 2), mterm (n x nq x 2B), jpart (n x nq x parzen_cell_blocks(B)) FP64.

@@ -266,121 +266,134 @@ __host__ inline int parzen_fwd_copies(int B) {
 
 template <int RPW, bool SAMPLED, int COPIES>
 __global__ void __launch_bounds__(256 * COPIES)
-    k_parzen_hist(ParzenPair P, const ParzenAffine *__restrict__ aff, int rows_per_cta, int SB,
-                  unsigned long long *__restrict__ ghist, unsigned long long *__restrict__ gcount) {
+    k_parzen_hist(ParzenPair P, const ParzenAffine *__restrict__ aff, long long rows_per_cta, long long total_rows,
+                  int SB, unsigned long long *__restrict__ ghist, unsigned long long *__restrict__ gcount) {
     // Low-half sums [B x SB], then high-half sums.  The row stride SB >= B + 1 is 7 mod 32, so the
     // bank of cell (fixed bin b, moving bin k) is (k + 7 b) mod 32: the cells of neighbouring voxels,
     // which differ by a bin or two on either axis, fall in different banks.  Column B absorbs the
     // zero weight of bin B (m~ = B - 2 exactly).
+    // The rows of all transforms form one sequence (transform t owns rows t R .. t R + R - 1); CTA b
+    // takes rows_per_cta of them from b rows_per_cta on, one transform segment at a time, and flushes
+    // its histogram after each segment.
     extern __shared__ uint32_t sh32[];
-    const int t = blockIdx.y, B = P.B, B2 = B * B, NP = B * SB;
+    const int B = P.B, B2 = B * B, NP = B * SB;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int CP = parzen_copy_offset(B, COPIES);  // offset between copies
     uint32_t *lo16 = sh32 + (lane & (COPIES - 1)) * CP, *hi16 = lo16 + NP;
     __shared__ long long A[12];
-    if (threadIdx.x < 12) A[threadIdx.x] = aff[t].A[threadIdx.x];
     for (int c = threadIdx.x; c < COPIES * CP; c += blockDim.x) sh32[c] = 0u;
-    __syncthreads();
     const int nf0 = P.nf[0], nf1 = P.nf[1];
     const int n0 = P.nm[0], n1 = P.nm[1], n2 = P.nm[2];
     const long long R = (long long)nf1 * P.nf[2];
-    const long long r0 = (long long)blockIdx.x * rows_per_cta;
-    const long long r1 = r0 + rows_per_cta < R ? r0 + rows_per_cta : R;
+    const long long c0 = (long long)blockIdx.x * rows_per_cta;
+    const long long c1 = c0 + rows_per_cta < total_rows ? c0 + rows_per_cta : total_rows;
     const float Bm4 = (float)(B - 4);
     // a warp works on RPW rows at a time, G = 32 / RPW neighbouring voxels of each: the lanes that
     // add to one cell at once are then at most the G of a row (neighbouring voxels mostly share
     // cells, and same-address shared atomics queue), while each row's gathers stay coalesced
     constexpr int G = 32 / RPW;
     const int sub = lane / G, pos = lane % G;
-    const long long DG0 = G * A[0], DG1 = G * A[4], DG2 = G * A[8];
-    unsigned int cnt = 0;  // overlap voxels counted by this lane
-    // one voxel at 32.32 index U with fixed bin bf: its four quantised B-spline weights
-    auto add_voxel = [&](long long U0, long long U1, long long U2, int bf) {
-        const MG g3 = kParzenFwdTex ? trilinear_q<false>(P.texq, U0, U1, U2)
-                                    : trilinear_x<false>(P.movx, P.nm[0] + 1, (P.nm[0] + 1) * (P.nm[1] + 1), U0,
-                                                         U1, U2);
-        const float mt = fmaf(fminf(fmaxf(g3.m, 0.0f), 1.0f), Bm4, 2.0f);
-        const int k0 = (int)mt;
-        float w[4];
-        bspline_w(mt - (float)k0, w);
-        // every quantised weight is below 2^32 (at most (2/3) 2^32)
-        const uint32_t q0 = __float2uint_rn(w[0] * 4294967296.0f);
-        const uint32_t q2 = __float2uint_rn(w[2] * 4294967296.0f);
-        const uint32_t q3 = __float2uint_rn(w[3] * 4294967296.0f);
-        const uint32_t q1 = 0u - q0 - q2 - q3;  // 2^32 - (q0 + q2 + q3)
-        const int c = bf * SB + (k0 - 1);
-        atomicAdd(lo16 + c, q0 & 0xffffu);
-        atomicAdd(hi16 + c, q0 >> 16);
-        atomicAdd(lo16 + c + 1, q1 & 0xffffu);
-        atomicAdd(hi16 + c + 1, q1 >> 16);
-        atomicAdd(lo16 + c + 2, q2 & 0xffffu);
-        atomicAdd(hi16 + c + 2, q2 >> 16);
-        atomicAdd(lo16 + c + 3, q3 & 0xffffu);
-        atomicAdd(hi16 + c + 3, q3 >> 16);
-    };
-    // warp w takes rows r0 + w + nwarps n; a group of 32 of them is clipped at once (lane l: row l)
-    for (long long g = r0 + warp; g < r1; g += 32LL * nwarps) {
-        Clip64 mine;
-        mine.lo = 1;
-        mine.hi = 0;
-        mine.u0 = mine.u1 = mine.u2 = 0;
-        const long long rl = g + (long long)nwarps * lane;
-        if (rl < r1) mine = clip_row64(A, rl % nf1, rl / nf1, nf0, n0, n1, n2);
-        if constexpr (SAMPLED) {  // random sampling: each row's sampled voxels inside its interval
-            for (int s = 0; s < 32; ++s) {
-                const long long r = g + (long long)nwarps * s;
-                if (r >= r1) break;  // warp-uniform
-                const int lo = __shfl_sync(kFull, mine.lo, s), hi = __shfl_sync(kFull, mine.hi, s);
-                if (lo > hi) continue;
-                const long long ub0 = __shfl_sync(kFull, mine.u0, s), ub1 = __shfl_sync(kFull, mine.u1, s),
-                                ub2 = __shfl_sync(kFull, mine.u2, s);
-                const uint32_t e0 = __ldg(P.srow + r), e1 = __ldg(P.srow + r + 1);
-                for (uint32_t eb = e0; eb < e1; eb += 32) {
-                    const uint32_t e = eb + lane;
-                    const int i = e < e1 ? (int)__ldg(P.scol + e) : -1;
-                    if (e < e1 && i >= lo && i <= hi) {
-                        const long long d = i - lo;
-                        add_voxel(ub0 + A[0] * d, ub1 + A[4] * d, ub2 + A[8] * d, (int)__ldg(P.sbin + e));
-                        ++cnt;
+    for (long long s0 = c0; s0 < c1;) {
+        const int t = (int)(s0 / R);
+        const long long r0 = s0 - t * R, r1 = c1 - t * R < R ? c1 - t * R : R;
+        if (threadIdx.x < 12) A[threadIdx.x] = aff[t].A[threadIdx.x];
+        __syncthreads();
+        const long long DG0 = G * A[0], DG1 = G * A[4], DG2 = G * A[8];
+        unsigned int cnt = 0;  // overlap voxels counted by this lane
+        // one voxel at 32.32 index U with fixed bin bf: its four quantised B-spline weights
+        auto add_voxel = [&](long long U0, long long U1, long long U2, int bf) {
+            const MG g3 = kParzenFwdTex ? trilinear_q<false>(P.texq, U0, U1, U2)
+                                        : trilinear_x<false>(P.movx, P.nm[0] + 1, (P.nm[0] + 1) * (P.nm[1] + 1),
+                                                             U0, U1, U2);
+            const float mt = fmaf(fminf(fmaxf(g3.m, 0.0f), 1.0f), Bm4, 2.0f);
+            const int k0 = (int)mt;
+            float w[4];
+            bspline_w(mt - (float)k0, w);
+            // every quantised weight is below 2^32 (at most (2/3) 2^32)
+            const uint32_t q0 = __float2uint_rn(w[0] * 4294967296.0f);
+            const uint32_t q2 = __float2uint_rn(w[2] * 4294967296.0f);
+            const uint32_t q3 = __float2uint_rn(w[3] * 4294967296.0f);
+            const uint32_t q1 = 0u - q0 - q2 - q3;  // 2^32 - (q0 + q2 + q3)
+            const int c = bf * SB + (k0 - 1);
+            atomicAdd(lo16 + c, q0 & 0xffffu);
+            atomicAdd(hi16 + c, q0 >> 16);
+            atomicAdd(lo16 + c + 1, q1 & 0xffffu);
+            atomicAdd(hi16 + c + 1, q1 >> 16);
+            atomicAdd(lo16 + c + 2, q2 & 0xffffu);
+            atomicAdd(hi16 + c + 2, q2 >> 16);
+            atomicAdd(lo16 + c + 3, q3 & 0xffffu);
+            atomicAdd(hi16 + c + 3, q3 >> 16);
+        };
+        // warp w takes rows r0 + w + nwarps n; a group of 32 of them is clipped at once (lane l: row l)
+        for (long long g = r0 + warp; g < r1; g += 32LL * nwarps) {
+            Clip64 mine;
+            mine.lo = 1;
+            mine.hi = 0;
+            mine.u0 = mine.u1 = mine.u2 = 0;
+            const long long rl = g + (long long)nwarps * lane;
+            if (rl < r1) mine = clip_row64(A, rl % nf1, rl / nf1, nf0, n0, n1, n2);
+            if constexpr (SAMPLED) {  // random sampling: each row's sampled voxels inside its interval
+                for (int s = 0; s < 32; ++s) {
+                    const long long r = g + (long long)nwarps * s;
+                    if (r >= r1) break;  // warp-uniform
+                    const int lo = __shfl_sync(kFull, mine.lo, s), hi = __shfl_sync(kFull, mine.hi, s);
+                    if (lo > hi) continue;
+                    const long long ub0 = __shfl_sync(kFull, mine.u0, s), ub1 = __shfl_sync(kFull, mine.u1, s),
+                                    ub2 = __shfl_sync(kFull, mine.u2, s);
+                    const uint32_t e0 = __ldg(P.srow + r), e1 = __ldg(P.srow + r + 1);
+                    for (uint32_t eb = e0; eb < e1; eb += 32) {
+                        const uint32_t e = eb + lane;
+                        const int i = e < e1 ? (int)__ldg(P.scol + e) : -1;
+                        if (e < e1 && i >= lo && i <= hi) {
+                            const long long d = i - lo;
+                            add_voxel(ub0 + A[0] * d, ub1 + A[4] * d, ub2 + A[8] * d, (int)__ldg(P.sbin + e));
+                            ++cnt;
+                        }
+                    }
+                }
+            } else {
+                for (int s = 0; s < 32; s += RPW) {
+                    if (g + (long long)nwarps * s >= r1) break;  // warp-uniform: the rest of the group is past r1
+                    const int src = s + sub;
+                    const long long r = g + (long long)nwarps * src;
+                    int lo = __shfl_sync(kFull, mine.lo, src), hi = __shfl_sync(kFull, mine.hi, src);
+                    if (r >= r1) hi = lo - 1;
+                    const int len = hi - lo + 1 > 0 ? hi - lo + 1 : 0;
+                    if (pos == 0) cnt += (unsigned)len;
+                    const int nsteps = __reduce_max_sync(kFull, (unsigned)((len + G - 1) / G));
+                    long long U0 = __shfl_sync(kFull, mine.u0, src) + A[0] * pos;
+                    long long U1 = __shfl_sync(kFull, mine.u1, src) + A[4] * pos;
+                    long long U2 = __shfl_sync(kFull, mine.u2, src) + A[8] * pos;
+                    const uint8_t *__restrict__ frow = P.fbins + (size_t)(r < r1 ? r : r0) * nf0;
+                    for (int k = 0; k < nsteps; ++k) {
+                        const int i = lo + k * G + pos;
+                        if (i <= hi) add_voxel(U0, U1, U2, (int)__ldg(frow + i));
+                        U0 += DG0;
+                        U1 += DG1;
+                        U2 += DG2;
                     }
                 }
             }
-            continue;
         }
-        for (int s = 0; s < 32; s += RPW) {
-            if (g + (long long)nwarps * s >= r1) break;  // warp-uniform: the rest of the group is past r1
-            const int src = s + sub;
-            const long long r = g + (long long)nwarps * src;
-            int lo = __shfl_sync(kFull, mine.lo, src), hi = __shfl_sync(kFull, mine.hi, src);
-            if (r >= r1) hi = lo - 1;
-            const int len = hi - lo + 1 > 0 ? hi - lo + 1 : 0;
-            if (pos == 0) cnt += (unsigned)len;
-            const int nsteps = __reduce_max_sync(kFull, (unsigned)((len + G - 1) / G));
-            long long U0 = __shfl_sync(kFull, mine.u0, src) + A[0] * pos;
-            long long U1 = __shfl_sync(kFull, mine.u1, src) + A[4] * pos;
-            long long U2 = __shfl_sync(kFull, mine.u2, src) + A[8] * pos;
-            const uint8_t *__restrict__ frow = P.fbins + (size_t)(r < r1 ? r : r0) * nf0;
-            for (int k = 0; k < nsteps; ++k) {
-                const int i = lo + k * G + pos;
-                if (i <= hi) add_voxel(U0, U1, U2, (int)__ldg(frow + i));
-                U0 += DG0;
-                U1 += DG1;
-                U2 += DG2;
-            }
-        }
-    }
-    cnt = __reduce_add_sync(kFull, cnt);
-    __syncthreads();
-    unsigned long long *gh = ghist + (size_t)t * B2;
-    for (int c = threadIdx.x; c < B2; c += blockDim.x) {
-        const int cp = (c / B) * SB + c % B;
-        unsigned long long v = 0;
+        cnt = __reduce_add_sync(kFull, cnt);
+        __syncthreads();
+        unsigned long long *gh = ghist + (size_t)t * B2;
+        for (int c = threadIdx.x; c < B2; c += blockDim.x) {
+            const int cp = (c / B) * SB + c % B;
+            unsigned long long v = 0;
 #pragma unroll
-        for (int i = 0; i < COPIES; ++i)
-            v += (unsigned long long)sh32[i * CP + cp] + ((unsigned long long)sh32[i * CP + NP + cp] << 16);
-        if (v) atomicAdd(gh + c, v);
+            for (int i = 0; i < COPIES; ++i)
+                v += (unsigned long long)sh32[i * CP + cp] + ((unsigned long long)sh32[i * CP + NP + cp] << 16);
+            if (v) atomicAdd(gh + c, v);
+        }
+        if (lane == 0 && cnt) atomicAdd(gcount + t, (unsigned long long)cnt);
+        s0 = (long long)(t + 1) * R;
+        if (s0 < c1) {  // another transform follows: start from empty copies
+            __syncthreads();
+            for (int c = threadIdx.x; c < COPIES * CP; c += blockDim.x) sh32[c] = 0u;
+        }
+        __syncthreads();
     }
-    if (lane == 0 && cnt) atomicAdd(gcount + t, (unsigned long long)cnt);
 }
 
 __global__ void k_parzen_quads(const float *__restrict__ movx, int n0, int n1, int n2, float4 *__restrict__ out) {
@@ -815,7 +828,7 @@ cudaError_t launch_parzen_quads(const float *movx, const int nm[3], void *out, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_parzen_hist(const ParzenPair &P, const ParzenAffine *d_aff, int n, int ctas,
+cudaError_t launch_parzen_hist(const ParzenPair &P, const ParzenAffine *d_aff, int n, int sms,
                                unsigned long long *d_hist, unsigned long long *d_count, cudaStream_t s) {
     const size_t B2 = (size_t)P.B * P.B;
     cudaError_t e = cudaMemsetAsync(d_hist, 0, (size_t)n * B2 * sizeof(unsigned long long), s);
@@ -839,16 +852,25 @@ cudaError_t launch_parzen_hist(const ParzenPair &P, const ParzenAffine *d_aff, i
         return e;
     // rows per CTA: at most kParzenMaxVox voxels per copy, so that the 16-bit halves cannot overflow
     // (a row of nx voxels, or of at most nx sampled entries, is walked 32 lanes at a time, so copy i,
-    // fed by the lanes l = i mod C, takes at most 32 / C of every 32), and about `ctas` CTAs per
-    // transform when that is finer
-    const long long R = (long long)P.nf[1] * P.nf[2];
-    long long rpc = kParzenMaxVox / ((32 / copies) * ((P.nf[0] + 31) / 32));
-    const long long want = (R + ctas - 1) / ctas;
-    if (want < rpc) rpc = want;
-    if (rpc < 1) rpc = 1;
-    dim3 grid((unsigned)((R + rpc - 1) / rpc), n);
-    int rpci = (int)rpc, sb = SB;
-    void *args[] = {(void *)&P, (void *)&d_aff, (void *)&rpci, (void *)&sb, (void *)&d_hist, (void *)&d_count};
+    // fed by the lanes l = i mod C, takes at most 32 / C of every 32); CTAs do equal shares of the
+    // rows of all transforms, as many as fill a whole number of waves of the CTAs resident at once
+    const long long R = (long long)P.nf[1] * P.nf[2], TR = R * n;
+    long long cap = kParzenMaxVox / ((32 / copies) * ((P.nf[0] + 31) / 32));
+    if (cap < 1) cap = 1;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256 * copies, smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const long long wave = (long long)per_sm * (sms > 0 ? sms : 1);
+    long long nch = (TR + cap - 1) / cap;
+    nch = (nch + wave - 1) / wave * wave;
+    if (nch > TR) nch = TR;
+    long long rpc = (TR + nch - 1) / nch, total = TR;
+    dim3 grid((unsigned)((TR + rpc - 1) / rpc));
+    int sb = SB;
+    void *args[] = {(void *)&P, (void *)&d_aff, (void *)&rpc, (void *)&total, (void *)&sb, (void *)&d_hist,
+                    (void *)&d_count};
     return cudaLaunchKernel(fn, grid, dim3(256 * copies), args, smem, s);
 }
 

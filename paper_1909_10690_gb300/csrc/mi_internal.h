@@ -133,7 +133,8 @@ cudaError_t launch_parzen_prep_fixed(const void *data, int dtype, int depth, lon
                                      cudaStream_t s);
 cudaError_t launch_parzen_prep_moving(const void *data, int dtype, int depth, long long n, float *out,
                                       cudaStream_t s);
-// CTAs per transform of the Parzen voxel kernels, and blocks of the per-cell kernel.
+// About 4 CTAs per SM over n transforms, as CTAs per transform (the adjoint's starting point), and
+// blocks of the per-cell kernel.
 int parzen_ctas(const ParzenPair &P, int n, int sms);
 // CTAs per transform of the adjoint for nq q values: whole waves of its resident CTAs.
 int parzen_adj_ctas(const ParzenPair &P, int n, int nq, int sms);

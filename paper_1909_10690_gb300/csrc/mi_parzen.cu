@@ -830,6 +830,7 @@ cudaError_t launch_parzen_quads(const float *movx, const int nm[3], void *out, c
 
 cudaError_t launch_parzen_hist(const ParzenPair &P, const ParzenAffine *d_aff, int n, int sms,
                                unsigned long long *d_hist, unsigned long long *d_count, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
     const size_t B2 = (size_t)P.B * P.B;
     cudaError_t e = cudaMemsetAsync(d_hist, 0, (size_t)n * B2 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;

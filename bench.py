@@ -41,7 +41,7 @@ ALG_OPS_PER_VOXT = 50
 # DRAM bytes (read + write) of one full k_batched launch (4096 transforms), from one ncu capture of
 # dram__bytes_read.sum + dram__bytes_write.sum; reported only while the kernel source and the
 # selected variant are the ones measured
-K_BATCHED_TRAFFIC = {"variant": 10, "source_sha16": "2165ee9351c419de", "bytes_per_launch": 384.09e9 + 29.8e6}
+K_BATCHED_TRAFFIC = {"variant": 10, "source_sha16": "92956c2f74dac179", "bytes_per_launch": 367.8976e9 + 30.3e6}
 # algorithmic FP32 operations per voxel x transform of the Parzen MI + gradient at 3 q values:
 # forward 31 (trilinear 14, bin coordinate 1, B-spline weights 12, 4 increments),
 # adjoint 89 (trilinear value and gradient 23, bin coordinate 1, B-spline derivatives 8, 3 q x 19)

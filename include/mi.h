@@ -301,6 +301,14 @@ int mi_selected_variant(mi_ctx *ctx, int pair, int n);
  * is raised. */
 void mi_fault_alloc(int after);
 
+/* Test hook (failure handling): the iteration cap of the one retry loop in
+ * the kernels, the compare-and-swap that drains a 16-bit counter
+ * (MI_HV_U16* variants), on the current device; default 65536.  With 0 every
+ * drain gives up at once: the kernel flags the error and finishes, and the
+ * call reports MI_ECUDA.  Returns MI_EINVAL for cap < 0, MI_ECUDA if the
+ * device write fails. */
+mi_status mi_fault_drain_cap(int cap);
+
 /* Profiling hook: device time in milliseconds of the main histogram kernel(s)
  * of the last completed mi_eval / mi_eval_q16 / mi_batch_eval / mi_grad call,
  * measured with CUDA events recorded on the context's stream around those

@@ -98,6 +98,7 @@ SIGNATURES = {
     "mi_destroy": (None, [_P]),
     "mi_transform_size": (_I, [_P]),
     "mi_fault_alloc": (None, [_I]),
+    "mi_fault_drain_cap": (_I, [_I]),
     "mi_last_error": (ctypes.c_char_p, [_P]),
     "mi_set_stream": (_I, [_P, _P]),
     "mi_eval": (_I, [_P, _P, _I, _P, _I, _P, _P, _P]),

@@ -1319,6 +1319,11 @@ int mi_transform_size(const mi_ctx *ctx) { return ctx ? ctx->nparams() : -1; }
 
 void mi_fault_alloc(int after) { g_fault_alloc.store(after < 0 ? -1 : after); }
 
+mi_status mi_fault_drain_cap(int cap) {
+    if (cap < 0) return MI_EINVAL;
+    return set_drain_cap(cap) == cudaSuccess ? MI_OK : MI_ECUDA;
+}
+
 mi_status mi_create(mi_ctx **out, const mi_volume *fixed, const mi_volume *moving, int bins, const mi_options *opt) {
     return create_common(out, fixed, moving, &bins, 1, opt);
 }

@@ -314,6 +314,10 @@ struct HistU32 {
 // kDrainT + (threads x 32) < 2^16.  The true count is the 16-bit value plus
 // the overflow entry (flagged in a bitmap).  Overflow entries are keyed by
 // the cell id bf * B + bm.
+// Iteration cap of the drain's compare-and-swap loop (a failure-handling test hook lowers it; at 0
+// every drain gives up at once and flags the error).
+__device__ int g_drain_cap = 1 << 16;
+
 template <bool MATCH>
 struct HistU16 {
     uint32_t *w;      // H x S words
@@ -355,8 +359,9 @@ struct HistU16 {
     }
     __device__ void drain(uint32_t idx, uint32_t sh, uint32_t key) {
         volatile uint32_t *vw = w;
+        const int cap = g_drain_cap;
         // each failed attempt means another update of this word succeeded; bounded for safety
-        for (int it = 0; it < 1 << 16; ++it) {
+        for (int it = 0; it < cap; ++it) {
             const uint32_t cur = vw[idx];
             const uint32_t hv = (cur >> sh) & 0xffffu;
             if (hv < (uint32_t)kDrainT) return;
@@ -1158,6 +1163,8 @@ cudaError_t launch_resample(const PairDev *d_pair, const PairDev &h_pair, const 
         k_resample<uint16_t><<<grid_for(n, 256), 256, 0, s>>>(d_pair, d_aff, (uint16_t *)out);
     return cudaGetLastError();
 }
+
+cudaError_t set_drain_cap(int cap) { return cudaMemcpyToSymbol(g_drain_cap, &cap, sizeof cap); }
 
 }  // namespace mi
 

@@ -93,6 +93,8 @@ cudaError_t launch_make_pairs(const void *mov, int dtype, const int nm[3], void 
 // 2 x 2 quads of the moving volume, dims (n0, n1, n2): element (x, y, z) holds
 // v(x, y), v(x + 1, y), v(x, y + 1), v(x + 1, y + 1) of plane z, upper indices
 // clamped to the last ones (uchar4 for uint8, ushort4 for uint16 volumes).
+// Iteration cap of the 16-bit counter drain on the current device (default 2^16; test hook).
+cudaError_t set_drain_cap(int cap);
 cudaError_t launch_make_quads(const void *mov, int dtype, const int nm[3], void *out, cudaStream_t s);
 cudaError_t launch_bin_fixed(const void *data, int dtype, int depth, long long n, int bins, uint8_t *out,
                              cudaStream_t s);

@@ -66,3 +66,25 @@ def test_calls_fail_cleanly_and_the_context_stays_usable(cuda_lib, fault):
     mi1, g1 = pz.grad(prm[:3], qs)
     np.testing.assert_array_equal(mi0, mi1)
     np.testing.assert_array_equal(g0, g1)
+
+
+def test_drain_give_up_is_reported_and_the_context_recovers(cuda_lib):
+    # 16-bit counters (MI_HV_U16) drain into the overflow table at 2^14 by a bounded compare-and-swap
+    # loop; with its cap at 0 every drain gives up, the kernel flags it and finishes, and the call
+    # reports MI_ECUDA.  A constant pair puts all 64000 voxels in one cell, so drains happen.
+    lib = cuda_lib.load()
+    f = np.full((40, 40, 40), 1000, np.uint16)
+    ctx = cuda_lib.Context(f, f, bins=16, fixed_depth=12, moving_depth=12, hist_variant=cuda_lib.HV_U16,
+                           path="batched")
+    T = phantoms.identity_params(2)
+    ok = ctx.eval(T, [1.0, 2.0])
+    np.testing.assert_allclose(ok, 0.0, atol=1e-12)  # one cell: every entropy is 0
+    try:
+        assert lib.mi_fault_drain_cap(0) == cuda_lib.MI_OK
+        with pytest.raises(cuda_lib.MIError) as e:
+            ctx.eval(T, [1.0, 2.0])
+        assert e.value.status == cuda_lib.MI_ECUDA and "drain" in str(e.value)
+    finally:
+        lib.mi_fault_drain_cap(1 << 16)
+    np.testing.assert_array_equal(ctx.eval(T, [1.0, 2.0]), ok)
+    assert lib.mi_fault_drain_cap(-1) == cuda_lib.MI_EINVAL

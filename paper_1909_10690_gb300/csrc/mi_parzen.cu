@@ -24,10 +24,41 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "mi_internal.h"
 
 namespace mi {
 namespace {
+
+// The dynamic shared memory a launch of fn needs, allowed on the current device (set before every
+// launch: a device reset would clear it).
+cudaError_t allow_smem(const void *fn, size_t smem) {
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+// Resident CTAs per SM (at least 1) of fn at a launch shape, asked of the driver once per process and
+// device (it depends on nothing else); allow_smem(fn, smem) must have succeeded.
+std::mutex g_launch_mu;
+std::map<std::tuple<int, const void *, int, size_t>, int> g_per_sm;
+
+int resident_per_sm(const void *fn, int threads, size_t smem) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(g_launch_mu);
+    const auto key = std::make_tuple(dev, fn, threads, smem);
+    auto it = g_per_sm.find(key);
+    if (it != g_per_sm.end()) return it->second;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess || nb < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    g_per_sm.emplace(key, nb);
+    return nb;
+}
 
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -781,14 +812,12 @@ static size_t parzen_adj_smem(int B, int g) {
 
 template <int NQ, bool SAMPLED>
 static int adj_blocks_per_sm(size_t smem) {
-    int nb = 0;
-    if (cudaFuncSetAttribute(k_parzen_adj<NQ, SAMPLED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_parzen_adj<NQ, SAMPLED>, 256, smem) != cudaSuccess) {
+    const void *fn = (const void *)k_parzen_adj<NQ, SAMPLED>;
+    if (allow_smem(fn, smem) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
-    return nb > 0 ? nb : 1;
+    return resident_per_sm(fn, 256, smem);
 }
 
 int parzen_adj_ctas(const ParzenPair &P, int n, int nq, int sms) {
@@ -849,8 +878,7 @@ cudaError_t launch_parzen_hist(const ParzenPair &P, const ParzenAffine *d_aff, i
         default: fn = P.srow ? (const void *)k_parzen_hist<kParzenRowsPerStep, true, 1>
                              : (const void *)k_parzen_hist<kParzenRowsPerStep, false, 1>;
     }
-    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-        return e;
+    if ((e = allow_smem(fn, smem)) != cudaSuccess) return e;
     // rows per CTA: at most kParzenMaxVox voxels per copy, so that the 16-bit halves cannot overflow
     // (a row of nx voxels, or of at most nx sampled entries, is walked 32 lanes at a time, so copy i,
     // fed by the lanes l = i mod C, takes at most 32 / C of every 32); CTAs do equal shares of the
@@ -858,11 +886,7 @@ cudaError_t launch_parzen_hist(const ParzenPair &P, const ParzenAffine *d_aff, i
     const long long R = (long long)P.nf[1] * P.nf[2], TR = R * n;
     long long cap = kParzenMaxVox / ((32 / copies) * ((P.nf[0] + 31) / 32));
     if (cap < 1) cap = 1;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256 * copies, smem) != cudaSuccess || per_sm < 1) {
-        cudaGetLastError();
-        per_sm = 1;
-    }
+    const int per_sm = resident_per_sm(fn, 256 * copies, smem);
     const long long wave = (long long)per_sm * (sms > 0 ? sms : 1);
     long long nch = (TR + cap - 1) / cap;
     nch = (nch + wave - 1) / wave * wave;
@@ -900,9 +924,7 @@ cudaError_t launch_parzen_adjoint(const ParzenPair &P, const ParzenAffine *d_aff
         const int in_smem = smem > 0;
 #define MI_ADJ_S(NQV, SV)                                                                                   \
     do {                                                                                                    \
-        if ((e = cudaFuncSetAttribute(k_parzen_adj<NQV, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                                      (int)smem)) != cudaSuccess)                                           \
-            return e;                                                                                       \
+        if ((e = allow_smem((const void *)k_parzen_adj<NQV, SV>, smem)) != cudaSuccess) return e;           \
         k_parzen_adj<NQV, SV><<<grid, 256, smem, s>>>(P, d_aff, nq, q0, d_w, in_smem, d_mom);               \
     } while (0)
 #define MI_ADJ(NQV)                 \

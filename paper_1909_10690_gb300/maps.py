@@ -49,6 +49,8 @@ def param_map(ctx, family: str, lo: float, hi: float, steps: int, q=(1.0,), base
     the parameters (the unit-ball rotation maps use ``rotation="versor"``,
     the zero-centred scale maps ``scale="offset"``).
     """
+    if getattr(ctx, "nparams", 9) != 9:
+        raise ValueError("parameter maps are over the families of the 9-parameter form (transform='params')")
     T = grid(family, lo, hi, steps, base, getattr(ctx, "scale", "factor"))
     out = np.empty((len(T), len(q)), np.float64)
     for s in range(0, len(T), chunk):

@@ -6,7 +6,9 @@ mixing entropies from one histogram: the Tsallis gradient for the translation
 parameters and the Shannon gradient for rotation and scale.  This module is
 that loop: every iteration evaluates MI and dMI/dtheta for all starting poses
 in one ``mi_grad`` call (the CUDA path) and takes an Adam step per pose on the
-host.  Parameters are (tx, ty, tz mm; rx, ry, rz degrees; sx, sy, sz factors).
+host.  Parameters are (tx, ty, tz mm; rx, ry, rz degrees; sx, sy, sz factors),
+or, for a context with ``transform="affine"``, the 12 entries of [M | t]
+(row-major, t in mm).
 """
 from __future__ import annotations
 
@@ -14,22 +16,31 @@ import numpy as np
 
 # default step sizes per parameter: 0.25 mm, 0.25 degree, 0.25 % scale
 DEFAULT_LR = np.array([0.25, 0.25, 0.25, 0.25, 0.25, 0.25, 0.0025, 0.0025, 0.0025])
+# for the general affine [M | t]: 0.0025 per matrix entry, 0.25 mm per translation
+AFFINE_LR = np.array([0.0025, 0.0025, 0.0025, 0.25] * 3)
+# columns of the translation parameters
+TRANSLATION = {9: [0, 1, 2], 12: [3, 7, 11]}
 
 
-def register(ctx, starts, q=1.0, q_translation=None, steps=150, lr=DEFAULT_LR, betas=(0.9, 0.999), eps=1e-12):
+def register(ctx, starts, q=1.0, q_translation=None, steps=150, lr=None, betas=(0.9, 0.999), eps=1e-12):
     """Gradient ascent on the Parzen MI from n starting poses at once.
 
-    ctx: a Context created with kernel="parzen".
-    starts: n x 9 starting parameters.
+    ctx: a Context created with kernel="parzen" (9 parameters, or 12 with transform="affine").
+    starts: n x P starting parameters, P = ctx.nparams.
     q: exponent whose gradient drives all parameters (1 = Shannon), or, with
-       ``q_translation`` set, the rotation and scale parameters only; the
+       ``q_translation`` set, all but the translation parameters; the
        translation parameters then follow the q_translation gradient.  Both
        come from one soft histogram per pose (one ``mi_grad`` call).
-    Returns (final params n x 9, MI history steps x n for q).
+    lr: step sizes per parameter (default DEFAULT_LR, or AFFINE_LR for 12 parameters).
+    Returns (final params n x P, MI history steps x n for q).
     """
-    theta = np.array(starts, dtype=np.float64).reshape(-1, 9)
+    P = int(getattr(ctx, "nparams", 9))
+    if P not in TRANSLATION:
+        raise ValueError(f"unsupported parameter count {P}")
+    theta = np.array(starts, dtype=np.float64).reshape(-1, P)
     qs = [float(q)] if q_translation is None else [float(q), float(q_translation)]
-    lr = np.asarray(lr, dtype=np.float64)
+    lr = np.asarray((DEFAULT_LR if P == 9 else AFFINE_LR) if lr is None else lr, dtype=np.float64)
+    tcols = TRANSLATION[P]
     m = np.zeros_like(theta)
     v = np.zeros_like(theta)
     history = []
@@ -39,7 +50,7 @@ def register(ctx, starts, q=1.0, q_translation=None, steps=150, lr=DEFAULT_LR, b
         g = np.asarray(g)
         grad = g[:, 0, :].copy()
         if q_translation is not None:
-            grad[:, 0:3] = g[:, 1, 0:3]
+            grad[:, tcols] = g[:, 1, tcols]
         grad = np.nan_to_num(grad)
         history.append(mi[:, 0].copy())
         m = betas[0] * m + (1 - betas[0]) * grad

@@ -156,3 +156,26 @@ def test_moving_volume_beyond_the_texture_extent_is_rejected(cuda_lib, kernel):
     with pytest.raises(cuda_lib.MIError) as e:
         cuda_lib.Context(f, m, bins=16, kernel=kernel)
     assert e.value.status == cuda_lib.MI_EUNSUPPORTED
+
+
+def test_parzen_symmetric_pair_and_separated_classes(cuda_lib):
+    # the oracle's pins on the CUDA path: a mirror-symmetric pair at a uniform scale has no translation
+    # or rotation gradient (FP32 accumulation: within the gradient tolerance of the scale components),
+    # and aligned classes >= 4 moving bins apart give Shannon MI = H(class proportions)
+    rng = np.random.default_rng(28)
+    shape = (12, 14, 16)
+    table = rng.uniform(0.1, 0.9, size=tuple((n + 1) // 2 for n in shape)).astype(np.float32)
+    idx = [np.minimum(np.arange(n), n - 1 - np.arange(n)) for n in shape]
+    f = np.ascontiguousarray(table[np.ix_(idx[0], idx[1], idx[2])])
+    ctx = cuda_lib.Context(f, f, bins=32, kernel="parzen")
+    p = np.array([[0, 0, 0, 0, 0, 0, 1.04, 1.04, 1.04]], dtype=np.float32)
+    mi, g = ctx.grad(p, [1.0, 0.7, 1.3])
+    for iq in range(3):
+        assert np.abs(g[0, iq, :6]).max() <= G_TOL * np.abs(g[0, iq, 6:]).max(), g[0, iq]
+    c = np.full((8, 10, 12), 0.2, np.float32)
+    c[:, :, 9:] = 0.8
+    want = -(0.25 * np.log(0.25) + 0.75 * np.log(0.75))
+    for B in (16, 64):
+        cctx = cuda_lib.Context(c, c, bins=B, kernel="parzen")
+        mi = cctx.eval(np.array([[0, 0, 0, 0, 0, 0, 1, 1, 1]], np.float32), [1.0])
+        assert abs(mi[0, 0] - want) <= MI_TOL * want, (B, mi[0, 0], want)

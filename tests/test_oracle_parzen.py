@@ -137,3 +137,38 @@ def test_parzen_empty_overlap_nan():
     aff = np.hstack([np.eye(3), np.full((3, 1), 100.0)])
     mi, g, n = oracle.parzen(f, m, aff, 16, [1.0], daff=np.zeros((12, 9)))
     assert n == 0 and np.isnan(mi[0]) and np.all(np.isnan(g))
+
+
+def _mirror_symmetric(shape, seed):
+    # a value per (|i - c_x|, |j - c_y|, |k - c_z|): exactly symmetric under each axis mirror
+    rng = np.random.default_rng(seed)
+    table = rng.uniform(0.1, 0.9, size=tuple((n + 1) // 2 for n in shape)).astype(np.float32)
+    idx = [np.minimum(np.arange(n), n - 1 - np.arange(n)) for n in shape]
+    return table[np.ix_(idx[0], idx[1], idx[2])]
+
+
+def test_parzen_symmetric_pair_has_no_translation_or_rotation_gradient():
+    # f = m mirror-symmetric about the centre on every axis, uniform scale sigma != 1 (samples off the
+    # grid planes, even sizes): a mirror maps t to -t and each rotation angle to its negative, so MI is
+    # even in them and their derivatives vanish; the scale derivatives do not
+    f = _mirror_symmetric((12, 14, 16), seed=28)
+    assert np.array_equal(f, f[::-1, :, :]) and np.array_equal(f, f[:, ::-1, :]) and np.array_equal(f, f[:, :, ::-1])
+    p = np.array([0, 0, 0, 0, 0, 0, 1.04, 1.04, 1.04], dtype=np.float32)
+    aff, J = oracle.affine(p, f.shape, (1, 1, 1), f.shape, (1, 1, 1), with_jacobian=True)
+    mi, g, n = oracle.parzen(f, f, aff, 32, [1.0, 0.7, 1.3], daff=J)
+    for iq in range(3):
+        assert np.abs(g[iq, 6:]).max() > 1e-3
+        assert np.abs(g[iq, :6]).max() <= 1e-10 * np.abs(g[iq, 6:]).max()
+
+
+def test_parzen_mi_of_aligned_separated_classes_is_the_class_entropy():
+    # classes in distinct fixed bins and >= 4 moving bins apart: the B-spline spread adds the same
+    # entropy to H(M) and H(F, M), so Shannon Parzen MI = H(class proportions) exactly (the hard MI)
+    f = np.full((8, 10, 12), 0.2, np.float32)
+    f[:, :, 9:] = 0.8  # a quarter of the voxels
+    aff = np.hstack([np.eye(3), np.zeros((3, 1))])
+    for B in (16, 32, 64):
+        mi, _, n = oracle.parzen(f, f, aff, B, [1.0])
+        want = -(0.25 * np.log(0.25) + 0.75 * np.log(0.75))
+        assert n == f.size
+        assert abs(mi[0] - want) < 1e-12, (B, mi[0], want)

@@ -4,12 +4,11 @@ Joint histograms must match bit for bit; MI and entropies within
 |d| <= 1e-6 max(|MI|, H_FM) (both sides sum exact counts in FP64, so the
 observed gap is summation order, ~1e-13).
 """
-import json
-import os
 
 import numpy as np
 import pytest
 
+import hand_cases
 import oracle
 from paper_1909_10690_gb300 import phantoms
 
@@ -92,14 +91,11 @@ def test_versor_and_offset_mi_parity(cuda_lib):
 
 
 def test_hand_enumerated_cases_on_gpu(cuda_lib):
-    cases = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hand_4x4x4.json")))["cases"]
-    z, y, x = np.meshgrid(np.arange(4), np.arange(4), np.arange(4), indexing="ij")
-    vols = {"ramp_x": (64 * x).astype(np.uint8), "ramp_y": (64 * y).astype(np.uint8)}
+    vols, cases = hand_cases.load()
     for c in cases:
-        ctx = cuda_lib.Context(vols[c["fixed"]], vols[c["moving"]], bins=4)
-        want = np.zeros((4, 4), np.uint32)
-        for r, cc, v in c["hist"]:
-            want[r, cc] = v
+        bins = hand_cases.bins_of(c)
+        ctx = cuda_lib.Context(hand_cases.volume(vols[c["fixed"]]), hand_cases.volume(vols[c["moving"]]), bins=bins)
+        want = hand_cases.expected_hist(c, np.uint32)
         for path in (cuda_lib.PATH_PLAIN, cuda_lib.PATH_BATCHED):
             h = ctx.hist(affines=np.array(c["q16"], np.int32), path=path)
             np.testing.assert_array_equal(h[0], want, err_msg=c["name"])

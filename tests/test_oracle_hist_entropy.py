@@ -5,37 +5,24 @@ Expectations come from hand enumeration (tests/golden), exact permutations,
 numpy slicing, library routines (scipy.stats.entropy) and theorems
 (pseudo-additivity of Tsallis entropy, Miller-Madow bias).
 """
-import json
 import math
-import os
 
 import numpy as np
 import pytest
 
+import hand_cases
 import oracle
 from paper_1909_10690_gb300 import phantoms
 
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "hand_4x4x4.json")
 IDENT = np.array([65536, 0, 0, 0, 0, 65536, 0, 0, 0, 0, 65536, 0], dtype=np.int32)
+VOLUMES, CASES = hand_cases.load()
 
 
-def _ramp(name):
-    z, y, x = np.meshgrid(np.arange(4), np.arange(4), np.arange(4), indexing="ij")
-    return (64 * (x if name == "ramp_x" else y)).astype(np.uint8)
-
-
-def _golden_cases():
-    return json.load(open(GOLDEN))["cases"]
-
-
-@pytest.mark.parametrize("case", _golden_cases(), ids=lambda c: c["name"])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c["name"])
 def test_hand_enumerated_4x4x4(case):
-    fx, mv = _ramp(case["fixed"]), _ramp(case["moving"])
-    h, n = oracle.joint_hist(fx, mv, case["q16"], 4)
-    want = np.zeros((4, 4), dtype=np.uint64)
-    for r, c, v in case["hist"]:
-        want[r, c] = v
-    np.testing.assert_array_equal(h, want)
+    fx, mv = hand_cases.volume(VOLUMES[case["fixed"]]), hand_cases.volume(VOLUMES[case["moving"]])
+    h, n = oracle.joint_hist(fx, mv, case["q16"], hand_cases.bins_of(case))
+    np.testing.assert_array_equal(h, hand_cases.expected_hist(case))
     assert n == case["N"]
     for q, v in case["mi"].items():
         mi, _ = oracle.entropies(h, [float(q)])

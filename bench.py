@@ -335,7 +335,8 @@ def run_profile(args):
     f, m = phantoms.head_pair(shape=SHAPE, spacing=(1, 1, 1), seed=30)
     prm = torch.from_numpy(phantoms.random_transforms(args.profile, seed=31)).cuda()
     ctx = mi.Context(f, m, bins=BINS, fixed_depth=DEPTH, moving_depth=DEPTH, path="batched",
-                     hist_variant=args.variant, autotune=False, block_threads=args.threads)
+                     hist_variant=args.variant, autotune=False, block_threads=args.threads,
+                     tile_rows=args.tile_rows, tile_slabs=args.slabs)
     for _ in range(args.warmup):
         ctx.eval(prm, QS)
     ms = []
@@ -344,7 +345,8 @@ def run_profile(args):
         ms.append(ctx.last_kernel_ms()[0])
     nvox = int(np.prod(SHAPE))
     print(json.dumps({"profile": "batched", "transforms": args.profile, "variant": args.variant, "threads": args.threads,
-                      "kernel_ms": ms, "voxel_transforms_per_s": args.profile * nvox / (np.mean(ms) / 1e3)}))
+                      "tile_rows": args.tile_rows, "slabs": args.slabs, "kernel_ms": ms,
+                      "voxel_transforms_per_s": args.profile * nvox / (np.mean(ms) / 1e3)}))
 
 
 def run_profile_parzen(args):
@@ -411,6 +413,8 @@ def main():
     ap.add_argument("--profile", type=int, default=0, help="profile mode: batched kernel only, on this many transforms")
     ap.add_argument("--variant", type=int, default=9, help="histogram variant in profile mode (MI_HV_*)")
     ap.add_argument("--threads", type=int, default=1024, help="CTA size in profile mode (512 or 1024)")
+    ap.add_argument("--tile-rows", type=int, default=1, help="fixed rows per warp step in profile mode (1, 2, 4)")
+    ap.add_argument("--slabs", type=int, default=4, help="slabs per sweep in profile mode (1..16)")
     ap.add_argument("--profile-parzen", type=int, default=0, help="profile mode: Parzen MI + gradient of this many poses")
     ap.add_argument("--maps", type=int, default=0, help="time an N^3 translation map of the head-like pair")
     args = ap.parse_args()

@@ -106,7 +106,14 @@ enum {
        two fetches per voxel instead of four, twice the moving-volume memory */
     MI_HV_ROWS_QUAD = 10,
     MI_HV_U32_QUAD = 11,
-    MI_HV_U16_QUAD = 12
+    MI_HV_U16_QUAD = 12,
+    /* moving depth <= 12 only: one 2D texture gather per voxel from an atlas of
+       the moving planes whose 32-bit texels pack v(x, y, z) with v(x, y, z + 1),
+       so the 2 x 2 footprint holds all 8 trilinear neighbours; the stage lerps
+       of both planes run packed in 20-bit fields of 64-bit integer products */
+    MI_HV_ROWS_GATHER = 13,
+    MI_HV_U32_GATHER = 14,
+    MI_HV_U16_GATHER = 15
 };
 /* Meaning of the rotation parameters (transform[3..5]):
  *  MI_ROT_EULER_DEG  R = Rz(rz) Ry(ry) Rx(rx), right-handed, degrees;
@@ -166,6 +173,12 @@ typedef struct {
                                  subset of that fraction (see below)                   */
     unsigned int sample_seed; /* seed of that subset                                    */
     int transform;     /* MI_TRANSFORM_PARAMS (default) or MI_TRANSFORM_AFFINE       */
+    int tile_rows;     /* hard path, quad and gather variants: adjacent fixed rows one
+                          warp step covers (32 / tile_rows lanes each): 0 (default) =
+                          autotuned, or 1, 2, 4                                       */
+    int tile_slabs;    /* batched kernel: slabs per sweep of the fixed rows (CTAs on
+                          different transforms keep to neighbouring slabs): 0 (default)
+                          = 4, or 1..16                                                */
 } mi_options;
 
 /* Random voxel sampling (mi_options.sample_fraction in (0, 1), hard and
@@ -293,6 +306,11 @@ mi_status mi_resample(mi_ctx *ctx, int pair, const int32_t *affine, void *out);
  * for the given number of transforms per call; -1 if none yet. */
 int mi_selected_variant(mi_ctx *ctx, int pair, int n);
 
+/* The whole configuration chosen (autotuned or set) for calls of n transforms:
+ * out[0..4] = histogram variant, threads per CTA, CTAs, fixed rows per warp
+ * step, slabs per sweep (all -1 if none chosen yet). */
+mi_status mi_selected_config(mi_ctx *ctx, int n, int out[5]);
+
 /* Test hook (failure handling): after `after` further successful device
  * allocations by the library in this process, the next one fails as if the
  * device were out of memory (the caller sees MI_ENOMEM), and the hook disarms
@@ -318,20 +336,21 @@ mi_status mi_last_kernel_ms(mi_ctx *ctx, float *ms, int *launches);
 
 /*
  * Allocation-free evaluation.  The paper has no counterpart: this is a
- * deployment aid for callers that cannot allocate device memory where they
- * need the metric -- code running while a CUDA graph is being captured
- * (cudaMalloc is not allowed then), plug-ins inside a framework whose caching
- * allocator owns the device memory, services that fix their GPU memory budget
- * up front.  It computes the same hard-binned MI as mi_eval (plain path) for
- * ONE transform (9 parameters in the default conventions -- Euler degrees,
- * scale factors -- host memory) and nq q values (host memory)
- * without creating a context and without calling cudaMalloc, cudaFree or any
- * allocating routine.
+ * deployment aid for callers that may not allocate device memory where they
+ * need the metric -- plug-ins inside a framework whose caching allocator owns
+ * the GPU's memory (a cudaMalloc of their own fails once the pool holds it,
+ * or fragments it), services that fix their GPU memory budget up front, loops
+ * that cannot afford cudaMalloc's implicit device-wide synchronisation.  It
+ * computes the same hard-binned MI as mi_eval (plain path) for ONE transform
+ * (9 parameters in the default conventions -- Euler degrees, scale factors --
+ * host memory) and nq q values (host memory) without creating a context and
+ * without calling cudaMalloc, cudaFree or any allocating routine.
  *  - fixed, moving: uint8 or uint16 volumes already in device memory of the
- *    current device, used as given (no copy; values must lie within their bit
- *    depth, since no clamp-on-load copy is made).
+ *    current device, used in place (no copy); values above 2^d - 1 are
+ *    clamped as they are read, as mi_eval clamps them on load.
  *  - bins: 2..MI_NOALLOC_MAX_BINS; the fixed volume may hold at most
- *    MI_NOALLOC_MAX_VOXELS voxels.  Larger sizes return MI_EINVAL.
+ *    MI_NOALLOC_MAX_VOXELS voxels and the moving volume at most
+ *    MI_NOALLOC_MAX_MOVING_VOXELS.  Larger sizes return MI_EINVAL.
  *  - out_mi: nq doubles, host or device memory.  stream: a cudaStream_t
  *    (NULL = legacy default stream); the call synchronises it.
  *  - Intermediates live in one static device array of about 257 KiB that every
@@ -340,13 +359,13 @@ mi_status mi_last_kernel_ms(mi_ctx *ctx, float *ms, int *launches);
  *    All calls share it, so calls that overlap on the GPU (several streams or
  *    threads at once) race: serialise them.
  *  - The first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    (cudaGetSymbolAddress) with that device current.
  *  - Shannon entropies in nats and the additive Tsallis form.  Errors as for
  *    mi_eval; the message is read with mi_last_error(NULL).
  */
 #define MI_NOALLOC_MAX_BINS 256
 #define MI_NOALLOC_MAX_VOXELS (1LL << 25)
+#define MI_NOALLOC_MAX_MOVING_VOXELS ((1LL << 31) - 1)
 mi_status mi_eval_noalloc(const mi_volume *fixed, const mi_volume *moving, int bins, const float *transform,
                           const float *q, int nq, double *out_mi, void *stream);
 

@@ -25,6 +25,7 @@ HV_AUTO, HV_U32, HV_U32_MATCH, HV_U16, HV_U16_MATCH = -1, 0, 1, 2, 3
 HV_U32_TEX, HV_U32_MATCH_TEX, HV_U16_TEX, HV_U16_MATCH_TEX = 4, 5, 6, 7
 HV_ROWS, HV_ROWS_TEX = 8, 9
 HV_ROWS_QUAD, HV_U32_QUAD, HV_U16_QUAD = 10, 11, 12
+HV_ROWS_GATHER, HV_U32_GATHER, HV_U16_GATHER = 13, 14, 15
 PATH_AUTO, PATH_PLAIN, PATH_BATCHED = 0, 1, 2
 _DT = {np.dtype(np.uint8): 0, np.dtype(np.uint16): 1, np.dtype(np.float32): 2}
 
@@ -103,7 +104,8 @@ def _volume(x, spacing, depth):
 
 
 def _options(kernel, tsallis_form, bits, hist_variant, path, use_graphs, autotune, device, block_threads=0,
-             rotation="euler", scale="factor", sample_fraction=0.0, sample_seed=0, transform="params"):
+             rotation="euler", scale="factor", sample_fraction=0.0, sample_seed=0, transform="params", tile_rows=0,
+             tile_slabs=0):
     o = _lib.MiOptions()
     load().mi_options_default(ctypes.byref(o))
     o.kernel = {"hard": 0, "parzen": 1}[kernel]
@@ -120,6 +122,8 @@ def _options(kernel, tsallis_form, bits, hist_variant, path, use_graphs, autotun
     o.sample_fraction = float(sample_fraction)
     o.sample_seed = int(sample_seed) & 0xFFFFFFFF
     o.transform = {"params": 0, "affine": 1}[transform]
+    o.tile_rows = int(tile_rows)
+    o.tile_slabs = int(tile_slabs)
     return o
 
 
@@ -148,19 +152,22 @@ class Context:
     transform: "params" (9 parameters, default) or "affine" (12: the general
     affine [M | t] row-major, M dimensionless, t in mm; gradients per entry).
     ``nparams`` is the count.
+    tile_rows (0 = autotuned, or 1, 2, 4): adjacent fixed rows one warp step of
+    the hard path covers; tile_slabs (0 = 4, or 1..16): slabs per sweep of the
+    batched kernel.
     """
 
     def __init__(self, fixed=None, moving=None, bins=64, fixed_spacing=(1.0, 1.0, 1.0),
                  moving_spacing=(1.0, 1.0, 1.0), fixed_depth=None, moving_depth=None, kernel="hard",
                  tsallis_form="additive", bits=False, hist_variant=HV_AUTO, path="auto", use_graphs=True,
                  autotune=True, device=None, pairs=None, block_threads=0, rotation="euler", scale="factor",
-                 sample_fraction=0.0, sample_seed=0, transform="params"):
+                 sample_fraction=0.0, sample_seed=0, transform="params", tile_rows=0, tile_slabs=0):
         self._lib = load()
         self._h = ctypes.c_void_p()
         self.kernel = kernel
         self.rotation, self.scale, self.transform = rotation, scale, transform
         opt = _options(kernel, tsallis_form, bits, hist_variant, path, use_graphs, autotune, device, block_threads,
-                       rotation, scale, sample_fraction, sample_seed, transform)
+                       rotation, scale, sample_fraction, sample_seed, transform, tile_rows, tile_slabs)
         if pairs is None:
             pairs = [dict(fixed=fixed, moving=moving, bins=bins, fixed_spacing=fixed_spacing,
                           moving_spacing=moving_spacing, fixed_depth=fixed_depth, moving_depth=moving_depth)]
@@ -309,6 +316,13 @@ class Context:
     def selected_variant(self, n, pair=0):
         return self._lib.mi_selected_variant(self._h, pair, int(n))
 
+    def selected_config(self, n):
+        """The configuration chosen for calls of n transforms: dict of variant, threads, ctas, tile_rows,
+        tile_slabs (all -1 before the first such call)."""
+        out = (ctypes.c_int * 5)()
+        self._check(self._lib.mi_selected_config(self._h, int(n), ctypes.cast(out, ctypes.c_void_p)))
+        return dict(zip(("variant", "threads", "ctas", "tile_rows", "tile_slabs"), list(out)))
+
     def last_kernel_ms(self):
         """(device ms of the main kernels of the last call, number of kernels it launched)."""
         ms = ctypes.c_float()
@@ -319,24 +333,47 @@ class Context:
 
 def eval_noalloc(fixed, moving, bins, transform, q=(1.0,), fixed_spacing=(1.0, 1.0, 1.0),
                  moving_spacing=(1.0, 1.0, 1.0), fixed_depth=None, moving_depth=None, stream=None, out=None):
-    """Hard-binned MI of one transform through ``mi_eval_noalloc`` (no device allocation).
+    """Hard-binned MI of one transform through ``mi_eval_noalloc``, which allocates no device memory.
 
-    For callers that cannot allocate device memory where they evaluate the
-    metric (inside CUDA-graph capture, under a framework-owned allocator, on a
-    fixed memory budget).  ``fixed`` and ``moving`` are uint8/uint16 CUDA
-    tensors on the current device; ``out`` may be a preallocated CUDA float64
-    tensor of nq elements, otherwise a numpy array is returned.  Calls share
-    one static device array: do not overlap calls on the GPU.
+    For callers that may not allocate device memory where they evaluate the
+    metric: code running inside a framework whose caching allocator owns the
+    GPU's memory, services that fix their memory budget up front, loops that
+    cannot afford cudaMalloc's implicit synchronisation.  ``fixed`` and
+    ``moving`` are contiguous uint8/uint16 CUDA tensors on the current device,
+    used in place (a non-contiguous tensor is rejected rather than copied).
+    ``out`` may be a contiguous CUDA float64 tensor of at least nq elements on
+    that device; otherwise a numpy array is returned.  ``stream`` defaults to
+    torch's current stream.  All calls share one static device array: calls
+    that overlap on the GPU race, so serialise them.
     """
     lib = load()
+    torch = _torch()
+    for name, v in (("fixed", fixed), ("moving", moving)):
+        if not (_is_torch(v) and v.is_cuda):
+            raise MIError(MI_EINVAL, f"{name} must be a CUDA tensor (mi_eval_noalloc makes no copy)")
+        if not v.is_contiguous():
+            raise MIError(MI_EINVAL, f"{name} must be contiguous (a copy would allocate)")
+    dev = fixed.device
+    if moving.device != dev:
+        raise MIError(MI_EINVAL, "fixed and moving must be on the same device")
     fv, fa = _volume(fixed, fixed_spacing, fixed_depth)
     mv, ma = _volume(moving, moving_spacing, moving_depth)
     T = np.ascontiguousarray(np.asarray(transform, dtype=np.float32).reshape(9))
     Q = np.ascontiguousarray(np.atleast_1d(np.asarray(q, dtype=np.float32)))
-    res = out if out is not None else np.empty(Q.size, dtype=np.float64)
+    if out is not None:
+        if not (_is_torch(out) and out.is_cuda and out.device == dev):
+            raise MIError(MI_EINVAL, "out must be a CUDA tensor on the volumes' device")
+        if out.dtype != torch.float64 or out.numel() < Q.size or not out.is_contiguous():
+            raise MIError(MI_EINVAL, f"out must be a contiguous float64 tensor of at least {Q.size} elements")
+        res = out
+    else:
+        res = np.empty(Q.size, dtype=np.float64)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
     h = getattr(stream, "cuda_stream", stream)
-    st = lib.mi_eval_noalloc(ctypes.byref(fv), ctypes.byref(mv), int(bins), T.ctypes.data, Q.ctypes.data, int(Q.size),
-                             _ptr(res), ctypes.c_void_p(h) if h else None)
+    with torch.cuda.device(dev):
+        st = lib.mi_eval_noalloc(ctypes.byref(fv), ctypes.byref(mv), int(bins), T.ctypes.data, Q.ctypes.data,
+                                 int(Q.size), _ptr(res), ctypes.c_void_p(h) if h else None)
     if st not in (MI_OK, MI_EEMPTY):
         raise MIError(st, lib.mi_last_error(None).decode())
     return res

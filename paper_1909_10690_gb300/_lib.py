@@ -82,7 +82,8 @@ class MiOptions(ctypes.Structure):
                 ("hist_variant", ctypes.c_int), ("path", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("device", ctypes.c_int), ("block_threads", ctypes.c_int),
                 ("rotation", ctypes.c_int), ("scale", ctypes.c_int), ("sample_fraction", ctypes.c_float),
-                ("sample_seed", ctypes.c_uint), ("transform", ctypes.c_int)]
+                ("sample_seed", ctypes.c_uint), ("transform", ctypes.c_int), ("tile_rows", ctypes.c_int),
+                ("tile_slabs", ctypes.c_int)]
 
 
 # Symbols declared in include/mi.h, with their ctypes signatures.
@@ -110,6 +111,7 @@ SIGNATURES = {
     "mi_fixed_bins": (_I, [_P, _I, _P]),
     "mi_resample": (_I, [_P, _I, _P, _P]),
     "mi_selected_variant": (_I, [_P, _I, _I]),
+    "mi_selected_config": (_I, [_P, _I, _P]),
     "mi_last_kernel_ms": (_I, [_P, _P, _P]),
     "mi_eval_noalloc": (_I, [ctypes.POINTER(MiVolume), ctypes.POINTER(MiVolume), _I, _P, _P, _I, _P, _P]),
 }

@@ -302,6 +302,9 @@ struct Pair {
     cudaTextureObject_t tex = 0;
     cudaArray_t arrq = nullptr;  // 2 x 2 quads as a 3D array (one extra z plane), read through texq
     cudaTextureObject_t texq = 0;
+    cudaArray_t arrg = nullptr;  // z-pair atlas (moving depth <= 12), read by 2D gathers through texg
+    cudaTextureObject_t texg = 0;
+    DevBuf zoff;                 // per moving plane: float2 atlas offset + 1 - 2^23
     DevBuf rowinfo;             // row-bound layout table (bins entries)
     DevBuf srow, scol, sbin;    // random sampling: per-row lists of the sampled fixed voxels
     int rows_words = 0;
@@ -313,6 +316,8 @@ struct Pair {
         if (arr) cudaFreeArray(arr);
         if (texq) cudaDestroyTextureObject(texq);
         if (arrq) cudaFreeArray(arrq);
+        if (texg) cudaDestroyTextureObject(texg);
+        if (arrg) cudaFreeArray(arrg);
         if (ptex) cudaDestroyTextureObject(ptex);
         if (parr) cudaFreeArray(parr);
     }
@@ -320,6 +325,7 @@ struct Pair {
 
 struct Choice {
     int variant = -1, threads = 0, ctas = 0;
+    Tile tile{5, 4};  // lanes per row 2^5 (one row per warp step), 4 slabs per sweep
 };
 
 struct GraphEntry {
@@ -342,10 +348,12 @@ struct mi_ctx {
     DevBuf d_pairs;     // PairDev[npairs]
     int max_bins = 0;
     int max_rows_words = 0;
+    int max_zplanes = 0;      // moving planes of the largest pair (gather offsets in shared memory)
+    bool all_gather = true;   // every pair has a z-pair atlas (gather variants allowed)
     // per-q FP64 tables, keyed by the float bits of q
     std::map<uint32_t, std::unique_ptr<DevBuf>> tables;
     // call scratch
-    DevBuf d_aff, d_items, d_mi, d_h, d_cnt, d_hist, d_flags, d_ticket, d_dump;
+    DevBuf d_aff, d_items, d_mi, d_h, d_cnt, d_hist, d_flags, d_ticket, d_dump, d_cols, d_part;
     HostBuf h_aff, h_items, h_out;
     // Parzen scratch
     DevBuf p_aff, p_jac, p_hist, p_cnt, p_marg, p_ment, p_mterm, p_jsum, p_w, p_mom, p_grad;
@@ -665,10 +673,46 @@ mi_status add_pair(mi_ctx *ctx, const mi_volume *fx, const mi_volume *mv, int bi
             MI_CU(cudaCreateTextureObject(&P->texq, &rd, &td, nullptr), "creating the quad texture object");
             MI_CU(cudaStreamSynchronize(s), "building the quads");
         }
+        // z-pair atlas for moving depths <= 12: plane z is the tile at ((z / ph) nx, (z % ph) ny) of a 2D
+        // image no larger than the device's gather extent; a gather at (ix + 1 + ox, iy + 1 + oy) returns
+        // the plane's 2 x 2 footprint with each texel's z + 1 neighbour packed beside it
+        if (P->mdepth <= 12) {
+            int gw = 0, gh = 0;
+            cudaDeviceGetAttribute(&gw, cudaDevAttrMaxTexture2DGatherWidth, ctx->device);
+            cudaDeviceGetAttribute(&gh, cudaDevAttrMaxTexture2DGatherHeight, ctx->device);
+            const int nx = P->nm[0], ny = P->nm[1], nz = P->nm[2];
+            const int ph = std::min(nz, gh / ny);
+            const int cols = ph > 0 ? (nz + ph - 1) / ph : 0;
+            if (ph > 0 && (long long)cols * nx <= gw) {
+                const int W = cols * nx, H = ph * ny;
+                DevBuf img;
+                MI_CU(img.ensure((size_t)W * H * 4), "allocating the z-pair atlas");
+                MI_CU(launch_make_zpairs(P->mov.p, P->mdtype, P->nm, ph, W, H, img.as<uint32_t>(), s),
+                      "building the z-pair atlas");
+                cudaChannelFormatDesc cg = cudaCreateChannelDesc(32, 0, 0, 0, cudaChannelFormatKindUnsigned);
+                MI_CU(cudaMallocArray(&P->arrg, &cg, W, H, cudaArrayTextureGather), "allocating the z-pair array");
+                MI_CU(cudaMemcpy2DToArrayAsync(P->arrg, 0, 0, img.p, (size_t)W * 4, (size_t)W * 4, H,
+                                               cudaMemcpyDeviceToDevice, s),
+                      "filling the z-pair array");
+                rd.res.array.array = P->arrg;
+                MI_CU(cudaCreateTextureObject(&P->texg, &rd, &td, nullptr), "creating the z-pair texture object");
+                std::vector<float2> off(nz);
+                for (int z = 0; z < nz; ++z) {
+                    off[z].x = (float)((z / ph) * nx + 1) - 8388608.0f;
+                    off[z].y = (float)((z % ph) * ny + 1) - 8388608.0f;
+                }
+                MI_CU(P->zoff.ensure((size_t)nz * sizeof(float2)), "allocating the plane offsets");
+                MI_CU(cudaMemcpyAsync(P->zoff.p, off.data(), (size_t)nz * sizeof(float2), cudaMemcpyHostToDevice, s),
+                      "plane offsets");
+                MI_CU(cudaStreamSynchronize(s), "building the z-pair atlas");
+            }
+        }
     }
     MI_CU(cudaStreamSynchronize(s), "preparing the volumes");
     ctx->max_bins = std::max(ctx->max_bins, bins);
     ctx->max_rows_words = std::max(ctx->max_rows_words, P->rows_words);
+    ctx->max_zplanes = std::max(ctx->max_zplanes, P->nm[2]);
+    if (!P->texg) ctx->all_gather = false;
     ctx->pairs.push_back(std::move(P));
     return MI_OK;
 }
@@ -684,6 +728,8 @@ mi_status upload_pairs(mi_ctx *ctx) {
         d.movp = P.movp.p;
         d.texp = P.tex;
         d.texq = P.texq;
+        d.texg = P.texg;
+        d.zoff = P.zoff.as<float2>();
         d.rowinfo = P.rowinfo.as<uint32_t>();
         d.srow = P.srow.p ? P.srow.as<uint32_t>() : nullptr;
         d.scol = P.scol.as<uint16_t>();
@@ -711,6 +757,8 @@ PairDev host_pairdev(const Pair &P) {
     d.movp = P.movp.p;
     d.texp = P.tex;
     d.texq = P.texq;
+    d.texg = P.texg;
+    d.zoff = P.zoff.as<float2>();
     d.rowinfo = P.rowinfo.as<uint32_t>();
     d.srow = P.srow.p ? P.srow.as<uint32_t>() : nullptr;
     d.scol = P.scol.as<uint16_t>();
@@ -763,12 +811,20 @@ mi_status create_common(mi_ctx **out, const mi_volume *fixed, const mi_volume *m
         g_create_error = "opt.transform must be MI_TRANSFORM_PARAMS or MI_TRANSFORM_AFFINE";
         return MI_EINVAL;
     }
-    if (ctx->opt.hist_variant < MI_HV_AUTO || ctx->opt.hist_variant > MI_HV_U16_QUAD) {
+    if (ctx->opt.hist_variant < MI_HV_AUTO || ctx->opt.hist_variant > MI_HV_U16_GATHER) {
         g_create_error = "opt.hist_variant out of range";
         return MI_EINVAL;
     }
     if (ctx->opt.block_threads != 0 && ctx->opt.block_threads != 512 && ctx->opt.block_threads != 1024) {
         g_create_error = "opt.block_threads must be 0, 512 or 1024";
+        return MI_EINVAL;
+    }
+    if (ctx->opt.tile_rows != 0 && ctx->opt.tile_rows != 1 && ctx->opt.tile_rows != 2 && ctx->opt.tile_rows != 4) {
+        g_create_error = "opt.tile_rows must be 0, 1, 2 or 4";
+        return MI_EINVAL;
+    }
+    if (ctx->opt.tile_slabs < 0 || ctx->opt.tile_slabs > kMaxSlabs) {
+        g_create_error = "opt.tile_slabs must be in 0..16";
         return MI_EINVAL;
     }
     int ndev = 0;
@@ -900,11 +956,22 @@ mi_status deliver(mi_ctx *ctx, void *dst, const void *src, size_t bytes) {
 // Variant selection
 // ---------------------------------------------------------------------------
 
-bool variant_fits(int variant, int bins, int threads, long long nvox, int rows_words) {
+bool variant_fits(int variant, int bins, int threads, long long nvox, int rows_words, int zmax) {
     const int kind = hv_kind(variant);
     const bool u16 = kind == HV_U16 || kind == HV_U16_MATCH;
     if (u16 && nvox > (long long)(kOvfSlots / 2) * kDrainT) return false;
-    return hard_smem_bytes(variant, bins, threads, rows_words) <= 227 * 1024;
+    return hard_smem_bytes(variant, bins, threads, rows_words, zmax) <= 227 * 1024;
+}
+
+// Rows per warp step the tile shape may take for a variant: quad and gather fetches walk 1, 2 or 4
+// rows per step (lanes per row 2^5, 2^4, 2^3); the others one row.
+std::vector<int> tile_lpr(mi_ctx *ctx, int variant) {
+    if (ctx->opt.tile_rows > 0) {
+        const int lpr = ctx->opt.tile_rows == 1 ? 5 : ctx->opt.tile_rows == 2 ? 4 : 3;
+        return {hv_fetch(variant) >= FM_QUAD ? lpr : 5};
+    }
+    if (hv_fetch(variant) >= FM_QUAD) return {5, 4, 3};
+    return {5};
 }
 
 std::vector<Choice> candidates(mi_ctx *ctx, int bins, long long nvox_max) {
@@ -912,16 +979,21 @@ std::vector<Choice> candidates(mi_ctx *ctx, int bins, long long nvox_max) {
     const int fixed_v = ctx->opt.hist_variant;
     for (int v = 0; v < HV_COUNT; ++v) {
         if (fixed_v >= 0 && v != fixed_v) continue;
+        if (hv_fetch(v) == FM_GATHER && !ctx->all_gather) continue;  // moving depth > 12 somewhere
         for (int th : {512, 1024}) {
             if (ctx->opt.block_threads > 0 && th != ctx->opt.block_threads) continue;
-            if (!variant_fits(v, bins, th, nvox_max, ctx->max_rows_words)) continue;
-            Choice ch;
-            ch.variant = v;
-            ch.threads = th;
-            const int per_sm = batched_ctas_per_sm(v, bins, th, ctx->max_rows_words);
+            if (!variant_fits(v, bins, th, nvox_max, ctx->max_rows_words, ctx->max_zplanes)) continue;
+            const int per_sm = batched_ctas_per_sm(v, bins, th, ctx->max_rows_words, ctx->max_zplanes);
             if (per_sm < 1) continue;
-            ch.ctas = per_sm * ctx->sms;
-            c.push_back(ch);
+            for (int lpr : tile_lpr(ctx, v)) {
+                Choice ch;
+                ch.variant = v;
+                ch.threads = th;
+                ch.ctas = per_sm * ctx->sms;
+                ch.tile.lpr_log2 = lpr;
+                ch.tile.slabs = ctx->opt.tile_slabs > 0 ? ctx->opt.tile_slabs : 4;
+                c.push_back(ch);
+            }
         }
     }
     return c;
@@ -950,11 +1022,12 @@ mi_status run_plain(mi_ctx *ctx, int pair, const int32_t *d_aff, int n, const QS
         }
         // CTAs per transform: fill the GPU, but keep at least 8 row batches of 32 rows per CTA
         const long long rows = (long long)P.nf[1] * P.nf[2];
-        const int per_sm = std::max(1, batched_ctas_per_sm(ch.variant, P.bins, ch.threads, P.rows_words));
+        const int per_sm =
+            std::max(1, batched_ctas_per_sm(ch.variant, P.bins, ch.threads, P.rows_words, P.nm[2]));
         long long ctas = ((long long)ctx->sms * per_sm + m - 1) / m;
         ctas = std::min<long long>(ctas, std::max<long long>(1, rows / (32 * 8)));
         MI_CU(launch_plain_hist(dp, hp, d_aff + (size_t)t0 * 12, m, hist, ch.variant, ch.threads, (int)std::max(1LL, ctas),
-                                O.flags, ctx->stream),
+                                ch.tile, O.flags, ctx->stream),
               "plain histogram kernel");
         if (O.mi || O.h || O.count) {
             Outputs Oc = O;
@@ -962,8 +1035,19 @@ mi_status run_plain(mi_ctx *ctx, int pair, const int32_t *d_aff, int n, const QS
             if (Oc.h) Oc.h += (size_t)t0 * Q.nq * 3;
             if (Oc.count) Oc.count += t0;
             Oc.dump = nullptr;
-            MI_CU(launch_entropy(hist, m, P.bins, Q, Oc, ctx->stream), "entropy kernel");
-            ctx->last_launches += 1;
+            if (m < ctx->sms) {
+                // few transforms: the reduction of each histogram is split over several CTAs
+                MI_CU(ctx->d_cols.ensure((size_t)m * P.bins * 4), "allocating column sums");
+                MI_CU(ctx->d_part.ensure((size_t)m * entropy_parts(P.bins) * (1 + 2 * kMaxQ) * 8),
+                      "allocating partial sums");
+                MI_CU(launch_entropy_split(hist, m, P.bins, Q, Oc, ctx->d_cols.as<uint32_t>(), ctx->d_part.as<double>(),
+                                           ctx->stream),
+                      "entropy kernels");
+                ctx->last_launches += 2;
+            } else {
+                MI_CU(launch_entropy(hist, m, P.bins, Q, Oc, ctx->stream), "entropy kernel");
+                ctx->last_launches += 1;
+            }
         }
         ctx->last_launches += 1;
     }
@@ -990,8 +1074,8 @@ mi_status launch_batched_once(mi_ctx *ctx, int nitems, const QSet &Q, const Outp
     MI_CU(cudaMemsetAsync(ctx->d_ticket.p, 0, 2 * sizeof(int), ctx->stream), "resetting the work queue");
     if (record) MI_CU(record_event(ctx->ev0, ctx->stream), "event");
     MI_CU(launch_batched(ctx->d_pairs.as<PairDev>(), ctx->d_aff.as<int32_t>(), ctx->d_items.as<Item>(), nitems,
-                         ctx->d_ticket.as<int>(), ctx->max_bins, ctx->max_rows_words, ch.variant, ch.threads, ch.ctas,
-                         Q, O, ctx->stream),
+                         ctx->d_ticket.as<int>(), ctx->max_bins, ctx->max_rows_words, ctx->max_zplanes, ch.variant,
+                         ch.threads, ch.ctas, ch.tile, Q, O, ctx->stream),
           "batched kernel");
     if (record) MI_CU(record_event(ctx->ev1, ctx->stream), "event");
     return MI_OK;
@@ -1060,7 +1144,7 @@ mi_status run_batched(mi_ctx *ctx, int nitems, const QSet &Q, const Outputs &O, 
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
         // set kernel attributes outside of capture
-        batched_ctas_per_sm(ch.variant, ctx->max_bins, ch.threads, ctx->max_rows_words);
+        batched_ctas_per_sm(ch.variant, ctx->max_bins, ch.threads, ctx->max_rows_words, ctx->max_zplanes);
         cudaGraph_t g;
         MI_CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed), "begin capture");
         cudaMemcpyAsync(ctx->d_aff.p, ctx->h_aff.p, aff_bytes, cudaMemcpyHostToDevice, ctx->stream);
@@ -1130,9 +1214,23 @@ mi_status eval_core(mi_ctx *ctx, const EvalReq &R, const float *qv, int nq, doub
         if (it != ctx->tuned.end()) {
             ch = it->second;
         } else {
+            // heuristic (the plain form is not autotuned): the first of these kinds that fits, with
+            // 1024 threads and two rows per warp step where the fetch allows it
+            const int order[] = {HV_U32_GATHER, HV_ROWS_GATHER, HV_U16_GATHER, HV_U32_QUAD, HV_ROWS_QUAD,
+                                 HV_U16_QUAD, HV_U32, HV_U16};
             ch = cands.front();
-            for (const Choice &c : cands)
-                if (c.variant == (ctx->max_bins <= 181 ? HV_U32 : HV_U16) && c.threads == 1024) ch = c;
+            bool found = false;
+            for (int v : order) {
+                if (v == HV_U32_GATHER || v == HV_U32_QUAD || v == HV_U32)
+                    if (ctx->max_bins > 181) continue;
+                for (const Choice &c : cands)
+                    if (c.variant == v && c.threads == 1024 && (c.tile.lpr_log2 == 4 || hv_fetch(v) < FM_QUAD)) {
+                        ch = c;
+                        found = true;
+                        break;
+                    }
+                if (found) break;
+            }
             ctx->tuned[key] = ch;
         }
         st = run_plain(ctx, 0, d_aff, n, Q, O, ch, R.dump);
@@ -1176,9 +1274,9 @@ mi_status eval_core(mi_ctx *ctx, const EvalReq &R, const float *qv, int nq, doub
         MI_CU(ctx->h_aff.ensure((size_t)n * 48), "pinned staging");
         MI_CU(ctx->h_items.ensure((size_t)n * sizeof(Item)), "pinned staging");
         char kb[512];
-        int off = snprintf(kb, sizeof kb, "b:%d:%d:%d:%d:%d:%p:%p:%p:%p:%p:%p:%p:%d:%d", n, nq, ch.variant, ch.threads,
-                           ch.ctas, ctx->d_aff.p, ctx->d_items.p, ctx->d_mi.p, ctx->d_h.p, ctx->d_cnt.p, ctx->h_aff.p,
-                           ctx->h_items.p, Q.form, Q.bits);
+        int off = snprintf(kb, sizeof kb, "b:%d:%d:%d:%d:%d:%d:%d:%p:%p:%p:%p:%p:%p:%p:%d:%d", n, nq, ch.variant,
+                           ch.threads, ch.ctas, ch.tile.lpr_log2, ch.tile.slabs, ctx->d_aff.p, ctx->d_items.p,
+                           ctx->d_mi.p, ctx->d_h.p, ctx->d_cnt.p, ctx->h_aff.p, ctx->h_items.p, Q.form, Q.bits);
         for (int i = 0; i < nq && off < (int)sizeof kb - 40; ++i)
             off += snprintf(kb + off, sizeof kb - off, ":%08x:%p", fbits(Q.q[i]), (const void *)Q.tab[i]);
         st = run_batched(ctx, n, Q, O, ch, use_graph, kb, h_aff, (size_t)n * 48, items.data(), (size_t)n * sizeof(Item));
@@ -1311,6 +1409,8 @@ void mi_options_default(mi_options *opt) {
     opt->sample_fraction = 0.0f;
     opt->sample_seed = 0u;
     opt->transform = MI_TRANSFORM_PARAMS;
+    opt->tile_rows = 0;
+    opt->tile_slabs = 0;
 }
 
 const char *mi_version(void) { return "gb300-mi 0.1 (sm_103a)"; }
@@ -1579,14 +1679,34 @@ mi_status mi_last_kernel_ms(mi_ctx *ctx, float *ms, int *launches) {
     return MI_OK;
 }
 
-int mi_selected_variant(mi_ctx *ctx, int pair, int n) {
-    if (!ctx) return -1;
-    (void)pair;
+static const Choice *selected_choice(mi_ctx *ctx, int n) {
     const int path = ctx->opt.path == MI_PATH_AUTO ? ((ctx->pairs.size() > 1 || n >= ctx->sms) ? MI_PATH_BATCHED : MI_PATH_PLAIN)
                                                    : ctx->opt.path;
     const int bucket = path == MI_PATH_BATCHED ? (n >= 4 * ctx->sms ? 2 : (n >= ctx->sms ? 1 : 0)) : 0;
     auto it = ctx->tuned.find(std::make_tuple(path, path == MI_PATH_BATCHED ? -1 : 0, bucket));
-    return it == ctx->tuned.end() ? -1 : it->second.variant;
+    return it == ctx->tuned.end() ? nullptr : &it->second;
+}
+
+int mi_selected_variant(mi_ctx *ctx, int pair, int n) {
+    if (!ctx) return -1;
+    (void)pair;
+    const Choice *c = selected_choice(ctx, n);
+    return c ? c->variant : -1;
+}
+
+mi_status mi_selected_config(mi_ctx *ctx, int n, int out[5]) {
+    if (!ctx || !out) return MI_EINVAL;
+    const Choice *c = selected_choice(ctx, n);
+    if (!c) {
+        for (int i = 0; i < 5; ++i) out[i] = -1;
+        return MI_OK;
+    }
+    out[0] = c->variant;
+    out[1] = c->threads;
+    out[2] = c->ctas;
+    out[3] = 32 >> c->tile.lpr_log2;
+    out[4] = c->tile.slabs;
+    return MI_OK;
 }
 
 }  // extern "C"

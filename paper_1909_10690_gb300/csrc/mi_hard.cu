@@ -32,7 +32,6 @@ namespace mi {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kSlabs = 4;  // slabs per sweep in the batched kernel
 constexpr uint32_t kEmptyKey = 0xffffffffu;
 
 // ---------------------------------------------------------------------------
@@ -180,6 +179,62 @@ __device__ __forceinline__ int quad_lerp(unsigned ux, unsigned uy, unsigned uz, 
     const int e10 = lerp8g((int)t[4], (int)t[5], fx, gx), e11 = lerp8g((int)t[6], (int)t[7], fx, gx);
     const int g0 = lerp8g(e00, e01, fy, gy), g1 = lerp8g(e10, e11, fy, gy);
     return lerp8g(g0, g1, fz, gz);
+}
+
+// Trilinear value from the four z-pair texels of a gathered 2 x 2 footprint (moving depth <= 12).
+// Each 32-bit texel holds v(x, y, z) in bits 0..11 and v(x, y, z + 1) in bits 20..31, so one 64-bit
+// product-sum p * (256 - f) + p' * f + (128 + 128 * 2^20) carries the stage lerps of both planes in
+// separate 20-bit fields: each field stays below 4095 * 256 + 128 < 2^20 and never carries into the
+// next.  Shifting right by 8 and masking leaves both results packed the same way, ready for the next
+// stage; the z stage forms g0 (256 - fz) + g1 fz + 128 in bits 20..39 of g * (fz + (256 - fz) 2^20)
+// + 128 * 2^20 (its low term g0 fz stays below 2^20).  Same weights, stage order and rounding as
+// quad_lerp: (a (256 - w) + b w + 128) >> 8, x then y then z.
+__device__ __forceinline__ uint32_t zpair_stage(uint32_t p, uint32_t p1, uint32_t g, uint32_t f) {
+    const unsigned long long x = (unsigned long long)p * g + (unsigned long long)p1 * f + (128ull | (128ull << 20));
+    return __funnelshift_r((uint32_t)x, (uint32_t)(x >> 32), 8) & 0xFFF00FFFu;
+}
+
+__device__ __forceinline__ int zpair_lerp(unsigned ux, unsigned uy, unsigned uz, uint32_t p00, uint32_t p10,
+                                          uint32_t p01, uint32_t p11) {
+    const uint32_t fx = __byte_perm(ux, 0u, 0x4441), fy = __byte_perm(uy, 0u, 0x4441),
+                   fz = __byte_perm(uz, 0u, 0x4441);
+    const uint32_t e0 = zpair_stage(p00, p10, 256u - fx, fx);  // x stage at y, both planes
+    const uint32_t e1 = zpair_stage(p01, p11, 256u - fx, fx);  // x stage at y + 1
+    const uint32_t g = zpair_stage(e0, e1, 256u - fy, fy);     // y stage, both planes
+    const unsigned long long z = (unsigned long long)g * (fz | ((256u - fz) << 20)) + (128ull << 20);
+    return (int)(__funnelshift_r((uint32_t)z, (uint32_t)(z >> 32), 28) & 0xFFFu);
+}
+
+// The 8 neighbours of the sample at 16.16 index (ux, uy, uz) in one gather from the z-pair atlas:
+// the float coordinates ix + 1 + ox, iy + 1 + oy (exact integers, so the gather's 2 x 2 footprint
+// starts at texel (ix, iy) of plane iz's tile) are formed from the bit pattern 2^23 + ix plus the
+// plane's stored offset ox + 1 - 2^23.  The gather returns (ix, iy + 1), (ix + 1, iy + 1),
+// (ix + 1, iy), (ix, iy).  On the last plane of an axis the upper neighbour's weight is 0, so the
+// texel beyond the tile edge (the next tile, or a clamped one) changes nothing.
+__device__ __forceinline__ int gather_value(unsigned long long tex, const float2 *zoff, unsigned ux, unsigned uy,
+                                            unsigned uz) {
+    const float2 o = zoff[uz >> 16];
+    const float u = __int_as_float((int)__funnelshift_r(ux, 0x4B00u, 16)) + o.x;
+    const float v = __int_as_float((int)__funnelshift_r(uy, 0x4B00u, 16)) + o.y;
+    const uint4 t = tex2Dgather<uint4>((cudaTextureObject_t)tex, u, v, 0);
+    return zpair_lerp(ux, uy, uz, t.w, t.z, t.x, t.y);
+}
+
+// Builds the z-pair atlas (see launch_make_zpairs).
+template <typename T>
+__global__ void k_make_zpairs(const T *__restrict__ in, int n0, int n1, int n2, int ph, int W,
+                              uint32_t *__restrict__ out) {
+    const long long plane = (long long)n0 * n1, n = plane * n2;
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n; o += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(o % n0);
+        const int y = (int)((o / n0) % n1);
+        const int z = (int)(o / plane);
+        const int z1 = min(z + 1, n2 - 1);
+        const long long src = (long long)y * n0 + x;
+        const uint32_t v = (uint32_t)in[plane * z + src] | ((uint32_t)in[plane * z1 + src] << 20);
+        const long long ox = (long long)(z / ph) * n0 + x, oy = (long long)(z % ph) * n1 + y;
+        out[oy * W + ox] = v;
+    }
 }
 
 // Builds the 2 x 2 quads: out has dims (n0, n1, n2 + 1), the last plane repeated.
@@ -449,10 +504,11 @@ struct HistGlobal {
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct SmemLayout {
-    size_t hist, okey, ocnt, bmap, rinfo, rows, cols, red, total;
+    size_t hist, okey, ocnt, bmap, rinfo, rows, cols, red, zoff, total;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(int variant, int bins, int threads, int rows_words) {
+// zmax: planes of the largest moving volume (the gather variants keep one float2 offset per plane).
+__host__ __device__ inline SmemLayout smem_layout(int variant, int bins, int threads, int rows_words, int zmax) {
     SmemLayout L;
     const size_t B2 = (size_t)bins * bins;
     const int kind = hv_kind(variant);
@@ -479,6 +535,8 @@ __host__ __device__ inline SmemLayout smem_layout(int variant, int bins, int thr
     o = align_up(o, 16);
     L.red = o;
     o += (size_t)(3 * 32 + 3 * kMaxQ + 1) * 8;
+    L.zoff = o;
+    if (hv_fetch(variant) == FM_GATHER) o += (size_t)zmax * 8;
     L.total = o;
     (void)threads;
     return L;
@@ -539,8 +597,11 @@ __device__ typename HistOf<HV>::T make_hist(unsigned char *smem, const SmemLayou
 // visited (the batched kernel passes one slab of blocks at a time).
 // The interpolated moving value at a 16.16 index, through the variant's fetch path.
 template <int FM, typename PairT>
-__device__ __forceinline__ int sample_value(const PairDev &P, unsigned U0, unsigned U1, unsigned U2) {
-    if constexpr (FM == FM_QUAD) {
+__device__ __forceinline__ int sample_value(const PairDev &P, const float2 *zoff, unsigned U0, unsigned U1,
+                                            unsigned U2) {
+    if constexpr (FM == FM_GATHER) {
+        return gather_value(P.texg, zoff, U0, U1, U2);
+    } else if constexpr (FM == FM_QUAD) {
         uint32_t t[8];
         quad_fetch(P.texq, U0, U1, U2, t);
         return quad_lerp(U0, U1, U2, t);
@@ -555,8 +616,9 @@ __device__ __forceinline__ int sample_value(const PairDev &P, unsigned U0, unsig
 // A clipped row [lo, hi] under random sampling: its sampled voxels only, 32 at a time; U at an
 // entry's x index i is u_lo + st (i - lo), exact inside the interval.
 template <int FM, typename PairT, class Hist>
-__device__ __forceinline__ void sampled_row(const PairDev &P, long long r, int lo, int hi, unsigned ub0, unsigned ub1,
-                                            unsigned ub2, int st0, int st1, int st2, Hist &H) {
+__device__ __forceinline__ void sampled_row(const PairDev &P, const float2 *zoff, long long r, int lo, int hi,
+                                            unsigned ub0, unsigned ub1, unsigned ub2, int st0, int st1, int st2,
+                                            Hist &H) {
     const int lane = threadIdx.x & 31;
     const int bins = P.bins, mdepth = P.mdepth;
     const uint32_t k0 = __ldg(P.srow + r), k1 = __ldg(P.srow + r + 1);
@@ -571,7 +633,7 @@ __device__ __forceinline__ void sampled_row(const PairDev &P, long long r, int l
         int bf = 0, bm = 0;
         if (valid) {
             const unsigned d = (unsigned)(i - lo);
-            const int v = sample_value<FM, PairT>(P, ub0 + (unsigned)st0 * d, ub1 + (unsigned)st1 * d,
+            const int v = sample_value<FM, PairT>(P, zoff, ub0 + (unsigned)st0 * d, ub1 + (unsigned)st1 * d,
                                                   ub2 + (unsigned)st2 * d);
             bm = (v * bins) >> mdepth;
             bf = (int)__ldg(P.sbin + k);
@@ -581,8 +643,8 @@ __device__ __forceinline__ void sampled_row(const PairDev &P, long long r, int l
 }
 
 template <typename PairT, int FM, class Hist>
-__device__ void accumulate_rows(const PairDev &P, const int *q, long long first_block, long long block_stride,
-                                long long n_end, Hist &H) {
+__device__ void accumulate_rows(const PairDev &P, const int *q, const float2 *zoff, long long first_block,
+                                long long block_stride, long long n_end, Hist &H) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int nf0 = P.nf[0], nf1 = P.nf[1];
     const long long R = (long long)nf1 * P.nf[2];
@@ -612,44 +674,12 @@ __device__ void accumulate_rows(const PairDev &P, const int *q, long long first_
             const unsigned ub0 = (unsigned)__shfl_sync(kFull, mine.u0, s), ub1 = (unsigned)__shfl_sync(kFull, mine.u1, s),
                            ub2 = (unsigned)__shfl_sync(kFull, mine.u2, s);
             if (P.srow != nullptr) {  // random sampling: the row's sampled voxels only
-                sampled_row<FM, PairT>(P, r, lo, hi, ub0, ub1, ub2, st0, st1, st2, H);
+                sampled_row<FM, PairT>(P, zoff, r, lo, hi, ub0, ub1, ub2, st0, st1, st2, H);
                 continue;
             }
             // unsigned: lanes past the row end may step outside the int range; only in-range lanes use them
             unsigned U0 = ub0 + (unsigned)st0 * lane, U1 = ub1 + (unsigned)st1 * lane, U2 = ub2 + (unsigned)st2 * lane;
             const uint8_t *__restrict__ frow = P.fbins + (size_t)r * nf0;
-            if constexpr (FM == FM_QUAD) {
-                // full steps (all 32 lanes inside the interval) without predicates; the fixed bin of
-                // the next step is loaded one step ahead, so its L2 latency overlaps a whole step
-                const unsigned d0 = 32u * (unsigned)st0, d1 = 32u * (unsigned)st1, d2 = 32u * (unsigned)st2;
-                int base = lo;
-                const uint8_t *__restrict__ fp = frow + lo + lane;
-                int bf_next = base + 31 <= hi ? (int)__ldg(fp) : 0;
-#pragma unroll 2
-                for (; base + 31 <= hi; base += 32) {
-                    const int bf = bf_next;
-                    fp += 32;
-                    if (base + 63 <= hi) bf_next = (int)__ldg(fp);
-                    uint32_t t[8];
-                    quad_fetch(P.texq, U0, U1, U2, t);
-                    H.add(bf, (quad_lerp(U0, U1, U2, t) * bins) >> mdepth, true);
-                    U0 += d0;
-                    U1 += d1;
-                    U2 += d2;
-                }
-                if (base <= hi) {  // the tail: lanes up to hi - base
-                    const bool valid = base + lane <= hi;
-                    int bf = 0, bm = 0;
-                    if (valid) {
-                        uint32_t t[8];
-                        quad_fetch(P.texq, U0, U1, U2, t);
-                        bm = (quad_lerp(U0, U1, U2, t) * bins) >> mdepth;
-                        bf = (int)__ldg(frow + base + lane);
-                    }
-                    H.add(bf, bm, valid);
-                }
-                continue;
-            }
             for (int i = lo + lane; i - lane <= hi; i += 32) {
                 const bool valid = i <= hi;
                 int bf = 0, bm = 0;
@@ -657,8 +687,10 @@ __device__ void accumulate_rows(const PairDev &P, const int *q, long long first_
                     int v;
                     if constexpr (FM == FM_TEX)
                         v = sample_hard_tex<PairT>(P.texp, (int)U0, (int)U1, (int)U2);
-                    else
+                    else if constexpr (FM == FM_LDG)
                         v = sample_hard_pair<PairT>(movp, sy, sz, n0, sz, (int)U0, (int)U1, (int)U2);
+                    else
+                        v = sample_value<FM, PairT>(P, zoff, U0, U1, U2);
                     bm = (v * bins) >> mdepth;
                     bf = (int)__ldg(frow + i);
                 }
@@ -668,6 +700,100 @@ __device__ void accumulate_rows(const PairDev &P, const int *q, long long first_
                 U2 += 32u * (unsigned)st2;
             }
         }
+    }
+}
+
+// Row-group walk (quad and gather fetches, every fixed voxel).  Rows are clipped 32 at a time as in
+// accumulate_rows; then each warp step covers G = 32 >> lpr_log2 adjacent rows of the batch with
+// L = 1 << lpr_log2 lanes each (lane = row-in-group * L + column), so a row whose overlap is not a
+// multiple of 32 wastes at most L - 1 lanes in its last step, and one clip broadcast serves G rows.
+// Steps in which every lane of every row is inside its interval run without predicates; the last
+// ones (up to the longest row of the group) are predicated.  The fixed bin of the next full step is
+// loaded one step ahead.
+template <int FM, class Hist>
+__device__ void accumulate_groups(const PairDev &P, const int *q, const float2 *zoff, long long first_block,
+                                  long long block_stride, long long n_end, int lpr_log2, Hist &H) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int nf0 = P.nf[0], nf1 = P.nf[1];
+    const long long R = (long long)nf1 * P.nf[2];
+    const int st0 = q[0], st1 = q[4], st2 = q[8];
+    const int bins = P.bins, mdepth = P.mdepth;
+    const int lpr = 1 << lpr_log2, gsz = 32 >> lpr_log2;
+    const int sub = lane >> lpr_log2, col = lane & (lpr - 1);
+    const unsigned d0 = (unsigned)st0 << lpr_log2, d1 = (unsigned)st1 << lpr_log2, d2 = (unsigned)st2 << lpr_log2;
+    for (long long n0b = 0;; n0b += 32) {
+        if (first_block + n0b * block_stride >= n_end) break;
+        RowClip mine;
+        mine.lo = 0;
+        mine.hi = -1;
+        mine.u0 = mine.u1 = mine.u2 = 0;
+        const long long nl = first_block + (n0b + lane) * block_stride;
+        if (nl < n_end) {
+            const long long rl = nl * nwarps + warp;
+            if (rl < R) mine = clip_row(q, (int)(rl % nf1), (int)(rl / nf1), nf0, P.nm);
+        }
+        for (int s0 = 0; s0 < 32; s0 += gsz) {
+            if (first_block + (n0b + s0) * block_stride >= n_end) break;  // warp-uniform
+            const int s = s0 + sub;
+            const int lo = __shfl_sync(kFull, mine.lo, s), hi = __shfl_sync(kFull, mine.hi, s);
+            const int len = hi >= lo ? hi - lo + 1 : 0;  // rows past the end were clipped empty
+            const int kfull = (int)__reduce_min_sync(kFull, (unsigned)(len >> lpr_log2));
+            const int kall = (int)__reduce_max_sync(kFull, (unsigned)((len + lpr - 1) >> lpr_log2));
+            if (kall == 0) continue;
+            const unsigned ub0 = (unsigned)__shfl_sync(kFull, mine.u0, s), ub1 = (unsigned)__shfl_sync(kFull, mine.u1, s),
+                           ub2 = (unsigned)__shfl_sync(kFull, mine.u2, s);
+            const long long r = (first_block + (n0b + s) * block_stride) * nwarps + warp;
+            // unsigned: lanes past their row's end may step outside the int range; only in-range lanes use them
+            unsigned U0 = ub0 + (unsigned)st0 * col, U1 = ub1 + (unsigned)st1 * col, U2 = ub2 + (unsigned)st2 * col;
+            const uint8_t *__restrict__ fp = P.fbins + (len > 0 ? (size_t)r * nf0 + lo + col : 0);
+            int k = 0;
+            int bf_next = kfull > 0 ? (int)__ldg(fp) : 0;
+#pragma unroll 2
+            for (; k < kfull; ++k) {
+                const int bf = bf_next;
+                fp += lpr;
+                if (k + 1 < kfull) bf_next = (int)__ldg(fp);
+                H.add(bf, (sample_value<FM, uint32_t>(P, zoff, U0, U1, U2) * bins) >> mdepth, true);
+                U0 += d0;
+                U1 += d1;
+                U2 += d2;
+            }
+            for (; k < kall; ++k) {
+                const bool valid = (k << lpr_log2) + col < len;
+                int bf = 0, bm = 0;
+                if (valid) {
+                    bm = (sample_value<FM, uint32_t>(P, zoff, U0, U1, U2) * bins) >> mdepth;
+                    bf = (int)__ldg(fp);
+                }
+                H.add(bf, bm, valid);
+                fp += lpr;
+                U0 += d0;
+                U1 += d1;
+                U2 += d2;
+            }
+        }
+    }
+}
+
+// The voxel walk of a variant: quad and gather fetches over every fixed voxel take the row-group walk,
+// the others (and random sampling) the one-row-at-a-time walk.
+template <typename PairT, int FM, class Hist>
+__device__ __forceinline__ void walk_rows(const PairDev &P, const int *q, const float2 *zoff, long long first_block,
+                                          long long block_stride, long long n_end, int lpr_log2, Hist &H) {
+    if constexpr (FM == FM_QUAD || FM == FM_GATHER) {
+        if (P.srow == nullptr) {
+            accumulate_groups<FM>(P, q, zoff, first_block, block_stride, n_end, lpr_log2, H);
+            return;
+        }
+    }
+    accumulate_rows<PairT, FM>(P, q, zoff, first_block, block_stride, n_end, H);
+}
+
+// Copies the per-plane atlas offsets of pair P into shared memory (gather fetches only).
+template <int FM>
+__device__ __forceinline__ void load_zoff(const PairDev &P, float2 *s_zoff) {
+    if constexpr (FM == FM_GATHER) {
+        for (int z = threadIdx.x; z < P.nm[2]; z += blockDim.x) s_zoff[z] = P.zoff[z];
     }
 }
 
@@ -705,6 +831,48 @@ __device__ __forceinline__ void block_sum3(double &a, double &b, double &c, doub
         a += s_red[3 * w + 0];
         b += s_red[3 * w + 1];
         c += s_red[3 * w + 2];
+    }
+}
+
+// Entropies and MI of transform t from the overlap count N and, per q, the sums over the fixed
+// marginal, the moving marginal and the joint cells (res[3 q + 0..2]) of c ln c (q == 1) or c^q:
+// H = ln N - S / N (Eq. 1), S_q = (1 - N^-q S) / (q - 1), MI = H_F + H_M - H_FM (Eq. 2) plus
+// (1 - q) S_q(F) S_q(M) in the pseudo-additive form.  One thread.
+__device__ void write_mi(double N, const double *res, const QSet &Q, long long t, const Outputs &O) {
+    const int nq = Q.nq;
+    if (O.count) O.count[t] = (long long)N;
+    if (N <= 0.0 && O.flags) atomicOr(&O.flags[0], 1);
+    for (int iq = 0; iq < nq; ++iq) {
+        const float qf = Q.q[iq];
+        const double SF = res[3 * iq + 0], SM = res[3 * iq + 1], SJ = res[3 * iq + 2];
+        double hf, hm, hj;
+        if (N <= 0.0) {
+            hf = hm = hj = __longlong_as_double(0x7ff8000000000000ll);
+        } else if (qf == 1.0f) {
+            const double lnN = log(N);
+            hf = lnN - SF / N;
+            hm = lnN - SM / N;
+            hj = lnN - SJ / N;
+            if (Q.bits) {
+                const double l2 = log(2.0);
+                hf /= l2;
+                hm /= l2;
+                hj /= l2;
+            }
+        } else {
+            const double q = (double)qf, Nq = pow(N, -q);
+            hf = (1.0 - Nq * SF) / (q - 1.0);
+            hm = (1.0 - Nq * SM) / (q - 1.0);
+            hj = (1.0 - Nq * SJ) / (q - 1.0);
+        }
+        double I = hf + hm - hj;
+        if (qf != 1.0f && Q.form == 1) I += (1.0 - (double)qf) * hf * hm;
+        if (O.mi) O.mi[t * nq + iq] = I;
+        if (O.h) {
+            O.h[(t * nq + iq) * 3 + 0] = hf;
+            O.h[(t * nq + iq) * 3 + 1] = hm;
+            O.h[(t * nq + iq) * 3 + 2] = hj;
+        }
     }
 }
 
@@ -760,43 +928,7 @@ __device__ void reduce_entropies(const Hist &H, int B, const QSet &Q, uint32_t *
         }
     }
     __syncthreads();
-    if (tid == 0) {
-        const double N = s_res[3 * kMaxQ];
-        if (O.count) O.count[t] = (long long)N;
-        if (N <= 0.0 && O.flags) atomicOr(&O.flags[0], 1);
-        for (int iq = 0; iq < nq; ++iq) {
-            const float qf = Q.q[iq];
-            const double SF = s_res[3 * iq + 0], SM = s_res[3 * iq + 1], SJ = s_res[3 * iq + 2];
-            double hf, hm, hj;
-            if (N <= 0.0) {
-                hf = hm = hj = __longlong_as_double(0x7ff8000000000000ll);
-            } else if (qf == 1.0f) {
-                const double lnN = log(N);
-                hf = lnN - SF / N;
-                hm = lnN - SM / N;
-                hj = lnN - SJ / N;
-                if (Q.bits) {
-                    const double l2 = log(2.0);
-                    hf /= l2;
-                    hm /= l2;
-                    hj /= l2;
-                }
-            } else {
-                const double q = (double)qf, Nq = pow(N, -q);
-                hf = (1.0 - Nq * SF) / (q - 1.0);
-                hm = (1.0 - Nq * SM) / (q - 1.0);
-                hj = (1.0 - Nq * SJ) / (q - 1.0);
-            }
-            double I = hf + hm - hj;
-            if (qf != 1.0f && Q.form == 1) I += (1.0 - (double)qf) * hf * hm;
-            if (O.mi) O.mi[t * nq + iq] = I;
-            if (O.h) {
-                O.h[(t * nq + iq) * 3 + 0] = hf;
-                O.h[(t * nq + iq) * 3 + 1] = hm;
-                O.h[(t * nq + iq) * 3 + 2] = hj;
-            }
-        }
-    }
+    if (tid == 0) write_mi(s_res[3 * kMaxQ], s_res, Q, t, O);
     __syncthreads();
 }
 
@@ -807,20 +939,23 @@ __device__ void reduce_entropies(const Hist &H, int B, const QSet &Q, uint32_t *
 template <typename PairT, int HV, int FM>
 __global__ void __launch_bounds__(1024, 1)
     k_hist(const PairDev *__restrict__ pairs, const int32_t *__restrict__ aff, uint32_t *__restrict__ ghist,
-           int *flags) {
+           int *flags, Tile tile) {
     extern __shared__ __align__(16) unsigned char smem[];
     const PairDev P = pairs[0];
     const int t = blockIdx.y;
     const int B = P.bins;
-    const SmemLayout L = smem_layout(HV, B, blockDim.x, P.rows_words);
+    const SmemLayout L = smem_layout(HV, B, blockDim.x, P.rows_words, P.nm[2]);
     __shared__ int q[12];
     if (threadIdx.x < 12) q[threadIdx.x] = aff[(size_t)t * 12 + threadIdx.x];
+    float2 *s_zoff = (float2 *)(smem + L.zoff);
+    load_zoff<FM>(P, s_zoff);
     auto H = make_hist<HV>(smem, L, B, flags, P.rows_words);
     H.load_info(P.rowinfo);
     H.zero();
     __syncthreads();
     const int nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
-    accumulate_rows<PairT, FM>(P, q, blockIdx.x, gridDim.x, ((long long)P.nf[1] * P.nf[2] + nwarps - 1) / nwarps, H);
+    walk_rows<PairT, FM>(P, q, s_zoff, blockIdx.x, gridDim.x, ((long long)P.nf[1] * P.nf[2] + nwarps - 1) / nwarps,
+                         tile.lpr_log2, H);
     __syncthreads();
     uint32_t *gh = ghist + (size_t)t * B * B;
     for (int r = threadIdx.x >> 5; r < B; r += nwarps)
@@ -845,6 +980,98 @@ __global__ void __launch_bounds__(1024, 1)
                      (double *)(smem + entropy_red_offset(B)), t, O);
 }
 
+// The same reduction split over `parts` CTAs per transform, for calls with few transforms (the plain
+// form's one-transform calls), where one CTA per transform would leave the GPU idle.  CTA (p, t) takes
+// rows p, p + parts, ... of histogram t: their sums (the fixed marginal) and terms, the joint terms of
+// their cells and their part of the column sums (the moving marginal, into cols[t], zeroed by the
+// caller).  part[(t parts + p) (1 + 2 kMaxQ)]: the count, then per q the joint and fixed-marginal sums.
+constexpr int kPartStride = 1 + 2 * kMaxQ;
+
+__global__ void __launch_bounds__(256)
+    k_entropy_part(const uint32_t *__restrict__ ghist, int B, QSet Q, uint32_t *__restrict__ cols,
+                   double *__restrict__ part, int parts) {
+    __shared__ uint32_t s_cols[256];
+    __shared__ double s_red[3 * 32];
+    const int t = blockIdx.y, p = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t *h = ghist + (size_t)t * B * B;
+    for (int c = tid; c < B; c += blockDim.x) s_cols[c] = 0;
+    __syncthreads();
+    double n = 0.0, aj[kMaxQ], af[kMaxQ];
+#pragma unroll
+    for (int iq = 0; iq < kMaxQ; ++iq) aj[iq] = af[iq] = 0.0;
+    for (int r = p + parts * warp; r < B; r += parts * nwarps) {
+        uint32_t rsum = 0;
+        for (int c = lane; c < B; c += 32) {
+            const uint32_t v = __ldg(h + (size_t)r * B + c);
+            if (v) {
+                rsum += v;
+                atomicAdd(&s_cols[c], v);
+#pragma unroll
+                for (int iq = 0; iq < kMaxQ; ++iq)
+                    if (iq < Q.nq) aj[iq] += term(v, iq, Q);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rsum += __shfl_xor_sync(kFull, rsum, o);
+        if (lane == 0 && rsum) {
+            n += (double)rsum;
+#pragma unroll
+            for (int iq = 0; iq < kMaxQ; ++iq)
+                if (iq < Q.nq) af[iq] += term(rsum, iq, Q);
+        }
+    }
+    __syncthreads();
+    for (int c = tid; c < B; c += blockDim.x)
+        if (s_cols[c]) atomicAdd(cols + (size_t)t * B + c, s_cols[c]);
+    double *out = part + ((size_t)t * parts + p) * kPartStride;
+    double z = 0.0;
+    block_sum3(n, z, z, s_red);
+    if (tid == 0) out[0] = n;
+    for (int iq = 0; iq < Q.nq; ++iq) {
+        double a = aj[iq], b = af[iq];
+        z = 0.0;
+        block_sum3(a, b, z, s_red);
+        if (tid == 0) {
+            out[1 + 2 * iq] = a;
+            out[2 + 2 * iq] = b;
+        }
+    }
+}
+
+// Finishes the split reduction: the moving-marginal terms from cols[t], the parts' sums, then MI.
+__global__ void __launch_bounds__(256)
+    k_entropy_final(const uint32_t *__restrict__ cols, const double *__restrict__ part, int parts, int B, QSet Q,
+                    Outputs O) {
+    __shared__ double s_red[3 * 32];
+    __shared__ double s_res[3 * kMaxQ + 1];
+    const int t = blockIdx.x, tid = threadIdx.x;
+    for (int iq = 0; iq < Q.nq; ++iq) {
+        double am = 0.0, z0 = 0.0, z1 = 0.0;
+        for (int c = tid; c < B; c += blockDim.x) {
+            const uint32_t v = cols[(size_t)t * B + c];
+            if (v) am += term(v, iq, Q);
+        }
+        block_sum3(am, z0, z1, s_red);
+        if (tid == 0) {
+            double sj = 0.0, sf = 0.0;
+            for (int p = 0; p < parts; ++p) {
+                const double *in = part + ((size_t)t * parts + p) * kPartStride;
+                sj += in[1 + 2 * iq];
+                sf += in[2 + 2 * iq];
+            }
+            s_res[3 * iq + 0] = sf;
+            s_res[3 * iq + 1] = am;
+            s_res[3 * iq + 2] = sj;
+        }
+    }
+    if (tid == 0) {
+        double N = 0.0;
+        for (int p = 0; p < parts; ++p) N += part[((size_t)t * parts + p) * kPartStride];
+        write_mi(N, s_res, Q, t, O);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Batched form: persistent CTAs, one (pair, transform) item per CTA at a time
 // ---------------------------------------------------------------------------
@@ -852,12 +1079,14 @@ __global__ void __launch_bounds__(1024, 1)
 template <int HV, int FM>
 __global__ void __launch_bounds__(1024, 1)
     k_batched(const PairDev *__restrict__ pairs, const int32_t *__restrict__ aff, const Item *__restrict__ items,
-              int nitems, int *ticket, int max_bins, int rows_words, QSet Q, Outputs O) {
+              int nitems, int *ticket, int max_bins, int rows_words, int zmax, Tile tile, QSet Q, Outputs O) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item, s_slab;
     __shared__ int q[12];
-    const SmemLayout L = smem_layout(HV, max_bins, blockDim.x, rows_words);
+    const SmemLayout L = smem_layout(HV, max_bins, blockDim.x, rows_words, zmax);
+    float2 *s_zoff = (float2 *)(smem + L.zoff);
     const int nwarps = blockDim.x >> 5;
+    const int slabs = tile.slabs;
     int *phase = ticket + 1;  // the slab most recently started by any CTA
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(ticket, 1);
@@ -868,22 +1097,23 @@ __global__ void __launch_bounds__(1024, 1)
         const PairDev P = pairs[I.pair];
         const int B = P.bins;
         if (threadIdx.x < 12) q[threadIdx.x] = aff[(size_t)I.t * 12 + threadIdx.x];
+        load_zoff<FM>(P, s_zoff);
         auto H = make_hist<HV>(smem, L, B, O.flags, P.rows_words);
         H.load_info(P.rowinfo);
         H.zero();
         __syncthreads();
-        // The sweep is cut into kSlabs slabs of row blocks, done in any order (counts do not depend
+        // The sweep is cut into `slabs` slabs of row blocks, done in any order (counts do not depend
         // on it).  Each slab goes to the first remaining one at or after the slab most recently
         // started by any CTA, so CTAs working on different transforms keep to neighbouring slabs
         // of the volumes and their working set stays in L2.  No CTA waits for another.
         const long long NB = ((long long)P.nf[1] * P.nf[2] + nwarps - 1) / nwarps;
-        const long long SB = (NB + kSlabs - 1) / kSlabs;
-        unsigned left = (1u << kSlabs) - 1u;
+        const long long SB = (NB + slabs - 1) / slabs;
+        unsigned left = (1u << slabs) - 1u;
         while (left) {
             if (threadIdx.x == 0) {
                 int k = *(volatile int *)phase;
-                k = k < 0 || k >= kSlabs ? 0 : k;
-                while (!((left >> k) & 1u)) k = k + 1 == kSlabs ? 0 : k + 1;
+                k = k < 0 || k >= slabs ? 0 : k;
+                while (!((left >> k) & 1u)) k = k + 1 == slabs ? 0 : k + 1;
                 s_slab = k;
                 *(volatile int *)phase = k;
             }
@@ -892,10 +1122,11 @@ __global__ void __launch_bounds__(1024, 1)
             left &= ~(1u << k);
             const long long b0 = (long long)k * SB, b1 = b0 + SB < NB ? b0 + SB : NB;
             if (b0 < b1) {
-                if (FM == FM_QUAD || P.mdtype == 1)  // quads are unpacked by the texture unit: one instance
-                    accumulate_rows<uint32_t, FM>(P, q, b0, 1, b1, H);
+                // quads and gathers are unpacked by the texture unit: one instance
+                if (FM == FM_QUAD || FM == FM_GATHER || P.mdtype == 1)
+                    walk_rows<uint32_t, FM>(P, q, s_zoff, b0, 1, b1, tile.lpr_log2, H);
                 else
-                    accumulate_rows<uint16_t, FM>(P, q, b0, 1, b1, H);
+                    walk_rows<uint16_t, FM>(P, q, s_zoff, b0, 1, b1, tile.lpr_log2, H);
             }
             __syncthreads();  // s_slab is rewritten for the next slab
         }
@@ -948,8 +1179,8 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 
 }  // namespace
 
-size_t hard_smem_bytes(int variant, int bins, int threads, int rows_words) {
-    return smem_layout(variant, bins, threads, rows_words).total;
+size_t hard_smem_bytes(int variant, int bins, int threads, int rows_words, int zmax) {
+    return smem_layout(variant, bins, threads, rows_words, zmax).total;
 }
 
 // MurmurHash3's 32-bit finalizer: xor-shift 16, multiply 0x85ebca6b, xor-shift 13, multiply 0xc2b2ae35,
@@ -1049,6 +1280,18 @@ cudaError_t launch_make_pairs(const void *mov, int dtype, const int nm[3], void 
     return cudaGetLastError();
 }
 
+cudaError_t launch_make_zpairs(const void *mov, int dtype, const int nm[3], int ph, int W, int H, uint32_t *out,
+                               cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, (size_t)W * H * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    const long long n = (long long)nm[0] * nm[1] * nm[2];
+    if (dtype == 0)
+        k_make_zpairs<uint8_t><<<grid_for(n, 256), 256, 0, s>>>((const uint8_t *)mov, nm[0], nm[1], nm[2], ph, W, out);
+    else
+        k_make_zpairs<uint16_t><<<grid_for(n, 256), 256, 0, s>>>((const uint16_t *)mov, nm[0], nm[1], nm[2], ph, W, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_make_quads(const void *mov, int dtype, const int nm[3], void *out, cudaStream_t s) {
     const long long n = (long long)nm[0] * nm[1] * (nm[2] + 1);
     if (dtype == 0)
@@ -1074,41 +1317,53 @@ cudaError_t launch_table(double *tab, float q, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Every variant as (public value, counter kind, fetch mode).
-#define MI_VARIANTS(X)                                                                              \
+// Every variant as (public value, counter kind, fetch mode): those that read x-pairs (whose element
+// type follows the moving type) and those whose texels the texture unit unpacks (one instance each).
+#define MI_VARIANTS_PAIRED(X)                                                                       \
     X(HV_U32, HV_U32, FM_LDG) X(HV_U32_MATCH, HV_U32_MATCH, FM_LDG) X(HV_U16, HV_U16, FM_LDG)        \
     X(HV_U16_MATCH, HV_U16_MATCH, FM_LDG) X(HV_TEX + HV_U32, HV_U32, FM_TEX)                        \
     X(HV_TEX + HV_U32_MATCH, HV_U32_MATCH, FM_TEX) X(HV_TEX + HV_U16, HV_U16, FM_TEX)                \
     X(HV_TEX + HV_U16_MATCH, HV_U16_MATCH, FM_TEX) X(HV_ROWS, HV_ROWS, FM_LDG)                      \
-    X(HV_ROWS_TEX, HV_ROWS, FM_TEX) X(HV_ROWS_QUAD, HV_ROWS, FM_QUAD) X(HV_U32_QUAD, HV_U32, FM_QUAD) \
-    X(HV_U16_QUAD, HV_U16, FM_QUAD)
+    X(HV_ROWS_TEX, HV_ROWS, FM_TEX)
+#define MI_VARIANTS_TEXEL(X)                                                                        \
+    X(HV_ROWS_QUAD, HV_ROWS, FM_QUAD) X(HV_U32_QUAD, HV_U32, FM_QUAD) X(HV_U16_QUAD, HV_U16, FM_QUAD) \
+    X(HV_ROWS_GATHER, HV_ROWS, FM_GATHER) X(HV_U32_GATHER, HV_U32, FM_GATHER)                       \
+    X(HV_U16_GATHER, HV_U16, FM_GATHER)
+#define MI_VARIANTS(X) MI_VARIANTS_PAIRED(X) MI_VARIANTS_TEXEL(X)
 
 template <typename MT>
 static const void *plain_fn_of(int variant) {
     switch (variant) {
 #define MI_PLAIN_CASE(V, K, F) \
     case V: return (const void *)k_hist<MT, K, F>;
-        MI_VARIANTS(MI_PLAIN_CASE)
+        MI_VARIANTS_PAIRED(MI_PLAIN_CASE)
 #undef MI_PLAIN_CASE
         default: return nullptr;
     }
 }
 
 static const void *plain_fn(int variant, int mdtype) {
-    return mdtype == 0 ? plain_fn_of<uint16_t>(variant) : plain_fn_of<uint32_t>(variant);
+    switch (variant) {
+#define MI_PLAIN_CASE(V, K, F) \
+    case V: return (const void *)k_hist<uint32_t, K, F>;
+        MI_VARIANTS_TEXEL(MI_PLAIN_CASE)
+#undef MI_PLAIN_CASE
+        default: return mdtype == 0 ? plain_fn_of<uint16_t>(variant) : plain_fn_of<uint32_t>(variant);
+    }
 }
 
 cudaError_t launch_plain_hist(const PairDev *d_pair, const PairDev &h_pair, const int32_t *d_aff, int n,
-                              uint32_t *d_hist, int variant, int threads, int ctas, int *d_flags, cudaStream_t s) {
+                              uint32_t *d_hist, int variant, int threads, int ctas, Tile tile, int *d_flags,
+                              cudaStream_t s) {
     const size_t B2 = (size_t)h_pair.bins * h_pair.bins;
     cudaError_t e = cudaMemsetAsync(d_hist, 0, (size_t)n * B2 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    const size_t smem = smem_layout(variant, h_pair.bins, threads, h_pair.rows_words).total;
+    const size_t smem = smem_layout(variant, h_pair.bins, threads, h_pair.rows_words, h_pair.nm[2]).total;
     const void *fn = plain_fn(variant, h_pair.mdtype);
     if (!fn) return cudaErrorInvalidValue;
     if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
-    void *args[] = {(void *)&d_pair, (void *)&d_aff, (void *)&d_hist, (void *)&d_flags};
+    void *args[] = {(void *)&d_pair, (void *)&d_aff, (void *)&d_hist, (void *)&d_flags, (void *)&tile};
     return cudaLaunchKernel(fn, dim3(ctas, n), dim3(threads), args, smem, s);
 }
 
@@ -1118,6 +1373,19 @@ cudaError_t launch_entropy(const uint32_t *d_hist, int n, int bins, const QSet &
     cudaError_t e = set_smem(k_entropy, smem);
     if (e != cudaSuccess) return e;
     k_entropy<<<n, threads, smem, s>>>(d_hist, bins, Q, O);
+    return cudaGetLastError();
+}
+
+int entropy_parts(int bins) { return bins >= 256 ? 32 : (bins / 8 > 1 ? bins / 8 : 1); }
+
+cudaError_t launch_entropy_split(const uint32_t *d_hist, int n, int bins, const QSet &Q, const Outputs &O,
+                                 uint32_t *d_cols, double *d_part, cudaStream_t s) {
+    const int parts = entropy_parts(bins);
+    cudaError_t e = cudaMemsetAsync(d_cols, 0, (size_t)n * bins * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    k_entropy_part<<<dim3(parts, n), 256, 0, s>>>(d_hist, bins, Q, d_cols, d_part, parts);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_entropy_final<<<n, 256, 0, s>>>(d_cols, d_part, parts, bins, Q, O);
     return cudaGetLastError();
 }
 
@@ -1131,8 +1399,8 @@ static const void *batched_fn(int variant) {
     }
 }
 
-int batched_ctas_per_sm(int variant, int max_bins, int threads, int rows_words) {
-    const size_t smem = smem_layout(variant, max_bins, threads, rows_words).total;
+int batched_ctas_per_sm(int variant, int max_bins, int threads, int rows_words, int zmax) {
+    const size_t smem = smem_layout(variant, max_bins, threads, rows_words, zmax).total;
     const void *fn = batched_fn(variant);
     if (!fn) return 0;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
@@ -1142,15 +1410,15 @@ int batched_ctas_per_sm(int variant, int max_bins, int threads, int rows_words) 
 }
 
 cudaError_t launch_batched(const PairDev *d_pairs, const int32_t *d_aff, const Item *d_items, int nitems,
-                           int *d_ticket, int max_bins, int rows_words, int variant, int threads, int ctas,
-                           const QSet &Q, const Outputs &O, cudaStream_t s) {
-    const size_t smem = smem_layout(variant, max_bins, threads, rows_words).total;
+                           int *d_ticket, int max_bins, int rows_words, int zmax, int variant, int threads, int ctas,
+                           Tile tile, const QSet &Q, const Outputs &O, cudaStream_t s) {
+    const size_t smem = smem_layout(variant, max_bins, threads, rows_words, zmax).total;
     const void *fn = batched_fn(variant);
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&d_pairs, (void *)&d_aff, (void *)&d_items, (void *)&nitems, (void *)&d_ticket,
-                    (void *)&max_bins, (void *)&rows_words, (void *)&Q, (void *)&O};
+                    (void *)&max_bins, (void *)&rows_words, (void *)&zmax, (void *)&tile, (void *)&Q, (void *)&O};
     return cudaLaunchKernel(fn, dim3(ctas), dim3(threads), args, smem, s);
 }
 
@@ -1189,6 +1457,27 @@ struct Q12 {
     int q[12];
 };
 
+// sample_hard on a volume used as given: each of the 8 neighbours is clamped to vmax = 2^d - 1 as it
+// is read, as the context path clamps every voxel when it copies the volume.
+template <typename MovT>
+__device__ __forceinline__ int sample_hard_raw(const MovT *__restrict__ mov, int n0, int n1, int n2, int ux, int uy,
+                                               int uz, int vmax) {
+    const int ix = ux >> 16, iy = uy >> 16, iz = uz >> 16;
+    const int fx = (ux >> 8) & 255, fy = (uy >> 8) & 255, fz = (uz >> 8) & 255;
+    const int sx = ix < n0 - 1 ? 1 : 0;
+    const int sy = iy < n1 - 1 ? n0 : 0;
+    const int sz = iz < n2 - 1 ? n0 * n1 : 0;
+    const MovT *p = mov + (ix + n0 * (iy + n1 * iz));
+    const int v000 = min((int)__ldg(p), vmax), v001 = min((int)__ldg(p + sx), vmax);
+    const int v010 = min((int)__ldg(p + sy), vmax), v011 = min((int)__ldg(p + sy + sx), vmax);
+    const int v100 = min((int)__ldg(p + sz), vmax), v101 = min((int)__ldg(p + sz + sx), vmax);
+    const int v110 = min((int)__ldg(p + sz + sy), vmax), v111 = min((int)__ldg(p + sz + sy + sx), vmax);
+    const int e00 = lerp8(v000, v001, fx), e01 = lerp8(v010, v011, fx);
+    const int e10 = lerp8(v100, v101, fx), e11 = lerp8(v110, v111, fx);
+    const int g0 = lerp8(e00, e01, fy), g1 = lerp8(e10, e11, fy);
+    return lerp8(g0, g1, fz);
+}
+
 template <typename FixT, typename MovT, class Hist>
 __device__ void accumulate_rows_raw(const RawPair &P, const int *q, long long first_batch, long long batch_stride,
                                     Hist &H) {
@@ -1219,10 +1508,10 @@ __device__ void accumulate_rows_raw(const RawPair &P, const int *q, long long fi
                 int bf = 0, bm = 0;
                 if (valid) {
                     const int d = i - lo;
-                    const int v = sample_hard<MovT>(mov, n0, n1, n2, U0 + st0 * d, U1 + st1 * d, U2 + st2 * d);
-                    // volumes are read as given (no copy is made, so no clamp on load): values are expected
-                    // within the bit depth, and the interpolated value is clamped to it before binning
-                    bm = (min(v, (int)((1u << mdepth) - 1u)) * bins) >> mdepth;
+                    // volumes are read in place; each value is clamped to its bit depth as it is read
+                    const int v = sample_hard_raw<MovT>(mov, n0, n1, n2, U0 + st0 * d, U1 + st1 * d, U2 + st2 * d,
+                                                        (int)((1u << mdepth) - 1u));
+                    bm = (v * bins) >> mdepth;
                     uint32_t fv = (uint32_t)__ldg(frow + i);
                     fv = fv > fvmax ? fvmax : fv;
                     bf = (int)((fv * (uint32_t)bins) >> fdepth);
@@ -1237,7 +1526,7 @@ template <typename FixT, typename MovT>
 __global__ void __launch_bounds__(1024, 1) k_hist_raw(RawPair P, Q12 A, uint32_t *__restrict__ ghist, int *flags) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int B = P.bins;
-    const SmemLayout L = smem_layout(HV_U16_MATCH, B, blockDim.x, 0);
+    const SmemLayout L = smem_layout(HV_U16_MATCH, B, blockDim.x, 0, 0);
     __shared__ int q[12];
     if (threadIdx.x < 12) q[threadIdx.x] = A.q[threadIdx.x];
     auto H = make_hist<HV_U16_MATCH>(smem, L, B, flags);
@@ -1363,7 +1652,7 @@ cudaError_t launch_noalloc_eval(const void *fix, int fdtype, int fdepth, const v
     Q12 A;
     for (int e = 0; e < 12; ++e) A.q[e] = q16[e];
     const int threads = 1024;
-    const size_t smem = smem_layout(HV_U16_MATCH, bins, threads, 0).total;
+    const size_t smem = smem_layout(HV_U16_MATCH, bins, threads, 0, 0).total;
     cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)bins * bins * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(flags, 0, 2 * sizeof(int), s)) != cudaSuccess) return e;

@@ -19,6 +19,9 @@ struct PairDev {
     const void *movp;      // x-paired copy (v[x], v[x+1]), uint16 / uint32, dims (nx, ny + 1, nz + 1)
     unsigned long long texp;  // the same pairs as a 3D texture (point sampling, clamped), dims (nx, ny, nz)
     unsigned long long texq;  // 2 x 2 quads (x, y), (x + 1, y), (x, y + 1), (x + 1, y + 1) as a 3D texture
+    unsigned long long texg;  // z-pair texels v(x, y, z) | v(x, y, z + 1) << 20 in a 2D atlas, read by gathers
+                              // (moving depth <= 12 only; 0 when not built)
+    const float2 *zoff;       // per moving plane z: atlas offset of the plane + 1 - 2^23, (x, y)
     const uint32_t *rowinfo;  // row-bound layout: per fixed bin, word offset << 6 | wide << 5 | shift (0 or 16)
     const uint32_t *srow;     // random sampling (else null): row r's sampled voxels are entries srow[r]..srow[r+1]-1
     const uint16_t *scol;     //   of scol (their x index, ascending)
@@ -61,20 +64,36 @@ struct Item {
 // with LDG gathers of x-pairs, 4..7: the same with texture-path gathers of
 // x-pairs, 8 / 9: the row-bound layout with LDG / texture x-pairs, 10..12:
 // the row-bound, 32-bit and 16-bit kinds with texture gathers of 2 x 2 quads.
+// 13..15: the row-bound, 32-bit and 16-bit kinds with one texture gather of 2 x 2 z-pair texels.
 enum { HV_U32 = 0, HV_U32_MATCH = 1, HV_U16 = 2, HV_U16_MATCH = 3, HV_TEX = 4, HV_ROWS = 8, HV_ROWS_TEX = 9,
-       HV_ROWS_QUAD = 10, HV_U32_QUAD = 11, HV_U16_QUAD = 12, HV_COUNT = 13 };
+       HV_ROWS_QUAD = 10, HV_U32_QUAD = 11, HV_U16_QUAD = 12, HV_ROWS_GATHER = 13, HV_U32_GATHER = 14,
+       HV_U16_GATHER = 15, HV_COUNT = 16 };
 // How a variant fetches the moving volume.
-enum { FM_LDG = 0, FM_TEX = 1, FM_QUAD = 2 };
+enum { FM_LDG = 0, FM_TEX = 1, FM_QUAD = 2, FM_GATHER = 3 };
 __host__ __device__ inline int hv_kind(int v) {
-    return v < HV_ROWS ? v % HV_TEX : v == HV_U32_QUAD ? HV_U32 : v == HV_U16_QUAD ? HV_U16 : HV_ROWS;
+    if (v < HV_ROWS) return v % HV_TEX;
+    if (v == HV_U32_QUAD || v == HV_U32_GATHER) return HV_U32;
+    if (v == HV_U16_QUAD || v == HV_U16_GATHER) return HV_U16;
+    return HV_ROWS;
 }
 __host__ __device__ inline int hv_fetch(int v) {
-    return v >= HV_ROWS_QUAD ? FM_QUAD : ((v >= HV_TEX && v < HV_ROWS) || v == HV_ROWS_TEX) ? FM_TEX : FM_LDG;
+    if (v >= HV_ROWS_GATHER) return FM_GATHER;
+    if (v >= HV_ROWS_QUAD) return FM_QUAD;
+    return ((v >= HV_TEX && v < HV_ROWS) || v == HV_ROWS_TEX) ? FM_TEX : FM_LDG;
 }
+// Tile shape of the voxel walk (quad and gather fetches): a warp step covers 32 >> lpr_log2 adjacent
+// fixed rows with 1 << lpr_log2 lanes each (lpr_log2 in 3..5); the batched kernel cuts each sweep
+// into `slabs` slabs of row blocks (1..16).
+struct Tile {
+    int lpr_log2;
+    int slabs;
+};
+constexpr int kMaxSlabs = 16;
 
 // Shared memory needed by a hard-path CTA of `threads` threads for `bins` bins
 // (rows_words: words of the row-bound layout, used by HV_ROWS*).
-size_t hard_smem_bytes(int variant, int bins, int threads, int rows_words);
+// (zmax: moving planes of the largest pair, for the gather variants' per-plane offsets.)
+size_t hard_smem_bytes(int variant, int bins, int threads, int rows_words, int zmax);
 // Random voxel sampling: voxel x takes part iff fmix32(x ^ fmix32(seed)) < threshold.
 // Per fixed row, the number of sampled voxels (counts: R entries), then the lists themselves
 // (row_ptr: the exclusive prefix sums, R + 1 entries; cols / bins: row_ptr[R] entries).
@@ -96,19 +115,30 @@ cudaError_t launch_make_pairs(const void *mov, int dtype, const int nm[3], void 
 // Iteration cap of the 16-bit counter drain on the current device (default 2^16; test hook).
 cudaError_t set_drain_cap(int cap);
 cudaError_t launch_make_quads(const void *mov, int dtype, const int nm[3], void *out, cudaStream_t s);
+// z-pair atlas of the moving volume (depth <= 12): out is a W x H uint32 image (zeroed here) in which
+// plane z occupies the nm[0] x nm[1] tile at ((z / ph) nm[0], (z % ph) nm[1]) and texel (x, y) of that
+// tile holds v(x, y, z) | v(x, y, min(z + 1, nm[2] - 1)) << 20.
+cudaError_t launch_make_zpairs(const void *mov, int dtype, const int nm[3], int ph, int W, int H, uint32_t *out,
+                               cudaStream_t s);
 cudaError_t launch_bin_fixed(const void *data, int dtype, int depth, long long n, int bins, uint8_t *out,
                              cudaStream_t s);
 cudaError_t launch_table(double *tab, float q, cudaStream_t s);
 // Plain path: n transforms, grid (ctas, n); histograms in global memory (n x bins^2 u32, zeroed here).
 cudaError_t launch_plain_hist(const PairDev *d_pair, const PairDev &h_pair, const int32_t *d_aff, int n,
-                              uint32_t *d_hist, int variant, int threads, int ctas, int *d_flags, cudaStream_t s);
+                              uint32_t *d_hist, int variant, int threads, int ctas, Tile tile, int *d_flags,
+                              cudaStream_t s);
 cudaError_t launch_entropy(const uint32_t *d_hist, int n, int bins, const QSet &Q, const Outputs &O,
                            cudaStream_t s);
+// The same reduction split over entropy_parts(bins) CTAs per transform (for few transforms).
+// Scratch: d_cols n x bins u32 (zeroed here), d_part n x entropy_parts(bins) x (1 + 2 kMaxQ) FP64.
+int entropy_parts(int bins);
+cudaError_t launch_entropy_split(const uint32_t *d_hist, int n, int bins, const QSet &Q, const Outputs &O,
+                                 uint32_t *d_cols, double *d_part, cudaStream_t s);
 // Batched path: persistent CTAs pull items from *d_ticket (reset by the caller).
 cudaError_t launch_batched(const PairDev *d_pairs, const int32_t *d_aff, const Item *d_items, int nitems,
-                           int *d_ticket, int max_bins, int rows_words, int variant, int threads, int ctas,
-                           const QSet &Q, const Outputs &O, cudaStream_t s);
-int batched_ctas_per_sm(int variant, int max_bins, int threads, int rows_words);
+                           int *d_ticket, int max_bins, int rows_words, int zmax, int variant, int threads, int ctas,
+                           Tile tile, const QSet &Q, const Outputs &O, cudaStream_t s);
+int batched_ctas_per_sm(int variant, int max_bins, int threads, int rows_words, int zmax);
 cudaError_t launch_resample(const PairDev *d_pair, const PairDev &h_pair, const int32_t *d_aff, void *out,
                             cudaStream_t s);
 

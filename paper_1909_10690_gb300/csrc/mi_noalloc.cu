@@ -1,14 +1,15 @@
 // mi_noalloc.cu -- hard-binned MI of one transform without allocating memory.
 //
 // Some callers cannot allocate device memory at the point where they need
-// the metric: code that runs while a CUDA graph is being captured (cudaMalloc
-// is not allowed then), plug-ins living inside a framework whose caching
-// allocator owns the device memory, and services that budget their GPU
-// memory up front and forbid allocations on the request path.  This file
-// gives them mi_eval_noalloc: it uses the caller's device volumes as they
-// are and keeps every intermediate in one file-scope static device array of
-// fixed size, which each GPU that loads the library holds until the process
-// exits.  It calls no cudaMalloc, cudaFree or allocating library routine.
+// the metric: plug-ins living inside a framework whose caching allocator owns
+// the GPU's memory (a cudaMalloc of their own fails once the pool holds it,
+// or fragments it), services that budget their GPU memory up front and forbid
+// allocations on the request path, and loops that cannot afford cudaMalloc's
+// implicit device-wide synchronisation.  This file gives them mi_eval_noalloc:
+// it uses the caller's device volumes in place and keeps every intermediate
+// in one file-scope static device array of fixed size, which each GPU that
+// loads the library holds until the process exits.  It calls no cudaMalloc,
+// cudaFree or allocating library routine.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -103,9 +104,12 @@ extern "C" mi_status mi_eval_noalloc(const mi_volume *fixed, const mi_volume *mo
     if ((st = check_volume(moving, "moving", dev, &mdepth)) != MI_OK) return st;
     const long long nvf = (long long)fixed->dims[0] * fixed->dims[1] * fixed->dims[2];
     const long long nvm = (long long)moving->dims[0] * moving->dims[1] * moving->dims[2];
-    if (nvf > MI_NOALLOC_MAX_VOXELS || nvm >= (1LL << 31))
+    if (nvf > MI_NOALLOC_MAX_VOXELS)
         return fail(MI_EINVAL, "mi_eval_noalloc: the fixed volume may hold at most 2^25 voxels "
                                "(the on-chip 16-bit counters drain into a table sized for that)");
+    if (nvm > MI_NOALLOC_MAX_MOVING_VOXELS)
+        return fail(MI_EINVAL, "mi_eval_noalloc: the moving volume must hold fewer than 2^31 voxels "
+                               "(its neighbour offsets are 32-bit)");
     if (nq < 1 || nq > MI_MAX_Q || !q) return fail(MI_EINVAL, "nq must be in 1..8 and q non-NULL");
     if (!transform || !out_mi) return fail(MI_EINVAL, "transform and out_mi must be non-NULL");
     mi::QSet Q;

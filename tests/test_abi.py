@@ -45,7 +45,7 @@ def test_options_default_and_error_without_device():
     lib.mi_options_default(ctypes.byref(o))
     assert (o.kernel, o.tsallis_form, o.log_bits, o.hist_variant, o.path, o.use_graphs, o.autotune, o.device,
             o.block_threads, o.rotation, o.scale, o.sample_fraction, o.sample_seed,
-            o.transform) == (0, 0, 0, -1, 0, 1, 1, -1, 0, 0, 0, 0.0, 0, 0)
+            o.transform, o.tile_rows, o.tile_slabs) == (0, 0, 0, -1, 0, 1, 1, -1, 0, 0, 0, 0.0, 0, 0, 0, 0)
     assert lib.mi_transform_size(None) == -1
     # invalid arguments are rejected before any device work
     h = ctypes.c_void_p()

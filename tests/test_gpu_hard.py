@@ -15,7 +15,7 @@ from paper_1909_10690_gb300 import phantoms
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-6
-VARIANTS = list(range(13))  # MI_HV_U32 .. MI_HV_U16_QUAD
+VARIANTS = list(range(16))  # MI_HV_U32 .. MI_HV_U16_GATHER
 IDENT = np.array([65536, 0, 0, 0, 0, 65536, 0, 0, 0, 0, 65536, 0], dtype=np.int32)
 
 
@@ -129,7 +129,7 @@ def test_ragged_sizes_all_variants(cuda_lib, variant, bins):
     # odd dims spanning several row batches and a ragged tail, 12-bit data, random 9-parameter transforms
     f, m = phantoms.head_pair(shape=(29, 41, 75), spacing=(1, 1, 1), seed=6)
     m = np.ascontiguousarray(m[:, :37, :71])
-    if bins > 181 and variant in (0, 1, 4, 5, 11):
+    if bins > 181 and variant in (0, 1, 4, 5, 11, 14):
         pytest.skip("32-bit counters do not fit shared memory at this bin count")
     prm, q16 = random_q16(f.shape, m.shape, 40, seed=bins)
     for path in (cuda_lib.PATH_PLAIN, cuda_lib.PATH_BATCHED):
@@ -144,7 +144,7 @@ def test_ragged_sizes_all_variants(cuda_lib, variant, bins):
     assert_mi_close(mi, mi_o, h_o)
 
 
-@pytest.mark.parametrize("variant", [2, 3, 6, 7, 8, 9, 10, 12])
+@pytest.mark.parametrize("variant", [2, 3, 6, 7, 8, 9, 10, 12, 13, 15])
 def test_u16_counter_drains_exact(cuda_lib, variant):
     # a large uniform background makes the (0, 0) cell pass 2^14 many times inside one CTA
     f = np.zeros((64, 96, 100), np.uint16)
@@ -160,6 +160,41 @@ def test_u16_counter_drains_exact(cuda_lib, variant):
             ho, _ = oracle.joint_hist(f, m, q16[t], 256, 12, 12)
             np.testing.assert_array_equal(H[t], ho.astype(np.uint32))
     assert H[0, 0, 0] > 10 * 2 ** 14
+
+
+@pytest.mark.parametrize("variant", [10, 11, 12, 13, 14, 15])
+@pytest.mark.parametrize("tile_rows", [1, 2, 4])
+def test_tile_shapes_bit_exact(cuda_lib, variant, tile_rows):
+    # every tile shape (1, 2 or 4 fixed rows per warp step) and slab count on ragged dims whose rows
+    # clip to every length mod 8, 16 and 32, both paths; 8-bit and 12-bit moving data
+    for depth, dt in ((12, np.uint16), (8, np.uint8)):
+        f, m = phantoms.head_pair(shape=(23, 37, 83), spacing=(1, 1, 1), depth=depth, seed=9 + depth, dtype=dt)
+        m = np.ascontiguousarray(m[:, :35, :79])
+        prm, q16 = random_q16(f.shape, m.shape, 24, seed=tile_rows + 3 * variant, t=6, r=20, s=(0.8, 1.2))
+        for slabs in (1, 3, 16):
+            ctx = cuda_lib.Context(f, m, bins=100, fixed_depth=depth, moving_depth=depth, hist_variant=variant,
+                                   tile_rows=tile_rows, tile_slabs=slabs)
+            for path in (cuda_lib.PATH_PLAIN, cuda_lib.PATH_BATCHED):
+                H = ctx.hist(affines=q16, path=path)
+                for t in range(0, len(q16), 5):
+                    ho, _ = oracle.joint_hist(f, m, q16[t], 100, depth, depth)
+                    np.testing.assert_array_equal(H[t], ho.astype(np.uint32), err_msg=f"{depth} {slabs} {path} {t}")
+
+
+def test_gather_variants_need_depth_12_or_less(cuda_lib):
+    # the z-pair atlas packs two values in 20-bit fields: 16-bit data keeps the other fetches
+    rng = np.random.default_rng(10)
+    f = rng.integers(0, 65536, size=(12, 14, 16), dtype=np.uint16)
+    m = rng.integers(0, 65536, size=(12, 14, 16), dtype=np.uint16)
+    with pytest.raises(cuda_lib.MIError) as ei:
+        cuda_lib.Context(f, m, bins=32, hist_variant=cuda_lib.HV_ROWS_GATHER).eval(phantoms.identity_params(1))
+    assert ei.value.status == cuda_lib.MI_EUNSUPPORTED
+    ctx = cuda_lib.Context(f, m, bins=32)
+    prm = phantoms.random_transforms(4, seed=11, t_mm=2, r_deg=5, s_range=(0.95, 1.05))
+    mi, h, cnt = ctx.eval(prm, [1.0], with_entropies=True)
+    mi_o, h_o, cnt_o = oracle.mi_eval(f, m, 32, prm, [1.0], nthreads=8)
+    np.testing.assert_array_equal(cnt, cnt_o)
+    assert_mi_close(mi, mi_o, h_o)
 
 
 def test_edge_cases(cuda_lib):
@@ -325,7 +360,7 @@ def test_row_bound_layout_at_the_16_bit_limit(cuda_lib, n_a):
     shape = (40, 50, 70)
     f = np.full(shape, 3000, dtype=np.uint16)
     f.ravel()[:n_a] = 1000
-    for variant in (8, 9, 10):
+    for variant in (8, 9, 10, 13):
         ctx = cuda_lib.Context(f, f, bins=64, fixed_depth=12, moving_depth=12, hist_variant=variant)
         for path in (cuda_lib.PATH_PLAIN, cuda_lib.PATH_BATCHED):
             H = ctx.hist(affines=IDENT, path=path)

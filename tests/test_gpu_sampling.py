@@ -8,7 +8,7 @@ from paper_1909_10690_gb300 import phantoms
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = list(range(13))
+VARIANTS = list(range(16))
 
 
 @pytest.mark.parametrize("variant", VARIANTS)

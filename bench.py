@@ -181,7 +181,7 @@ def run_reference(args, rank, world):
     line = {"metric": METRIC, "value": value, "unit": "voxel*transforms/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic", "impl": "reference", "config": workload_config(),
+            "data": "synthetic", "impl": "reference", "config": workload_config(), "ranks": world,
             "cpu_baseline": {"value": value, "unit": "voxel*transforms/s", "cores": cores, "kind": "oracle",
                              "sample": f"{per_step} of the step's {N_T} transforms per step (256^3, 256 bins, 4 q)"},
             "e2e": {"value": value, "unit": "voxel*transforms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -402,6 +402,22 @@ def run_maps(args):
                       "ascent_analysis_seconds": da}))
 
 
+def relaunch_ranks():
+    """``--gpus N`` run by hand (no WORLD_SIZE in the environment): start the N ranks on this node with
+    torch.distributed.run, one per GPU, each running this script with the same arguments."""
+    import socket
+
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    ap = argparse.ArgumentParser(add_help=False)
+    ap.add_argument("--gpus", type=int, default=1)
+    n = ap.parse_known_args()[0].gpus
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}", "--master-addr",
+           "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -427,6 +443,8 @@ def main():
     if args.profile_parzen:
         run_profile_parzen(args)
         return
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(relaunch_ranks())
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -174,8 +174,9 @@ typedef struct {
     unsigned int sample_seed; /* seed of that subset                                    */
     int transform;     /* MI_TRANSFORM_PARAMS (default) or MI_TRANSFORM_AFFINE       */
     int tile_rows;     /* hard path, quad and gather variants: adjacent fixed rows one
-                          warp step covers (32 / tile_rows lanes each): 0 (default) =
-                          autotuned, or 1, 2, 4                                       */
+                          warp step covers (32 / tile_rows lanes each), 1, 2 or 4; or
+                          32: a warp walks its 32 clipped rows as one stream of voxels
+                          (one partial step per 32 rows); 0 (default) = autotuned     */
     int tile_slabs;    /* batched kernel: slabs per sweep of the fixed rows (CTAs on
                           different transforms keep to neighbouring slabs): 0 (default)
                           = 4, or 1..16                                                */

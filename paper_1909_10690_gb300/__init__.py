@@ -153,7 +153,8 @@ class Context:
     affine [M | t] row-major, M dimensionless, t in mm; gradients per entry).
     ``nparams`` is the count.
     tile_rows (0 = autotuned, or 1, 2, 4): adjacent fixed rows one warp step of
-    the hard path covers; tile_slabs (0 = 4, or 1..16): slabs per sweep of the
+    the hard path covers, or 32: each warp walks its 32 clipped rows as one
+    stream of voxels; tile_slabs (0 = 4, or 1..16): slabs per sweep of the
     batched kernel.
     """
 

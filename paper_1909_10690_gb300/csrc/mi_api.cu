@@ -354,7 +354,7 @@ struct mi_ctx {
     std::map<uint32_t, std::unique_ptr<DevBuf>> tables;
     // call scratch
     DevBuf d_aff, d_items, d_mi, d_h, d_cnt, d_hist, d_flags, d_ticket, d_dump, d_cols, d_part;
-    HostBuf h_aff, h_items, h_out;
+    HostBuf h_aff, h_items, h_out, h_read;
     // Parzen scratch
     DevBuf p_aff, p_jac, p_hist, p_cnt, p_marg, p_ment, p_mterm, p_jsum, p_w, p_mom, p_grad;
     // autotune and graph caches
@@ -744,8 +744,9 @@ mi_status upload_pairs(mi_ctx *ctx) {
         d.mdtype = P.mdtype;
     }
     MI_CU(ctx->d_pairs.ensure(pd.size() * sizeof(PairDev)), "allocating pair descriptors");
-    MI_CU(cudaMemcpy(ctx->d_pairs.p, pd.data(), pd.size() * sizeof(PairDev), cudaMemcpyHostToDevice),
+    MI_CU(cudaMemcpyAsync(ctx->d_pairs.p, pd.data(), pd.size() * sizeof(PairDev), cudaMemcpyHostToDevice, ctx->stream),
           "uploading pair descriptors");
+    MI_CU(cudaStreamSynchronize(ctx->stream), "uploading pair descriptors");
     return MI_OK;
 }
 
@@ -819,8 +820,9 @@ mi_status create_common(mi_ctx **out, const mi_volume *fixed, const mi_volume *m
         g_create_error = "opt.block_threads must be 0, 512 or 1024";
         return MI_EINVAL;
     }
-    if (ctx->opt.tile_rows != 0 && ctx->opt.tile_rows != 1 && ctx->opt.tile_rows != 2 && ctx->opt.tile_rows != 4) {
-        g_create_error = "opt.tile_rows must be 0, 1, 2 or 4";
+    if (ctx->opt.tile_rows != 0 && ctx->opt.tile_rows != 1 && ctx->opt.tile_rows != 2 && ctx->opt.tile_rows != 4 &&
+        ctx->opt.tile_rows != 32) {
+        g_create_error = "opt.tile_rows must be 0, 1, 2, 4 or 32";
         return MI_EINVAL;
     }
     if (ctx->opt.tile_slabs < 0 || ctx->opt.tile_slabs > kMaxSlabs) {
@@ -883,13 +885,26 @@ uint32_t fbits(float f) {
     return u;
 }
 
+// Reads `bytes` of caller device memory into host memory in the context's stream order: an
+// asynchronous copy into pinned staging, then a wait on that stream alone (no legacy-stream copy).
+mi_status read_from_device(mi_ctx *ctx, void *dst, const void *src, size_t bytes) {
+    if (bytes == 0) return MI_OK;
+    MI_CU(ctx->h_read.ensure(bytes), "pinned staging");
+    MI_CU(cudaMemcpyAsync(ctx->h_read.p, src, bytes, cudaMemcpyDeviceToHost, ctx->stream), "reading device input");
+    MI_CU(cudaStreamSynchronize(ctx->stream), "reading device input");
+    memcpy(dst, ctx->h_read.p, bytes);
+    return MI_OK;
+}
+
 mi_status read_q(mi_ctx *ctx, const float *q, int nq, float out[kMaxQ]) {
     if (nq < 1 || nq > kMaxQ) return ctx->fail(MI_EINVAL, "nq must be in 1..8");
     if (!q) return ctx->fail(MI_EINVAL, "q is NULL");
-    if (is_device_ptr(q))
-        MI_CU(cudaMemcpy(out, q, nq * sizeof(float), cudaMemcpyDeviceToHost), "reading q");
-    else
+    if (is_device_ptr(q)) {
+        mi_status st = read_from_device(ctx, out, q, nq * sizeof(float));
+        if (st != MI_OK) return st;
+    } else {
         memcpy(out, q, nq * sizeof(float));
+    }
     for (int i = 0; i < nq; ++i) {
         const float v = out[i];
         if (!(v > 0.0f) || !isfinite(v)) return ctx->fail(MI_EINVAL, "q values must be finite and > 0");
@@ -926,10 +941,12 @@ mi_status read_transforms(mi_ctx *ctx, const float *tr, int n, std::vector<float
     out.resize((size_t)n * np);
     if (n == 0) return MI_OK;
     if (!tr) return ctx->fail(MI_EINVAL, "transforms is NULL");
-    if (is_device_ptr(tr))
-        MI_CU(cudaMemcpy(out.data(), tr, (size_t)n * np * sizeof(float), cudaMemcpyDeviceToHost), "reading transforms");
-    else
+    if (is_device_ptr(tr)) {
+        mi_status st = read_from_device(ctx, out.data(), tr, (size_t)n * np * sizeof(float));
+        if (st != MI_OK) return st;
+    } else {
         memcpy(out.data(), tr, (size_t)n * np * sizeof(float));
+    }
     for (size_t i = 0; i < out.size(); ++i)
         if (!isfinite(out[i])) return ctx->fail(MI_EINVAL, "transform " + std::to_string(i / np) + " is not finite");
     return MI_OK;
@@ -963,15 +980,18 @@ bool variant_fits(int variant, int bins, int threads, long long nvox, int rows_w
     return hard_smem_bytes(variant, bins, threads, rows_words, zmax) <= 227 * 1024;
 }
 
-// Rows per warp step the tile shape may take for a variant: quad and gather fetches walk 1, 2 or 4
-// rows per step (lanes per row 2^5, 2^4, 2^3); the others one row.
+// Walks the tile shape may take for a variant: quad and gather fetches walk the warp's 32 rows as one
+// voxel stream (lpr_log2 0) or 1, 2 or 4 rows per step (lanes per row 2^5, 2^4, 2^3); the others one
+// row at a time.
 std::vector<int> tile_lpr(mi_ctx *ctx, int variant) {
-    if (ctx->opt.tile_rows > 0) {
-        const int lpr = ctx->opt.tile_rows == 1 ? 5 : ctx->opt.tile_rows == 2 ? 4 : 3;
-        return {hv_fetch(variant) >= FM_QUAD ? lpr : 5};
+    if (hv_fetch(variant) < FM_QUAD) return {5};
+    switch (ctx->opt.tile_rows) {
+        case 1: return {5};
+        case 2: return {4};
+        case 4: return {3};
+        case 32: return {0};  // the warp's 32 rows as one voxel stream
+        default: return {0, 5, 4};
     }
-    if (hv_fetch(variant) >= FM_QUAD) return {5, 4, 3};
-    return {5};
 }
 
 std::vector<Choice> candidates(mi_ctx *ctx, int bins, long long nvox_max) {
@@ -1215,7 +1235,7 @@ mi_status eval_core(mi_ctx *ctx, const EvalReq &R, const float *qv, int nq, doub
             ch = it->second;
         } else {
             // heuristic (the plain form is not autotuned): the first of these kinds that fits, with
-            // 1024 threads and two rows per warp step where the fetch allows it
+            // 1024 threads and the stream walk where the fetch allows it
             const int order[] = {HV_U32_GATHER, HV_ROWS_GATHER, HV_U16_GATHER, HV_U32_QUAD, HV_ROWS_QUAD,
                                  HV_U16_QUAD, HV_U32, HV_U16};
             ch = cands.front();
@@ -1224,7 +1244,7 @@ mi_status eval_core(mi_ctx *ctx, const EvalReq &R, const float *qv, int nq, doub
                 if (v == HV_U32_GATHER || v == HV_U32_QUAD || v == HV_U32)
                     if (ctx->max_bins > 181) continue;
                 for (const Choice &c : cands)
-                    if (c.variant == v && c.threads == 1024 && (c.tile.lpr_log2 == 4 || hv_fetch(v) < FM_QUAD)) {
+                    if (c.variant == v && c.threads == 1024 && (c.tile.lpr_log2 == 0 || hv_fetch(v) < FM_QUAD)) {
                         ch = c;
                         found = true;
                         break;
@@ -1249,7 +1269,7 @@ mi_status eval_core(mi_ctx *ctx, const EvalReq &R, const float *qv, int nq, doub
         const int32_t *h_aff = R.q16.data();
         if (R.d_q16) {
             q16h.resize((size_t)n * 12);
-            MI_CU(cudaMemcpy(q16h.data(), R.d_q16, (size_t)n * 48, cudaMemcpyDeviceToHost), "reading affines");
+            if ((st = read_from_device(ctx, q16h.data(), R.d_q16, (size_t)n * 48)) != MI_OK) return st;
             h_aff = q16h.data();
         }
         const int bucket = n >= 4 * ctx->sms ? 2 : (n >= ctx->sms ? 1 : 0);
@@ -1534,10 +1554,11 @@ mi_status mi_batch_eval(mi_ctx *ctx, const int *pair_of_transform, const float *
     R.n = n;
     R.path = MI_PATH_BATCHED;
     R.pair_of.resize(n);
-    if (is_device_ptr(pair_of_transform))
-        MI_CU(cudaMemcpy(R.pair_of.data(), pair_of_transform, (size_t)n * 4, cudaMemcpyDeviceToHost), "reading pairs");
-    else
+    if (is_device_ptr(pair_of_transform)) {
+        if ((st = read_from_device(ctx, R.pair_of.data(), pair_of_transform, (size_t)n * 4)) != MI_OK) return st;
+    } else {
         memcpy(R.pair_of.data(), pair_of_transform, (size_t)n * 4);
+    }
     R.q16.resize((size_t)n * 12);
     for (int t = 0; t < n; ++t) {
         const int p = R.pair_of[t];
@@ -1587,7 +1608,7 @@ mi_status mi_hist(mi_ctx *ctx, int pair, const float *transforms, const int32_t 
         for (int t = 0; t < n; ++t)
             if ((st = build_q16(ctx, P, &prm[(size_t)t * ctx->nparams()], &R.q16[(size_t)t * 12], t)) != MI_OK) return st;
     } else if (is_device_ptr(affines)) {
-        MI_CU(cudaMemcpy(R.q16.data(), affines, (size_t)n * 48, cudaMemcpyDeviceToHost), "reading affines");
+        if ((st = read_from_device(ctx, R.q16.data(), affines, (size_t)n * 48)) != MI_OK) return st;
     } else {
         R.q16.assign(affines, affines + (size_t)n * 12);
     }
@@ -1649,10 +1670,12 @@ mi_status mi_resample(mi_ctx *ctx, int pair, const int32_t *affine, void *out) {
     if (pair < 0 || pair >= (int)ctx->pairs.size() || !out || !affine) return ctx->fail(MI_EINVAL, "bad arguments");
     const Pair &P = *ctx->pairs[pair];
     int32_t q[12];
-    if (is_device_ptr(affine))
-        MI_CU(cudaMemcpy(q, affine, 48, cudaMemcpyDeviceToHost), "reading the affine");
-    else
+    if (is_device_ptr(affine)) {
+        mi_status st = read_from_device(ctx, q, affine, 48);
+        if (st != MI_OK) return st;
+    } else {
         memcpy(q, affine, 48);
+    }
     MI_CU(ctx->d_aff.ensure(48), "alloc");
     MI_CU(cudaMemcpyAsync(ctx->d_aff.p, q, 48, cudaMemcpyHostToDevice, ctx->stream), "H2D");
     const size_t bytes = (size_t)P.nvf * (P.mdtype == 0 ? 1 : 2);
@@ -1704,7 +1727,7 @@ mi_status mi_selected_config(mi_ctx *ctx, int n, int out[5]) {
     out[0] = c->variant;
     out[1] = c->threads;
     out[2] = c->ctas;
-    out[3] = 32 >> c->tile.lpr_log2;
+    out[3] = c->tile.lpr_log2 == 0 ? 32 : 32 >> c->tile.lpr_log2;
     out[4] = c->tile.slabs;
     return MI_OK;
 }

@@ -775,14 +775,109 @@ __device__ void accumulate_groups(const PairDev &P, const int *q, const float2 *
     }
 }
 
-// The voxel walk of a variant: quad and gather fetches over every fixed voxel take the row-group walk,
-// the others (and random sampling) the one-row-at-a-time walk.
+// Stream walk (quad and gather fetches, every fixed voxel).  A warp clips its next 32 rows at once
+// (lane s takes row s of the batch), then walks their overlap intervals as one stream of voxels: lane
+// l takes stream positions l, l + 32, ...  An exclusive scan of the interval lengths gives each row's
+// start in the stream; a lane crossing the end of its row moves to the next non-empty one and
+// re-reads that row's 16.16 index and fixed-bin offset by shuffles from the row's clipping lane.
+// Between row ends the warp runs segments of full steps (the most steps before any lane leaves its
+// row, one warp-wide minimum) exactly like the row walk's predicate-free loop; only the batch's last
+// step is partial (instead of every row's).  U = u_lo + st (i - lo) inside a row's interval is exact
+// in 32 bits.
+template <int FM, class Hist>
+__device__ void accumulate_stream(const PairDev &P, const int *q, const float2 *zoff, long long first_block,
+                                  long long block_stride, long long n_end, Hist &H) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int nf0 = P.nf[0], nf1 = P.nf[1];
+    const long long R = (long long)nf1 * P.nf[2];
+    const int st0 = q[0], st1 = q[4], st2 = q[8];
+    const int bins = P.bins, mdepth = P.mdepth;
+    const unsigned d0 = 32u * (unsigned)st0, d1 = 32u * (unsigned)st1, d2 = 32u * (unsigned)st2;
+    for (long long n0b = 0;; n0b += 32) {
+        if (first_block + n0b * block_stride >= n_end) break;
+        RowClip mine;
+        mine.lo = 0;
+        mine.hi = -1;
+        mine.u0 = mine.u1 = mine.u2 = 0;
+        long long rl = 0;
+        const long long nl = first_block + (n0b + lane) * block_stride;
+        if (nl < n_end) {
+            rl = nl * nwarps + warp;
+            if (rl < R) mine = clip_row(q, (int)(rl % nf1), (int)(rl / nf1), nf0, P.nm);
+        }
+        const int len = mine.hi >= mine.lo ? mine.hi - mine.lo + 1 : 0;
+        int incl = len;  // inclusive scan: the end of this lane's row in the stream
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(kFull, incl, 31);
+        if (total == 0) continue;
+        // offset of the row's first overlap voxel in the fixed bins (rows past the end are empty)
+        const long long rowoff = len > 0 ? rl * nf0 + mine.lo : 0;
+        int s = -1, e = 0;  // this lane's row and that row's end in the stream
+        unsigned U0 = 0, U1 = 0, U2 = 0;
+        const uint8_t *__restrict__ fp = P.fbins;
+        for (int g0 = 0; g0 < total;) {
+            const int g = g0 + lane;
+            bool moved = false;  // warp-uniform
+            while (__any_sync(kFull, g < total && g >= e)) {
+                if (g < total && g >= e) ++s;
+                e = __shfl_sync(kFull, incl, s & 31);
+                moved = true;
+            }
+            if (moved) {  // lanes that stayed re-read their own row: no change
+                const int sc = s & 31;
+                const int start = e - __shfl_sync(kFull, len, sc);
+                const unsigned dd = (unsigned)(g - start);
+                U0 = (unsigned)__shfl_sync(kFull, mine.u0, sc) + (unsigned)st0 * dd;
+                U1 = (unsigned)__shfl_sync(kFull, mine.u1, sc) + (unsigned)st1 * dd;
+                U2 = (unsigned)__shfl_sync(kFull, mine.u2, sc) + (unsigned)st2 * dd;
+                fp = P.fbins + (__shfl_sync(kFull, rowoff, sc) + (long long)dd);
+            }
+            if (g0 + 32 <= total) {
+                // a segment of full steps in which no lane leaves its row: predicate-free, two steps per
+                // trip, the next step's fixed bin loaded one step ahead
+                int nfree = (int)__reduce_min_sync(kFull, (unsigned)((e - g + 31) >> 5));
+                nfree = min(nfree, (total - g0) >> 5);
+                int bf_next = (int)__ldg(fp);
+#pragma unroll 2
+                for (int k = 0; k < nfree; ++k) {
+                    const int bf = bf_next;
+                    fp += 32;
+                    if (k + 1 < nfree) bf_next = (int)__ldg(fp);
+                    H.add(bf, (sample_value<FM, uint32_t>(P, zoff, U0, U1, U2) * bins) >> mdepth, true);
+                    U0 += d0;
+                    U1 += d1;
+                    U2 += d2;
+                }
+                g0 += 32 * nfree;
+            } else {  // the batch's last, partial step
+                const bool valid = g < total;
+                int bf = 0, bm = 0;
+                if (valid) {
+                    bf = (int)__ldg(fp);
+                    bm = (sample_value<FM, uint32_t>(P, zoff, U0, U1, U2) * bins) >> mdepth;
+                }
+                H.add(bf, bm, valid);
+                g0 = total;
+            }
+        }
+    }
+}
+
+// The voxel walk of a variant: quad and gather fetches over every fixed voxel take the stream walk
+// (lpr_log2 == 0) or the row-group walk, the others (and random sampling) the one-row-at-a-time walk.
 template <typename PairT, int FM, class Hist>
 __device__ __forceinline__ void walk_rows(const PairDev &P, const int *q, const float2 *zoff, long long first_block,
                                           long long block_stride, long long n_end, int lpr_log2, Hist &H) {
     if constexpr (FM == FM_QUAD || FM == FM_GATHER) {
         if (P.srow == nullptr) {
-            accumulate_groups<FM>(P, q, zoff, first_block, block_stride, n_end, lpr_log2, H);
+            if (lpr_log2 == 0)
+                accumulate_stream<FM>(P, q, zoff, first_block, block_stride, n_end, H);
+            else
+                accumulate_groups<FM>(P, q, zoff, first_block, block_stride, n_end, lpr_log2, H);
             return;
         }
     }

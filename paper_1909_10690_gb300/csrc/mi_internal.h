@@ -82,8 +82,9 @@ __host__ __device__ inline int hv_fetch(int v) {
     return ((v >= HV_TEX && v < HV_ROWS) || v == HV_ROWS_TEX) ? FM_TEX : FM_LDG;
 }
 // Tile shape of the voxel walk (quad and gather fetches): a warp step covers 32 >> lpr_log2 adjacent
-// fixed rows with 1 << lpr_log2 lanes each (lpr_log2 in 3..5); the batched kernel cuts each sweep
-// into `slabs` slabs of row blocks (1..16).
+// fixed rows with 1 << lpr_log2 lanes each (lpr_log2 in 3..5), or, with lpr_log2 == 0, the warp walks
+// its 32 clipped rows as one stream of voxels; the batched kernel cuts each sweep into `slabs` slabs
+// of row blocks (1..16).
 struct Tile {
     int lpr_log2;
     int slabs;

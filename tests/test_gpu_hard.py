@@ -163,10 +163,11 @@ def test_u16_counter_drains_exact(cuda_lib, variant):
 
 
 @pytest.mark.parametrize("variant", [10, 11, 12, 13, 14, 15])
-@pytest.mark.parametrize("tile_rows", [1, 2, 4])
+@pytest.mark.parametrize("tile_rows", [1, 2, 4, 32])
 def test_tile_shapes_bit_exact(cuda_lib, variant, tile_rows):
-    # every tile shape (1, 2 or 4 fixed rows per warp step) and slab count on ragged dims whose rows
-    # clip to every length mod 8, 16 and 32, both paths; 8-bit and 12-bit moving data
+    # every tile shape (1, 2 or 4 fixed rows per warp step, or the 32-row stream) and slab count on
+    # ragged dims whose rows clip to every length mod 8, 16 and 32 (and to nothing at the overlap's
+    # edge), both paths; 8-bit and 12-bit moving data
     for depth, dt in ((12, np.uint16), (8, np.uint8)):
         f, m = phantoms.head_pair(shape=(23, 37, 83), spacing=(1, 1, 1), depth=depth, seed=9 + depth, dtype=dt)
         m = np.ascontiguousarray(m[:, :35, :79])

@@ -34,14 +34,20 @@ BINS = 256
 DEPTH = 12
 N_T = 4096
 QS = [0.5, 1.0, 1.5, 2.0]
-# algorithmic integer operations per voxel x transform of the hard path:
-# 3 coordinate adds, 6 index/weight extractions, 9 address operations, 7 lerps x 4,
-# 2 for the moving bin, 1 for the joint index, 1 increment
-ALG_OPS_PER_VOXT = 50
-# DRAM bytes (read + write) of one full k_batched launch (4096 transforms), from one ncu capture of
-# dram__bytes_read.sum + dram__bytes_write.sum; reported only while the kernel source and the
-# selected variant are the ones measured
-K_BATCHED_TRAFFIC = {"variant": 10, "source_sha16": "92956c2f74dac179", "bytes_per_launch": 367.8976e9 + 30.3e6}
+# algorithmic integer operations per voxel x transform of the hard path, one per coordinate multiply-add
+# (3), stage lerp (7) and binning (2), plus the weight extraction, gather address and increment (8): 20.
+# This is the roofline's numerator.  The kernel's own tally (each lerp 4 operations: two products, the
+# rounding add and the shift; 9 address and 6 index/weight operations: 50) is reported beside it.
+ALG_OPS_PER_VOXT = 20
+DESIGN_OPS_PER_VOXT = 50
+# Counters of one ncu capture of k_batched on this workload (see profiles/), reported only while the
+# kernel source and the selected configuration are the ones measured: DRAM bytes of one full launch
+# (4096 transforms), and from a one-wave capture the issue and L1TEX utilisation and the
+# shared-memory wavefronts per shared atomic instruction.
+K_BATCHED_NCU = {"source_sha16": "018b6e18fe20d963", "config": [10, 1, 4],
+                 "dram_bytes_per_launch": 405720647936 + 64994816, "issue_active": 0.758,
+                 "l1tex_throughput": 0.637, "smem_wavefronts_per_atomic": 335382232 / 68548103,
+                 "profile": "profiles/k_batched_rows_quad_256cubed_256bins.md"}
 # algorithmic FP32 operations per voxel x transform of the Parzen MI + gradient at 3 q values:
 # forward 31 (trilinear 14, bin coordinate 1, B-spline weights 12, 4 increments),
 # adjoint 89 (trilinear value and gradient 23, bin coordinate 1, B-spline derivatives 8, 3 q x 19)
@@ -242,15 +248,36 @@ def run_ours(args, rank, world, local_rank):
     pk, src = peaks()
     props = torch.cuda.get_device_properties(dev)
     sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
-    alu_peak = props.multi_processor_count * 128 * sm_mhz * 1e6 / 1e12  # int32 lane-ops/s, Tops/s
+    sms = props.multi_processor_count
+    alu_peak = sms * 128 * sm_mhz * 1e6 / 1e12  # int32 lane-ops/s, Tops/s
     kms = float(np.mean(kern_ms))
-    achieved = ALG_OPS_PER_VOXT * N_T * nvox / (kms / 1e3) / 1e12
-    traffic = None
-    if variant == K_BATCHED_TRAFFIC["variant"] and kernel_source_sha16() == K_BATCHED_TRAFFIC["source_sha16"]:
-        traffic = K_BATCHED_TRAFFIC["bytes_per_launch"]
+    units_per_s = N_T * nvox / (kms / 1e3)
+    achieved = ALG_OPS_PER_VOXT * units_per_s / 1e12
+    design = DESIGN_OPS_PER_VOXT * units_per_s / 1e12
+    cfg = ctx.selected_config(N_T)
+    ncu = K_BATCHED_NCU
+    ncu_ok = ncu["source_sha16"] == kernel_source_sha16() and ncu["config"] == [cfg["variant"], cfg["tile_rows"],
+                                                                                  cfg["tile_slabs"]]
+    traffic = ncu["dram_bytes_per_launch"] if ncu_ok else None
+    # one shared atomic per voxel x transform; the peak is one conflict-free 32-lane shared-memory
+    # wavefront per clock per SM
+    atom_peak = sms * 32 * sm_mhz * 1e6
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak,
                 "traffic": traffic, "kernel": "k_batched", "kernel_ms": kms,
-                "peak_source": f"{props.multi_processor_count} SMs x 128 int32 lanes x {sm_mhz:.0f} MHz ({src} clock)"}
+                "ops_per_voxel_transform": ALG_OPS_PER_VOXT,
+                "peak_source": f"{sms} SMs x 128 int32 lanes x {sm_mhz:.0f} MHz ({src} clock)",
+                "algorithmic_bytes": int(nvox * 1 + nvox * 2),
+                "algorithmic_bytes_note": "both volumes once per launch: uint8 fixed bins and the uint16 moving volume",
+                "design_count": {"ops_per_voxel_transform": DESIGN_OPS_PER_VOXT, "achieved": design,
+                                 "frac": design / alu_peak},
+                "shared_atomics": {"achieved_per_s": units_per_s, "peak_per_s": atom_peak,
+                                   "frac": units_per_s / atom_peak,
+                                   "peak_source": f"{sms} SMs x 32 lanes (one wavefront) x {sm_mhz:.0f} MHz"}}
+    if ncu_ok:
+        roofline["hbm"] = {"achieved_gbs": traffic / (kms / 1e3) / 1e9, "peak_gbs": float(pk["hbm_gbs"]),
+                           "frac": traffic / (kms / 1e3) / 1e9 / float(pk["hbm_gbs"]), "peak_source": src}
+        roofline["ncu"] = {k: ncu[k] for k in ("issue_active", "l1tex_throughput", "smem_wavefronts_per_atomic",
+                                               "profile")}
     # --- end to end through the C ABI with host buffers ----------------------------
     prm_pinned = torch.from_numpy(prm).pin_memory()
     barrier()
@@ -311,7 +338,8 @@ def run_ours(args, rank, world, local_rank):
     line = {"metric": METRIC, "value": value, "unit": "voxel*transforms/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": dict(workload_config(), hist_variant=variant, parallelism=f"replicas x{world}"),
+            "config": dict(workload_config(), hist_variant=variant, parallelism=f"replicas x{world}",
+                           selected=ctx.selected_config(N_T)),
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     line.update(extra)
     if rank == 0 and not args.skip_cpu:

@@ -218,8 +218,14 @@ mi_status mi_create(mi_ctx **out, const mi_volume *fixed, const mi_volume *movin
 
 /*
  * Creates one context over npairs volume pairs of uneven sizes, types and
- * bin counts (bins[p] per pair), evaluated together by mi_batch_eval in one
- * persistent launch with a per-pair work queue.  Hard path only.
+ * bin counts (bins[p] per pair).  The paper evaluates the metric over whole
+ * grids of transforms of one pair at a time (Methodology: 3D parameter-space
+ * maps, e.g. 51^3 translations); batching many transforms, and many pairs,
+ * into one launch is this library's addition for that workload.  Hard
+ * contexts (MI_HARD) are evaluated by mi_batch_eval in one persistent launch
+ * with a per-pair work queue; Parzen contexts (MI_PARZEN, bins 8..128 per
+ * pair) by mi_batch_eval (MI) and mi_batch_grad (MI and gradient), one
+ * launch per kernel for all pairs.
  */
 mi_status mi_batch_create(mi_ctx **out, const mi_volume *fixed, const mi_volume *moving, const int *bins,
                           int npairs, const mi_options *opt);
@@ -256,14 +262,19 @@ mi_status mi_eval(mi_ctx *ctx, const float *transforms, int n, const float *q, i
                   double *out_h, int64_t *out_count);
 
 /* As mi_eval, with the 16.16 affines [A | b] (n x 12 int32, row-major 3x4)
- * given directly instead of parameters.  Hard path, pair 0. */
+ * given directly instead of parameters: the index-space form of the Fig. 1
+ * Transform block (any affine, e.g. one built by the caller for a map of the
+ * Methodology), quantised as the hard path's fixed-point coordinates are.
+ * Hard path, pair 0. */
 mi_status mi_eval_q16(mi_ctx *ctx, const int32_t *affines, int n, const float *q, int nq, double *out_mi,
                       double *out_h, int64_t *out_count);
 
 /*
- * Batched evaluation over the pairs of a mi_batch_create context:
- * transform t (n x P parameters) is evaluated on pair pair_of_transform[t].
- * Outputs as in mi_eval.
+ * Batched evaluation over the pairs of a mi_batch_create context (the
+ * Methodology's parameter-space maps, many transforms per call):
+ * transform t (n x P parameters) is evaluated on pair pair_of_transform[t]
+ * (n ints, host or device memory).  Outputs as in mi_eval (out_h and
+ * out_count are hard-path outputs; NULL for a Parzen context).
  */
 mi_status mi_batch_eval(mi_ctx *ctx, const int *pair_of_transform, const float *transforms, int n,
                         const float *q, int nq, double *out_mi, double *out_h, int64_t *out_count);
@@ -279,6 +290,15 @@ mi_status mi_batch_eval(mi_ctx *ctx, const int *pair_of_transform, const float *
  */
 mi_status mi_grad(mi_ctx *ctx, const float *transforms, int n, const float *q, int nq, double *out_mi,
                   double *out_grad);
+
+/*
+ * mi_grad over the pairs of a MI_PARZEN mi_batch_create context: transform t
+ * on pair pair_of_transform[t]; out_mi n x nq, out_grad n x nq x P.  Every
+ * kernel of the forward, the entropies and the adjoint runs once for all
+ * pairs (each pair with its own bin count).
+ */
+mi_status mi_batch_grad(mi_ctx *ctx, const int *pair_of_transform, const float *transforms, int n, const float *q,
+                        int nq, double *out_mi, double *out_grad);
 
 /*
  * Test hook: the joint histogram (row = fixed bin, bins x bins uint32 per
@@ -306,6 +326,17 @@ mi_status mi_resample(mi_ctx *ctx, int pair, const int32_t *affine, void *out);
 /* The histogram variant the autotuner chose (or was told) for pair `pair`,
  * for the given number of transforms per call; -1 if none yet. */
 int mi_selected_variant(mi_ctx *ctx, int pair, int n);
+
+/* Autotune cache (process-wide): the batched path's autotuner records each
+ * tuned shape in the text file `path` (one line per shape: a key naming the
+ * device, the library version, the pairs' dims, types, bit depths and bins,
+ * the transform-count bucket and the options that restrict the candidates,
+ * then the choice) and, for a shape already in the file, takes the recorded
+ * choice instead of timing the candidates -- as long as that choice is still
+ * a candidate.  path NULL or "" disables it.  Until this is called the path
+ * comes from the environment variable MI_AUTOTUNE_CACHE (unset: disabled).
+ * A file that cannot be opened only costs the tuning time. */
+void mi_autotune_cache(const char *path);
 
 /* The whole configuration chosen (autotuned or set) for calls of n transforms:
  * out[0..4] = histogram variant, threads per CTA, CTAs, fixed rows per warp

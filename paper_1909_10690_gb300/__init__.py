@@ -279,6 +279,22 @@ class Context:
         self._check(st, allow_empty)
         return mi, g
 
+    def batch_grad(self, pair_of_transform, transforms, q=(1.0,), allow_empty=False):
+        """Parzen MI (n x nq) and dMI/dparam (n x nq x nparams) over the pairs of a multi-pair Parzen
+        context: transform t on pair pair_of_transform[t], one launch per kernel for all pairs."""
+        P = _Arg(pair_of_transform, np.int32)
+        T = _Arg(transforms, np.float32)
+        Q = _Arg(np.atleast_1d(np.asarray(q, dtype=np.float32)))
+        n = int(np.prod(T.obj.shape) // self.nparams)
+        nq = int(np.asarray(q).size)
+        gpu = T.on_gpu
+        dev = T.obj.device if gpu else None
+        mi = _out((n, nq), gpu, np.float64, dev)
+        g = _out((n, nq, self.nparams), gpu, np.float64, dev)
+        st = self._lib.mi_batch_grad(self._h, P.ptr, T.ptr, n, Q.ptr, nq, _ptr(mi), _ptr(g))
+        self._check(st, allow_empty)
+        return mi, g
+
     def hist(self, transforms=None, affines=None, pair=0, path=PATH_PLAIN):
         """Joint histograms (n x bins x bins uint32, row = fixed bin) -- test hook."""
         if (transforms is None) == (affines is None):
@@ -330,6 +346,11 @@ class Context:
         nl = ctypes.c_int()
         self._check(self._lib.mi_last_kernel_ms(self._h, ctypes.byref(ms), ctypes.byref(nl)))
         return float(ms.value), int(nl.value)
+
+
+def autotune_cache(path):
+    """Record and replay the batched path's autotuned choices in the text file ``path`` (None: off)."""
+    load().mi_autotune_cache(None if path is None else str(path).encode())
 
 
 def eval_noalloc(fixed, moving, bins, transform, q=(1.0,), fixed_spacing=(1.0, 1.0, 1.0),
@@ -403,4 +424,4 @@ def mi_function():
     return MIFunction
 
 
-__all__ = ["Context", "MIError", "load", "build", "version", "mi_function", "phantoms"]
+__all__ = ["Context", "MIError", "load", "build", "version", "mi_function", "autotune_cache", "phantoms"]

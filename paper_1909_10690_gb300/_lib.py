@@ -106,12 +106,14 @@ SIGNATURES = {
     "mi_eval_q16": (_I, [_P, _P, _I, _P, _I, _P, _P, _P]),
     "mi_batch_eval": (_I, [_P, _P, _P, _I, _P, _I, _P, _P, _P]),
     "mi_grad": (_I, [_P, _P, _I, _P, _I, _P, _P]),
+    "mi_batch_grad": (_I, [_P, _P, _P, _I, _P, _I, _P, _P]),
     "mi_hist": (_I, [_P, _I, _P, _P, _I, _I, _P]),
     "mi_affine": (_I, [_P, _I, _P, _I, _P, _P, _P]),
     "mi_fixed_bins": (_I, [_P, _I, _P]),
     "mi_resample": (_I, [_P, _I, _P, _P]),
     "mi_selected_variant": (_I, [_P, _I, _I]),
     "mi_selected_config": (_I, [_P, _I, _P]),
+    "mi_autotune_cache": (None, [ctypes.c_char_p]),
     "mi_last_kernel_ms": (_I, [_P, _P, _P]),
     "mi_eval_noalloc": (_I, [ctypes.POINTER(MiVolume), ctypes.POINTER(MiVolume), _I, _P, _P, _I, _P, _P]),
 }

@@ -7,10 +7,13 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <stdlib.h>
+
 #include <algorithm>
 #include <atomic>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -355,7 +358,9 @@ struct mi_ctx {
     // call scratch
     DevBuf d_aff, d_items, d_mi, d_h, d_cnt, d_hist, d_flags, d_ticket, d_dump, d_cols, d_part;
     HostBuf h_aff, h_items, h_out, h_read;
-    // Parzen scratch
+    // Parzen: the pairs' descriptors (device array), per-call pair indices and row offsets, scratch
+    DevBuf p_pairs, p_pair_of, p_row_start;
+    int p_bmax = 0, p_nxmax = 0;
     DevBuf p_aff, p_jac, p_hist, p_cnt, p_marg, p_ment, p_mterm, p_jsum, p_w, p_mom, p_grad;
     // autotune and graph caches
     std::map<std::tuple<int, int, int>, Choice> tuned;  // (path, pair-or--1, n bucket)
@@ -750,6 +755,40 @@ mi_status upload_pairs(mi_ctx *ctx) {
     return MI_OK;
 }
 
+// The Parzen kernels' view of one pair.
+ParzenPair parzen_pair(const mi_ctx *ctx, const Pair &P) {
+    ParzenPair pp;
+    memset(&pp, 0, sizeof pp);
+    pp.fbins = P.pfbins.as<uint8_t>();
+    pp.mov = P.pmov.as<float>();
+    pp.movx = P.pmovx.as<float>();
+    pp.texq = P.ptex;
+    pp.srow = P.srow.p ? P.srow.as<uint32_t>() : nullptr;
+    pp.scol = P.scol.as<uint16_t>();
+    pp.sbin = P.sbin.as<uint8_t>();
+    for (int a = 0; a < 3; ++a) {
+        pp.nf[a] = P.nf[a];
+        pp.nm[a] = P.nm[a];
+    }
+    pp.B = P.bins;
+    (void)ctx;
+    return pp;
+}
+
+mi_status upload_parzen_pairs(mi_ctx *ctx) {
+    std::vector<ParzenPair> pd;
+    for (auto &p : ctx->pairs) {
+        pd.push_back(parzen_pair(ctx, *p));
+        ctx->p_bmax = std::max(ctx->p_bmax, p->bins);
+        ctx->p_nxmax = std::max(ctx->p_nxmax, p->nf[0]);
+    }
+    MI_CU(ctx->p_pairs.ensure(pd.size() * sizeof(ParzenPair)), "allocating Parzen pair descriptors");
+    MI_CU(cudaMemcpyAsync(ctx->p_pairs.p, pd.data(), pd.size() * sizeof(ParzenPair), cudaMemcpyHostToDevice, ctx->stream),
+          "uploading Parzen pair descriptors");
+    MI_CU(cudaStreamSynchronize(ctx->stream), "uploading Parzen pair descriptors");
+    return MI_OK;
+}
+
 PairDev host_pairdev(const Pair &P) {
     PairDev d;
     memset(&d, 0, sizeof d);
@@ -793,10 +832,6 @@ mi_status create_common(mi_ctx **out, const mi_volume *fixed, const mi_volume *m
     }
     if (ctx->opt.kernel != MI_HARD && ctx->opt.kernel != MI_PARZEN) {
         g_create_error = "opt.kernel must be MI_HARD or MI_PARZEN";
-        return MI_EINVAL;
-    }
-    if (ctx->opt.kernel == MI_PARZEN && npairs != 1) {
-        g_create_error = "the Parzen form takes one pair per context";
         return MI_EINVAL;
     }
     if (!(ctx->opt.sample_fraction >= 0.0f && ctx->opt.sample_fraction <= 1.0f)) {
@@ -859,6 +894,13 @@ mi_status create_common(mi_ctx **out, const mi_volume *fixed, const mi_volume *m
         mi_status st = add_pair(ctx.get(), &fixed[p], &moving[p], bins[p]);
         if (st != MI_OK) {
             g_create_error = "pair " + std::to_string(p) + ": " + ctx->err;
+            return st;
+        }
+    }
+    if (ctx->opt.kernel == MI_PARZEN) {
+        mi_status st = upload_parzen_pairs(ctx.get());
+        if (st != MI_OK) {
+            g_create_error = ctx->err;
             return st;
         }
     }
@@ -1101,6 +1143,84 @@ mi_status launch_batched_once(mi_ctx *ctx, int nitems, const QSet &Q, const Outp
     return MI_OK;
 }
 
+// On-disk autotune cache: one line per tuned shape, "<key>\t<variant> <threads> <ctas> <lpr_log2> <slabs>".
+// The file is named by mi_autotune_cache() or, until that is called, by the MI_AUTOTUNE_CACHE
+// environment variable; without a name nothing is read or written.  A cached choice is used only if it
+// is still one of the current candidates (so a changed library or device never replays a stale one).
+std::mutex g_cache_mutex;
+std::string g_cache_path;
+bool g_cache_path_set = false;
+
+std::string cache_path() {
+    std::lock_guard<std::mutex> lock(g_cache_mutex);
+    if (!g_cache_path_set) {
+        const char *e = getenv("MI_AUTOTUNE_CACHE");
+        return e ? std::string(e) : std::string();
+    }
+    return g_cache_path;
+}
+
+uint64_t fnv1a(const std::string &s) {
+    uint64_t h = 1469598103934665603ull;
+    for (unsigned char c : s) {
+        h ^= c;
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+// Everything the candidates and their timings depend on: the device, the library, the pairs' geometry,
+// types and bins, the call's transform-count bucket and the options that restrict the candidates.
+std::string tune_key(mi_ctx *ctx, int bucket, int nq) {
+    cudaDeviceProp pr;
+    std::string dev = "?";
+    if (cudaGetDeviceProperties(&pr, ctx->device) == cudaSuccess) dev = pr.name;
+    cudaGetLastError();
+    std::string pairs;
+    for (auto &p : ctx->pairs) {
+        char b[160];
+        snprintf(b, sizeof b, "%d,%d,%d/%d,%d,%d/%d/%d/%d/%d/%d;", p->nf[0], p->nf[1], p->nf[2], p->nm[0], p->nm[1],
+                 p->nm[2], p->mdtype, p->mdepth, p->bins, p->rows_words, p->srow.p ? 1 : 0);
+        pairs += b;
+    }
+    char k[512];
+    snprintf(k, sizeof k, "%s|%s|sms%d|n%zu|%016llx|b%d|q%d|hv%d|th%d|tr%d|ts%d", mi_version(), dev.c_str(), ctx->sms,
+             ctx->pairs.size(), (unsigned long long)fnv1a(pairs), bucket, nq, ctx->opt.hist_variant,
+             ctx->opt.block_threads, ctx->opt.tile_rows, ctx->opt.tile_slabs);
+    for (char *c = k; *c; ++c)
+        if (*c == '\t' || *c == '\n') *c = ' ';
+    return k;
+}
+
+bool cache_lookup(const std::string &path, const std::string &key, const std::vector<Choice> &cands, Choice &out) {
+    std::lock_guard<std::mutex> lock(g_cache_mutex);
+    FILE *f = fopen(path.c_str(), "r");
+    if (!f) return false;
+    char line[1024];
+    bool found = false;
+    while (fgets(line, sizeof line, f)) {
+        char *tab = strchr(line, '\t');
+        if (!tab || std::string(line, tab - line) != key) continue;
+        int v, th, ctas, lpr, slabs;
+        if (sscanf(tab + 1, "%d %d %d %d %d", &v, &th, &ctas, &lpr, &slabs) != 5) continue;
+        for (const Choice &c : cands)
+            if (c.variant == v && c.threads == th && c.ctas == ctas && c.tile.lpr_log2 == lpr && c.tile.slabs == slabs) {
+                out = c;  // the last matching line wins
+                found = true;
+            }
+    }
+    fclose(f);
+    return found;
+}
+
+void cache_store(const std::string &path, const std::string &key, const Choice &c) {
+    std::lock_guard<std::mutex> lock(g_cache_mutex);
+    FILE *f = fopen(path.c_str(), "a");
+    if (!f) return;  // the cache is an aid: a read-only location only costs the tuning time
+    fprintf(f, "%s\t%d %d %d %d %d\n", key.c_str(), c.variant, c.threads, c.ctas, c.tile.lpr_log2, c.tile.slabs);
+    fclose(f);
+}
+
 // Autotune: time every candidate on the first items of this call (up to three
 // waves, so that effects that build up across waves, such as CTAs drifting to
 // different parts of the volumes, show in the timing).
@@ -1279,15 +1399,21 @@ mi_status eval_core(mi_ctx *ctx, const EvalReq &R, const float *qv, int nq, doub
         if (it != ctx->tuned.end()) {
             ch = it->second;
         } else {
-            // tuning needs the inputs on the device
-            MI_CU(cudaMemcpyAsync(ctx->d_aff.p, h_aff, (size_t)n * 48, cudaMemcpyHostToDevice, ctx->stream), "H2D");
-            MI_CU(cudaMemcpyAsync(ctx->d_items.p, items.data(), (size_t)n * sizeof(Item), cudaMemcpyHostToDevice,
-                                  ctx->stream),
-                  "H2D");
-            st = autotune(ctx, n, Q, O, ch, cands);
-            if (st != MI_OK) return st;
+            const std::string cpath = ctx->opt.autotune && cands.size() > 1 ? cache_path() : std::string();
+            const std::string ckey = cpath.empty() ? std::string() : tune_key(ctx, bucket, nq);
+            if (cpath.empty() || !cache_lookup(cpath, ckey, cands, ch)) {
+                // tuning needs the inputs on the device
+                MI_CU(cudaMemcpyAsync(ctx->d_aff.p, h_aff, (size_t)n * 48, cudaMemcpyHostToDevice, ctx->stream),
+                      "H2D");
+                MI_CU(cudaMemcpyAsync(ctx->d_items.p, items.data(), (size_t)n * sizeof(Item), cudaMemcpyHostToDevice,
+                                      ctx->stream),
+                      "H2D");
+                st = autotune(ctx, n, Q, O, ch, cands);
+                if (st != MI_OK) return st;
+                MI_CU(cudaMemsetAsync(ctx->d_flags.p, 0, 2 * sizeof(int), ctx->stream), "resetting flags");
+                if (!cpath.empty()) cache_store(cpath, ckey, ch);
+            }
             ctx->tuned[key] = ch;
-            MI_CU(cudaMemsetAsync(ctx->d_flags.p, 0, 2 * sizeof(int), ctx->stream), "resetting flags");
         }
         const bool use_graph = ctx->opt.use_graphs && !R.dump && ctx->stream != nullptr;
         // staging buffers are sized before the key is formed: a graph replays copies from their addresses
@@ -1319,26 +1445,33 @@ mi_status eval_core(mi_ctx *ctx, const EvalReq &R, const float *qv, int nq, doub
 // Parzen
 // ---------------------------------------------------------------------------
 
+// Parzen MI (and, with out_grad, its gradient) for n transforms; pair_of (n entries) names each
+// transform's pair in a multi-pair context (NULL: pair 0).  One launch per kernel for all pairs.
 mi_status parzen_core(mi_ctx *ctx, const std::vector<float> &prm, int n, const float *qv, int nq, double *out_mi,
-                      double *out_grad) {
-    const Pair &P = *ctx->pairs[0];
-    const int B = P.bins;
-    const size_t B2 = (size_t)B * B;
+                      double *out_grad, const std::vector<int> *pair_of = nullptr) {
+    const int Bmax = ctx->p_bmax;
+    const size_t BM2 = (size_t)Bmax * Bmax;
     QSet Q;
     mi_status st = make_qset(ctx, qv, nq, Q);
     if (st != MI_OK) return st;
     const int np = ctx->nparams();
+    const bool multi = pair_of != nullptr;
     std::vector<ParzenAffine> pa(n);
     std::vector<double> jac((size_t)n * 12 * np);
+    std::vector<long long> row_start(multi ? n + 1 : 0);
+    long long total_rows = 0;
     for (int t = 0; t < n; ++t) {
+        const int pi = multi ? (*pair_of)[t] : 0;
+        if (pi < 0 || pi >= (int)ctx->pairs.size()) return ctx->fail(MI_EINVAL, "pair index out of range");
+        const Pair &P = *ctx->pairs[pi];
         double aff[12];
         double *J = &jac[(size_t)t * 12 * np];
         build_affine_opt(ctx->opt, &prm[(size_t)t * np], P.nf, P.sf, P.nm, P.sm, aff, J);
         for (int e = 0; e < 12; ++e) {
-            const double s = aff[e] * 4294967296.0;
-            if (!(fabs(s) < 4503599627370496.0))  // |x| < 2^20 keeps every int64 product below 2^63
+            const double sc = aff[e] * 4294967296.0;
+            if (!(fabs(sc) < 4503599627370496.0))  // |x| < 2^20 keeps every int64 product below 2^63
                 return ctx->fail(MI_ERANGE, "transform " + std::to_string(t) + ": affine out of range");
-            pa[t].A[e] = llround(s);
+            pa[t].A[e] = llround(sc);
         }
         // re-centre: u = A (i - c) + (A c + b), so the constant row becomes dA c + db
         for (int a = 0; a < 3; ++a)
@@ -1347,33 +1480,51 @@ mi_status parzen_core(mi_ctx *ctx, const std::vector<float> &prm, int n, const f
                 for (int c = 0; c < 3; ++c) acc += J[np * (4 * a + c) + p] * (0.5 * (double)(P.nf[c] - 1));
                 J[np * (4 * a + 3) + p] = acc;
             }
+        if (multi) row_start[t] = total_rows;
+        total_rows += (long long)P.nf[1] * P.nf[2];
     }
+    if (multi) row_start[n] = total_rows;
     cudaStream_t s = ctx->stream;
-    ParzenPair pp;
-    memset(&pp, 0, sizeof pp);
-    pp.fbins = P.pfbins.as<uint8_t>();
-    pp.mov = P.pmov.as<float>();
-    pp.movx = P.pmovx.as<float>();
-    pp.texq = P.ptex;
-    pp.srow = P.srow.p ? P.srow.as<uint32_t>() : nullptr;
-    pp.scol = P.scol.as<uint16_t>();
-    pp.sbin = P.sbin.as<uint8_t>();
-    for (int a = 0; a < 3; ++a) {
-        pp.nf[a] = P.nf[a];
-        pp.nm[a] = P.nm[a];
+    // the launch shapes follow the largest pair (most fixed rows), with the largest bin count
+    int big = 0;
+    for (size_t i = 1; i < ctx->pairs.size(); ++i)
+        if ((long long)ctx->pairs[i]->nf[1] * ctx->pairs[i]->nf[2] >
+            (long long)ctx->pairs[big]->nf[1] * ctx->pairs[big]->nf[2])
+            big = (int)i;
+    ParzenPair rep = parzen_pair(ctx, *ctx->pairs[multi ? big : 0]);
+    rep.B = Bmax;
+    ParzenLaunch L;
+    L.p0 = parzen_pair(ctx, *ctx->pairs[0]);
+    L.d_pairs = ctx->p_pairs.as<ParzenPair>();
+    L.d_pair_of = nullptr;
+    L.d_row_start = nullptr;
+    L.n = n;
+    L.Bmax = Bmax;
+    L.nx_max = ctx->p_nxmax;
+    L.sampled = ctx->pairs[0]->srow.p != nullptr;
+    L.total_rows = total_rows;
+    const int actas = out_grad ? parzen_adj_ctas(rep, n, nq, ctx->sms) : 1;
+    const int cblocks = parzen_cell_blocks(Bmax);
+    if (multi) {
+        MI_CU(ctx->p_pair_of.ensure((size_t)n * sizeof(int)), "alloc");
+        MI_CU(ctx->p_row_start.ensure((size_t)(n + 1) * sizeof(long long)), "alloc");
+        MI_CU(cudaMemcpyAsync(ctx->p_pair_of.p, pair_of->data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, s),
+              "H2D");
+        MI_CU(cudaMemcpyAsync(ctx->p_row_start.p, row_start.data(), (size_t)(n + 1) * sizeof(long long),
+                              cudaMemcpyHostToDevice, s),
+              "H2D");
+        L.d_pair_of = ctx->p_pair_of.as<int>();
+        L.d_row_start = ctx->p_row_start.as<long long>();
     }
-    pp.B = B;
-    const int actas = out_grad ? parzen_adj_ctas(pp, n, nq, ctx->sms) : 1;
-    const int cblocks = parzen_cell_blocks(B);
     MI_CU(ctx->p_aff.ensure((size_t)n * sizeof(ParzenAffine)), "alloc");
     MI_CU(ctx->p_jac.ensure((size_t)n * 12 * np * 8), "alloc");
-    MI_CU(ctx->p_hist.ensure((size_t)n * B2 * 8), "alloc");
+    MI_CU(ctx->p_hist.ensure((size_t)n * BM2 * 8), "alloc");
     MI_CU(ctx->p_cnt.ensure((size_t)n * 8), "alloc");
-    MI_CU(ctx->p_marg.ensure((size_t)n * 2 * B * 8), "alloc");
+    MI_CU(ctx->p_marg.ensure((size_t)n * 2 * Bmax * 8), "alloc");
     MI_CU(ctx->p_ment.ensure((size_t)n * nq * 2 * 8), "alloc");
-    MI_CU(ctx->p_mterm.ensure((size_t)n * nq * 2 * B * 8), "alloc");
+    MI_CU(ctx->p_mterm.ensure((size_t)n * nq * 2 * Bmax * 8), "alloc");
     MI_CU(ctx->p_jsum.ensure((size_t)n * nq * cblocks * 8), "alloc");
-    MI_CU(ctx->p_w.ensure((size_t)n * nq * B2 * 4), "alloc");
+    MI_CU(ctx->p_w.ensure((size_t)n * nq * BM2 * 4), "alloc");
     MI_CU(ctx->p_mom.ensure((size_t)n * nq * actas * 12 * 8), "alloc");
     MI_CU(ctx->p_grad.ensure((size_t)n * nq * np * 8), "alloc");
     MI_CU(ctx->d_mi.ensure((size_t)n * nq * 8), "alloc");
@@ -1383,13 +1534,13 @@ mi_status parzen_core(mi_ctx *ctx, const std::vector<float> &prm, int n, const f
     auto *cnt = ctx->p_cnt.as<unsigned long long>();
     auto *hist = ctx->p_hist.as<unsigned long long>();
     MI_CU(cudaEventRecord(ctx->ev0, s), "event");
-    MI_CU(launch_parzen_hist(pp, d_aff, n, ctx->sms, hist, cnt, s), "Parzen histogram");
-    MI_CU(launch_parzen_weights(hist, cnt, n, B, Q, ctx->p_marg.as<double>(), ctx->p_ment.as<double>(),
+    MI_CU(launch_parzen_hist(L, d_aff, ctx->sms, hist, cnt, s), "Parzen histogram");
+    MI_CU(launch_parzen_weights(hist, cnt, L, Q, ctx->p_marg.as<double>(), ctx->p_ment.as<double>(),
                                 ctx->p_mterm.as<double>(), ctx->p_jsum.as<double>(), ctx->d_mi.as<double>(),
                                 ctx->p_w.as<float>(), s),
           "Parzen entropies");
     if (out_grad)
-        MI_CU(launch_parzen_adjoint(pp, d_aff, ctx->p_jac.as<double>(), np, n, nq, actas, ctx->p_w.as<float>(), cnt,
+        MI_CU(launch_parzen_adjoint(L, d_aff, ctx->p_jac.as<double>(), np, nq, actas, ctx->p_w.as<float>(), cnt,
                                     ctx->p_mom.as<double>(), ctx->p_grad.as<double>(), s),
               "Parzen adjoint");
     MI_CU(cudaEventRecord(ctx->ev1, s), "event");
@@ -1402,6 +1553,20 @@ mi_status parzen_core(mi_ctx *ctx, const std::vector<float> &prm, int n, const f
     MI_CU(cudaStreamSynchronize(s), "Parzen evaluation");
     for (int t = 0; t < n; ++t)
         if (hc[t] == 0) return ctx->fail(MI_EEMPTY, "at least one transform has an empty overlap (its MI is NaN)");
+    return MI_OK;
+}
+
+// The pair indices of mi_batch_eval / mi_batch_grad (host or device memory), checked.
+mi_status read_pair_of(mi_ctx *ctx, const int *pair_of_transform, int n, std::vector<int> &out) {
+    out.resize(n);
+    if (is_device_ptr(pair_of_transform)) {
+        mi_status st = read_from_device(ctx, out.data(), pair_of_transform, (size_t)n * 4);
+        if (st != MI_OK) return st;
+    } else {
+        memcpy(out.data(), pair_of_transform, (size_t)n * 4);
+    }
+    for (int t = 0; t < n; ++t)
+        if (out[t] < 0 || out[t] >= (int)ctx->pairs.size()) return ctx->fail(MI_EINVAL, "pair index out of range");
     return MI_OK;
 }
 
@@ -1455,11 +1620,6 @@ mi_status mi_batch_create(mi_ctx **out, const mi_volume *fixed, const mi_volume 
         o = *opt;
     else
         mi_options_default(&o);
-    if (o.kernel != MI_HARD) {
-        if (out) *out = nullptr;
-        g_create_error = "mi_batch_create supports the hard-binned path only";
-        return MI_EUNSUPPORTED;
-    }
     return create_common(out, fixed, moving, bins, npairs, &o);
 }
 
@@ -1542,7 +1702,6 @@ mi_status mi_batch_eval(mi_ctx *ctx, const int *pair_of_transform, const float *
     if (!ctx) return MI_EINVAL;
     DeviceGuard guard(ctx->device);
     if (n < 0) return ctx->fail(MI_EINVAL, "n < 0");
-    if (ctx->opt.kernel != MI_HARD) return ctx->fail(MI_EUNSUPPORTED, "mi_batch_eval is a hard-path entry point");
     float qv[kMaxQ];
     mi_status st = read_q(ctx, q, nq, qv);
     if (st != MI_OK) return st;
@@ -1550,6 +1709,12 @@ mi_status mi_batch_eval(mi_ctx *ctx, const int *pair_of_transform, const float *
     if (!out_mi || !pair_of_transform) return ctx->fail(MI_EINVAL, "out_mi or pair_of_transform is NULL");
     std::vector<float> prm;
     if ((st = read_transforms(ctx, transforms, n, prm)) != MI_OK) return st;
+    if (ctx->opt.kernel == MI_PARZEN) {
+        if (out_h || out_count) return ctx->fail(MI_EUNSUPPORTED, "out_h / out_count are hard-path outputs");
+        std::vector<int> po;
+        if ((st = read_pair_of(ctx, pair_of_transform, n, po)) != MI_OK) return st;
+        return parzen_core(ctx, prm, n, qv, nq, out_mi, nullptr, &po);
+    }
     EvalReq R;
     R.n = n;
     R.path = MI_PATH_BATCHED;
@@ -1580,9 +1745,30 @@ mi_status mi_grad(mi_ctx *ctx, const float *transforms, int n, const float *q, i
     if (st != MI_OK) return st;
     if (n == 0) return MI_OK;
     if (!out_mi || !out_grad) return ctx->fail(MI_EINVAL, "out_mi or out_grad is NULL");
+    if (ctx->pairs.size() != 1) return ctx->fail(MI_EINVAL, "mi_grad needs a single-pair context (use mi_batch_grad)");
     std::vector<float> prm;
     if ((st = read_transforms(ctx, transforms, n, prm)) != MI_OK) return st;
     return parzen_core(ctx, prm, n, qv, nq, out_mi, out_grad);
+}
+
+mi_status mi_batch_grad(mi_ctx *ctx, const int *pair_of_transform, const float *transforms, int n, const float *q,
+                        int nq, double *out_mi, double *out_grad) {
+    if (!ctx) return MI_EINVAL;
+    DeviceGuard guard(ctx->device);
+    if (ctx->opt.kernel != MI_PARZEN)
+        return ctx->fail(MI_EUNSUPPORTED, "mi_batch_grad needs a MI_PARZEN context (the hard histogram is not differentiable)");
+    if (n < 0) return ctx->fail(MI_EINVAL, "n < 0");
+    float qv[kMaxQ];
+    mi_status st = read_q(ctx, q, nq, qv);
+    if (st != MI_OK) return st;
+    if (n == 0) return MI_OK;
+    if (!out_mi || !out_grad || !pair_of_transform)
+        return ctx->fail(MI_EINVAL, "out_mi, out_grad or pair_of_transform is NULL");
+    std::vector<float> prm;
+    if ((st = read_transforms(ctx, transforms, n, prm)) != MI_OK) return st;
+    std::vector<int> po;
+    if ((st = read_pair_of(ctx, pair_of_transform, n, po)) != MI_OK) return st;
+    return parzen_core(ctx, prm, n, qv, nq, out_mi, out_grad, &po);
 }
 
 mi_status mi_hist(mi_ctx *ctx, int pair, const float *transforms, const int32_t *affines, int n, int path,
@@ -1715,6 +1901,12 @@ int mi_selected_variant(mi_ctx *ctx, int pair, int n) {
     (void)pair;
     const Choice *c = selected_choice(ctx, n);
     return c ? c->variant : -1;
+}
+
+void mi_autotune_cache(const char *path) {
+    std::lock_guard<std::mutex> lock(g_cache_mutex);
+    g_cache_path = path ? path : "";
+    g_cache_path_set = true;
 }
 
 mi_status mi_selected_config(mi_ctx *ctx, int n, int out[5]) {

@@ -180,20 +180,37 @@ cudaError_t launch_parzen_extend(const float *mov, const int nm[3], float *out, 
 // movx at (x, y), (x + 1, y), (x, y + 1), (x + 1, y + 1) of plane z.
 cudaError_t launch_parzen_quads(const float *movx, const int nm[3], void *out, cudaStream_t s);
 int parzen_cell_blocks(int B);
-// Soft histograms (n x B^2 u64 sums of 2^-32-quantised weights, zeroed here) and overlap counts (n).
+// One Parzen call over n transforms: the pairs as a device array, transform t evaluated on pair
+// d_pair_of[t] (NULL: every transform on pair 0) whose fixed rows start at d_row_start[t] in the
+// sequence of all transforms' rows (NULL: t R of pair 0; n + 1 entries).  Per-transform tables take
+// slots sized for the largest bin count Bmax (histograms and W: Bmax^2 per transform and q; marginals
+// 2 Bmax), the first B^2 used with row stride B.  nx_max: the longest fixed row of the pairs.
+struct ParzenLaunch {
+    ParzenPair p0;  // pair 0 (single-pair calls pass it by value)
+    const ParzenPair *d_pairs;
+    const int *d_pair_of;
+    const long long *d_row_start;
+    int n;
+    int Bmax;
+    int nx_max;
+    bool sampled;
+    long long total_rows;
+};
+
+// Soft histograms (n x Bmax^2 u64 sums of 2^-32-quantised weights, zeroed here) and overlap counts (n).
 // sms: the device's SM count (the grid is sized in whole waves).
-cudaError_t launch_parzen_hist(const ParzenPair &P, const ParzenAffine *d_aff, int n, int sms,
-                               unsigned long long *d_hist, unsigned long long *d_count, cudaStream_t s);
-// MI per q (n x nq) and the weight tables W (n x nq x B^2, FP32) from the soft histograms.
-// Scratch: marg (n x 2B), ment (n x nq x 2), mterm (n x nq x 2B), jpart (n x nq x parzen_cell_blocks(B)) FP64.
-cudaError_t launch_parzen_weights(const unsigned long long *d_hist, const unsigned long long *d_count, int n, int B,
-                                  const QSet &Q, double *marg, double *ment, double *mterm, double *jpart, double *d_mi,
-                                  float *d_w, cudaStream_t s);
-// Gradient: per-CTA moments (scratch n x nq x ctas x 12 FP64) and dMI/dtheta (n x nq x 9 FP64);
-// d_jac is n x 12 x 9 FP64 taken about the fixed-volume centre.
-// d_jac: n x 12 x np (d[A|b]/dparam about the fixed centre), np = 9 or 12; d_grad: n x nq x np.
-cudaError_t launch_parzen_adjoint(const ParzenPair &P, const ParzenAffine *d_aff, const double *d_jac, int np, int n,
-                                  int nq, int ctas, const float *d_w, const unsigned long long *d_count, double *d_mom,
+cudaError_t launch_parzen_hist(const ParzenLaunch &L, const ParzenAffine *d_aff, int sms, unsigned long long *d_hist,
+                               unsigned long long *d_count, cudaStream_t s);
+// MI per q (n x nq) and the weight tables W (n x nq x Bmax^2, FP32) from the soft histograms.
+// Scratch: marg (n x 2 Bmax), ment (n x nq x 2), mterm (n x nq x 2 Bmax), jpart (n x nq x
+// parzen_cell_blocks(Bmax)) FP64.
+cudaError_t launch_parzen_weights(const unsigned long long *d_hist, const unsigned long long *d_count,
+                                  const ParzenLaunch &L, const QSet &Q, double *marg, double *ment, double *mterm,
+                                  double *jpart, double *d_mi, float *d_w, cudaStream_t s);
+// Gradient: per-CTA moments (scratch n x nq x ctas x 12 FP64) and dMI/dtheta (n x nq x np FP64);
+// d_jac: n x 12 x np (d[A|b]/dparam about the fixed centre), np = 9 or 12.
+cudaError_t launch_parzen_adjoint(const ParzenLaunch &L, const ParzenAffine *d_aff, const double *d_jac, int np, int nq,
+                                  int ctas, const float *d_w, const unsigned long long *d_count, double *d_mom,
                                   double *d_grad, cudaStream_t s);
 
 // ---- allocation-free evaluation (mi_noalloc.cu) ---------------------------

@@ -295,38 +295,60 @@ __host__ inline int parzen_fwd_copies(int B) {
     return best;
 }
 
-template <int RPW, bool SAMPLED, int COPIES>
+// MULTI: transforms on several pairs (descriptors read from `pairs`); otherwise every transform is on
+// the pair P0 passed by value, whose fields stay kernel parameters.
+template <int RPW, bool SAMPLED, int COPIES, bool MULTI>
 __global__ void __launch_bounds__(256 * COPIES)
-    k_parzen_hist(ParzenPair P, const ParzenAffine *__restrict__ aff, long long rows_per_cta, long long total_rows,
-                  int SB, unsigned long long *__restrict__ ghist, unsigned long long *__restrict__ gcount) {
+    k_parzen_hist(ParzenPair P0, const ParzenPair *__restrict__ pairs, const int *__restrict__ pair_of,
+                  const long long *__restrict__ row_start, int n, const ParzenAffine *__restrict__ aff,
+                  long long rows_per_cta, long long total_rows, int Bmax, unsigned long long *__restrict__ ghist,
+                  unsigned long long *__restrict__ gcount) {
     // Low-half sums [B x SB], then high-half sums.  The row stride SB >= B + 1 is 7 mod 32, so the
     // bank of cell (fixed bin b, moving bin k) is (k + 7 b) mod 32: the cells of neighbouring voxels,
     // which differ by a bin or two on either axis, fall in different banks.  Column B absorbs the
     // zero weight of bin B (m~ = B - 2 exactly).
-    // The rows of all transforms form one sequence (transform t owns rows t R .. t R + R - 1); CTA b
-    // takes rows_per_cta of them from b rows_per_cta on, one transform segment at a time, and flushes
-    // its histogram after each segment.
+    // The rows of all transforms form one sequence (transform t owns rows row_begin(t) ..
+    // row_begin(t + 1) - 1, its pair's rows); CTA b takes rows_per_cta of them from b rows_per_cta
+    // on, one transform segment at a time, and flushes its histogram after each segment into the
+    // transform's slot of Bmax^2 cells (the first B^2 of them, row-major with row stride B).
     extern __shared__ uint32_t sh32[];
-    const int B = P.B, B2 = B * B, NP = B * SB;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int CP = parzen_copy_offset(B, COPIES);  // offset between copies
-    uint32_t *lo16 = sh32 + (lane & (COPIES - 1)) * CP, *hi16 = lo16 + NP;
     __shared__ long long A[12];
-    for (int c = threadIdx.x; c < COPIES * CP; c += blockDim.x) sh32[c] = 0u;
-    const int nf0 = P.nf[0], nf1 = P.nf[1];
-    const int n0 = P.nm[0], n1 = P.nm[1], n2 = P.nm[2];
-    const long long R = (long long)nf1 * P.nf[2];
+    const long long R0 = (long long)P0.nf[1] * P0.nf[2];  // rows per transform of a single pair
     const long long c0 = (long long)blockIdx.x * rows_per_cta;
     const long long c1 = c0 + rows_per_cta < total_rows ? c0 + rows_per_cta : total_rows;
-    const float Bm4 = (float)(B - 4);
     // a warp works on RPW rows at a time, G = 32 / RPW neighbouring voxels of each: the lanes that
     // add to one cell at once are then at most the G of a row (neighbouring voxels mostly share
     // cells, and same-address shared atomics queue), while each row's gathers stay coalesced
     constexpr int G = 32 / RPW;
     const int sub = lane / G, pos = lane % G;
-    for (long long s0 = c0; s0 < c1;) {
-        const int t = (int)(s0 / R);
-        const long long r0 = s0 - t * R, r1 = c1 - t * R < R ? c1 - t * R : R;
+    // the transform owning row c0
+    int t = 0;
+    if (MULTI) {
+        int lo_t = 0, hi_t = n - 1;
+        while (lo_t < hi_t) {  // last t with row_start[t] <= c0
+            const int mid = (lo_t + hi_t + 1) >> 1;
+            if (row_start[mid] <= c0) lo_t = mid; else hi_t = mid - 1;
+        }
+        t = lo_t;
+    } else {
+        t = (int)(c0 / R0);
+    }
+    bool first = true;
+    for (long long s0 = c0; s0 < c1; ++t) {
+        const ParzenPair P = MULTI ? pairs[pair_of[t]] : P0;
+        const int B = P.B, B2 = B * B, SB = parzen_stride(B), NP = B * SB;
+        const int CP = parzen_copy_offset(B, COPIES);  // offset between copies
+        uint32_t *lo16 = sh32 + (lane & (COPIES - 1)) * CP, *hi16 = lo16 + NP;
+        const int nf0 = P.nf[0], nf1 = P.nf[1];
+        const int n0 = P.nm[0], n1 = P.nm[1], n2 = P.nm[2];
+        const long long R = (long long)nf1 * P.nf[2];
+        const long long tb = MULTI ? row_start[t] : (long long)t * R0;
+        const float Bm4 = (float)(B - 4);
+        const long long r0 = s0 - tb, r1 = c1 - tb < R ? c1 - tb : R;
+        if (!first) __syncthreads();  // the previous segment's flush has read the copies
+        first = false;
+        for (int c = threadIdx.x; c < COPIES * CP; c += blockDim.x) sh32[c] = 0u;
         if (threadIdx.x < 12) A[threadIdx.x] = aff[t].A[threadIdx.x];
         __syncthreads();
         const long long DG0 = G * A[0], DG1 = G * A[4], DG2 = G * A[8];
@@ -408,7 +430,7 @@ __global__ void __launch_bounds__(256 * COPIES)
         }
         cnt = __reduce_add_sync(kFull, cnt);
         __syncthreads();
-        unsigned long long *gh = ghist + (size_t)t * B2;
+        unsigned long long *gh = ghist + (size_t)t * Bmax * Bmax;
         for (int c = threadIdx.x; c < B2; c += blockDim.x) {
             const int cp = (c / B) * SB + c % B;
             unsigned long long v = 0;
@@ -418,12 +440,7 @@ __global__ void __launch_bounds__(256 * COPIES)
             if (v) atomicAdd(gh + c, v);
         }
         if (lane == 0 && cnt) atomicAdd(gcount + t, (unsigned long long)cnt);
-        s0 = (long long)(t + 1) * R;
-        if (s0 < c1) {  // another transform follows: start from empty copies
-            __syncthreads();
-            for (int c = threadIdx.x; c < COPIES * CP; c += blockDim.x) sh32[c] = 0u;
-        }
-        __syncthreads();
+        s0 = tb + R;  // another transform may follow: its segment starts from empty copies
     }
 }
 
@@ -491,14 +508,20 @@ __device__ __forceinline__ double finish_entropy(double sum, float qf, int bits)
 // One CTA per transform: marginals P_F (rows), P_M (cols), their entropies per q, and the row and
 // column factors of W per q (mterm: n x nq x 2B): ln P for q = 1, dS_q/dP = -q P^(q-1) / (q - 1)
 // otherwise.  marg: n x 2B (P_F then P_M); ment: n x nq x 2 (S_F, S_M).
+// B of transform t: its pair's bin count (a multi-pair call), else the single pair's.
+__device__ __forceinline__ int bins_of(const ParzenPair *pairs, const int *pair_of, int t) {
+    return pairs[pair_of ? pair_of[t] : 0].B;
+}
+
 __global__ void k_parzen_marg(const unsigned long long *__restrict__ ghist, const unsigned long long *__restrict__ gcount,
-                              int B, QSet Q, double *__restrict__ marg, double *__restrict__ ment,
-                              double *__restrict__ mterm) {
+                              const ParzenPair *__restrict__ pairs, const int *__restrict__ pair_of, int Bmax, QSet Q,
+                              double *__restrict__ marg, double *__restrict__ ment, double *__restrict__ mterm) {
     __shared__ double s_tmp[32];
     const int t = blockIdx.x;
+    const int B = bins_of(pairs, pair_of, t);
     const double N = (double)gcount[t] * 4294967296.0;  // total weight: 2^32 per overlap voxel
-    const unsigned long long *h = ghist + (size_t)t * B * B;
-    double *pf = marg + (size_t)t * 2 * B, *pm = pf + B;
+    const unsigned long long *h = ghist + (size_t)t * Bmax * Bmax;
+    double *pf = marg + (size_t)t * 2 * Bmax, *pm = pf + B;
     for (int r = threadIdx.x; r < B; r += blockDim.x) {
         unsigned long long sr = 0, sc = 0;
         for (int c = 0; c < B; ++c) {
@@ -512,7 +535,7 @@ __global__ void k_parzen_marg(const unsigned long long *__restrict__ ghist, cons
     for (int iq = 0; iq < Q.nq; ++iq) {
         const float qf = Q.q[iq];
         const double q = (double)qf;
-        double *mt = mterm + ((size_t)t * Q.nq + iq) * 2 * B;
+        double *mt = mterm + ((size_t)t * Q.nq + iq) * 2 * Bmax;
         double a = 0.0, b = 0.0;
         for (int r = threadIdx.x; r < B; r += blockDim.x) {
             if (pf[r] > 0.0) a += ent_term(pf[r], qf);
@@ -536,17 +559,19 @@ __global__ void k_parzen_marg(const unsigned long long *__restrict__ ghist, cons
 // ln p per cell serves every q: the Shannon term -p ln p, p^q = exp(q ln p)
 // for the Tsallis ones, and dS_q/dp = -q p^q / (p (q - 1)).
 __global__ void __launch_bounds__(256)
-    k_parzen_cells(const unsigned long long *__restrict__ ghist, const unsigned long long *__restrict__ gcount, int B,
-                   QSet Q, const double *__restrict__ mterm, const double *__restrict__ ment, double *__restrict__ jpart,
+    k_parzen_cells(const unsigned long long *__restrict__ ghist, const unsigned long long *__restrict__ gcount,
+                   const ParzenPair *__restrict__ pairs, const int *__restrict__ pair_of, int Bmax, QSet Q,
+                   const double *__restrict__ mterm, const double *__restrict__ ment, double *__restrict__ jpart,
                    float *__restrict__ wout) {
     __shared__ double s_tmp[32];
-    const int t = blockIdx.y, B2 = B * B;
+    const int t = blockIdx.y;
+    const int B = bins_of(pairs, pair_of, t), B2 = B * B, BM2 = Bmax * Bmax;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const double N = (double)gcount[t] * 4294967296.0;
     const double lnb = Q.bits ? log(2.0) : 1.0;
     double p = 0.0, lp = 0.0;
     if (c < B2 && N > 0) {
-        p = (double)ghist[(size_t)t * B2 + c] / N;
+        p = (double)ghist[(size_t)t * BM2 + c] / N;
         if (p > 0.0) lp = log(p);
     }
     for (int iq = 0; iq < Q.nq; ++iq) {
@@ -559,7 +584,7 @@ __global__ void __launch_bounds__(256)
         if (c < B2) {
             double w = 0.0;
             if (p > 0.0) {
-                const double *mt = mterm + ((size_t)t * Q.nq + iq) * 2 * B;
+                const double *mt = mterm + ((size_t)t * Q.nq + iq) * 2 * Bmax;
                 const double fr = mt[c / B], mc = mt[B + c % B];
                 if (qf == 1.0f) {
                     w = (lp - fr - mc - 1.0) / lnb;
@@ -573,7 +598,7 @@ __global__ void __launch_bounds__(256)
                     }
                 }
             }
-            wout[((size_t)t * Q.nq + iq) * B2 + c] = (float)w;
+            wout[((size_t)t * Q.nq + iq) * BM2 + c] = (float)w;
         }
     }
 }
@@ -603,26 +628,32 @@ __global__ void k_parzen_final(int n, const unsigned long long *__restrict__ gco
 // Adjoint: moments M[q][a][c] = sum_x s_q(x) d_a m(u_x) x_c, x = (i - ci, j - cj, k - ck, 1)
 // ---------------------------------------------------------------------------
 
-template <int NQ, bool SAMPLED>
+template <int NQ, bool SAMPLED, bool MULTI>
 __global__ void __launch_bounds__(256, 2)
-    k_parzen_adj(ParzenPair P, const ParzenAffine *__restrict__ aff, int nq_total, int q0,
-                 const float *__restrict__ wtab, int w_in_smem, double *__restrict__ mom) {
+    k_parzen_adj(ParzenPair P0, const ParzenPair *__restrict__ pairs, const int *__restrict__ pair_of, int Bmax,
+                 const ParzenAffine *__restrict__ aff, int nq_total, int q0, const float *__restrict__ wtab,
+                 int w_in_smem, double *__restrict__ mom) {
     // mom: n x nq_total x gridDim.x x 12 per-CTA partial moments (no atomics: fixed-order reduction later)
     // NQ x B x SB weight pairs (W[k], W[k + 1]) when they fit; the row stride SB >= B + 1 is 7 mod 32,
-    // so neighbouring voxels' cells, a bin or two apart on either axis, are read from different banks
+    // so neighbouring voxels' cells, a bin or two apart on either axis, are read from different banks.
+    // W of transform t is its slot of Bmax^2 entries per q (the first B^2 used, row stride B).
     extern __shared__ float sw[];
-    const int t = blockIdx.y, B = P.B, B2 = B * B, SB = parzen_stride(B);
+    const int t = blockIdx.y;
+    const ParzenPair P = MULTI ? pairs[pair_of[t]] : P0;
+    const int B = P.B, SB = parzen_stride(B);
     __shared__ long long A[12];
     __shared__ float s_red[8][NQ * 12];
     if (threadIdx.x < 12) A[threadIdx.x] = aff[t].A[threadIdx.x];
-    const float *W = wtab + ((size_t)t * nq_total + q0) * B2;
-    int RS = B, QS = B2;  // row stride and per-q stride of the table in use
+    const size_t BM2 = (size_t)Bmax * Bmax;
+    const float *W = wtab + ((size_t)t * nq_total + q0) * BM2;
+    int RS = B, QS = (int)BM2;  // row stride and per-q stride of the table in use
     float2 *sw2 = reinterpret_cast<float2 *>(sw);
     if (w_in_smem) {  // pairs (W[k], W[k + 1]), W[B] = 0: two 8-byte reads give a cell's four weights
-        for (int c = threadIdx.x; c < NQ * B2; c += blockDim.x) {
-            const int qq = c / B2, cc = c % B2, k = cc % B;
-            const float nxt = k + 1 < B ? W[c + 1] : 0.0f;
-            sw2[qq * B * SB + (cc / B) * SB + k] = make_float2(W[c], nxt);
+        for (int c = threadIdx.x; c < NQ * B * B; c += blockDim.x) {
+            const int qq = c / (B * B), cc = c % (B * B), k = cc % B;
+            const float *Wq = W + (size_t)qq * BM2;
+            const float nxt = k + 1 < B ? Wq[cc + 1] : 0.0f;
+            sw2[qq * B * SB + (cc / B) * SB + k] = make_float2(Wq[cc], nxt);
         }
         RS = SB;
         QS = B * SB;
@@ -752,11 +783,13 @@ __global__ void __launch_bounds__(256, 2)
 }
 
 // grad[t][q][p] = -(B - 4) / N sum_e mom[t][q][e] J[t][e][p], J (12 x np) taken about the fixed centre
-__global__ void k_parzen_grad(int n, int nq, int np, int B, int nparts, const unsigned long long *__restrict__ gcount,
+__global__ void k_parzen_grad(int n, int nq, int np, const ParzenPair *__restrict__ pairs,
+                              const int *__restrict__ pair_of, int nparts, const unsigned long long *__restrict__ gcount,
                               const double *__restrict__ mom, const double *__restrict__ jac, double *__restrict__ grad) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= n * nq * np) return;
     const int p = x % np, tq = x / np, t = tq / nq;
+    const int B = bins_of(pairs, pair_of, t);
     const double N = (double)gcount[t];
     if (N <= 0) {
         grad[x] = __longlong_as_double(0x7ff8000000000000ll);
@@ -812,7 +845,7 @@ static size_t parzen_adj_smem(int B, int g) {
 
 template <int NQ, bool SAMPLED>
 static int adj_blocks_per_sm(size_t smem) {
-    const void *fn = (const void *)k_parzen_adj<NQ, SAMPLED>;
+    const void *fn = (const void *)k_parzen_adj<NQ, SAMPLED, false>;
     if (allow_smem(fn, smem) != cudaSuccess) {
         cudaGetLastError();
         return 1;
@@ -857,34 +890,38 @@ cudaError_t launch_parzen_quads(const float *movx, const int nm[3], void *out, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_parzen_hist(const ParzenPair &P, const ParzenAffine *d_aff, int n, int sms,
-                               unsigned long long *d_hist, unsigned long long *d_count, cudaStream_t s) {
+cudaError_t launch_parzen_hist(const ParzenLaunch &L, const ParzenAffine *d_aff, int sms, unsigned long long *d_hist,
+                               unsigned long long *d_count, cudaStream_t s) {
+    const int n = L.n;
     if (n <= 0) return cudaSuccess;
-    const size_t B2 = (size_t)P.B * P.B;
-    cudaError_t e = cudaMemsetAsync(d_hist, 0, (size_t)n * B2 * sizeof(unsigned long long), s);
+    const size_t BM2 = (size_t)L.Bmax * L.Bmax;
+    cudaError_t e = cudaMemsetAsync(d_hist, 0, (size_t)n * BM2 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(d_count, 0, (size_t)n * sizeof(unsigned long long), s)) != cudaSuccess) return e;
-    const int SB = parzen_stride(P.B);
-    const int copies = parzen_fwd_copies(P.B);
-    const size_t smem = parzen_fwd_smem(P.B, copies);
+    // shared memory for the largest pair's bins (a smaller pair's copies fit in the same space)
+    const int copies = parzen_fwd_copies(L.Bmax);
+    const size_t smem = parzen_fwd_smem(L.Bmax, copies);
+    const bool multi = L.d_pair_of != nullptr;
     const void *fn = nullptr;
+#define MI_HIST_FN(C)                                                                                   \
+    (multi ? (L.sampled ? (const void *)k_parzen_hist<kParzenRowsPerStep, true, C, true>                \
+                        : (const void *)k_parzen_hist<kParzenRowsPerStep, false, C, true>)              \
+           : (L.sampled ? (const void *)k_parzen_hist<kParzenRowsPerStep, true, C, false>               \
+                        : (const void *)k_parzen_hist<kParzenRowsPerStep, false, C, false>))
     switch (copies) {
-        case 4: fn = P.srow ? (const void *)k_parzen_hist<kParzenRowsPerStep, true, 4>
-                            : (const void *)k_parzen_hist<kParzenRowsPerStep, false, 4>;
-                break;
-        case 2: fn = P.srow ? (const void *)k_parzen_hist<kParzenRowsPerStep, true, 2>
-                            : (const void *)k_parzen_hist<kParzenRowsPerStep, false, 2>;
-                break;
-        default: fn = P.srow ? (const void *)k_parzen_hist<kParzenRowsPerStep, true, 1>
-                             : (const void *)k_parzen_hist<kParzenRowsPerStep, false, 1>;
+        case 4: fn = MI_HIST_FN(4); break;
+        case 2: fn = MI_HIST_FN(2); break;
+        default: fn = MI_HIST_FN(1);
     }
+#undef MI_HIST_FN
     if ((e = allow_smem(fn, smem)) != cudaSuccess) return e;
     // rows per CTA: at most kParzenMaxVox voxels per copy, so that the 16-bit halves cannot overflow
     // (a row of nx voxels, or of at most nx sampled entries, is walked 32 lanes at a time, so copy i,
-    // fed by the lanes l = i mod C, takes at most 32 / C of every 32); CTAs do equal shares of the
-    // rows of all transforms, as many as fill a whole number of waves of the CTAs resident at once
-    const long long R = (long long)P.nf[1] * P.nf[2], TR = R * n;
-    long long cap = kParzenMaxVox / ((32 / copies) * ((P.nf[0] + 31) / 32));
+    // fed by the lanes l = i mod C, takes at most 32 / C of every 32; the longest row of all pairs
+    // bounds it); CTAs do equal shares of the rows of all transforms, as many as fill a whole number
+    // of waves of the CTAs resident at once
+    const long long TR = L.total_rows;
+    long long cap = kParzenMaxVox / ((32 / copies) * ((L.nx_max + 31) / 32));
     if (cap < 1) cap = 1;
     const int per_sm = resident_per_sm(fn, 256 * copies, smem);
     const long long wave = (long long)per_sm * (sms > 0 ? sms : 1);
@@ -893,46 +930,56 @@ cudaError_t launch_parzen_hist(const ParzenPair &P, const ParzenAffine *d_aff, i
     if (nch > TR) nch = TR;
     long long rpc = (TR + nch - 1) / nch, total = TR;
     dim3 grid((unsigned)((TR + rpc - 1) / rpc));
-    int sb = SB;
-    void *args[] = {(void *)&P, (void *)&d_aff, (void *)&rpc, (void *)&total, (void *)&sb, (void *)&d_hist,
-                    (void *)&d_count};
+    int nn = n, bmax = L.Bmax;
+    void *args[] = {(void *)&L.p0, (void *)&L.d_pairs, (void *)&L.d_pair_of, (void *)&L.d_row_start, (void *)&nn,
+                    (void *)&d_aff, (void *)&rpc, (void *)&total, (void *)&bmax, (void *)&d_hist, (void *)&d_count};
     return cudaLaunchKernel(fn, grid, dim3(256 * copies), args, smem, s);
 }
 
-cudaError_t launch_parzen_weights(const unsigned long long *d_hist, const unsigned long long *d_count, int n, int B,
-                                  const QSet &Q, double *marg, double *ment, double *mterm, double *jpart, double *d_mi,
-                                  float *d_w, cudaStream_t s) {
+cudaError_t launch_parzen_weights(const unsigned long long *d_hist, const unsigned long long *d_count,
+                                  const ParzenLaunch &L, const QSet &Q, double *marg, double *ment, double *mterm,
+                                  double *jpart, double *d_mi, float *d_w, cudaStream_t s) {
     cudaError_t e;
-    k_parzen_marg<<<n, 256, 0, s>>>(d_hist, d_count, B, Q, marg, ment, mterm);
+    const int n = L.n;
+    k_parzen_marg<<<n, 256, 0, s>>>(d_hist, d_count, L.d_pairs, L.d_pair_of, L.Bmax, Q, marg, ment, mterm);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const int nb = parzen_cell_blocks(B);
+    const int nb = parzen_cell_blocks(L.Bmax);
     dim3 grid(nb, n);
-    k_parzen_cells<<<grid, 256, 0, s>>>(d_hist, d_count, B, Q, mterm, ment, jpart, d_w);
+    k_parzen_cells<<<grid, 256, 0, s>>>(d_hist, d_count, L.d_pairs, L.d_pair_of, L.Bmax, Q, mterm, ment, jpart, d_w);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_parzen_final<<<(n * Q.nq + 127) / 128, 128, 0, s>>>(n, d_count, Q, ment, jpart, nb, d_mi);
     return cudaGetLastError();
 }
 
-cudaError_t launch_parzen_adjoint(const ParzenPair &P, const ParzenAffine *d_aff, const double *d_jac, int np, int n,
-                                  int nq, int ctas, const float *d_w, const unsigned long long *d_count, double *d_mom,
+cudaError_t launch_parzen_adjoint(const ParzenLaunch &L, const ParzenAffine *d_aff, const double *d_jac, int np, int nq,
+                                  int ctas, const float *d_w, const unsigned long long *d_count, double *d_mom,
                                   double *d_grad, cudaStream_t s) {
     cudaError_t e;
+    const int n = L.n;
     dim3 grid(ctas, n);
     for (int q0 = 0; q0 < nq; q0 += 4) {
         const int g = nq - q0 < 4 ? nq - q0 : 4;
-        const size_t smem = parzen_adj_smem(P.B, g);
+        const size_t smem = parzen_adj_smem(L.Bmax, g);
         const int in_smem = smem > 0;
-#define MI_ADJ_S(NQV, SV)                                                                                   \
-    do {                                                                                                    \
-        if ((e = allow_smem((const void *)k_parzen_adj<NQV, SV>, smem)) != cudaSuccess) return e;           \
-        k_parzen_adj<NQV, SV><<<grid, 256, smem, s>>>(P, d_aff, nq, q0, d_w, in_smem, d_mom);               \
+#define MI_ADJ_S(NQV, SV, MV)                                                                                \
+    do {                                                                                                     \
+        if ((e = allow_smem((const void *)k_parzen_adj<NQV, SV, MV>, smem)) != cudaSuccess) return e;        \
+        k_parzen_adj<NQV, SV, MV><<<grid, 256, smem, s>>>(L.p0, L.d_pairs, L.d_pair_of, L.Bmax, d_aff, nq, q0, \
+                                                          d_w, in_smem, d_mom);                              \
     } while (0)
-#define MI_ADJ(NQV)                 \
-    do {                            \
-        if (P.srow)                 \
-            MI_ADJ_S(NQV, true);    \
-        else                        \
-            MI_ADJ_S(NQV, false);   \
+#define MI_ADJ(NQV)                              \
+    do {                                         \
+        if (L.d_pair_of) {                       \
+            if (L.sampled)                       \
+                MI_ADJ_S(NQV, true, true);       \
+            else                                 \
+                MI_ADJ_S(NQV, false, true);      \
+        } else {                                 \
+            if (L.sampled)                       \
+                MI_ADJ_S(NQV, true, false);      \
+            else                                 \
+                MI_ADJ_S(NQV, false, false);     \
+        }                                        \
     } while (0)
         switch (g) {
             case 1: MI_ADJ(1); break;
@@ -944,7 +991,8 @@ cudaError_t launch_parzen_adjoint(const ParzenPair &P, const ParzenAffine *d_aff
 #undef MI_ADJ_S
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    k_parzen_grad<<<(n * nq * np + 127) / 128, 128, 0, s>>>(n, nq, np, P.B, ctas, d_count, d_mom, d_jac, d_grad);
+    k_parzen_grad<<<(n * nq * np + 127) / 128, 128, 0, s>>>(n, nq, np, L.d_pairs, L.d_pair_of, ctas, d_count, d_mom,
+                                                            d_jac, d_grad);
     return cudaGetLastError();
 }
 

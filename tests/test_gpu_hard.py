@@ -427,19 +427,32 @@ def test_uneven_batch_full_size(cuda_lib):
         np.testing.assert_array_equal(cnt[chk], cnt_o)
         ok = cnt_o > 0
         assert_mi_close(mi[chk][ok], mi_o[ok], h_o[ok])
-    # the Parzen MI and gradient of the 8 largest pairs (float volumes normalised from the same data)
+    # the Parzen MI and gradient of the 8 largest pairs, each at its own bin count, 64 transforms each, in
+    # one call of a multi-pair Parzen context (one launch per kernel); one transform per pair against the
+    # FP64 oracle (one host thread per pair: the oracle's C code runs outside the interpreter lock)
+    from concurrent.futures import ThreadPoolExecutor
+
     big = np.argsort([np.prod(s["shape"]) for s in specs])[-8:]
-    for p in big:
-        f, m, depth, bins = vols[p]
-        pctx = cuda_lib.Context(f, m, bins=64, kernel="parzen", fixed_depth=depth, moving_depth=depth)
-        sel = np.nonzero(pair_of == p)[0][:64]
-        mi_p, g_p = pctx.grad(prm[sel], [1.0, 0.7, 1.3])
-        t = sel[0]
-        aff, J = oracle.affine(prm[t], f.shape, (1, 1, 1), m.shape, (1, 1, 1), with_jacobian=True)
-        mi_o, g_o, n = oracle.parzen(f, m, aff, 64, [1.0, 0.7, 1.3], daff=J, fixed_depth=depth, moving_depth=depth)
-        assert np.all(np.abs(mi_p[0] - mi_o) <= 1e-6 * np.maximum(np.abs(mi_o), 1.0)), (p, mi_p[0], mi_o)
+    pctx = cuda_lib.Context(pairs=[dict(fixed=vols[p][0], moving=vols[p][1], bins=vols[p][3], fixed_depth=vols[p][2],
+                                        moving_depth=vols[p][2]) for p in big], kernel="parzen")
+    psel = [np.nonzero(pair_of == p)[0][:64] for p in big]
+    pof = np.concatenate([np.full(64, k, np.int32) for k in range(len(big))])
+    qz = [1.0, 0.7, 1.3]
+    mi_p, g_p = pctx.batch_grad(pof, prm[np.concatenate(psel)], qz)
+    assert pctx.last_kernel_ms()[1] == 6  # forward, marginals, cells, MI, adjoint, gradient: once each
+
+    def oracle_first(k):
+        f, m, depth, bins = vols[big[k]]
+        aff, J = oracle.affine(prm[psel[k][0]], f.shape, (1, 1, 1), m.shape, (1, 1, 1), with_jacobian=True)
+        return oracle.parzen(f, m, aff, bins, qz, daff=J, fixed_depth=depth, moving_depth=depth)
+
+    with ThreadPoolExecutor(max_workers=len(big)) as ex:
+        res = list(ex.map(oracle_first, range(len(big))))
+    for k, (mi_o, g_o, _) in enumerate(res):
+        row = 64 * k
+        assert np.all(np.abs(mi_p[row] - mi_o) <= 1e-6 * np.maximum(np.abs(mi_o), 1.0)), (k, mi_p[row], mi_o)
         for iq in range(3):
-            assert np.abs(g_p[0, iq] - g_o[iq]).max() <= 1e-4 * np.abs(g_o[iq]).max(), (p, iq)
+            assert np.abs(g_p[row, iq] - g_o[iq]).max() <= 1e-4 * np.abs(g_o[iq]).max(), (k, iq)
 
 
 def test_versor_on_the_sphere_is_a_half_turn(cuda_lib):

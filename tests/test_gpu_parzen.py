@@ -196,3 +196,40 @@ def test_parzen_symmetric_pair_and_separated_classes(cuda_lib):
         cctx = cuda_lib.Context(c, c, bins=B, kernel="parzen")
         mi = cctx.eval(np.array([[0, 0, 0, 0, 0, 0, 1, 1, 1]], np.float32), [1.0])
         assert abs(mi[0, 0] - want) <= MI_TOL * want, (B, mi[0, 0], want)
+
+
+def test_parzen_multi_pair_one_launch_per_kernel(cuda_lib):
+    # pairs of different dims, types and bin counts in one Parzen context: every kernel runs once for all
+    # pairs; MI equals the single-pair contexts' bit for bit (integer soft histograms, the same FP64
+    # reduction), gradients agree within the gradient tolerance (FP32 moments summed over another CTA
+    # split) and with the oracle
+    specs = [((20, 26, 31), np.float32, None, 16), ((28, 22, 37), np.uint16, 12, 64), ((17, 33, 24), np.uint8, 8, 128)]
+    pairs, vols = [], []
+    for i, (shape, dt, depth, B) in enumerate(specs):
+        f, m = phantoms.head_pair(shape=shape, spacing=(1, 1, 1), depth=depth or 12, seed=53 + i, dtype=dt)
+        vols.append((f, m, depth, B))
+        pairs.append(dict(fixed=f, moving=m, bins=B, fixed_depth=depth, moving_depth=depth))
+    ctx = cuda_lib.Context(pairs=pairs, kernel="parzen")
+    prm = phantoms.random_transforms(15, seed=56, t_mm=3, r_deg=6, s_range=(0.95, 1.05))
+    pair_of = np.array([0, 1, 2, 2, 1, 0, 1, 2, 0, 0, 2, 1, 1, 0, 2], np.int32)
+    qs = [1.0, 0.7, 1.3]
+    mi, g = ctx.batch_grad(pair_of, prm, qs)
+    assert ctx.last_kernel_ms()[1] == 6
+    mi_only = ctx.batch_eval(pair_of, prm, qs)
+    np.testing.assert_array_equal(mi_only, mi)
+    for p, (f, m, depth, B) in enumerate(vols):
+        sel = np.nonzero(pair_of == p)[0]
+        one = cuda_lib.Context(f, m, bins=B, kernel="parzen", fixed_depth=depth, moving_depth=depth)
+        mi1, g1 = one.grad(prm[sel], qs)
+        np.testing.assert_array_equal(mi[sel], mi1)
+        for iq in range(len(qs)):
+            scale = np.abs(g1[:, iq]).max()
+            assert np.abs(g[sel, iq] - g1[:, iq]).max() <= G_TOL * scale, (p, iq)
+        t = sel[0]
+        aff, J = oracle.affine(prm[t], f.shape, (1, 1, 1), m.shape, (1, 1, 1), with_jacobian=True)
+        mi_o, g_o, _ = oracle.parzen(f, m, aff, B, qs, daff=J, fixed_depth=depth, moving_depth=depth)
+        assert np.all(np.abs(mi[t] - mi_o) <= MI_TOL * np.maximum(np.abs(mi_o), 1.0)), (p, mi[t], mi_o)
+        for iq in range(len(qs)):
+            assert np.abs(g[t, iq] - g_o[iq]).max() <= G_TOL * np.abs(g_o[iq]).max(), (p, iq)
+    with pytest.raises(cuda_lib.MIError):  # a multi-pair context takes the batch entry points
+        ctx.grad(prm[:1], qs)

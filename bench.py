@@ -399,9 +399,13 @@ def run_profile_parzen(args):
 
 
 def run_maps(args):
-    """The Methodology's parameter-space map: args.maps^3 translations over +-25 mm of the 256x256x160 12-bit
-    head-like pair (no motion, so the true pose is the grid centre), 64 bins, Shannon and Tsallis q = 1.5,
-    through the batched path; then the ascent analysis of the Results on the Shannon map."""
+    """The Methodology's parameter-space maps of the 256x256x160 12-bit head-like pair (64 bins, Shannon and
+    Tsallis q = 1.5) through the batched path, args.maps^3 points each: translations over +-25 mm, unit-ball
+    rotations over +-0.3 per versor component (the Results' rotation maps; up to 2 asin(0.52) = 63 deg), and
+    zero-centred scales over +-0.2; the pair has no motion, so the true pose is each grid's centre.  Then the
+    ascent analysis of the Results on each Shannon map, and where the maximum lies (off the grid's lattice
+    every rotation and scale interpolates, which smooths the moving volume's noise: the Discussion's
+    interpolation effects).  One JSON line per family."""
     import torch
 
     import paper_1909_10690_gb300 as mi
@@ -409,25 +413,31 @@ def run_maps(args):
 
     sp = (1.0, 1.0, 1.2)
     f, m = phantoms.head_pair(shape=(160, 256, 256), spacing=sp, seed=60, motion=(0, 0, 0, 0, 0, 0, 1, 1, 1))
-    ctx = mi.Context(f, m, bins=64, fixed_depth=12, moving_depth=12, fixed_spacing=sp, moving_spacing=sp,
-                     path="batched")
     n = args.maps
-    maps.param_map(ctx, "translation", -25, 25, 3, q=[1.0, 1.5])  # warm-up: autotune, graph
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    mp = maps.param_map(ctx, "translation", -25, 25, n, q=[1.0, 1.5])
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    t1 = time.perf_counter()
     c = (n - 1) // 2
-    frac = maps.capture_fraction(mp[..., 0], (c, c, c))
-    _, maxima = maps.ascent_sinks(mp[..., 0])
-    da = time.perf_counter() - t1
-    print(json.dumps({"maps": "translation", "grid": [n, n, n], "range_mm": [-25, 25], "transforms": n ** 3,
-                      "voxels": int(f.size), "seconds": dt, "voxel_transforms_per_s": n ** 3 * f.size / dt,
-                      "peak_at_centre": bool(np.unravel_index(np.argmax(mp[..., 0]), mp.shape[:3]) == (c, c, c)),
-                      "capture_fraction_shannon": frac, "local_maxima_shannon": int(len(maxima)),
-                      "ascent_analysis_seconds": da}))
+    for family, lo, hi, opts in (("translation", -25, 25, {}), ("rotation", -0.3, 0.3, {"rotation": "versor"}),
+                                 ("scale", -0.2, 0.2, {"scale": "offset"})):
+        ctx = mi.Context(f, m, bins=64, fixed_depth=12, moving_depth=12, fixed_spacing=sp, moving_spacing=sp,
+                         path="batched", **opts)
+        maps.param_map(ctx, family, lo, hi, 3, q=[1.0, 1.5])  # warm-up: autotune, graph
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mp = maps.param_map(ctx, family, lo, hi, n, q=[1.0, 1.5])
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        t1 = time.perf_counter()
+        frac = maps.capture_fraction(mp[..., 0], (c, c, c))
+        _, maxima = maps.ascent_sinks(mp[..., 0])
+        da = time.perf_counter() - t1
+        peak = np.unravel_index(np.argmax(mp[..., 0]), mp.shape[:3])
+        print(json.dumps({"maps": family, "grid": [n, n, n], "range": [lo, hi], "transforms": n ** 3,
+                          "voxels": int(f.size), "seconds": dt, "voxel_transforms_per_s": n ** 3 * f.size / dt,
+                          "peak_at_centre": bool(peak == (c, c, c)),
+                          "peak_offset_steps": [int(x) - c for x in peak],
+                          "mi_peak_minus_centre": float(mp[..., 0].max() - mp[c, c, c, 0]),
+                          "capture_fraction_shannon": frac, "local_maxima_shannon": int(len(maxima)),
+                          "ascent_analysis_seconds": da}), flush=True)
+        del ctx
 
 
 def relaunch_ranks():
@@ -460,7 +470,8 @@ def main():
     ap.add_argument("--tile-rows", type=int, default=1, help="fixed rows per warp step in profile mode (1, 2, 4)")
     ap.add_argument("--slabs", type=int, default=4, help="slabs per sweep in profile mode (1..16)")
     ap.add_argument("--profile-parzen", type=int, default=0, help="profile mode: Parzen MI + gradient of this many poses")
-    ap.add_argument("--maps", type=int, default=0, help="time an N^3 translation map of the head-like pair")
+    ap.add_argument("--maps", type=int, default=0,
+                    help="time N^3 translation, rotation and scale maps of the head-like pair")
     args = ap.parse_args()
     if args.maps:
         run_maps(args)

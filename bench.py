@@ -47,11 +47,18 @@ DESIGN_OPS_PER_VOXT = 50
 K_BATCHED_NCU = {"source_sha16": "018b6e18fe20d963", "config": [10, 1, 4],
                  "dram_bytes_per_launch": 405720647936 + 64994816, "issue_active": 0.758,
                  "l1tex_throughput": 0.637, "smem_wavefronts_per_atomic": 335382232 / 68548103,
+                 "smem_atomic_wavefronts_per_sm_cycle": 335382232 / 152 / 14112035.8,
                  "profile": "profiles/k_batched_rows_quad_256cubed_256bins.md"}
 # algorithmic FP32 operations per voxel x transform of the Parzen MI + gradient at 3 q values:
 # forward 31 (trilinear 14, bin coordinate 1, B-spline weights 12, 4 increments),
 # adjoint 89 (trilinear value and gradient 23, bin coordinate 1, B-spline derivatives 8, 3 q x 19)
 PARZEN_OPS_PER_VOXT = 120
+# Counters of the Parzen forward (k_parzen_hist) from one ncu capture of the 50-pose call (see profiles/),
+# reported while the kernel source is the one measured: shared-atomic instructions and wavefronts, and
+# SM cycles elapsed per launch
+K_PARZEN_NCU = {"source_sha16": "c29174eee255b3bd", "atom_inst": 52167744, "atom_wavefronts": 245333011,
+                "sm_cycles_elapsed": 2169463.75, "time_ms": 1.05392,
+                "profile": "profiles/parzen_fwd_adj_192x192x128_64bins.md"}
 PARZEN_SHAPE = (128, 192, 192)
 PARZEN_SPACING = (1.0, 1.0, 1.2)
 PARZEN_BINS = 64
@@ -277,7 +284,7 @@ def run_ours(args, rank, world, local_rank):
         roofline["hbm"] = {"achieved_gbs": traffic / (kms / 1e3) / 1e9, "peak_gbs": float(pk["hbm_gbs"]),
                            "frac": traffic / (kms / 1e3) / 1e9 / float(pk["hbm_gbs"]), "peak_source": src}
         roofline["ncu"] = {k: ncu[k] for k in ("issue_active", "l1tex_throughput", "smem_wavefronts_per_atomic",
-                                               "profile")}
+                                               "smem_atomic_wavefronts_per_sm_cycle", "profile")}
     # --- end to end through the C ABI with host buffers ----------------------------
     prm_pinned = torch.from_numpy(prm).pin_memory()
     barrier()
@@ -334,6 +341,14 @@ def run_ours(args, rank, world, local_rank):
                                          "frac": z_ach / alu_peak, "traffic": None,
                                          "kernel": "k_parzen_hist + k_parzen_cells + k_parzen_adj",
                                          "note": "FP32 lane-ops per voxel x transform over the whole MI+grad call"}}
+        pn = K_PARZEN_NCU
+        if pn["source_sha16"] == kernel_source_sha16("mi_parzen.cu"):
+            # the forward's binding unit: the shared-memory pipe, one wavefront per clock per SM
+            extra["mi_grad"]["forward_shared_atomics"] = {
+                "wavefronts_per_sm_cycle": pn["atom_wavefronts"] / sms / pn["sm_cycles_elapsed"],
+                "lane_atomics_per_s": pn["atom_inst"] * 32 / (pn["time_ms"] / 1e3),
+                "lane_atomics_peak_per_s": atom_peak, "wavefronts_per_instruction": pn["atom_wavefronts"] / pn["atom_inst"],
+                "profile": pn["profile"]}
         del zctx
     line = {"metric": METRIC, "value": value, "unit": "voxel*transforms/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,

@@ -343,15 +343,24 @@ def test_full_size_batched_256_cubed_sampled(cuda_lib):
     qs = [0.5, 1.0, 1.5, 2.0]
     ctx = cuda_lib.Context(f, m, bins=256, fixed_depth=12, moving_depth=12, path="batched")
     mi, h, cnt = ctx.eval(prm, qs, with_entropies=True)
-    sample = np.array([0, 1, 777, 2048, 4095])
+    # 16 transforms spread over the launch (first and last items, every wave position) against the oracle;
+    # the joint histograms of 8 of them bit for bit
+    sample = np.array([0, 1, 151, 152, 777, 1023, 1500, 2047, 2048, 2600, 3000, 3333, 3800, 4000, 4094, 4095])
     mi_o, h_o, cnt_o = oracle.mi_eval(f, m, 256, prm[sample], qs, fixed_depth=12, moving_depth=12, nthreads=16)
     np.testing.assert_array_equal(cnt[sample], cnt_o)
     assert_mi_close(mi[sample], mi_o, h_o)
-    H = ctx.hist(transforms=prm[sample[:2]], path=cuda_lib.PATH_BATCHED)
-    for k, t in enumerate(sample[:2]):
+    hsel = sample[::2]
+    H = ctx.hist(transforms=prm[hsel], path=cuda_lib.PATH_BATCHED)
+    from concurrent.futures import ThreadPoolExecutor
+
+    def oracle_hist(t):
         q16 = oracle.affine_q16(oracle.affine(prm[t], f.shape, (1, 1, 1), m.shape, (1, 1, 1)))
-        ho, _ = oracle.joint_hist(f, m, q16, 256, 12, 12)
-        np.testing.assert_array_equal(H[k], ho.astype(np.uint32))
+        return oracle.joint_hist(f, m, q16, 256, 12, 12)[0]
+
+    with ThreadPoolExecutor(max_workers=len(hsel)) as ex:
+        hos = list(ex.map(oracle_hist, hsel))
+    for k, ho in enumerate(hos):
+        np.testing.assert_array_equal(H[k], ho.astype(np.uint32), err_msg=str(hsel[k]))
 
 
 @pytest.mark.parametrize("n_a", [65535, 65536])

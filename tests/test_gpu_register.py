@@ -83,3 +83,26 @@ def test_central_differences_equal_the_mean_gradient(cuda_lib, head):
             gsum += gn.reshape(P, chunk, len(qs), 9)[:, :, :, k].sum(1)
         gap = np.abs(fd - gsum / n) / scale
         assert gap.max() <= 1e-4, (k, gap.max())
+
+
+@pytest.mark.parametrize("q, q_t", [(1.0, None), (1.0, 1.5)], ids=["shannon", "mixed_t1.5"])
+def test_kiefer_wolfowitz_recovers_motion_on_the_hard_metric(cuda_lib, q, q_t):
+    """Kiefer-Wolfowitz on the hard-binned MI (Eq. 2; the Introduction's stochastic approximation):
+    each iteration is one batched evaluation of 18 perturbations for each of the 16 poses.
+
+    The fixed volume is a centred crop (same centre, so the same transform) that stays inside the
+    moving volume near the solution.  Over the whole field of view the overlap shrinks as the
+    rotation grows, and with background the largest class plain MI rises as background leaves the
+    overlap: its maximum there sits up to ~5 degrees beyond the true angles."""
+    f, m = phantoms.head_pair(shape=(128, 192, 192), spacing=SP, seed=50)
+    fc = np.ascontiguousarray(f[16:112, 24:168, 24:168])
+    ctx = cuda_lib.Context(fc, m, bins=64, fixed_spacing=SP, moving_spacing=SP, fixed_depth=12, moving_depth=12)
+    truth = np.array(phantoms.HEAD_MOTION)
+    rng = np.random.default_rng(8)
+    n = 16
+    d = np.concatenate([rng.uniform(-8, 8, (n, 3)), rng.uniform(-10, 10, (n, 3)), rng.uniform(-0.08, 0.08, (n, 3))], 1)
+    theta, hist = register.register_kw(ctx, truth[None] + d, q=q, q_translation=q_t, steps=200)
+    et, er, es = register.pose_error(theta, truth)
+    ok = (et < 0.5) & (er < 0.75) & (es < 0.005)  # measured: 0.19 mm, 0.39 deg, 0.0022
+    assert ok.all(), (et, er, es)
+    assert np.all(hist[-1] > hist[0])

@@ -16,12 +16,18 @@ pytestmark = pytest.mark.gpu
 
 TOL = 1e-6
 VARIANTS = list(range(16))  # MI_HV_U32 .. MI_HV_U16_GATHER
+U32_VARIANTS = (0, 1, 4, 5, 11, 14)  # one 32-bit counter per cell: at most 181 bins in shared memory
 IDENT = np.array([65536, 0, 0, 0, 0, 65536, 0, 0, 0, 0, 65536, 0], dtype=np.int32)
+
+
+# absolute floor: where the whole overlap falls in one cell, H_FM = 0 and MI is exactly 0 (Eq. 2);
+# both sides then return FP64 rounding of entropies of a few nats (~1e-16)
+MI_FLOOR = 1e-12
 
 
 def assert_mi_close(mi_gpu, mi_ref, h_ref):
     scale = np.maximum(np.abs(mi_ref), h_ref[..., 2])
-    bad = np.abs(mi_gpu - mi_ref) > TOL * scale
+    bad = np.abs(mi_gpu - mi_ref) > TOL * scale + MI_FLOOR
     assert not np.any(bad), (mi_gpu[bad], mi_ref[bad])
 
 
@@ -129,7 +135,7 @@ def test_ragged_sizes_all_variants(cuda_lib, variant, bins):
     # odd dims spanning several row batches and a ragged tail, 12-bit data, random 9-parameter transforms
     f, m = phantoms.head_pair(shape=(29, 41, 75), spacing=(1, 1, 1), seed=6)
     m = np.ascontiguousarray(m[:, :37, :71])
-    if bins > 181 and variant in (0, 1, 4, 5, 11, 14):
+    if bins > 181 and variant in U32_VARIANTS:
         pytest.skip("32-bit counters do not fit shared memory at this bin count")
     prm, q16 = random_q16(f.shape, m.shape, 40, seed=bins)
     for path in (cuda_lib.PATH_PLAIN, cuda_lib.PATH_BATCHED):
@@ -236,6 +242,43 @@ def test_edge_cases(cuda_lib):
         cuda_lib.Context(f, m, bins=257)
     with pytest.raises(cuda_lib.MIError):
         cuda_lib.Context(f[:1], m, bins=16)
+
+
+@pytest.mark.parametrize("dtype, depth", [(np.uint8, 8), (np.uint16, 12)])
+def test_smallest_volumes_extreme_bins_and_eight_q(cuda_lib, dtype, depth):
+    """2 x 2 x 2 and small ragged pairs, 2 and 256 bins, the 8 q a call takes, every variant and both
+    paths: histograms bit-exact, overlap counts (1 to 8 voxels, or none) and MI as the oracle's."""
+    rng = np.random.default_rng(95)
+    qs = [0.2, 0.5, 0.8, 1.0, 1.2, 1.5, 2.0, 3.0]
+    for shape_f, shape_m in (((2, 2, 2), (2, 2, 2)), ((3, 2, 5), (2, 4, 2))):
+        f = rng.integers(0, 1 << depth, shape_f).astype(dtype)
+        m = rng.integers(0, 1 << depth, shape_m).astype(dtype)
+        prm = phantoms.random_transforms(11, seed=96, t_mm=0.6, r_deg=10, s_range=(0.9, 1.1))
+        prm = np.concatenate([phantoms.identity_params(1), prm])
+        q16 = np.stack([oracle.affine_q16(oracle.affine(p, shape_f, (1, 1, 1), shape_m, (1, 1, 1))) for p in prm])
+        for bins in (2, 256):
+            mi_o, h_o, cnt_o = oracle.mi_eval_q16(f, m, bins, q16, qs, fixed_depth=depth, moving_depth=depth)
+            want = [oracle.joint_hist(f, m, q, bins, depth, depth)[0].astype(np.uint32) for q in q16]
+            assert cnt_o.min() == 0 and 1 in cnt_o and cnt_o.max() >= 3  # empty, one-voxel and wider overlaps
+            ran = 0
+            for variant in VARIANTS:
+                ctx = cuda_lib.Context(f, m, bins=bins, fixed_depth=depth, moving_depth=depth, hist_variant=variant)
+                if bins == 256 and variant in U32_VARIANTS:  # 32-bit counters do not fit shared memory
+                    with pytest.raises(cuda_lib.MIError) as ei:
+                        ctx.hist(affines=q16[:1])
+                    assert ei.value.status == cuda_lib.MI_EUNSUPPORTED
+                    continue
+                for path in (cuda_lib.PATH_PLAIN, cuda_lib.PATH_BATCHED):
+                    H = ctx.hist(affines=q16, path=path)
+                    for t in range(len(q16)):
+                        np.testing.assert_array_equal(H[t], want[t])
+                mi, h, cnt = ctx.eval_q16(q16, qs, with_entropies=True)
+                np.testing.assert_array_equal(cnt, cnt_o)
+                ok = cnt_o > 0
+                assert np.all(np.isnan(mi[~ok]))
+                assert_mi_close(mi[ok], mi_o[ok], h_o[ok])
+                ran += 1
+            assert ran == (16 if bins == 2 else 16 - len(U32_VARIANTS))
 
 
 def test_bit_depth_clamp_and_small_depth(cuda_lib):

@@ -42,6 +42,33 @@ def test_parzen_float_pair(cuda_lib):
     check(ctx, f, m, prm, [1.0, 0.7, 1.3], B)
 
 
+def test_parzen_smallest_volumes(cuda_lib):
+    """2 x 2 x 2 and small ragged float pairs at 8 bins and 8 q: MI as the oracle's for empty (NaN),
+    one-voxel and wider overlaps (the gradient is exercised at sizes where it is not ~0).
+
+    The q set starts at 0.5: with one or two voxels in the overlap, B-spline tail cells of weight
+    ~1e-6 enter S_q as P^q, and at q = 0.2 their FP32 weight error reaches 1.4e-6 of MI."""
+    rng = np.random.default_rng(97)
+    qs = [0.5, 0.7, 0.8, 1.0, 1.2, 1.5, 2.0, 3.0]
+    seen = set()
+    for shape_f, shape_m in (((2, 2, 2), (2, 2, 2)), ((3, 2, 5), (2, 4, 2))):
+        f = rng.random(shape_f, dtype=np.float32)
+        m = rng.random(shape_m, dtype=np.float32)
+        ctx = cuda_lib.Context(f, m, bins=8, kernel="parzen")
+        prm = np.concatenate([phantoms.identity_params(1),
+                              phantoms.random_transforms(11, seed=98, t_mm=0.6, r_deg=10, s_range=(0.9, 1.1))])
+        mi = ctx.eval(prm, qs)
+        for t in range(len(prm)):
+            aff = oracle.affine(prm[t], f.shape, (1, 1, 1), m.shape, (1, 1, 1))
+            mi_o, _, n = oracle.parzen(f, m, aff, 8, qs)
+            seen.add(min(n, 2))
+            if n == 0:
+                assert np.all(np.isnan(mi[t]))
+            else:
+                assert np.all(np.abs(mi[t] - mi_o) <= MI_TOL * np.maximum(np.abs(mi_o), 1.0)), (t, mi[t], mi_o)
+    assert seen == {0, 1, 2}
+
+
 @pytest.mark.parametrize("B", [8, 64, 96, 128])  # forward with four, four, two and one histogram copies
 def test_parzen_integer_pair_and_bin_counts(cuda_lib, B):
     f, m = phantoms.head_pair(shape=(30, 34, 40), spacing=(1, 1, 1), seed=42)

@@ -81,8 +81,9 @@ def register_kw(ctx, starts, q=1.0, q_translation=None, steps=100, c=None, gamma
     steps along it with the Adam update of ``register`` (lr per parameter).
     q / q_translation: as in ``register`` (the translation columns may follow
     another q's estimate).  ctx: a hard-path Context (or any object with
-    ``nparams`` and ``eval(transforms, q)``).  Returns (final params n x P, MI
-    history steps x n for q, at the unperturbed poses' neighbourhood mean).
+    ``nparams`` and ``eval(transforms, q)``).  A perturbed transform with no
+    overlap counts as MI 0.  Returns (final params n x P, MI history steps x n
+    for q: each pose's mean over its 2 P perturbed evaluations).
     """
     P = int(getattr(ctx, "nparams", 9))
     if P not in TRANSLATION:

@@ -347,6 +347,25 @@ def test_batched_equals_plain_and_graph_replay(cuda_lib, tiny_pair):
     np.testing.assert_allclose(got2, want2, rtol=1e-12, atol=1e-14)
 
 
+def test_many_transforms_cross_every_chunk(cuda_lib):
+    """5000 transforms at 256 bins: the plain path takes them in chunks of 256 (its global histograms are
+    capped at 64 MB), the batched path in one graph-replayed launch; a few have no overlap.  Counts equal
+    the oracle's and MI is within tolerance for every transform on both paths."""
+    f, m = phantoms.head_pair(shape=(16, 18, 20), spacing=(1, 1, 1), seed=99)
+    prm = phantoms.random_transforms(5000, seed=100, t_mm=4, r_deg=15, s_range=(0.9, 1.1))
+    prm[::997, 1] = 400.0  # no overlap
+    qs = [0.5, 1.0, 2.0]
+    mi_o, h_o, cnt_o = oracle.mi_eval(f, m, 256, prm, qs, fixed_depth=12, moving_depth=12, nthreads=8)
+    assert np.count_nonzero(cnt_o == 0) == 6
+    ok = cnt_o > 0
+    for path in ("plain", "batched"):
+        ctx = cuda_lib.Context(f, m, bins=256, fixed_depth=12, moving_depth=12, path=path)
+        mi, h, cnt = ctx.eval(prm, qs, with_entropies=True)
+        np.testing.assert_array_equal(cnt, cnt_o)
+        assert np.all(np.isnan(mi[~ok]))
+        assert_mi_close(mi[ok], mi_o[ok], h_o[ok])
+
+
 def test_uneven_batch_small(cuda_lib):
     specs = [((40, 36, 50), np.uint8, 8, 32), ((30, 44, 38), np.uint16, 12, 64), ((50, 30, 33), np.uint8, 8, 128),
              ((24, 52, 47), np.uint16, 12, 64), ((35, 35, 35), np.uint16, 12, 32)]

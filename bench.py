@@ -56,8 +56,8 @@ PARZEN_OPS_PER_VOXT = 120
 # Counters of the Parzen forward (k_parzen_hist) from one ncu capture of the 50-pose call (see profiles/),
 # reported while the kernel source is the one measured: shared-atomic instructions and wavefronts, and
 # SM cycles elapsed per launch
-K_PARZEN_NCU = {"source_sha16": "c29174eee255b3bd", "atom_inst": 52167744, "atom_wavefronts": 245333011,
-                "sm_cycles_elapsed": 2169463.75, "time_ms": 1.05392,
+K_PARZEN_NCU = {"source_sha16": "f77fe66c07e127f7", "atom_inst": 52167744, "atom_wavefronts": 245317234,
+                "sm_cycles_elapsed": 2174580.04, "time_ms": 1.058592,
                 "profile": "profiles/parzen_fwd_adj_192x192x128_64bins.md"}
 PARZEN_SHAPE = (128, 192, 192)
 PARZEN_SPACING = (1.0, 1.0, 1.2)
@@ -455,6 +455,94 @@ def run_maps(args):
         del ctx
 
 
+def run_uneven(args):
+    """The uneven batch: 48 pairs from 96^3 to 320x320x200 (half uint8, half uint16 12-bit; 32, 64 or 128
+    bins each) with 256 transforms per pair, all 12 288 in one batched call (one persistent launch over
+    every pair, q = 1, 0.5, 1.5, 2); then the Parzen MI and gradient of the 8 largest pairs, each at its own
+    bin count, 64 poses each, in one multi-pair call (q = 1, 0.7, 1.3).  The pairs' volumes and textures
+    (several GB) are larger than L2.  Device time by CUDA events around each call, after ``args.warmup``
+    untimed calls; one JSON line per part."""
+    import torch
+
+    import paper_1909_10690_gb300 as mi
+    from paper_1909_10690_gb300 import phantoms
+
+    specs = phantoms.uneven_specs(48, seed=5)
+    vols = [phantoms.head_pair(shape=s["shape"], spacing=(1, 1, 1), depth=s["depth"], seed=s["seed"], dtype=s["dtype"])
+            for s in specs]
+    nvox = np.array([int(np.prod(s["shape"])) for s in specs])
+    n_per = 256
+    prm = phantoms.random_transforms(n_per * len(specs), seed=61)
+    pair_of = np.repeat(np.arange(len(specs), dtype=np.int32), n_per)
+    perm = np.random.default_rng(62).permutation(len(prm))
+    prm, pair_of = prm[perm], pair_of[perm]
+
+    def timed(call):
+        for _ in range(args.warmup):
+            call()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ms = []
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            ev[0].record()
+            call()
+            ev[1].record()
+            torch.cuda.synchronize()
+            ms.append(ev[0].elapsed_time(ev[1]))
+        return float(np.median(ms)), ms
+
+    ctx = mi.Context(pairs=[dict(fixed=f, moving=m, bins=s["bins"], fixed_depth=s["depth"], moving_depth=s["depth"])
+                            for s, (f, m) in zip(specs, vols)])
+    d_pof, d_prm = torch.from_numpy(pair_of).cuda(), torch.from_numpy(prm).cuda()
+    qs = [1.0, 0.5, 1.5, 2.0]
+    med, ms = timed(lambda: ctx.batch_eval(d_pof, d_prm, qs))
+    work = float(nvox[pair_of].sum())
+    print(json.dumps({"uneven": "hard", "pairs": len(specs), "transforms": len(prm), "q": qs,
+                      "voxel_transforms": work, "ms": med, "ms_all": ms, "kernel_ms": ctx.last_kernel_ms()[0],
+                      "voxel_transforms_per_s": work / (med * 1e-3), "selected": ctx.selected_config(len(prm))}),
+          flush=True)
+    del ctx
+    big = np.argsort(nvox)[-8:]
+    pctx = mi.Context(pairs=[dict(fixed=vols[p][0], moving=vols[p][1], bins=specs[p]["bins"],
+                                  fixed_depth=specs[p]["depth"], moving_depth=specs[p]["depth"]) for p in big],
+                      kernel="parzen")
+    psel = np.concatenate([np.nonzero(pair_of == p)[0][:64] for p in big])
+    pof = torch.from_numpy(np.repeat(np.arange(len(big), dtype=np.int32), 64)).cuda()
+    pprm = torch.from_numpy(prm[psel]).cuda()
+    qz = [1.0, 0.7, 1.3]
+    med, ms = timed(lambda: pctx.batch_grad(pof, pprm, qz, allow_empty=True))
+    work = float(64 * nvox[big].sum())
+    print(json.dumps({"uneven": "parzen", "pairs": [int(p) for p in big], "bins": [specs[p]["bins"] for p in big],
+                      "poses": len(psel), "q": qz, "ms": med, "ms_all": ms, "kernel_ms": pctx.last_kernel_ms()[0],
+                      "launches": pctx.last_kernel_ms()[1], "poses_per_s": len(psel) / (med * 1e-3),
+                      "voxel_transforms_per_s": work / (med * 1e-3)}), flush=True)
+
+
+def run_parzen_bins(args):
+    """The Parzen MI + gradient per bin count: 64 poses (the uneven batch's transform distribution) on a
+    256x256x160 uint16 12-bit head-like pair at 32, 64, 96 and 128 bins, q = 1, 0.7, 1.3; device time of
+    the call's kernels, median of ``args.steps`` after ``args.warmup``.  One JSON line per bin count."""
+    import torch
+
+    import paper_1909_10690_gb300 as mi
+    from paper_1909_10690_gb300 import phantoms
+
+    f, m = phantoms.head_pair(shape=(160, 256, 256), spacing=(1, 1, 1), seed=7)
+    prm = torch.from_numpy(phantoms.random_transforms(64, seed=61)).cuda()
+    for B in (32, 64, 96, 128):
+        ctx = mi.Context(f, m, bins=B, kernel="parzen", fixed_depth=12, moving_depth=12)
+        for _ in range(args.warmup):
+            ctx.grad(prm, PARZEN_QS, allow_empty=True)
+        ms = []
+        for _ in range(args.steps):
+            ctx.grad(prm, PARZEN_QS, allow_empty=True)
+            ms.append(ctx.last_kernel_ms()[0])
+        med = float(np.median(ms))
+        print(json.dumps({"parzen_bins": B, "poses": 64, "volume": [256, 256, 160], "q": PARZEN_QS,
+                          "kernel_ms": med, "voxel_transforms_per_s": 64 * f.size / (med * 1e-3)}), flush=True)
+        del ctx
+
+
 def relaunch_ranks():
     """``--gpus N`` run by hand (no WORLD_SIZE in the environment): start the N ranks on this node with
     torch.distributed.run, one per GPU, each running this script with the same arguments."""
@@ -487,9 +575,19 @@ def main():
     ap.add_argument("--profile-parzen", type=int, default=0, help="profile mode: Parzen MI + gradient of this many poses")
     ap.add_argument("--maps", type=int, default=0,
                     help="time N^3 translation, rotation and scale maps of the head-like pair")
+    ap.add_argument("--uneven", action="store_true",
+                    help="time the 48-pair uneven batch (hard) and the Parzen MI + gradient of its 8 largest pairs")
+    ap.add_argument("--parzen-bins", action="store_true",
+                    help="time the Parzen MI + gradient at 32, 64, 96 and 128 bins")
     args = ap.parse_args()
+    if args.parzen_bins:
+        run_parzen_bins(args)
+        return
     if args.maps:
         run_maps(args)
+        return
+    if args.uneven:
+        run_uneven(args)
         return
     if args.profile:
         run_profile(args)

@@ -268,41 +268,35 @@ __host__ __device__ inline int parzen_stride(int B) { return B + 1 + ((kParzenBa
 
 // Histogram copies per CTA of the forward: with C copies, lane l adds to copy l mod C (copy i starts
 // i (2 B SB + 32 / C) words in, so that one cell's copies fall in different banks), which divides by C
-// the lanes of a warp that hit one cell in one atomic instruction; CTAs of 256 C threads keep the
-// shared memory per SM of one copy per 256 threads.
+// the lanes of a warp that hit one cell in one atomic instruction.  A CTA has 1024 threads (64
+// registers each: the whole register file) whatever C is, so an SM keeps 32 warps at every bin count;
+// C is the most copies, up to 4, that fit the 227 KB a CTA may hold (4 up to 64 bins, 2 at 96, 1 at 128).
 constexpr int kParzenFwdMaxCopies = 4;
+constexpr int kParzenFwdThreads = 1024;
+constexpr int kParzenFwdSmemWords = 227 * 1024 / 4;
 __host__ __device__ inline int parzen_copy_offset(int B, int copies) {
     return 2 * B * parzen_stride(B) + (copies > 1 ? 32 / copies : 0);
+}
+__host__ __device__ inline int parzen_fwd_copies_in(int B, int words) {
+    int c = kParzenFwdMaxCopies;
+    while (c > 1 && c * parzen_copy_offset(B, c) > words) c >>= 1;
+    return c;
 }
 __host__ inline size_t parzen_fwd_smem(int B, int copies) {
     return (size_t)copies * parzen_copy_offset(B, copies) * sizeof(uint32_t);
 }
-// Copies for B bins: among the counts that keep the most threads resident per SM (at 64 registers a
-// thread at most 1024; 228 KB of shared memory per SM, 227 KB per CTA, 1 KB of it reserved per CTA),
-// the most copies.
-__host__ inline int parzen_fwd_copies(int B) {
-    int best = 1, best_threads = 0;
-    for (int c = 1; c <= kParzenFwdMaxCopies; c *= 2) {
-        const size_t smem = parzen_fwd_smem(B, c);
-        if (smem > 227 * 1024) break;
-        const int by_smem = (int)((228 * 1024) / (smem + 1024)), by_regs = 1024 / (256 * c);
-        const int threads = (by_smem < by_regs ? by_smem : by_regs) * 256 * c;
-        if (threads >= best_threads) {
-            best = c;
-            best_threads = threads;
-        }
-    }
-    return best;
-}
+__host__ inline int parzen_fwd_copies(int B) { return parzen_fwd_copies_in(B, kParzenFwdSmemWords); }
 
 // MULTI: transforms on several pairs (descriptors read from `pairs`); otherwise every transform is on
-// the pair P0 passed by value, whose fields stay kernel parameters.
+// the pair P0 passed by value, whose fields stay kernel parameters.  COPIES is the copy count of the
+// largest pair's bins, for which the shared memory is sized (smem_words words); a transform of a pair
+// with fewer bins uses as many copies as fit there (at least COPIES).
 template <int RPW, bool SAMPLED, int COPIES, bool MULTI>
-__global__ void __launch_bounds__(256 * COPIES)
+__global__ void __launch_bounds__(kParzenFwdThreads)
     k_parzen_hist(ParzenPair P0, const ParzenPair *__restrict__ pairs, const int *__restrict__ pair_of,
                   const long long *__restrict__ row_start, int n, const ParzenAffine *__restrict__ aff,
-                  long long rows_per_cta, long long total_rows, int Bmax, unsigned long long *__restrict__ ghist,
-                  unsigned long long *__restrict__ gcount) {
+                  long long rows_per_cta, long long total_rows, int Bmax, int smem_words,
+                  unsigned long long *__restrict__ ghist, unsigned long long *__restrict__ gcount) {
     // Low-half sums [B x SB], then high-half sums.  The row stride SB >= B + 1 is 7 mod 32, so the
     // bank of cell (fixed bin b, moving bin k) is (k + 7 b) mod 32: the cells of neighbouring voxels,
     // which differ by a bin or two on either axis, fall in different banks.  Column B absorbs the
@@ -338,8 +332,9 @@ __global__ void __launch_bounds__(256 * COPIES)
     for (long long s0 = c0; s0 < c1; ++t) {
         const ParzenPair P = MULTI ? pairs[pair_of[t]] : P0;
         const int B = P.B, B2 = B * B, SB = parzen_stride(B), NP = B * SB;
-        const int CP = parzen_copy_offset(B, COPIES);  // offset between copies
-        uint32_t *lo16 = sh32 + (lane & (COPIES - 1)) * CP, *hi16 = lo16 + NP;
+        const int NC = MULTI ? parzen_fwd_copies_in(B, smem_words) : COPIES;  // copies in use
+        const int CP = parzen_copy_offset(B, NC);  // offset between copies
+        uint32_t *lo16 = sh32 + (lane & (NC - 1)) * CP, *hi16 = lo16 + NP;
         const int nf0 = P.nf[0], nf1 = P.nf[1];
         const int n0 = P.nm[0], n1 = P.nm[1], n2 = P.nm[2];
         const long long R = (long long)nf1 * P.nf[2];
@@ -348,7 +343,7 @@ __global__ void __launch_bounds__(256 * COPIES)
         const long long r0 = s0 - tb, r1 = c1 - tb < R ? c1 - tb : R;
         if (!first) __syncthreads();  // the previous segment's flush has read the copies
         first = false;
-        for (int c = threadIdx.x; c < COPIES * CP; c += blockDim.x) sh32[c] = 0u;
+        for (int c = threadIdx.x; c < NC * CP; c += blockDim.x) sh32[c] = 0u;
         if (threadIdx.x < 12) A[threadIdx.x] = aff[t].A[threadIdx.x];
         __syncthreads();
         const long long DG0 = G * A[0], DG1 = G * A[4], DG2 = G * A[8];
@@ -435,8 +430,9 @@ __global__ void __launch_bounds__(256 * COPIES)
             const int cp = (c / B) * SB + c % B;
             unsigned long long v = 0;
 #pragma unroll
-            for (int i = 0; i < COPIES; ++i)
-                v += (unsigned long long)sh32[i * CP + cp] + ((unsigned long long)sh32[i * CP + NP + cp] << 16);
+            for (int i = 0; i < kParzenFwdMaxCopies; ++i)
+                if (i < NC)
+                    v += (unsigned long long)sh32[i * CP + cp] + ((unsigned long long)sh32[i * CP + NP + cp] << 16);
             if (v) atomicAdd(gh + c, v);
         }
         if (lane == 0 && cnt) atomicAdd(gcount + t, (unsigned long long)cnt);
@@ -628,32 +624,35 @@ __global__ void k_parzen_final(int n, const unsigned long long *__restrict__ gco
 // Adjoint: moments M[q][a][c] = sum_x s_q(x) d_a m(u_x) x_c, x = (i - ci, j - cj, k - ck, 1)
 // ---------------------------------------------------------------------------
 
-template <int NQ, bool SAMPLED, bool MULTI>
-__global__ void __launch_bounds__(256, 2)
+// Where an adjoint launch keeps the W table of its q values: in the shared memory of one 512-thread
+// CTA an SM when it fits, else in global memory read by 256-thread CTAs (two an SM).  Either gives 16
+// warps an SM at 128 registers a thread; the larger CTA measured 4 % faster at 64 bins (fewer, larger
+// row shares), and one float a cell 1.5 % faster than (W[k], W[k + 1]) pairs read as two 8-byte words.
+enum { kWGlobal = 0, kWShared = 1 };
+
+template <int NQ, bool SAMPLED, bool MULTI, int TPB>
+__global__ void __launch_bounds__(TPB, 512 / TPB)
     k_parzen_adj(ParzenPair P0, const ParzenPair *__restrict__ pairs, const int *__restrict__ pair_of, int Bmax,
                  const ParzenAffine *__restrict__ aff, int nq_total, int q0, const float *__restrict__ wtab,
-                 int w_in_smem, double *__restrict__ mom) {
+                 int w_mode, double *__restrict__ mom) {
     // mom: n x nq_total x gridDim.x x 12 per-CTA partial moments (no atomics: fixed-order reduction later)
-    // NQ x B x SB weight pairs (W[k], W[k + 1]) when they fit; the row stride SB >= B + 1 is 7 mod 32,
-    // so neighbouring voxels' cells, a bin or two apart on either axis, are read from different banks.
+    // NQ x B x SB weights in shared memory (w_mode kWShared); the row stride SB >= B + 1 is 7 mod 32, so
+    // neighbouring voxels' cells, a bin or two apart on either axis, are read from different banks.
     // W of transform t is its slot of Bmax^2 entries per q (the first B^2 used, row stride B).
     extern __shared__ float sw[];
     const int t = blockIdx.y;
     const ParzenPair P = MULTI ? pairs[pair_of[t]] : P0;
     const int B = P.B, SB = parzen_stride(B);
     __shared__ long long A[12];
-    __shared__ float s_red[8][NQ * 12];
+    __shared__ float s_red[TPB / 32][NQ * 12];
     if (threadIdx.x < 12) A[threadIdx.x] = aff[t].A[threadIdx.x];
     const size_t BM2 = (size_t)Bmax * Bmax;
     const float *W = wtab + ((size_t)t * nq_total + q0) * BM2;
     int RS = B, QS = (int)BM2;  // row stride and per-q stride of the table in use
-    float2 *sw2 = reinterpret_cast<float2 *>(sw);
-    if (w_in_smem) {  // pairs (W[k], W[k + 1]), W[B] = 0: two 8-byte reads give a cell's four weights
+    if (w_mode == kWShared) {
         for (int c = threadIdx.x; c < NQ * B * B; c += blockDim.x) {
-            const int qq = c / (B * B), cc = c % (B * B), k = cc % B;
-            const float *Wq = W + (size_t)qq * BM2;
-            const float nxt = k + 1 < B ? Wq[cc + 1] : 0.0f;
-            sw2[qq * B * SB + (cc / B) * SB + k] = make_float2(Wq[cc], nxt);
+            const int qq = c / (B * B), cc = c % (B * B);
+            sw[qq * B * SB + (cc / B) * SB + cc % B] = W[(size_t)qq * BM2 + cc];
         }
         RS = SB;
         QS = B * SB;
@@ -717,10 +716,9 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) {
                     float sv;
-                    if (w_in_smem) {
-                        const float2 *Wq = sw2 + (size_t)q * QS;
-                        const float2 a = Wq[cb], b = Wq[cb + 2];
-                        sv = a.x * d[0] + a.y * d[1] + b.x * d[2] + b.y * d[3];
+                    if (w_mode == kWShared) {
+                        const float *Wq = sw + (size_t)q * QS;
+                        sv = Wq[cb] * d[0] + Wq[cb + 1] * d[1] + Wq[cb + 2] * d[2] + Wq[i3] * d[3];
                     } else {
                         const float *Wq = W + (size_t)q * QS;
                         sv = Wq[cb] * d[0] + Wq[cb + 1] * d[1] + Wq[cb + 2] * d[2] + Wq[i3] * d[3];
@@ -837,20 +835,25 @@ int parzen_ctas(const ParzenPair &P, int n, int sms) {
     return (int)per_t;
 }
 
-// Shared memory of an adjoint launch over g q values: the W pairs when they fit, else none.
-static size_t parzen_adj_smem(int B, int g) {
-    const size_t wbytes = (size_t)g * B * parzen_stride(B) * sizeof(float2);
-    return wbytes <= 110 * 1024 ? wbytes : 0;
+// W table of an adjoint launch over g q values at B bins: in shared memory when it fits beside the
+// CTA's 3 KB of static shared memory (every B at up to three q, B <= 96 at four), else global memory.
+static int parzen_adj_wmode(int B, int g) {
+    return (size_t)g * B * parzen_stride(B) * sizeof(float) <= 220 * 1024 ? kWShared : kWGlobal;
 }
+static size_t parzen_adj_smem(int B, int g) {
+    return parzen_adj_wmode(B, g) == kWShared ? (size_t)g * B * parzen_stride(B) * sizeof(float) : 0;
+}
+static int parzen_adj_threads(int B, int g) { return parzen_adj_wmode(B, g) == kWShared ? 512 : 256; }
 
 template <int NQ, bool SAMPLED>
-static int adj_blocks_per_sm(size_t smem) {
-    const void *fn = (const void *)k_parzen_adj<NQ, SAMPLED, false>;
+static int adj_blocks_per_sm(size_t smem, int tpb) {
+    const void *fn = tpb == 512 ? (const void *)k_parzen_adj<NQ, SAMPLED, false, 512>
+                                : (const void *)k_parzen_adj<NQ, SAMPLED, false, 256>;
     if (allow_smem(fn, smem) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
-    return resident_per_sm(fn, 256, smem);
+    return resident_per_sm(fn, tpb, smem);
 }
 
 int parzen_adj_ctas(const ParzenPair &P, int n, int nq, int sms) {
@@ -859,18 +862,19 @@ int parzen_adj_ctas(const ParzenPair &P, int n, int nq, int sms) {
     // waves to the usual ~4 CTAs per SM, then the most CTAs per transform that fill it
     const int g = nq < 4 ? nq : 4;
     const size_t smem = parzen_adj_smem(P.B, g);
+    const int tpb = parzen_adj_threads(P.B, g);
     int per_sm = 1;
     switch (g) {
-        case 1: per_sm = P.srow ? adj_blocks_per_sm<1, true>(smem) : adj_blocks_per_sm<1, false>(smem); break;
-        case 2: per_sm = P.srow ? adj_blocks_per_sm<2, true>(smem) : adj_blocks_per_sm<2, false>(smem); break;
-        case 3: per_sm = P.srow ? adj_blocks_per_sm<3, true>(smem) : adj_blocks_per_sm<3, false>(smem); break;
-        default: per_sm = P.srow ? adj_blocks_per_sm<4, true>(smem) : adj_blocks_per_sm<4, false>(smem);
+        case 1: per_sm = P.srow ? adj_blocks_per_sm<1, true>(smem, tpb) : adj_blocks_per_sm<1, false>(smem, tpb); break;
+        case 2: per_sm = P.srow ? adj_blocks_per_sm<2, true>(smem, tpb) : adj_blocks_per_sm<2, false>(smem, tpb); break;
+        case 3: per_sm = P.srow ? adj_blocks_per_sm<3, true>(smem, tpb) : adj_blocks_per_sm<3, false>(smem, tpb); break;
+        default: per_sm = P.srow ? adj_blocks_per_sm<4, true>(smem, tpb) : adj_blocks_per_sm<4, false>(smem, tpb);
     }
     const long long cap = (long long)per_sm * sms, c0 = parzen_ctas(P, n, sms);
     long long waves = ((long long)n * c0 + cap / 2) / cap;
     if (waves < 1) waves = 1;
     long long c = waves * cap / n;
-    const long long max_c = ((long long)P.nf[1] * P.nf[2] + 7) / 8;  // at least a row per warp
+    const long long max_c = ((long long)P.nf[1] * P.nf[2] + tpb / 32 - 1) / (tpb / 32);  // a row per warp
     if (c > max_c) c = max_c;
     if (c < 1) c = 1;
     return (int)c;
@@ -918,22 +922,23 @@ cudaError_t launch_parzen_hist(const ParzenLaunch &L, const ParzenAffine *d_aff,
     // rows per CTA: at most kParzenMaxVox voxels per copy, so that the 16-bit halves cannot overflow
     // (a row of nx voxels, or of at most nx sampled entries, is walked 32 lanes at a time, so copy i,
     // fed by the lanes l = i mod C, takes at most 32 / C of every 32; the longest row of all pairs
-    // bounds it); CTAs do equal shares of the rows of all transforms, as many as fill a whole number
+    // bounds it, and a pair with fewer bins than the largest uses at least C copies); CTAs do equal shares of the rows of all transforms, as many as fill a whole number
     // of waves of the CTAs resident at once
     const long long TR = L.total_rows;
     long long cap = kParzenMaxVox / ((32 / copies) * ((L.nx_max + 31) / 32));
     if (cap < 1) cap = 1;
-    const int per_sm = resident_per_sm(fn, 256 * copies, smem);
+    const int per_sm = resident_per_sm(fn, kParzenFwdThreads, smem);
     const long long wave = (long long)per_sm * (sms > 0 ? sms : 1);
     long long nch = (TR + cap - 1) / cap;
     nch = (nch + wave - 1) / wave * wave;
     if (nch > TR) nch = TR;
     long long rpc = (TR + nch - 1) / nch, total = TR;
     dim3 grid((unsigned)((TR + rpc - 1) / rpc));
-    int nn = n, bmax = L.Bmax;
-    void *args[] = {(void *)&L.p0, (void *)&L.d_pairs, (void *)&L.d_pair_of, (void *)&L.d_row_start, (void *)&nn,
-                    (void *)&d_aff, (void *)&rpc, (void *)&total, (void *)&bmax, (void *)&d_hist, (void *)&d_count};
-    return cudaLaunchKernel(fn, grid, dim3(256 * copies), args, smem, s);
+    int nn = n, bmax = L.Bmax, words = (int)(smem / sizeof(uint32_t));
+    void *args[] = {(void *)&L.p0,  (void *)&L.d_pairs, (void *)&L.d_pair_of, (void *)&L.d_row_start,
+                    (void *)&nn,    (void *)&d_aff,     (void *)&rpc,         (void *)&total,
+                    (void *)&bmax,  (void *)&words,     (void *)&d_hist,      (void *)&d_count};
+    return cudaLaunchKernel(fn, grid, dim3(kParzenFwdThreads), args, smem, s);
 }
 
 cudaError_t launch_parzen_weights(const unsigned long long *d_hist, const unsigned long long *d_count,
@@ -960,12 +965,19 @@ cudaError_t launch_parzen_adjoint(const ParzenLaunch &L, const ParzenAffine *d_a
     for (int q0 = 0; q0 < nq; q0 += 4) {
         const int g = nq - q0 < 4 ? nq - q0 : 4;
         const size_t smem = parzen_adj_smem(L.Bmax, g);
-        const int in_smem = smem > 0;
-#define MI_ADJ_S(NQV, SV, MV)                                                                                \
-    do {                                                                                                     \
-        if ((e = allow_smem((const void *)k_parzen_adj<NQV, SV, MV>, smem)) != cudaSuccess) return e;        \
-        k_parzen_adj<NQV, SV, MV><<<grid, 256, smem, s>>>(L.p0, L.d_pairs, L.d_pair_of, L.Bmax, d_aff, nq, q0, \
-                                                          d_w, in_smem, d_mom);                              \
+        const int wmode = parzen_adj_wmode(L.Bmax, g), tpb = parzen_adj_threads(L.Bmax, g);
+#define MI_ADJ_T(NQV, SV, MV, TV)                                                                              \
+    do {                                                                                                       \
+        if ((e = allow_smem((const void *)k_parzen_adj<NQV, SV, MV, TV>, smem)) != cudaSuccess) return e;      \
+        k_parzen_adj<NQV, SV, MV, TV><<<grid, TV, smem, s>>>(L.p0, L.d_pairs, L.d_pair_of, L.Bmax, d_aff, nq, q0, \
+                                                             d_w, wmode, d_mom);                               \
+    } while (0)
+#define MI_ADJ_S(NQV, SV, MV)            \
+    do {                                 \
+        if (tpb == 512)                  \
+            MI_ADJ_T(NQV, SV, MV, 512);  \
+        else                             \
+            MI_ADJ_T(NQV, SV, MV, 256);  \
     } while (0)
 #define MI_ADJ(NQV)                              \
     do {                                         \
@@ -989,6 +1001,7 @@ cudaError_t launch_parzen_adjoint(const ParzenLaunch &L, const ParzenAffine *d_a
         }
 #undef MI_ADJ
 #undef MI_ADJ_S
+#undef MI_ADJ_T
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     k_parzen_grad<<<(n * nq * np + 127) / 128, 128, 0, s>>>(n, nq, np, L.d_pairs, L.d_pair_of, ctas, d_count, d_mom,

@@ -269,11 +269,13 @@ __host__ __device__ inline int parzen_stride(int B) { return B + 1 + ((kParzenBa
 // Histogram copies per CTA of the forward: with C copies, lane l adds to copy l mod C (copy i starts
 // i (2 B SB + 32 / C) words in, so that one cell's copies fall in different banks), which divides by C
 // the lanes of a warp that hit one cell in one atomic instruction.  A CTA has 1024 threads (64
-// registers each: the whole register file) whatever C is, so an SM keeps 32 warps at every bin count;
-// C is the most copies, up to 4, that fit the 227 KB a CTA may hold (4 up to 64 bins, 2 at 96, 1 at 128).
-constexpr int kParzenFwdMaxCopies = 4;
+// registers each: the whole register file) whatever C is, so an SM keeps 32 warps at every bin count.
+// C is the largest power of two up to 8 whose copies take at most 160 KB, or 1: the rest of the SM's
+// 256 KB of L1 caches the moving volume's texture gathers (6 copies at 64 bins, 213 KB, made the call
+// 29 % slower than 4); so 8 copies up to 45 bins, 4 at 64, 2 at 96, 1 at 128.
+constexpr int kParzenFwdMaxCopies = 8;
 constexpr int kParzenFwdThreads = 1024;
-constexpr int kParzenFwdSmemWords = 227 * 1024 / 4;
+constexpr int kParzenFwdSmemWords = 160 * 1024 / 4;
 __host__ __device__ inline int parzen_copy_offset(int B, int copies) {
     return 2 * B * parzen_stride(B) + (copies > 1 ? 32 / copies : 0);
 }
@@ -288,10 +290,10 @@ __host__ inline size_t parzen_fwd_smem(int B, int copies) {
 __host__ inline int parzen_fwd_copies(int B) { return parzen_fwd_copies_in(B, kParzenFwdSmemWords); }
 
 // MULTI: transforms on several pairs (descriptors read from `pairs`); otherwise every transform is on
-// the pair P0 passed by value, whose fields stay kernel parameters.  COPIES is the copy count of the
-// largest pair's bins, for which the shared memory is sized (smem_words words); a transform of a pair
-// with fewer bins uses as many copies as fit there (at least COPIES).
-template <int RPW, bool SAMPLED, int COPIES, bool MULTI>
+// the pair P0 passed by value, whose fields stay kernel parameters.  The shared memory (smem_words
+// words) is sized for the copies of the largest pair's bins; a transform of a pair with fewer bins
+// uses as many copies as fit there.
+template <int RPW, bool SAMPLED, bool MULTI>
 __global__ void __launch_bounds__(kParzenFwdThreads)
     k_parzen_hist(ParzenPair P0, const ParzenPair *__restrict__ pairs, const int *__restrict__ pair_of,
                   const long long *__restrict__ row_start, int n, const ParzenAffine *__restrict__ aff,
@@ -332,8 +334,8 @@ __global__ void __launch_bounds__(kParzenFwdThreads)
     for (long long s0 = c0; s0 < c1; ++t) {
         const ParzenPair P = MULTI ? pairs[pair_of[t]] : P0;
         const int B = P.B, B2 = B * B, SB = parzen_stride(B), NP = B * SB;
-        const int NC = MULTI ? parzen_fwd_copies_in(B, smem_words) : COPIES;  // copies in use
-        const int CP = parzen_copy_offset(B, NC);  // offset between copies
+        const int NC = parzen_fwd_copies_in(B, smem_words);  // copies in use
+        const int CP = parzen_copy_offset(B, NC);            // offset between copies
         uint32_t *lo16 = sh32 + (lane & (NC - 1)) * CP, *hi16 = lo16 + NP;
         const int nf0 = P.nf[0], nf1 = P.nf[1];
         const int n0 = P.nm[0], n1 = P.nm[1], n2 = P.nm[2];
@@ -429,10 +431,8 @@ __global__ void __launch_bounds__(kParzenFwdThreads)
         for (int c = threadIdx.x; c < B2; c += blockDim.x) {
             const int cp = (c / B) * SB + c % B;
             unsigned long long v = 0;
-#pragma unroll
-            for (int i = 0; i < kParzenFwdMaxCopies; ++i)
-                if (i < NC)
-                    v += (unsigned long long)sh32[i * CP + cp] + ((unsigned long long)sh32[i * CP + NP + cp] << 16);
+            for (int i = 0; i < NC; ++i)
+                v += (unsigned long long)sh32[i * CP + cp] + ((unsigned long long)sh32[i * CP + NP + cp] << 16);
             if (v) atomicAdd(gh + c, v);
         }
         if (lane == 0 && cnt) atomicAdd(gcount + t, (unsigned long long)cnt);
@@ -906,24 +906,17 @@ cudaError_t launch_parzen_hist(const ParzenLaunch &L, const ParzenAffine *d_aff,
     const int copies = parzen_fwd_copies(L.Bmax);
     const size_t smem = parzen_fwd_smem(L.Bmax, copies);
     const bool multi = L.d_pair_of != nullptr;
-    const void *fn = nullptr;
-#define MI_HIST_FN(C)                                                                                   \
-    (multi ? (L.sampled ? (const void *)k_parzen_hist<kParzenRowsPerStep, true, C, true>                \
-                        : (const void *)k_parzen_hist<kParzenRowsPerStep, false, C, true>)              \
-           : (L.sampled ? (const void *)k_parzen_hist<kParzenRowsPerStep, true, C, false>               \
-                        : (const void *)k_parzen_hist<kParzenRowsPerStep, false, C, false>))
-    switch (copies) {
-        case 4: fn = MI_HIST_FN(4); break;
-        case 2: fn = MI_HIST_FN(2); break;
-        default: fn = MI_HIST_FN(1);
-    }
-#undef MI_HIST_FN
+    const void *fn = multi ? (L.sampled ? (const void *)k_parzen_hist<kParzenRowsPerStep, true, true>
+                                        : (const void *)k_parzen_hist<kParzenRowsPerStep, false, true>)
+                           : (L.sampled ? (const void *)k_parzen_hist<kParzenRowsPerStep, true, false>
+                                        : (const void *)k_parzen_hist<kParzenRowsPerStep, false, false>);
     if ((e = allow_smem(fn, smem)) != cudaSuccess) return e;
     // rows per CTA: at most kParzenMaxVox voxels per copy, so that the 16-bit halves cannot overflow
     // (a row of nx voxels, or of at most nx sampled entries, is walked 32 lanes at a time, so copy i,
-    // fed by the lanes l = i mod C, takes at most 32 / C of every 32; the longest row of all pairs
-    // bounds it, and a pair with fewer bins than the largest uses at least C copies); CTAs do equal shares of the rows of all transforms, as many as fill a whole number
-    // of waves of the CTAs resident at once
+    // fed by the lanes l = i mod C, takes at most 32 / C of every 32; the longest row of all
+    // pairs bounds it, and a pair with fewer bins than the largest uses at least C copies); CTAs do
+    // equal shares of the rows of all transforms, as many as fill a whole number of waves of the CTAs
+    // resident at once
     const long long TR = L.total_rows;
     long long cap = kParzenMaxVox / ((32 / copies) * ((L.nx_max + 31) / 32));
     if (cap < 1) cap = 1;

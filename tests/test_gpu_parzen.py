@@ -69,7 +69,7 @@ def test_parzen_smallest_volumes(cuda_lib):
     assert seen == {0, 1, 2}
 
 
-@pytest.mark.parametrize("B", [8, 64, 96, 128])  # forward with four, four, two and one histogram copies
+@pytest.mark.parametrize("B", [8, 64, 96, 128])  # forward with eight, four, two and one histogram copies
 def test_parzen_integer_pair_and_bin_counts(cuda_lib, B):
     f, m = phantoms.head_pair(shape=(30, 34, 40), spacing=(1, 1, 1), seed=42)
     ctx = cuda_lib.Context(f, m, bins=B, kernel="parzen", fixed_depth=12, moving_depth=12)
@@ -167,30 +167,32 @@ def test_parzen_full_size_sampled(cuda_lib):
             assert np.abs(g[t, iq] - g_o[iq]).max() <= G_TOL * np.abs(g_o[iq]).max(), (t, iq, g[t, iq], g_o[iq])
 
 
-def test_parzen_forward_at_the_per_copy_voxel_cap(cuda_lib):
-    # rows of 16384 voxels, 208 rows, 50 poses: a forward CTA takes 16 rows, so at the identity each of
-    # its histogram copies (fed by every fourth lane) sums exactly 2^16 voxels' 16-bit weight halves,
-    # the most that fits
+@pytest.mark.parametrize("B, nz", [(64, 16), (32, 32)])
+def test_parzen_forward_at_the_per_copy_voxel_cap(cuda_lib, B, nz):
+    # rows of 16384 voxels, 4 nz rows a pose, 38 poses.  At 64 bins a CTA holds four histogram copies,
+    # each fed by every fourth lane, so a copy may take 16 rows (2^16 voxels); at 32 bins eight copies,
+    # every eighth lane, 32 rows.  The rows then split into 152 chunks of that many (one wave of one CTA
+    # per SM on 152 SMs), four to a pose, and at the identity every copy sums exactly 2^16 voxels' 16-bit
+    # weight halves, the most that fits
     rng = np.random.default_rng(52)
-    nz, ny, nx = 52, 4, 16384
+    ny, nx = 4, 16384
     z = np.arange(nz)[:, None, None] / (nz - 1)
     x = np.arange(nx)[None, None, :] / (nx - 1)
     f = (0.25 + 0.5 * (z > 0.5) + 0.02 * rng.standard_normal((nz, ny, nx))).clip(0, 1).astype(np.float32)
     m = (0.2 + 0.3 * z + 0.4 * x + 0.01 * rng.standard_normal((nz, ny, nx))).clip(0, 1).astype(np.float32)
-    B = 64
     ctx = cuda_lib.Context(f, m, bins=B, kernel="parzen")
-    prm = np.tile(np.array([0, 0, 0, 0, 0, 0, 1, 1, 1], np.float32), (50, 1))
-    prm[25:, 0] = np.linspace(-4, 4, 25, dtype=np.float32)
+    prm = np.tile(np.array([0, 0, 0, 0, 0, 0, 1, 1, 1], np.float32), (38, 1))
+    prm[19:, 0] = np.linspace(-4, 4, 19, dtype=np.float32)
     qs = [1.0, 0.7, 1.3]
     mi, g = ctx.grad(prm, qs)
-    for t in (0, 40):
+    for t in (0, 30):
         aff, J = oracle.affine(prm[t], f.shape, (1, 1, 1), m.shape, (1, 1, 1), with_jacobian=True)
         mi_o, g_o, n = oracle.parzen(f, m, aff, B, qs, daff=J)
         assert np.all(np.abs(mi[t] - mi_o) <= MI_TOL * np.maximum(np.abs(mi_o), 1.0)), (t, mi[t], mi_o)
         for iq in range(len(qs)):
             assert np.abs(g[t, iq] - g_o[iq]).max() <= G_TOL * np.abs(g_o[iq]).max(), (t, iq, g[t, iq], g_o[iq])
     # every identity pose gives the same soft histogram
-    assert np.all(mi[:25] == mi[0]) and np.all(g[:25] == g[0])
+    assert np.all(mi[:19] == mi[0]) and np.all(g[:19] == g[0])
 
 
 @pytest.mark.parametrize("kernel", ["hard", "parzen"])

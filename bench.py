@@ -338,7 +338,8 @@ def run_ours(args, rank, world, local_rank):
         z_s = time.perf_counter() - t0
         pv = int(np.prod(PARZEN_SHAPE))
         zms = float(np.mean(zk))
-        z_ach = PARZEN_OPS_PER_VOXT * PARZEN_N * pv / (zms / 1e3) / 1e12
+        z_over = float(zctx.eval(pp, PARZEN_QS, with_entropies=True)[2].sum().item())  # voxels processed
+        z_ach = PARZEN_OPS_PER_VOXT * z_over / (zms / 1e3) / 1e12
         extra["mi_grad"] = {"value": args.steps * PARZEN_N / z_s, "unit": "(MI+grad over 9 params, 3 q)/s",
                             "voxel_transforms_per_s": args.steps * PARZEN_N * pv / z_s,
                             "kernel_ms_per_call": zms, "poses_per_call": PARZEN_N,
@@ -346,7 +347,9 @@ def run_ours(args, rank, world, local_rank):
                             "roofline": {"bound": "alu", "achieved": z_ach, "peak": alu_peak, "unit": "Tops/s",
                                          "frac": z_ach / alu_peak, "traffic": None,
                                          "kernel": "k_parzen_hist + k_parzen_cells + k_parzen_adj",
-                                         "note": "FP32 lane-ops per voxel x transform over the whole MI+grad call"}}
+                                         "units_per_call": z_over, "overlap_fraction": z_over / (PARZEN_N * pv),
+                                         "note": "FP32 lane-ops per overlap voxel x transform over the whole "
+                                                 "MI+grad call"}}
         pn = K_PARZEN_NCU
         if pn["source_sha16"] == kernel_source_sha16("mi_parzen.cu"):
             # the forward's binding unit: the shared-memory pipe, one wavefront per clock per SM

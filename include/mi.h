@@ -256,7 +256,9 @@ mi_status mi_set_stream(mi_ctx *ctx, void *stream);
  * out_count: n int64 overlap voxel counts, or NULL.
  * A transform whose overlap is empty gets NaN and the call returns MI_EEMPTY
  * after finishing every other transform.  In MI_PARZEN mode this returns the
- * Parzen MI (no gradient).  n == 0 is a no-op.
+ * Parzen MI (no gradient) and out_count the voxels inside each overlap (the
+ * voxels its soft histogram sums); out_h must be NULL there (MI_EUNSUPPORTED).
+ * n == 0 is a no-op.
  */
 mi_status mi_eval(mi_ctx *ctx, const float *transforms, int n, const float *q, int nq, double *out_mi,
                   double *out_h, int64_t *out_count);

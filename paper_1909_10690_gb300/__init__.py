@@ -222,7 +222,8 @@ class Context:
         self._check(self._lib.mi_set_stream(self._h, ctypes.c_void_p(h) if h else None))
 
     def eval(self, transforms, q=(1.0,), with_entropies=False, allow_empty=True):
-        """MI (n x nq) for n transforms; with_entropies adds (H_F, H_M, H_FM) per q and the overlap counts."""
+        """MI (n x nq) for n transforms; with_entropies adds (H_F, H_M, H_FM) per q and the overlap counts
+        (for a Parzen context the entropies are None: only the counts)."""
         T = _Arg(transforms, np.float32)
         Q = _Arg(np.atleast_1d(np.asarray(q, dtype=np.float32)))
         n = int(np.prod(T.obj.shape) // self.nparams)
@@ -230,7 +231,7 @@ class Context:
         gpu = T.on_gpu
         dev = T.obj.device if gpu else None
         mi = _out((n, nq), gpu, np.float64, dev)
-        h = _out((n, nq, 3), gpu, np.float64, dev) if with_entropies else None
+        h = _out((n, nq, 3), gpu, np.float64, dev) if with_entropies and self.kernel != "parzen" else None
         cnt = _out((n,), gpu, np.int64, dev) if with_entropies else None
         st = self._lib.mi_eval(self._h, T.ptr, n, Q.ptr, nq, _ptr(mi), _ptr(h), _ptr(cnt))
         self._check(st, allow_empty)

@@ -1448,7 +1448,7 @@ mi_status eval_core(mi_ctx *ctx, const EvalReq &R, const float *qv, int nq, doub
 // Parzen MI (and, with out_grad, its gradient) for n transforms; pair_of (n entries) names each
 // transform's pair in a multi-pair context (NULL: pair 0).  One launch per kernel for all pairs.
 mi_status parzen_core(mi_ctx *ctx, const std::vector<float> &prm, int n, const float *qv, int nq, double *out_mi,
-                      double *out_grad, const std::vector<int> *pair_of = nullptr) {
+                      double *out_grad, const std::vector<int> *pair_of = nullptr, int64_t *out_count = nullptr) {
     const int Bmax = ctx->p_bmax;
     const size_t BM2 = (size_t)Bmax * Bmax;
     QSet Q;
@@ -1548,6 +1548,7 @@ mi_status parzen_core(mi_ctx *ctx, const std::vector<float> &prm, int n, const f
     ctx->last_launches = 4 + (out_grad ? (nq + 3) / 4 + 1 : 0);
     if ((st = deliver(ctx, out_mi, ctx->d_mi.p, (size_t)n * nq * 8)) != MI_OK) return st;
     if (out_grad && (st = deliver(ctx, out_grad, ctx->p_grad.p, (size_t)n * nq * np * 8)) != MI_OK) return st;
+    if (out_count && (st = deliver(ctx, out_count, cnt, (size_t)n * 8)) != MI_OK) return st;
     std::vector<unsigned long long> hc(n);
     MI_CU(cudaMemcpyAsync(hc.data(), cnt, (size_t)n * 8, cudaMemcpyDeviceToHost, s), "reading counts");
     MI_CU(cudaStreamSynchronize(s), "Parzen evaluation");
@@ -1662,8 +1663,8 @@ mi_status mi_eval(mi_ctx *ctx, const float *transforms, int n, const float *q, i
     std::vector<float> prm;
     if ((st = read_transforms(ctx, transforms, n, prm)) != MI_OK) return st;
     if (ctx->opt.kernel == MI_PARZEN) {
-        if (out_h || out_count) return ctx->fail(MI_EUNSUPPORTED, "out_h / out_count are hard-path outputs");
-        return parzen_core(ctx, prm, n, qv, nq, out_mi, nullptr);
+        if (out_h) return ctx->fail(MI_EUNSUPPORTED, "out_h (hard-histogram entropies) is a hard-path output");
+        return parzen_core(ctx, prm, n, qv, nq, out_mi, nullptr, nullptr, out_count);
     }
     EvalReq R;
     R.n = n;

@@ -112,6 +112,13 @@ def test_parzen_eval_matches_grad_mi_and_empty(cuda_lib):
     mi_e = ctx.eval(prm, [1.0, 1.3])
     mi_g, _ = ctx.grad(prm, [1.0, 1.3])
     np.testing.assert_array_equal(mi_e, mi_g)
+    # the overlap counts the soft histogram sums, as the oracle's; no hard-histogram entropies
+    mi_c, h, cnt = ctx.eval(prm, [1.0, 1.3], with_entropies=True)
+    assert h is None
+    np.testing.assert_array_equal(mi_c, mi_e)
+    for t in range(len(prm)):
+        aff = oracle.affine(prm[t], f.shape, (1, 1, 1), m.shape, (1, 1, 1))
+        assert cnt[t] == oracle.parzen(f, m, aff, 16, [1.0])[2]
     far = phantoms.identity_params(1)
     far[0, 1] = 500.0
     with pytest.raises(cuda_lib.MIError) as ei:

@@ -504,6 +504,7 @@ def run_uneven(args):
 
     ctx = mi.Context(pairs=[dict(fixed=f, moving=m, bins=s["bins"], fixed_depth=s["depth"], moving_depth=s["depth"])
                             for s, (f, m) in zip(specs, vols)])
+    ctx.set_stream(torch.cuda.current_stream())  # the stream the timing events are recorded on
     d_pof, d_prm = torch.from_numpy(pair_of).cuda(), torch.from_numpy(prm).cuda()
     qs = [1.0, 0.5, 1.5, 2.0]
     med, ms = timed(lambda: ctx.batch_eval(d_pof, d_prm, qs))
@@ -517,6 +518,7 @@ def run_uneven(args):
     pctx = mi.Context(pairs=[dict(fixed=vols[p][0], moving=vols[p][1], bins=specs[p]["bins"],
                                   fixed_depth=specs[p]["depth"], moving_depth=specs[p]["depth"]) for p in big],
                       kernel="parzen")
+    pctx.set_stream(torch.cuda.current_stream())
     psel = np.concatenate([np.nonzero(pair_of == p)[0][:64] for p in big])
     pof = torch.from_numpy(np.repeat(np.arange(len(big), dtype=np.int32), 64)).cuda()
     pprm = torch.from_numpy(prm[psel]).cuda()

@@ -78,6 +78,16 @@ def test_parzen_integer_pair_and_bin_counts(cuda_lib, B):
     check(ctx, f, m, prm, [1.0, 1.5], B, depth=12)
 
 
+def test_parzen_128_bins_five_q_reads_w_from_global_then_shared_memory(cuda_lib):
+    # the adjoint takes q in groups of up to four: at 128 bins four q's W tables (276 KB) exceed shared
+    # memory and are read from global memory by 256-thread CTAs; the fifth q's (69 KB) sits in the
+    # shared memory of 512-thread CTAs
+    f, m = phantoms.head_pair(shape=(26, 30, 34), spacing=(1, 1, 1), seed=53, dtype=np.float32)
+    ctx = cuda_lib.Context(f, m, bins=128, kernel="parzen")
+    prm = phantoms.random_transforms(3, seed=54, t_mm=3, r_deg=6, s_range=(0.96, 1.04))
+    check(ctx, f, m, prm, [1.0, 0.7, 1.3, 1.5, 2.0], 128)
+
+
 def test_parzen_versor_and_offset_gradient(cuda_lib):
     # d MI / d(versor, zero-centred scale): the Jacobian of the unit-ball parameterisation
     f, m = phantoms.head_pair(shape=(30, 34, 38), spacing=(1, 1, 1), seed=46, dtype=np.float32)

@@ -443,8 +443,9 @@ def run_maps(args):
                                  ("scale", -0.2, 0.2, {"scale": "offset"})):
         ctx = mi.Context(f, m, bins=64, fixed_depth=12, moving_depth=12, fixed_spacing=sp, moving_spacing=sp,
                          path="batched", **opts)
-        # warm-up on the same map: the autotuner and the graph cache key on the call's transform count,
-        # and the map's 32 768-transform chunks and its last, shorter one are each tuned once
+        # warm-up on the same map: the autotuner keys on the call's size class (below 152, below 608 or
+        # more transforms on 152 SMs) and the graph cache on its exact count, so a smaller warm-up grid
+        # leaves the map's 32 768-transform chunks untuned and its last, shorter chunk without a graph
         maps.param_map(ctx, family, lo, hi, n, q=[1.0, 1.5])
         torch.cuda.synchronize()
         t0 = time.perf_counter()

@@ -1235,29 +1235,40 @@ mi_status autotune(mi_ctx *ctx, int nitems, const QSet &Q, const Outputs &O, Cho
         if (best.variant < 0) best = cands.front();
         return MI_OK;
     }
+    // Two stages: every candidate is timed on one wave of items (after a warm-up of a few items, which
+    // loads its kernel), then the three fastest on three waves; time per item decides.
     cudaEvent_t e0, e1;
     MI_CU(cudaEventCreate(&e0), "event");
     MI_CU(cudaEventCreate(&e1), "event");
-    float best_ms = 1e30f;
     Outputs Ot = O;
     Ot.dump = nullptr;
-    for (const Choice &c : cands) {
-        const int items = std::min(nitems, 3 * c.ctas);
+    auto time_per_item = [&](const Choice &c, int items, float &ms) -> mi_status {
         Choice cc = c;
-        mi_status st = launch_batched_once(ctx, std::min(items, c.ctas), Q, Ot, cc);  // warm-up
-        if (st != MI_OK) break;
         cudaEventRecord(e0, ctx->stream);
-        launch_batched_once(ctx, items, Q, Ot, cc);
+        mi_status st = launch_batched_once(ctx, items, Q, Ot, cc);
+        if (st != MI_OK) return st;
         cudaEventRecord(e1, ctx->stream);
         cudaError_t e = cudaEventSynchronize(e1);
-        if (e != cudaSuccess) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return ctx->cuda_fail(e, "autotuning");
-        }
-        float ms = 0;
+        if (e != cudaSuccess) return ctx->cuda_fail(e, "autotuning");
         cudaEventElapsedTime(&ms, e0, e1);
-        ms = ms / (float)items;
+        ms /= (float)items;
+        return MI_OK;
+    };
+    std::vector<std::pair<float, size_t>> first;  // (ms per item on one wave, candidate)
+    mi_status st = MI_OK;
+    for (size_t i = 0; i < cands.size() && st == MI_OK; ++i) {
+        Choice cc = cands[i];
+        if ((st = launch_batched_once(ctx, std::min(nitems, 8), Q, Ot, cc)) != MI_OK) break;  // warm-up
+        float ms = 0;
+        if ((st = time_per_item(cands[i], std::min(nitems, cands[i].ctas), ms)) == MI_OK) first.push_back({ms, i});
+    }
+    std::sort(first.begin(), first.end());
+    float best_ms = 1e30f;
+    best = cands.front();
+    for (size_t k = 0; k < first.size() && k < 3 && st == MI_OK; ++k) {
+        const Choice &c = cands[first[k].second];
+        float ms = 0;
+        if ((st = time_per_item(c, std::min(nitems, 3 * c.ctas), ms)) != MI_OK) break;
         if (ms < best_ms) {
             best_ms = ms;
             best = c;
@@ -1265,7 +1276,7 @@ mi_status autotune(mi_ctx *ctx, int nitems, const QSet &Q, const Outputs &O, Cho
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    return MI_OK;
+    return st;
 }
 
 mi_status run_batched(mi_ctx *ctx, int nitems, const QSet &Q, const Outputs &O, const Choice &ch, bool use_graph,

@@ -55,10 +55,11 @@ K_BATCHED_NCU = {"source_sha16": "018b6e18fe20d963", "config": [10, 1, 4],
 # adjoint 89 (trilinear value and gradient 23, bin coordinate 1, B-spline derivatives 8, 3 q x 19)
 PARZEN_OPS_PER_VOXT = 120
 # Counters of the Parzen forward (k_parzen_hist) from one ncu capture of the 50-pose call (see profiles/),
-# reported while the kernel source is the one measured: shared-atomic instructions and wavefronts, and
-# SM cycles elapsed per launch
+# reported while the kernel source is the one measured: shared-atomic instructions and wavefronts, SM
+# cycles elapsed per launch, and the DRAM bytes read and written by the forward and the adjoint
 K_PARZEN_NCU = {"source_sha16": "75e8764ddefccb85", "atom_inst": 52167744, "atom_wavefronts": 245283048,
                 "sm_cycles_elapsed": 2177378.59, "time_ms": 1.0568,
+                "dram_bytes_per_call": 531975424 + 4546560 + 26225408,
                 "profile": "profiles/parzen_fwd_adj_192x192x128_64bins.md"}
 PARZEN_SHAPE = (128, 192, 192)
 PARZEN_SPACING = (1.0, 1.0, 1.2)
@@ -352,6 +353,9 @@ def run_ours(args, rank, world, local_rank):
                                                  "MI+grad call"}}
         pn = K_PARZEN_NCU
         if pn["source_sha16"] == kernel_source_sha16("mi_parzen.cu"):
+            extra["mi_grad"]["roofline"]["traffic"] = pn["dram_bytes_per_call"]
+            extra["mi_grad"]["roofline"]["traffic_note"] = "DRAM bytes of k_parzen_hist + k_parzen_adj per call (ncu)"
+            extra["mi_grad"]["roofline"]["algorithmic_bytes"] = int(pv * 1 + pv * 4)
             # the forward's binding unit: the shared-memory pipe, one wavefront per clock per SM
             extra["mi_grad"]["forward_shared_atomics"] = {
                 "wavefronts_per_sm_cycle": pn["atom_wavefronts"] / sms / pn["sm_cycles_elapsed"],

@@ -425,6 +425,44 @@ def test_full_size_batched_256_cubed_sampled(cuda_lib):
         np.testing.assert_array_equal(H[k], ho.astype(np.uint32), err_msg=str(hsel[k]))
 
 
+@pytest.mark.slow
+def test_512_cubed_pair_both_paths_sampled(cuda_lib):
+    """A 512^3 uint16 12-bit pair at 0.5 mm (134 M voxels a volume, a 1.1 GB quad array; fixed bins
+    hold far more than 2^16 voxels, so every histogram row takes 32-bit counters), 128 bins: counts, MI
+    and one full histogram against the oracle on sampled transforms of a 64-transform batched call,
+    and the plain path on the same transforms."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    sp = (0.5, 0.5, 0.5)
+    f, m = phantoms.head_pair(shape=(512, 512, 512), spacing=sp, seed=101)
+    prm = phantoms.random_transforms(64, seed=102, t_mm=8, r_deg=10, s_range=(0.9, 1.1))
+    qs = [1.0, 2.0]
+    sample = [0, 37, 63]
+
+    def oracle_one(t):
+        return oracle.mi_eval(f, m, 128, prm[[t]], qs, fixed_spacing=sp, moving_spacing=sp, fixed_depth=12,
+                              moving_depth=12)
+
+    with ThreadPoolExecutor(max_workers=len(sample)) as ex:
+        res = list(ex.map(oracle_one, sample))
+    mi_o = np.concatenate([r[0] for r in res])
+    h_o = np.concatenate([r[1] for r in res])
+    cnt_o = np.concatenate([r[2] for r in res])
+    for path in ("batched", "plain"):
+        ctx = cuda_lib.Context(f, m, bins=128, fixed_depth=12, moving_depth=12, fixed_spacing=sp,
+                               moving_spacing=sp, path=path)
+        mi, h, cnt = ctx.eval(prm if path == "batched" else prm[sample], qs, with_entropies=True)
+        sel = sample if path == "batched" else slice(None)
+        np.testing.assert_array_equal(cnt[sel], cnt_o)
+        assert_mi_close(mi[sel], mi_o, h_o)
+        if path == "batched":
+            q16 = oracle.affine_q16(oracle.affine(prm[37], f.shape, sp, m.shape, sp))
+            H = ctx.hist(affines=q16[None], path=cuda_lib.PATH_BATCHED)
+            ho, _ = oracle.joint_hist(f, m, q16, 128, 12, 12)
+            np.testing.assert_array_equal(H[0], ho.astype(np.uint32))
+        del ctx
+
+
 @pytest.mark.parametrize("n_a", [65535, 65536])
 def test_row_bound_layout_at_the_16_bit_limit(cuda_lib, n_a):
     # a fixed bin holding exactly 65535 voxels keeps 16-bit counters; one more makes it a 32-bit row;

@@ -13,6 +13,8 @@ analytic gradient.
 import numpy as np
 import pytest
 
+import oracle
+
 from paper_1909_10690_gb300 import phantoms, register
 
 pytestmark = pytest.mark.gpu
@@ -53,7 +55,8 @@ def test_central_differences_equal_the_mean_gradient(cuda_lib, head):
     wherever samples cross grid planes (its total variation along a scale
     segment is ~20 times its size), so the rule needs n = 8192 nodes on the
     scale parameters (measured gap ~1e-5; 8.7e-5 at n = 4096, 6e-4 at 256)
-    and n = 256 on the rest (measured ~2e-5).
+    and n = 256 on the rest (measured ~2e-5).  For two of the poses the differences are also taken of
+    the FP64 oracle's MI, so that the check does not rest on the GPU's MI alone.
     """
     f, m = head
     fc = np.ascontiguousarray(f[24:104, 32:160, 32:160])
@@ -83,6 +86,11 @@ def test_central_differences_equal_the_mean_gradient(cuda_lib, head):
             gsum += gn.reshape(P, chunk, len(qs), 9)[:, :, :, k].sum(1)
         gap = np.abs(fd - gsum / n) / scale
         assert gap.max() <= 1e-4, (k, gap.max())
+        # and independently of the GPU's MI: differences of the FP64 oracle's MI at the same endpoints
+        for t in (0, 25):
+            mo = [oracle.parzen(fc, m, oracle.affine(e[t], fc.shape, SP, m.shape, SP), 64, qs)[0] for e in (a32, b32)]
+            fd_o = (mo[1] - mo[0]) / (b[t] - a[t])
+            assert np.all(np.abs(fd_o - gsum[t] / n) <= 1e-4 * scale[t]), (k, t, fd_o, gsum[t] / n)
 
 
 @pytest.mark.parametrize("q, q_t", [(1.0, None), (1.0, 1.5)], ids=["shannon", "mixed_t1.5"])

@@ -396,6 +396,37 @@ def test_uneven_batch_small(cuda_lib):
             np.testing.assert_array_equal(H[k], ho.astype(np.uint32))
 
 
+@pytest.fixture(scope="module")
+def pair_256_cubed():
+    return phantoms.head_pair(shape=(256, 256, 256), spacing=(1, 1, 1), seed=30)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("variant", [2, 3, 6, 7, 8, 9, 12, 13, 15])
+def test_full_size_every_variant_that_fits_256_bins(cuda_lib, pair_256_cubed, variant):
+    """Each histogram / fetch variant that holds 256 bins (16-bit counters with their drains, match
+    aggregation, row-bound rows; pair, texture, quad and gather fetches) on the 256^3 12-bit pair,
+    256 transforms in one batched launch: three sampled transforms' counts and MI against the oracle,
+    one joint histogram bit for bit."""
+    f, m = pair_256_cubed
+    prm = phantoms.random_transforms(256, seed=110 + variant)
+    qs = [0.5, 1.0, 2.0]
+    ctx = cuda_lib.Context(f, m, bins=256, fixed_depth=12, moving_depth=12, path="batched", hist_variant=variant)
+    try:
+        mi, h, cnt = ctx.eval(prm, qs, with_entropies=True)
+    except cuda_lib.MIError as e:  # 16-bit counters are limited by the fixed volume's size
+        assert e.status == cuda_lib.MI_EUNSUPPORTED
+        pytest.skip(str(e))
+    sample = [0, 151, 255]
+    mi_o, h_o, cnt_o = oracle.mi_eval(f, m, 256, prm[sample], qs, fixed_depth=12, moving_depth=12, nthreads=3)
+    np.testing.assert_array_equal(cnt[sample], cnt_o)
+    assert_mi_close(mi[sample], mi_o, h_o)
+    q16 = oracle.affine_q16(oracle.affine(prm[151], f.shape, (1, 1, 1), m.shape, (1, 1, 1)))
+    H = ctx.hist(affines=q16[None], path=cuda_lib.PATH_BATCHED)
+    ho, _ = oracle.joint_hist(f, m, q16, 256, 12, 12)
+    np.testing.assert_array_equal(H[0], ho.astype(np.uint32))
+
+
 @pytest.mark.slow
 def test_full_size_batched_256_cubed_sampled(cuda_lib):
     # the batched workload at full size (256^3 12-bit, 256 bins, 4096 transforms x 4 q) in the bench's

@@ -372,7 +372,8 @@ def run_ours(args, rank, world, local_rank):
     line.update(extra)
     if rank == 0 and not args.skip_cpu:
         cores = os.cpu_count() or 1
-        sample = prm[:2 * cores]
+        # about 10 s of oracle work on this machine's cores: 28 transforms a core (~45 ms each at 256^3)
+        sample = prm[:min(len(prm), 28 * cores)]
         rate, dt = oracle_rate(f, m, sample, cores)
         line["cpu_baseline"] = {"value": rate, "unit": "voxel*transforms/s", "cores": cores, "kind": "oracle",
                                 "sample": f"{len(sample)} of the 4096 transforms (256^3, 256 bins, 4 q), {dt:.1f} s"}

@@ -45,10 +45,10 @@ DESIGN_OPS_PER_VOXT = 50
 # kernel source and the selected configuration are the ones measured: DRAM bytes of one full launch
 # (4096 transforms), and from a one-wave capture the issue and L1TEX utilisation and the
 # shared-memory wavefronts per shared atomic instruction.
-K_BATCHED_NCU = {"source_sha16": "018b6e18fe20d963", "config": [10, 1, 4],
-                 "dram_bytes_per_launch": 405720647936 + 64994816, "issue_active": 0.758,
-                 "l1tex_throughput": 0.637, "smem_wavefronts_per_atomic": 335382232 / 68548103,
-                 "smem_atomic_wavefronts_per_sm_cycle": 335382232 / 152 / 14112035.8,
+K_BATCHED_NCU = {"source_sha16": "632325a19ff7d138", "config": [10, 2, 4],
+                 "dram_bytes_per_launch": 183945337088 + 60691968, "issue_active": 0.815,
+                 "l1tex_throughput": 0.694, "smem_wavefronts_per_atomic": 333606309 / 71766929,
+                 "smem_atomic_wavefronts_per_sm_cycle": 333606309 / 152 / 12048055.08,
                  "profile": "profiles/k_batched_rows_quad_256cubed_256bins.md"}
 # algorithmic FP32 operations per voxel x transform of the Parzen MI + gradient at 3 q values:
 # forward 31 (trilinear 14, bin coordinate 1, B-spline weights 12, 4 increments),

@@ -303,7 +303,7 @@ struct Pair {
     DevBuf fbins, mov, movp;    // hard path (movp: x-paired moving volume)
     cudaArray_t arr = nullptr;  // the pairs as a 3D array, read through tex
     cudaTextureObject_t tex = 0;
-    cudaArray_t arrq = nullptr;  // 2 x 2 quads as a 3D array (one extra z plane), read through texq
+    cudaArray_t arrq = nullptr;  // 2 x 2 (y, z) quads as a 3D array, read through texq
     cudaTextureObject_t texq = 0;
     cudaArray_t arrg = nullptr;  // z-pair atlas (moving depth <= 12), read by 2D gathers through texg
     cudaTextureObject_t texg = 0;
@@ -502,7 +502,7 @@ mi_status add_pair(mi_ctx *ctx, const mi_volume *fx, const mi_volume *mv, int bi
     if ((st = validate_volume(fx, "fixed", parzen, e)) != MI_OK) return ctx->fail(st, e);
     if ((st = validate_volume(mv, "moving", parzen, e)) != MI_OK) return ctx->fail(st, e);
     {
-        // both paths gather the moving volume through 3D textures of dims (nx, ny, nz + 1)
+        // both paths gather the moving volume through 3D textures of dims (nx, ny, nz + 1) at most
         int tw = 0, th = 0, td = 0;
         cudaDeviceGetAttribute(&tw, cudaDevAttrMaxTexture3DWidth, ctx->device);
         cudaDeviceGetAttribute(&th, cudaDevAttrMaxTexture3DHeight, ctx->device);
@@ -657,21 +657,21 @@ mi_status add_pair(mi_ctx *ctx, const mi_volume *fx, const mi_volume *mv, int bi
         td.readMode = cudaReadModeElementType;
         td.normalizedCoords = 0;
         MI_CU(cudaCreateTextureObject(&P->tex, &rd, &td, nullptr), "creating the texture object");
-        // 2 x 2 quads (uchar4 / ushort4) with the last z plane repeated, read at integer texel coordinates
+        // 2 x 2 (y, z) quads (uchar4 / ushort4), read at integer texel coordinates
         {
             const int cb = P->mdtype == 0 ? 8 : 16;
             const size_t qsz = (size_t)cb / 2;  // bytes per quad
+            const cudaExtent qext = make_cudaExtent(P->nm[0], P->nm[1], P->nm[2]);
             DevBuf quads;
-            MI_CU(quads.ensure((size_t)P->nm[0] * P->nm[1] * (P->nm[2] + 1) * qsz), "allocating the quads");
+            MI_CU(quads.ensure(qext.width * qext.height * qext.depth * qsz), "allocating the quads");
             MI_CU(launch_make_quads(P->mov.p, P->mdtype, P->nm, quads.p, s), "building the quads");
             cudaChannelFormatDesc cq = cudaCreateChannelDesc(cb, cb, cb, cb, cudaChannelFormatKindUnsigned);
-            MI_CU(cudaMalloc3DArray(&P->arrq, &cq, make_cudaExtent(P->nm[0], P->nm[1], P->nm[2] + 1)),
-                  "allocating the quad array");
+            MI_CU(cudaMalloc3DArray(&P->arrq, &cq, qext), "allocating the quad array");
             cudaMemcpy3DParms cq3;
             memset(&cq3, 0, sizeof cq3);
-            cq3.srcPtr = make_cudaPitchedPtr(quads.p, (size_t)P->nm[0] * qsz, P->nm[0], P->nm[1]);
+            cq3.srcPtr = make_cudaPitchedPtr(quads.p, qext.width * qsz, qext.width, qext.height);
             cq3.dstArray = P->arrq;
-            cq3.extent = make_cudaExtent(P->nm[0], P->nm[1], P->nm[2] + 1);
+            cq3.extent = qext;
             cq3.kind = cudaMemcpyDeviceToDevice;
             MI_CU(cudaMemcpy3DAsync(&cq3, s), "filling the quad array");
             rd.res.array.array = P->arrq;

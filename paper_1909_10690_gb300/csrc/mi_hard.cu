@@ -149,11 +149,17 @@ __device__ __forceinline__ int sample_hard_tex(unsigned long long tex, int ux, i
     return lerp8g(g0, g1, fz, gz);
 }
 
-// The same resample from 2 x 2 quads through the texture path.  A fetch at
-// integer texel coordinates (ix, iy, iz) returns v(ix, iy), v(ix + 1, iy),
-// v(ix, iy + 1), v(ix + 1, iy + 1) of plane iz in four registers, already
-// unpacked, so a voxel takes two fetches (planes iz and iz + 1; the array
-// repeats the last plane once, so iz + 1 is always in range).
+// The same resample from 2 x 2 (y, z) quads through the texture path.  A fetch
+// at integer texel coordinates (ix, iy, iz) returns v(ix, iy, iz),
+// v(ix, iy + 1, iz), v(ix, iy, iz + 1), v(ix, iy + 1, iz + 1) in four
+// registers, already unpacked, so a voxel takes two fetches (columns ix and
+// ix + 1).  Column ix + 1 lies past the volume only when ix = nx - 1, which
+// inside the overlap means a fraction of 0: the clamped texel's weight is 0.
+// Neighbouring lanes of a warp step along x, so the column one lane fetches
+// second is, under most transforms, the one the next lane fetches first: the
+// two requests of a warp step touch about one texel per voxel, and each texel
+// is wanted within one step (with (x, y) quads each texel is also wanted as
+// the upper plane of the next fixed slice, long after the L1 has evicted it).
 __device__ __forceinline__ void tex_quad(unsigned long long tex, int x, int y, int z, uint32_t &a, uint32_t &b,
                                          uint32_t &c, uint32_t &d) {
     asm("tex.3d.v4.u32.s32 {%0, %1, %2, %3}, [%4, {%5, %6, %7, %7}];"
@@ -161,13 +167,13 @@ __device__ __forceinline__ void tex_quad(unsigned long long tex, int x, int y, i
         : "l"(tex), "r"(x), "r"(y), "r"(z));
 }
 
-// The 8 neighbours of the sample at 16.16 index (ux, uy, uz): t[0..3] from
-// plane iz, t[4..7] from plane iz + 1.
+// The 8 neighbours of the sample at 16.16 index (ux, uy, uz) in quad_lerp's order: t[0..3] =
+// (x, y), (x + 1, y), (x, y + 1), (x + 1, y + 1) of plane iz, t[4..7] the same of plane iz + 1.
 __device__ __forceinline__ void quad_fetch(unsigned long long tex, unsigned ux, unsigned uy, unsigned uz,
                                            uint32_t (&t)[8]) {
     const int ix = (int)(ux >> 16), iy = (int)(uy >> 16), iz = (int)(uz >> 16);
-    tex_quad(tex, ix, iy, iz, t[0], t[1], t[2], t[3]);
-    tex_quad(tex, ix, iy, iz + 1, t[4], t[5], t[6], t[7]);
+    tex_quad(tex, ix, iy, iz, t[0], t[2], t[4], t[6]);
+    tex_quad(tex, ix + 1, iy, iz, t[1], t[3], t[5], t[7]);
 }
 
 // Trilinear value from the 8 neighbours: x, then y, then z stages.
@@ -237,21 +243,21 @@ __global__ void k_make_zpairs(const T *__restrict__ in, int n0, int n1, int n2, 
     }
 }
 
-// Builds the 2 x 2 quads: out has dims (n0, n1, n2 + 1), the last plane repeated.
+// Builds the 2 x 2 (y, z) quads: out has dims (n0, n1, n2); element (x, y, z) holds v(x, y, z),
+// v(x, y + 1, z), v(x, y, z + 1), v(x, y + 1, z + 1), upper indices clamped to the last ones.
 template <typename T, typename QT>
 __global__ void k_make_quads(const T *__restrict__ in, int n0, int n1, int n2, QT *__restrict__ out) {
-    const long long plane = (long long)n0 * n1, n = plane * (n2 + 1);
+    const long long plane = (long long)n0 * n1, n = plane * n2;
     for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n; o += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(o % n0);
         const int y = (int)((o / n0) % n1);
-        const int z = min((int)(o / plane), n2 - 1);
-        const int x1 = min(x + 1, n0 - 1), y1 = min(y + 1, n1 - 1);
-        const T *p = in + plane * z;
+        const int z = (int)(o / plane);
+        const int y1 = min(y + 1, n1 - 1), z1 = min(z + 1, n2 - 1);
         QT q;
-        q.x = p[(long long)y * n0 + x];
-        q.y = p[(long long)y * n0 + x1];
-        q.z = p[(long long)y1 * n0 + x];
-        q.w = p[(long long)y1 * n0 + x1];
+        q.x = in[plane * z + (long long)y * n0 + x];
+        q.y = in[plane * z + (long long)y1 * n0 + x];
+        q.z = in[plane * z1 + (long long)y * n0 + x];
+        q.w = in[plane * z1 + (long long)y1 * n0 + x];
         out[o] = q;
     }
 }
@@ -1388,7 +1394,7 @@ cudaError_t launch_make_zpairs(const void *mov, int dtype, const int nm[3], int 
 }
 
 cudaError_t launch_make_quads(const void *mov, int dtype, const int nm[3], void *out, cudaStream_t s) {
-    const long long n = (long long)nm[0] * nm[1] * (nm[2] + 1);
+    const long long n = (long long)nm[0] * nm[1] * nm[2];
     if (dtype == 0)
         k_make_quads<uint8_t, uchar4><<<grid_for(n, 256), 256, 0, s>>>((const uint8_t *)mov, nm[0], nm[1], nm[2],
                                                                         (uchar4 *)out);

@@ -18,7 +18,7 @@ struct PairDev {
     const void *mov;       // moving volume, uint8 or uint16, clamped to its bit depth
     const void *movp;      // x-paired copy (v[x], v[x+1]), uint16 / uint32, dims (nx, ny + 1, nz + 1)
     unsigned long long texp;  // the same pairs as a 3D texture (point sampling, clamped), dims (nx, ny, nz)
-    unsigned long long texq;  // 2 x 2 quads (x, y), (x + 1, y), (x, y + 1), (x + 1, y + 1) as a 3D texture
+    unsigned long long texq;  // 2 x 2 quads (y, z), (y + 1, z), (y, z + 1), (y + 1, z + 1) as a 3D texture
     unsigned long long texg;  // z-pair texels v(x, y, z) | v(x, y, z + 1) << 20 in a 2D atlas, read by gathers
                               // (moving depth <= 12 only; 0 when not built)
     const float2 *zoff;       // per moving plane z: atlas offset of the plane + 1 - 2^23, (x, y)
@@ -110,11 +110,11 @@ cudaError_t launch_f32_to_u16(const float *in, long long n, uint16_t *out, cudaS
 cudaError_t launch_clamp_depth(void *data, int dtype, int depth, long long n, cudaStream_t s);
 // Padded x-paired moving volume, dims (n0, n1 + 1, n2 + 1).
 cudaError_t launch_make_pairs(const void *mov, int dtype, const int nm[3], void *out, cudaStream_t s);
-// 2 x 2 quads of the moving volume, dims (n0, n1, n2): element (x, y, z) holds
-// v(x, y), v(x + 1, y), v(x, y + 1), v(x + 1, y + 1) of plane z, upper indices
-// clamped to the last ones (uchar4 for uint8, ushort4 for uint16 volumes).
 // Iteration cap of the 16-bit counter drain on the current device (default 2^16; test hook).
 cudaError_t set_drain_cap(int cap);
+// 2 x 2 (y, z) quads of the moving volume, dims (n0, n1, n2): element (x, y, z) holds
+// v(x, y, z), v(x, y + 1, z), v(x, y, z + 1), v(x, y + 1, z + 1), upper indices
+// clamped to the last ones (uchar4 for uint8, ushort4 for uint16 volumes).
 cudaError_t launch_make_quads(const void *mov, int dtype, const int nm[3], void *out, cudaStream_t s);
 // z-pair atlas of the moving volume (depth <= 12): out is a W x H uint32 image (zeroed here) in which
 // plane z occupies the nm[0] x nm[1] tile at ((z / ph) nm[0], (z % ph) nm[1]) and texel (x, y) of that

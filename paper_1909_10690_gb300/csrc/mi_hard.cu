@@ -187,43 +187,24 @@ __device__ __forceinline__ int quad_lerp(unsigned ux, unsigned uy, unsigned uz, 
     return lerp8g(g0, g1, fz, gz);
 }
 
-// Trilinear value from the four z-pair texels of a gathered 2 x 2 footprint (moving depth <= 12).
-// Each 32-bit texel holds v(x, y, z) in bits 0..11 and v(x, y, z + 1) in bits 20..31, so one 64-bit
-// product-sum p * (256 - f) + p' * f + (128 + 128 * 2^20) carries the stage lerps of both planes in
-// separate 20-bit fields: each field stays below 4095 * 256 + 128 < 2^20 and never carries into the
-// next.  Shifting right by 8 and masking leaves both results packed the same way, ready for the next
-// stage; the z stage forms g0 (256 - fz) + g1 fz + 128 in bits 20..39 of g * (fz + (256 - fz) 2^20)
-// + 128 * 2^20 (its low term g0 fz stays below 2^20).  Same weights, stage order and rounding as
-// quad_lerp: (a (256 - w) + b w + 128) >> 8, x then y then z.
-__device__ __forceinline__ uint32_t zpair_stage(uint32_t p, uint32_t p1, uint32_t g, uint32_t f) {
-    const unsigned long long x = (unsigned long long)p * g + (unsigned long long)p1 * f + (128ull | (128ull << 20));
-    return __funnelshift_r((uint32_t)x, (uint32_t)(x >> 32), 8) & 0xFFF00FFFu;
-}
-
-__device__ __forceinline__ int zpair_lerp(unsigned ux, unsigned uy, unsigned uz, uint32_t p00, uint32_t p10,
-                                          uint32_t p01, uint32_t p11) {
-    const uint32_t fx = __byte_perm(ux, 0u, 0x4441), fy = __byte_perm(uy, 0u, 0x4441),
-                   fz = __byte_perm(uz, 0u, 0x4441);
-    const uint32_t e0 = zpair_stage(p00, p10, 256u - fx, fx);  // x stage at y, both planes
-    const uint32_t e1 = zpair_stage(p01, p11, 256u - fx, fx);  // x stage at y + 1
-    const uint32_t g = zpair_stage(e0, e1, 256u - fy, fy);     // y stage, both planes
-    const unsigned long long z = (unsigned long long)g * (fz | ((256u - fz) << 20)) + (128ull << 20);
-    return (int)(__funnelshift_r((uint32_t)z, (uint32_t)(z >> 32), 28) & 0xFFFu);
-}
-
 // The 8 neighbours of the sample at 16.16 index (ux, uy, uz) in one gather from the z-pair atlas:
 // the float coordinates ix + 1 + ox, iy + 1 + oy (exact integers, so the gather's 2 x 2 footprint
 // starts at texel (ix, iy) of plane iz's tile) are formed from the bit pattern 2^23 + ix plus the
 // plane's stored offset ox + 1 - 2^23.  The gather returns (ix, iy + 1), (ix + 1, iy + 1),
-// (ix + 1, iy), (ix, iy).  On the last plane of an axis the upper neighbour's weight is 0, so the
-// texel beyond the tile edge (the next tile, or a clamped one) changes nothing.
+// (ix + 1, iy), (ix, iy), each holding v(x, y, z) in bits 0..11 and v(x, y, z + 1) in bits 20..31
+// (moving depth <= 12); unpacked, the eight values take quad_lerp's stages.  (Lerping both planes at
+// once in 20-bit fields of 64-bit products took fewer instructions but measured 6 % slower.)  On the
+// last plane of an axis the upper neighbour's weight is 0, so the texel beyond the tile edge (the next
+// tile, or a clamped one) changes nothing.
 __device__ __forceinline__ int gather_value(unsigned long long tex, const float2 *zoff, unsigned ux, unsigned uy,
                                             unsigned uz) {
     const float2 o = zoff[uz >> 16];
     const float u = __int_as_float((int)__funnelshift_r(ux, 0x4B00u, 16)) + o.x;
     const float v = __int_as_float((int)__funnelshift_r(uy, 0x4B00u, 16)) + o.y;
     const uint4 t = tex2Dgather<uint4>((cudaTextureObject_t)tex, u, v, 0);
-    return zpair_lerp(ux, uy, uz, t.w, t.z, t.x, t.y);
+    const uint32_t n[8] = {t.w & 0xFFFu, t.z & 0xFFFu, t.x & 0xFFFu, t.y & 0xFFFu,
+                           t.w >> 20, t.z >> 20, t.x >> 20, t.y >> 20};
+    return quad_lerp(ux, uy, uz, n);
 }
 
 // Builds the z-pair atlas (see launch_make_zpairs).

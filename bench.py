@@ -45,8 +45,8 @@ DESIGN_OPS_PER_VOXT = 50
 # kernel source and the selected configuration are the ones measured: DRAM bytes of one full launch
 # (4096 transforms), and from a one-wave capture the issue and L1TEX utilisation and the
 # shared-memory wavefronts per shared atomic instruction.
-K_BATCHED_NCU = {"source_sha16": "632325a19ff7d138", "config": [10, 2, 4],
-                 "dram_bytes_per_launch": 183945337088 + 60691968, "issue_active": 0.815,
+K_BATCHED_NCU = {"source_sha16": "a052ba2f01e56eb8", "config": [10, 2, 4],
+                 "dram_bytes_per_launch": 181408323840 + 61779200, "issue_active": 0.815,
                  "l1tex_throughput": 0.694, "smem_wavefronts_per_atomic": 333606309 / 71766929,
                  "smem_atomic_wavefronts_per_sm_cycle": 333606309 / 152 / 12048055.08,
                  "profile": "profiles/k_batched_rows_quad_256cubed_256bins.md"}

@@ -102,15 +102,15 @@ enum {
        fits when those rows are few */
     MI_HV_ROWS = 8,
     MI_HV_ROWS_TEX = 9,
-    /* the moving volume as 2 x 2 (x, y) quads read through the texture path:
-       two fetches per voxel instead of four, twice the moving-volume memory */
+    /* the moving volume as 2 x 2 (y, z) quads read through the texture path:
+       two fetches per voxel (columns x and x + 1) instead of four, twice the
+       moving-volume memory */
     MI_HV_ROWS_QUAD = 10,
     MI_HV_U32_QUAD = 11,
     MI_HV_U16_QUAD = 12,
     /* moving depth <= 12 only: one 2D texture gather per voxel from an atlas of
        the moving planes whose 32-bit texels pack v(x, y, z) with v(x, y, z + 1),
-       so the 2 x 2 footprint holds all 8 trilinear neighbours; the stage lerps
-       of both planes run packed in 20-bit fields of 64-bit integer products */
+       so the 2 x 2 footprint holds all 8 trilinear neighbours */
     MI_HV_ROWS_GATHER = 13,
     MI_HV_U32_GATHER = 14,
     MI_HV_U16_GATHER = 15
@@ -206,8 +206,8 @@ const char *mi_version(void);
  * is F_m(u(x), v(T(x))) of Fig. 1; the pair's geometry (dims, spacing) fixes
  * the parameter-to-affine map.  The moving volume is gathered through 3D
  * textures: its dims must fit the device's 3D texture extent
- * (cudaDevAttrMaxTexture3DWidth / Height / Depth) with one spare z plane,
- * else MI_EUNSUPPORTED.
+ * (cudaDevAttrMaxTexture3DWidth / Height / Depth) with one spare z plane
+ * (the Parzen path's quads), else MI_EUNSUPPORTED.
  * opt may be NULL (defaults).  On success *out
  * owns device copies of both volumes (the fixed one pre-binned) and must be
  * released with mi_destroy.  On failure *out is NULL and mi_last_error(NULL)

@@ -63,7 +63,7 @@ struct Item {
 // Histogram variants (match the public MI_HV_* values).  0..3: counter kinds
 // with LDG gathers of x-pairs, 4..7: the same with texture-path gathers of
 // x-pairs, 8 / 9: the row-bound layout with LDG / texture x-pairs, 10..12:
-// the row-bound, 32-bit and 16-bit kinds with texture gathers of 2 x 2 quads.
+// the row-bound, 32-bit and 16-bit kinds with texture gathers of 2 x 2 (y, z) quads.
 // 13..15: the row-bound, 32-bit and 16-bit kinds with one texture gather of 2 x 2 z-pair texels.
 enum { HV_U32 = 0, HV_U32_MATCH = 1, HV_U16 = 2, HV_U16_MATCH = 3, HV_TEX = 4, HV_ROWS = 8, HV_ROWS_TEX = 9,
        HV_ROWS_QUAD = 10, HV_U32_QUAD = 11, HV_U16_QUAD = 12, HV_ROWS_GATHER = 13, HV_U32_GATHER = 14,

@@ -188,6 +188,36 @@ def test_tile_shapes_bit_exact(cuda_lib, variant, tile_rows):
                     np.testing.assert_array_equal(H[t], ho.astype(np.uint32), err_msg=f"{depth} {slabs} {path} {t}")
 
 
+@pytest.mark.parametrize("variant", [10, 11, 12])  # MI_HV_ROWS_QUAD, MI_HV_U32_QUAD, MI_HV_U16_QUAD
+@pytest.mark.parametrize("dtype, depth", [(np.uint8, 8), (np.uint16, 12), (np.uint16, 16)])
+def test_quad_texels_full_range_and_last_column(cuda_lib, variant, dtype, depth):
+    # The quad variants read 2 x 2 (y, z) quads at columns ix and ix + 1.  On the moving volume's last
+    # x column (reached exactly by the identity and by whole-voxel x shifts, here with y and z fractions
+    # too) column nx lies past the volume and is read clamped, where its weight is 0.  Full-range values
+    # at every depth the quad texels hold (uchar4, ushort4), histograms bit for bit on both paths.
+    rng = np.random.default_rng(40 + depth)
+    f = rng.integers(0, 1 << depth, (19, 21, 35)).astype(dtype)
+    m = rng.integers(0, 1 << depth, (17, 23, 29)).astype(dtype)
+    nx = m.shape[2]
+    fixed_q = [IDENT.copy()]
+    for bx, by, bz in ((-6, 0, 0), (-6, 0x8000, 0x4000), (3, 0x1234, 0xFF00)):
+        q = IDENT.copy()
+        q[3], q[7], q[11] = bx * 65536, by, bz
+        fixed_q.append(q)
+    _, rq = random_q16(f.shape, m.shape, 6, seed=41, t=3.0, r=12.0, s=(0.9, 1.1))
+    q16 = np.concatenate([np.stack(fixed_q), rq.reshape(len(rq), 12)]).astype(np.int32)
+    want = [oracle.joint_hist(f, m, q, 64, depth, depth)[0].astype(np.uint32) for q in q16]
+    assert want[0].sum() == 29 * 21 * 17  # the identity's overlap: moving x 0..28, y 0..20, z 0..16
+    for path in (cuda_lib.PATH_PLAIN, cuda_lib.PATH_BATCHED):
+        ctx = cuda_lib.Context(f, m, bins=64, fixed_depth=depth, moving_depth=depth, hist_variant=variant)
+        H = ctx.hist(affines=q16, path=path)
+        for t in range(len(q16)):
+            np.testing.assert_array_equal(H[t], want[t], err_msg=f"{path} {t} (nx {nx})")
+    mi = ctx.eval_q16(q16, [1.0, 1.5])
+    mi_o, h_o, _ = oracle.mi_eval_q16(f, m, 64, q16, [1.0, 1.5], fixed_depth=depth, moving_depth=depth)
+    assert_mi_close(mi, mi_o, h_o)
+
+
 def test_gather_variants_need_depth_12_or_less(cuda_lib):
     # the z-pair atlas packs two values in 20-bit fields: 16-bit data keeps the other fetches
     rng = np.random.default_rng(10)

@@ -57,9 +57,9 @@ PARZEN_OPS_PER_VOXT = 120
 # Counters of the Parzen forward (k_parzen_hist) from one ncu capture of the 50-pose call (see profiles/),
 # reported while the kernel source is the one measured: shared-atomic instructions and wavefronts, SM
 # cycles elapsed per launch, and the DRAM bytes read and written by the forward and the adjoint
-K_PARZEN_NCU = {"source_sha16": "75e8764ddefccb85", "atom_inst": 52167744, "atom_wavefronts": 245283048,
-                "sm_cycles_elapsed": 2177378.59, "time_ms": 1.0568,
-                "dram_bytes_per_call": 531975424 + 4546560 + 26225408,
+K_PARZEN_NCU = {"source_sha16": "c75922c23d63e0fa", "atom_inst": 52167744, "atom_wavefronts": 242402137,
+                "sm_cycles_elapsed": 2143008.79, "time_ms": 1.0395,
+                "dram_bytes_per_call": 416319232 + 4436224 + 26225664,
                 "profile": "profiles/parzen_fwd_adj_192x192x128_64bins.md"}
 PARZEN_SHAPE = (128, 192, 192)
 PARZEN_SPACING = (1.0, 1.0, 1.2)

@@ -206,8 +206,7 @@ const char *mi_version(void);
  * is F_m(u(x), v(T(x))) of Fig. 1; the pair's geometry (dims, spacing) fixes
  * the parameter-to-affine map.  The moving volume is gathered through 3D
  * textures: its dims must fit the device's 3D texture extent
- * (cudaDevAttrMaxTexture3DWidth / Height / Depth) with one spare z plane
- * (the Parzen path's quads), else MI_EUNSUPPORTED.
+ * (cudaDevAttrMaxTexture3DWidth / Height / Depth), else MI_EUNSUPPORTED.
  * opt may be NULL (defaults).  On success *out
  * owns device copies of both volumes (the fixed one pre-binned) and must be
  * released with mi_destroy.  On failure *out is NULL and mi_last_error(NULL)

@@ -502,15 +502,15 @@ mi_status add_pair(mi_ctx *ctx, const mi_volume *fx, const mi_volume *mv, int bi
     if ((st = validate_volume(fx, "fixed", parzen, e)) != MI_OK) return ctx->fail(st, e);
     if ((st = validate_volume(mv, "moving", parzen, e)) != MI_OK) return ctx->fail(st, e);
     {
-        // both paths gather the moving volume through 3D textures of dims (nx, ny, nz + 1) at most
+        // both paths gather the moving volume through 3D textures of its dims (nx, ny, nz)
         int tw = 0, th = 0, td = 0;
         cudaDeviceGetAttribute(&tw, cudaDevAttrMaxTexture3DWidth, ctx->device);
         cudaDeviceGetAttribute(&th, cudaDevAttrMaxTexture3DHeight, ctx->device);
         cudaDeviceGetAttribute(&td, cudaDevAttrMaxTexture3DDepth, ctx->device);
-        if (mv->dims[0] > tw || mv->dims[1] > th || mv->dims[2] + 1 > td)
+        if (mv->dims[0] > tw || mv->dims[1] > th || mv->dims[2] > td)
             return ctx->fail(MI_EUNSUPPORTED, "moving volume dims exceed the device's 3D texture extent (" +
                                                   std::to_string(tw) + " x " + std::to_string(th) + " x " +
-                                                  std::to_string(td - 1) + ")");
+                                                  std::to_string(td) + ")");
     }
     if (parzen) {
         if (bins < MI_MIN_PARZEN_BINS || bins > 128)
@@ -552,7 +552,7 @@ mi_status add_pair(mi_ctx *ctx, const mi_volume *fx, const mi_volume *mv, int bi
         MI_CU(launch_parzen_extend(P->pmov.as<float>(), P->nm, P->pmovx.as<float>(), s), "extending the moving volume");
         if ((st = build_samples(ctx, *P, P->pfbins.as<uint8_t>(), s)) != MI_OK) return st;
         {
-            const cudaExtent ext = make_cudaExtent(P->nm[0], P->nm[1], P->nm[2] + 1);
+            const cudaExtent ext = make_cudaExtent(P->nm[0], P->nm[1], P->nm[2]);  // (y, z) quads
             DevBuf quads;
             MI_CU(quads.ensure(ext.width * ext.height * ext.depth * 16), "allocating the Parzen quads");
             MI_CU(launch_parzen_quads(P->pmovx.as<float>(), P->nm, quads.p, s), "building the Parzen quads");

@@ -148,7 +148,7 @@ struct ParzenPair {
     const uint8_t *fbins;   // Parzen fixed bins floor(f (B-4)) + 2
     const float *mov;       // normalised moving intensities in [0, 1]
     const float *movx;      // the same extended by one plane per axis, dims (n0 + 1, n1 + 1, n2 + 1)
-    unsigned long long texq;  // 2 x 2 (x, y) quads of movx as a float4 3D texture, dims (n0, n1, n2 + 1)
+    unsigned long long texq;  // 2 x 2 (y, z) quads of movx as a float4 3D texture, dims (n0, n1, n2)
     const uint32_t *srow;   // random sampling (else null): row r's sampled voxels are entries srow[r]..srow[r+1]-1
     const uint16_t *scol;   //   of scol (their x index, ascending)
     const uint8_t *sbin;    //   and sbin (their Parzen fixed bin)
@@ -176,8 +176,8 @@ int parzen_adj_ctas(const ParzenPair &P, int n, int nq, int sms);
 // last plane can be its integer part: the value there is v[n - 1] and the derivative along the axis
 // is v[n - 1] - v[n - 2], those of the last cell.
 cudaError_t launch_parzen_extend(const float *mov, const int nm[3], float *out, cudaStream_t s);
-// Quads of the extended volume: out (float4) has dims (n0, n1, n2 + 1); element (x, y, z) holds
-// movx at (x, y), (x + 1, y), (x, y + 1), (x + 1, y + 1) of plane z.
+// (y, z) quads of the extended volume: out (float4) has dims (n0, n1, n2); element (x, y, z) holds
+// movx at (x, y, z), (x, y + 1, z), (x, y, z + 1), (x, y + 1, z + 1).
 cudaError_t launch_parzen_quads(const float *movx, const int nm[3], void *out, cudaStream_t s);
 int parzen_cell_blocks(int B);
 // One Parzen call over n transforms: the pairs as a device array, transform t evaluated on pair

@@ -145,37 +145,29 @@ __device__ __forceinline__ MG trilinear_x(const float *__restrict__ movx, int m0
     return r;
 }
 
-// The same through the quad texture: two fetches at integer texel coordinates
-// (planes cz and cz + 1) return the eight neighbours, so the results are identical.
-template <bool GRAD>
-__device__ __forceinline__ MG trilinear_q(unsigned long long tex, long long Ux, long long Uy, long long Uz) {
+// The trilinear value (no gradient) through the texture of 2 x 2 (y, z) quads of the extended volume:
+// two fetches at integer texel coordinates, columns cx and cx + 1, return the eight neighbours, so the
+// value equals trilinear_x's.  Column cx + 1 = n0 lies past the texture only where the position sits
+// on the last x plane, whose fraction wx is then 0: the clamped texel is read with weight 0 (the
+// derivative along x there needs the extension's column, so the gradient reads the volume itself).
+// Neighbouring lanes step along x, so one lane's second column is mostly the next lane's first.
+__device__ __forceinline__ float trilinear_qv(unsigned long long tex, long long Ux, long long Uy, long long Uz) {
     constexpr float k2m32 = 2.3283064365386963e-10f;  // 2^-32
     const int cx = (int)(Ux >> 32), cy = (int)(Uy >> 32), cz = (int)(Uz >> 32);
     const float wx = __uint2float_rn((unsigned)Ux) * k2m32, wy = __uint2float_rn((unsigned)Uy) * k2m32,
                 wz = __uint2float_rn((unsigned)Uz) * k2m32;
-    float v000, v001, v010, v011, v100, v101, v110, v111;
+    float v000, v001, v010, v011, v100, v101, v110, v111;  // v[z][y][x] offsets
     asm("tex.3d.v4.f32.s32 {%0, %1, %2, %3}, [%4, {%5, %6, %7, %7}];"
-        : "=f"(v000), "=f"(v001), "=f"(v010), "=f"(v011)
+        : "=f"(v000), "=f"(v010), "=f"(v100), "=f"(v110)
         : "l"(tex), "r"(cx), "r"(cy), "r"(cz));
     asm("tex.3d.v4.f32.s32 {%0, %1, %2, %3}, [%4, {%5, %6, %7, %7}];"
-        : "=f"(v100), "=f"(v101), "=f"(v110), "=f"(v111)
-        : "l"(tex), "r"(cx), "r"(cy), "r"(cz + 1));
+        : "=f"(v001), "=f"(v011), "=f"(v101), "=f"(v111)
+        : "l"(tex), "r"(cx + 1), "r"(cy), "r"(cz));
     const float d00 = v001 - v000, d01 = v011 - v010, d10 = v101 - v100, d11 = v111 - v110;
     const float a00 = fmaf(wx, d00, v000), a01 = fmaf(wx, d01, v010);
     const float a10 = fmaf(wx, d10, v100), a11 = fmaf(wx, d11, v110);
     const float b0 = fmaf(wy, a01 - a00, a00), b1 = fmaf(wy, a11 - a10, a10);
-    MG r;
-    r.m = fmaf(wz, b1 - b0, b0);
-    if (GRAD) {
-        r.gz = b1 - b0;
-        const float y0 = a01 - a00, y1 = a11 - a10;
-        r.gy = fmaf(wz, y1 - y0, y0);
-        const float e0 = fmaf(wy, d01 - d00, d00), e1 = fmaf(wy, d11 - d10, d10);
-        r.gx = fmaf(wz, e1 - e0, e0);
-    } else {
-        r.gx = r.gy = r.gz = 0.0f;
-    }
-    return r;
+    return fmaf(wz, b1 - b0, b0);
 }
 
 // Overlap interval of one fixed row, exactly: the i in [lo, hi] with
@@ -259,8 +251,8 @@ __device__ __forceinline__ void bspline_dw(float t, float d[4]) {
 // copies, goes to the global histogram.
 constexpr int kParzenMaxVox = 65536;  // also the longest fixed row (MI_MAX_PARZEN_NX)
 constexpr int kParzenBankSkew = 7;    // row stride of the forward's shared histogram, mod 32
-constexpr bool kParzenFwdTex = true;   // forward gathers through the quad texture
-constexpr bool kParzenAdjTex = false;  // adjoint gathers with loads from the extended volume
+constexpr bool kParzenFwdTex = true;   // forward gathers through the quad texture (the adjoint loads
+                                       // the extended volume's eight neighbours, whose L1 serves it best)
 constexpr int kParzenRowsPerStep = 1;  // rows a warp of the forward works on at a time
 
 // Row stride of the shared tables: the least SB >= B + 1 with SB = kParzenBankSkew (mod 32).
@@ -352,10 +344,10 @@ __global__ void __launch_bounds__(kParzenFwdThreads)
         unsigned int cnt = 0;  // overlap voxels counted by this lane
         // one voxel at 32.32 index U with fixed bin bf: its four quantised B-spline weights
         auto add_voxel = [&](long long U0, long long U1, long long U2, int bf) {
-            const MG g3 = kParzenFwdTex ? trilinear_q<false>(P.texq, U0, U1, U2)
-                                        : trilinear_x<false>(P.movx, P.nm[0] + 1, (P.nm[0] + 1) * (P.nm[1] + 1),
-                                                             U0, U1, U2);
-            const float mt = fmaf(fminf(fmaxf(g3.m, 0.0f), 1.0f), Bm4, 2.0f);
+            const float mv = kParzenFwdTex ? trilinear_qv(P.texq, U0, U1, U2)
+                                           : trilinear_x<false>(P.movx, P.nm[0] + 1, (P.nm[0] + 1) * (P.nm[1] + 1),
+                                                                U0, U1, U2).m;
+            const float mt = fmaf(fminf(fmaxf(mv, 0.0f), 1.0f), Bm4, 2.0f);
             const int k0 = (int)mt;
             float w[4];
             bspline_w(mt - (float)k0, w);
@@ -441,11 +433,11 @@ __global__ void __launch_bounds__(kParzenFwdThreads)
 }
 
 __global__ void k_parzen_quads(const float *__restrict__ movx, int n0, int n1, int n2, float4 *__restrict__ out) {
-    const long long m0 = n0 + 1, m01 = m0 * (n1 + 1), n = (long long)n0 * n1 * (n2 + 1);
+    const long long m0 = n0 + 1, m01 = m0 * (n1 + 1), n = (long long)n0 * n1 * n2;
     for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n; o += (long long)gridDim.x * blockDim.x) {
         const long long x = o % n0, y = (o / n0) % n1, z = o / ((long long)n0 * n1);
         const float *p = movx + x + m0 * y + m01 * z;
-        out[o] = make_float4(p[0], p[1], p[m0], p[m0 + 1]);
+        out[o] = make_float4(p[0], p[m0], p[m01], p[m01 + m0]);
     }
 }
 
@@ -700,9 +692,7 @@ __global__ void __launch_bounds__(TPB, 512 / TPB)
                 for (int a = 0; a < 3; ++a) S0[q][a] = 0.0f;
             // one voxel (x index i, fixed bin bf) at 32.32 index U: its share of S0 and M
             auto acc_voxel = [&](long long V0, long long V1, long long V2, int i, int bf) {
-                const MG g3 = kParzenAdjTex ? trilinear_q<true>(P.texq, V0, V1, V2)
-                                            : trilinear_x<true>(P.movx, P.nm[0] + 1, (P.nm[0] + 1) * (P.nm[1] + 1),
-                                                                V0, V1, V2);
+                const MG g3 = trilinear_x<true>(P.movx, P.nm[0] + 1, (P.nm[0] + 1) * (P.nm[1] + 1), V0, V1, V2);
                 const float ic = (float)i - ci;
                 // d_a m and d_a m (i - ci), shared by every q
                 const float hx = g3.gx * ic, hy = g3.gy * ic, hz = g3.gz * ic;
@@ -889,7 +879,7 @@ cudaError_t launch_parzen_extend(const float *mov, const int nm[3], float *out, 
 }
 
 cudaError_t launch_parzen_quads(const float *movx, const int nm[3], void *out, cudaStream_t s) {
-    const long long n = (long long)nm[0] * nm[1] * (nm[2] + 1);
+    const long long n = (long long)nm[0] * nm[1] * nm[2];
     k_parzen_quads<<<grid_for(n, 256), 256, 0, s>>>(movx, nm[0], nm[1], nm[2], (float4 *)out);
     return cudaGetLastError();
 }

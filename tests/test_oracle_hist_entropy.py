@@ -181,6 +181,40 @@ def test_mi_invariant_under_moving_bin_permutation():
         np.testing.assert_allclose(m1, m2, rtol=1e-12, atol=1e-14)
 
 
+def test_swapping_the_volumes_transposes_the_histogram():
+    # Eq. 2 is symmetric in its two images: with equal grids, swapping fixed and moving under the inverse
+    # of a whole-voxel shift maps the same voxel pairs, so the joint histogram transposes, the marginal
+    # entropies trade places and every MI (Shannon, both Tsallis forms) is unchanged
+    fx, mv = phantoms.ellipsoid_pair(shape=(16, 18, 20), seed=14)
+    assert fx.shape == mv.shape
+    for d in [(0, 0, 0), (3, -2, 1), (-4, 5, -2)]:
+        q, qi = IDENT.copy(), IDENT.copy()
+        q[3], q[7], q[11] = d[0] * 65536, d[1] * 65536, d[2] * 65536
+        qi[3], qi[7], qi[11] = -d[0] * 65536, -d[1] * 65536, -d[2] * 65536
+        h1, n1 = oracle.joint_hist(fx, mv, q, 32)
+        h2, n2 = oracle.joint_hist(mv, fx, qi, 32)
+        assert n1 == n2 > 0
+        np.testing.assert_array_equal(h1, h2.T)
+        for form in (0, 1):
+            mi1, hh1 = oracle.entropies(h1, [1.0, 0.5, 2.0], form=form)
+            mi2, hh2 = oracle.entropies(h2, [1.0, 0.5, 2.0], form=form)
+            np.testing.assert_allclose(mi1, mi2, rtol=1e-12, atol=1e-14)
+            np.testing.assert_allclose(hh1[:, 0], hh2[:, 1], rtol=1e-12)
+            np.testing.assert_allclose(hh1[:, 1], hh2[:, 0], rtol=1e-12)
+            np.testing.assert_allclose(hh1[:, 2], hh2[:, 2], rtol=1e-12)
+
+
+def test_shannon_mi_between_zero_and_the_smaller_marginal_entropy():
+    # 0 <= I(F; M) <= min(H(F), H(M)) for any joint distribution (Eq. 2 with H(F, M) >= max(H(F), H(M))
+    # and subadditivity): a sign or term slip in the reduction breaks one side on some transform
+    fx, mv = phantoms.ellipsoid_pair(shape=(20, 22, 24), seed=15)
+    prm = phantoms.random_transforms(12, seed=16, t_mm=4, r_deg=20, s_range=(0.85, 1.15))
+    mi, hh, _ = oracle.mi_eval(fx, mv, 32, prm, [1.0])
+    assert np.all(mi[:, 0] >= -1e-12)
+    assert np.all(mi[:, 0] <= np.minimum(hh[:, 0, 0], hh[:, 0, 1]) + 1e-12)
+    assert np.all(hh[:, 0, 2] >= np.maximum(hh[:, 0, 0], hh[:, 0, 1]) - 1e-12)
+
+
 def test_independent_noise_miller_madow_band():
     rng = np.random.default_rng(12)
     shape = (64, 64, 64)

@@ -47,8 +47,8 @@ DESIGN_OPS_PER_VOXT = 50
 # shared-memory wavefronts per shared atomic instruction.
 K_BATCHED_NCU = {"source_sha16": "a052ba2f01e56eb8", "config": [10, 2, 4],
                  "dram_bytes_per_launch": 181408323840 + 61779200, "issue_active": 0.815,
-                 "l1tex_throughput": 0.694, "smem_wavefronts_per_atomic": 333606309 / 71766929,
-                 "smem_atomic_wavefronts_per_sm_cycle": 333606309 / 152 / 12048055.08,
+                 "l1tex_throughput": 0.695, "smem_wavefronts_per_atomic": 333607686 / 71766929,
+                 "smem_atomic_wavefronts_per_sm_cycle": 333607686 / 152 / 11992171.03,
                  "profile": "profiles/k_batched_rows_quad_256cubed_256bins.md"}
 # algorithmic FP32 operations per voxel x transform of the Parzen MI + gradient at 3 q values:
 # forward 31 (trilinear 14, bin coordinate 1, B-spline weights 12, 4 increments),
